@@ -1,0 +1,375 @@
+"""Pins for the FP64 oracle: closed forms, invariants and brute force from the paper.
+
+Each test checks an oracle function against something other than itself: a
+value fixed by the mathematics or by the paper's theorems. A plausible slip
+in the oracle (a dropped term, a sign, a transposed operand, a wrong index or
+summation order) fails at least one of these.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1512_06500_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_sym(rng, m, scale=1.0):
+    A = rng.standard_normal((m, m)) * scale
+    return 0.5 * (A + A.T)
+
+
+def _known_spectrum(rng, w):
+    """Q diag(w) Q^T with Q a product of two explicit Householder reflectors."""
+    m = len(w)
+    u = rng.standard_normal(m); u /= np.linalg.norm(u)
+    v = rng.standard_normal(m); v /= np.linalg.norm(v)
+    Q = (np.eye(m) - 2 * np.outer(u, u)) @ (np.eye(m) - 2 * np.outer(v, v))
+    return Q @ np.diag(w) @ Q.T, Q
+
+
+# ------------------------------------------------------------------ Section 1
+
+def test_segment_brute_force_and_stability():
+    rng = np.random.default_rng(1)
+    k = 7
+    labels = rng.integers(0, k, size=200).astype(np.int32)
+    labels[:k] = np.arange(k)                      # no empty class
+    counts, offsets, perm = O.segment(labels, k)
+    for j in range(k):
+        members = [i for i in range(labels.size) if labels[i] == j]
+        assert counts[j] == len(members)
+        assert list(perm[offsets[j]:offsets[j + 1]]) == members    # class-major, input order
+    assert offsets[0] == 0 and offsets[-1] == labels.size
+    assert sorted(perm.tolist()) == list(range(labels.size))
+
+
+@pytest.mark.parametrize("bad", [[0, 1, 3], [0, -1, 2], [0, 0, 2]])
+def test_segment_rejects_bad_labels(bad):
+    with pytest.raises(ValueError):
+        O.segment(np.array(bad), 3)
+
+
+def test_scatter_factors_exact_means_and_identities():
+    p = synth.gaussian_clusters(d=16, k=4, n_per_class=[1, 3, 5, 2], seed=3)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    n, d = p.X.shape
+    # centroids equal the exact rational means up to the rounding of the running sum
+    for j in range(p.k):
+        idx = [i for i in range(n) if p.labels[i] == j]
+        for q in range(d):
+            exact = sum(Fraction(float(p.X[i, q])) for i in idx) / len(idx)
+            assert abs(float(exact) - f["mu_j"][j, q]) <= 8 * np.finfo(float).eps * max(1.0, abs(float(exact)))
+    for q in range(d):
+        exact = sum(Fraction(float(v)) for v in p.X[:, q]) / n
+        assert abs(float(exact) - f["mu"][q]) <= 8 * np.finfo(float).eps
+    # H_W columns of one class sum to zero; sum_j sqrt(n_j) H_B[:, j] = sum_j n_j (mu_j - mu) = 0
+    HW, HB = f["HW"], f["HB"]
+    for j in range(p.k):
+        cols = HW[:, f["offsets"][j]:f["offsets"][j + 1]]
+        assert np.abs(cols.sum(axis=1)).max() < 1e-14
+    s = HB @ np.sqrt(f["counts"].astype(float))
+    assert np.abs(s).max() < 1e-13
+    # S_W + S_B equals the total scatter sum_i (chi_i - mu)(chi_i - mu)^T
+    C = p.X.T - f["mu"][:, None]
+    assert np.allclose(HW @ HW.T + HB @ HB.T, C @ C.T, atol=1e-12)
+    # column p of H_W is sample perm[p] minus its own class mean
+    for q in range(n):
+        i = f["perm"][q]
+        assert np.array_equal(HW[:, q], p.X[i] - f["mu_j"][p.labels[i]])
+
+
+def test_scatter_factors_summation_order_is_input_order():
+    # values whose sum depends on the order: 1e16 + 1 - 1e16
+    X = np.zeros((3, 1))
+    X[:, 0] = [1e16, 1.0, -1e16]
+    f = O.scatter_factors(X, np.array([0, 0, 0]), 1)
+    assert f["mu"][0] == ((0.0 + 1e16) + 1.0 + -1e16) / 3.0
+    assert f["mu"][0] == 0.0       # 1e16 + 1 rounds to 1e16
+
+
+# ------------------------------------------------------------------ Section 2
+
+def test_jacobi_closed_forms():
+    w, U = O.jacobi_eigh(np.diag([3.0, -1.0, 2.0]))
+    assert np.allclose(w, [-1.0, 2.0, 3.0])
+    a, b, c = 2.0, 1.0, 5.0
+    w, U = O.jacobi_eigh(np.array([[a, b], [b, c]]))
+    disc = math.sqrt(((a - c) / 2) ** 2 + b * b)
+    assert np.allclose(w, [(a + c) / 2 - disc, (a + c) / 2 + disc], rtol=0, atol=1e-14)
+
+
+def test_jacobi_known_spectrum():
+    rng = np.random.default_rng(2)
+    w0 = np.array([-2.0, -0.5, 0.0, 0.0, 1e-3, 1.0, 4.0, 9.0])
+    A, _ = _known_spectrum(rng, w0)
+    w, U = O.jacobi_eigh(A)
+    assert np.allclose(w, np.sort(w0), atol=1e-13)
+    assert np.allclose(U.T @ U, np.eye(8), atol=1e-13)
+    assert np.allclose(A @ U, U * w, atol=1e-13)
+
+
+def test_expm_taylor_closed_forms():
+    assert np.array_equal(O.expm_taylor(np.zeros((4, 4))), np.eye(4))
+    D = np.diag([-3.0, 0.0, 0.5, 7.0])
+    assert np.allclose(O.expm_taylor(D), np.diag(np.exp([-3.0, 0.0, 0.5, 7.0])), rtol=1e-14, atol=0)
+    th = 2.3
+    R = O.expm_taylor(np.array([[0.0, th], [-th, 0.0]]))
+    assert np.allclose(R, [[math.cos(th), math.sin(th)], [-math.sin(th), math.cos(th)]], atol=1e-14)
+    rng = np.random.default_rng(4)
+    A = _rand_sym(rng, 6, 1.5)
+    assert np.allclose(O.expm_taylor(A) @ O.expm_taylor(-A), np.eye(6), atol=1e-12)
+
+
+def test_exp_eigen_routes_agree_with_taylor():
+    rng = np.random.default_rng(5)
+    A = _rand_sym(rng, 10, 2.0)
+    E = O.expm_taylor(A)
+    scale = np.abs(E).max()
+    assert np.abs(O.sym_fun(A, np.exp, "eigh") - E).max() < 1e-13 * scale
+    assert np.abs(O.sym_fun(A, np.exp, "jacobi") - E).max() < 1e-13 * scale
+
+
+def test_phi_and_phi_operator_series():
+    assert O.phi(np.array([0.0]))[0] == 1.0
+    z = np.array([1e-12, -3e-9, 0.7, -5.0])
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    # the defining series summed in 40-digit arithmetic
+    ref = np.array([float(mpmath.nsum(lambda j: mpmath.mpf(x) ** j / mpmath.factorial(j + 1), [0, mpmath.inf]))
+                    for x in z])
+    assert np.allclose(O.phi(z), ref, rtol=4e-16, atol=0)
+    rng = np.random.default_rng(6)
+    H = rng.standard_normal((9, 5))
+    G = H.T @ H
+    G /= np.linalg.eigvalsh(G)[-1]
+    for alpha in (1.0, -0.5, -3.0):
+        ser = np.zeros_like(G)
+        term = np.eye(5)                      # alpha^j G^(j-1) / j!, j = 1..
+        for j in range(1, 60):
+            ser += alpha ** j * term / math.factorial(j)
+            term = term @ G
+        assert np.abs(O.phi_operator(G, alpha) - ser).max() < 1e-14 * max(1.0, np.abs(ser).max())
+
+
+# ---------------------------------------------------------------- Section 3.1
+
+@pytest.mark.parametrize("alpha", [1.0, -0.5, -1.0])
+def test_theorem_3_1_low_rank_identity(alpha):
+    rng = np.random.default_rng(7)
+    d, m, b = 40, 9, 3
+    H = rng.standard_normal((d, m)) * 0.25
+    X = rng.standard_normal((d, b))
+    Y_ref = O.dense_exp_apply(H, alpha, X, route="taylor")
+    Y = O.lowrank_exp_apply(H, alpha, X)
+    assert np.linalg.norm(Y - Y_ref) / np.linalg.norm(Y_ref) < 1e-13
+    # the phi form of the same identity: exp(alpha H H^T) = I + H K(alpha) H^T
+    Yk = X + H @ (O.phi_operator(H.T @ H, alpha) @ (H.T @ X))
+    assert np.linalg.norm(Yk - Y_ref) / np.linalg.norm(Y_ref) < 1e-13
+
+
+def test_theorem_3_1_rank_deficient_and_zero():
+    rng = np.random.default_rng(8)
+    d = 30
+    B = rng.standard_normal((d, 3))
+    H = np.concatenate([B, B @ rng.standard_normal((3, 4))], axis=1) * 0.3   # rank 3, 7 columns
+    X = rng.standard_normal((d, 2))
+    Y_ref = O.dense_exp_apply(H, -1.0, X)
+    assert np.linalg.norm(O.lowrank_exp_apply(H, -1.0, X) - Y_ref) < 1e-13 * np.linalg.norm(Y_ref)
+    Z = np.zeros((d, 5))
+    assert np.array_equal(O.lowrank_exp_apply(Z, 2.0, X), X)        # exp(0) = I
+    assert np.array_equal(O.phi_operator(np.zeros((4, 4)), 2.5), 2.5 * np.eye(4))
+
+
+def test_m_apply_matches_dense_symmetric_form():
+    rng = np.random.default_rng(9)
+    p = synth.gaussian_clusters(d=24, k=3, n_per_class=3, seed=9)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    c2 = 0.3
+    X = rng.standard_normal((24, 2))
+    EWmh = O.expm_taylor(-0.5 * c2 * f["HW"] @ f["HW"].T)
+    EB = O.expm_taylor(c2 * f["HB"] @ f["HB"].T)
+    ref = EWmh @ EB @ EWmh @ X
+    assert np.linalg.norm(O.m_apply(f["HW"], f["HB"], c2, X) - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+# ---------------------------------------------------------------- Section 3.2/3.3
+
+def test_commuting_diagonal_closed_form():
+    # H_W and H_B supported on shared coordinate axes: S_W = diag(w), S_B = diag(b)
+    d = 12
+    w = np.array([0.5, 2.0, 0.0, 1.0, 3.0])
+    b = np.array([4.0, 1.0, 2.5, 0.0, 0.2])
+    HW = np.zeros((d, 5)); HB = np.zeros((d, 5))
+    for i in range(5):
+        HW[i, i] = math.sqrt(w[i]); HB[i, i] = math.sqrt(b[i])
+    c2 = 0.7
+    expect = np.sort(np.concatenate([np.exp(c2 * (b - w)), np.ones(d - 5)]))[::-1]
+    t = 2                                  # b_i - w_i > 0 for exactly two axes
+    for sol in (O.eda_dense(HW, HB, t, c2), O.eda_dense(HW, HB, t, c2, route="jacobi"),
+                O.eda_projected(HW, HB, t, c2)):
+        assert np.allclose(sol["lam"], expect, rtol=1e-13, atol=0)
+        top = np.argsort(-(b - w))[:t]
+        E = np.zeros((d, t)); E[top, np.arange(t)] = 1.0
+        assert O.sin_angle(E, sol["V"]) < 1e-12
+
+
+def _load_golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, val = line.split(":", 1)
+            out[key.strip()] = [float(v) for v in val.split()]
+    return out
+
+
+def test_example_1_1_golden():
+    g = _load_golden("example_1_1.txt")
+    d, k = int(g["d"][0]), int(g["k"][0])
+    X = np.array(g["X_rows"]).reshape(d, d)
+    labels = np.array(g["labels"], dtype=np.int32)
+    f = O.scatter_factors(X, labels, k)
+    assert np.array_equal(f["HW"], np.zeros((d, d)))                 # H_W = O
+    sol = O.eda_dense(f["HW"], f["HB"], 3, g["c2"][0])
+    assert np.allclose(sol["lam"], g["lambda"], rtol=1e-14, atol=0)
+    u = np.array(g["unit_eigvec_for_lambda_1"])
+    assert abs(abs(u @ sol["Y"][:, 2]) - 1.0) < 1e-13                 # eigenvector 1/sqrt(3) (1,1,1)
+
+
+def test_example_1_1_general_n_equals_k():
+    # n_j = 1 for all classes: H_W = O and the eigenvalues are exp(c^2 mu_i(G_B))
+    rng = np.random.default_rng(11)
+    d, k = 10, 5
+    X = rng.standard_normal((k, d))
+    f = O.scatter_factors(X, np.arange(k), k)
+    c2 = 0.4
+    mu = np.linalg.eigvalsh(f["HB"].T @ f["HB"])
+    expect = np.sort(np.concatenate([np.exp(c2 * np.maximum(mu, 0)), np.ones(d - k)]))[::-1]
+    sol = O.eda_dense(f["HW"], f["HB"], k - 1, c2)
+    assert np.allclose(sol["lam"], expect, rtol=1e-13, atol=1e-13)
+    assert np.sum(sol["lam"] > 1 + 1e-9) == k - 1
+
+
+def _random_problem(d, k, nj, seed, tau=3.0):
+    p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=seed)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    lw = np.linalg.eigvalsh(f["HW"].T @ f["HW"])[-1]
+    lb = np.linalg.eigvalsh(f["HB"].T @ f["HB"])[-1]
+    return p, f, O.scale_c2(lw, lb, tau)
+
+
+def test_theorem_3_7_unit_eigenvalue_count():
+    d, k, nj = 40, 4, 4
+    p, f, c2 = _random_problem(d, k, nj, seed=12)
+    n = k * nj
+    lam = O.eda_dense(f["HW"], f["HB"], k - 1, c2)["lam"]
+    delta = 1e-9 * lam[0]
+    assert np.sum(np.abs(lam - 1) <= delta) >= d - n + 1                  # Theorem 3.7
+    # sharper count for affinely independent samples (rank S_B = k-1, rank S_W = n-k)
+    assert np.sum(lam > 1 + delta) == k - 1
+    assert np.sum(np.abs(lam - 1) <= delta) == d - n + 1
+    assert np.sum(lam < 1 - delta) == n - k
+
+
+def test_theorem_3_3_bounds():
+    d = 20
+    p, f, c2 = _random_problem(d, 3, 3, seed=13)
+    lam = O.eda_dense(f["HW"], f["HB"], 2, c2)["lam"]
+    nu = np.sort(np.linalg.eigvalsh(c2 * f["HW"] @ f["HW"].T))[::-1]     # nu_1 >= ... >= nu_d
+    mu = np.sort(np.linalg.eigvalsh(c2 * f["HB"] @ f["HB"].T))[::-1]
+    for i in range(d):
+        lo = max(math.exp(mu[i] - nu[0]), math.exp(mu[d - 1] - nu[d - 1 - i]))
+        hi = min(math.exp(mu[i] - nu[d - 1]), math.exp(mu[0] - nu[d - 1 - i]))
+        assert lo * (1 - 1e-12) <= lam[i] <= hi * (1 + 1e-12)
+
+
+def test_lemma_3_4_theorem_3_5_trace_ratio():
+    d, t = 16, 3
+    p, f, c2 = _random_problem(d, 4, 3, seed=14)
+    sol = O.eda_dense(f["HW"], f["HB"], t, c2)
+    rho = O.trace_ratio(sol["Xt"], f["HW"], f["HB"], c2)
+    assert abs(rho - sol["lam_t"].sum()) < 1e-11 * rho
+    # invariance under V -> V R and the maximality of the top eigenvectors
+    rng = np.random.default_rng(15)
+    R = rng.standard_normal((t, t))
+    assert abs(O.trace_ratio(sol["Xt"] @ R, f["HW"], f["HB"], c2) - rho) < 1e-10 * rho
+    Vr = O.orth(rng.standard_normal((d, t)))
+    assert O.trace_ratio(Vr, f["HW"], f["HB"], c2) <= rho * (1 + 1e-12)
+    nu = np.sort(np.linalg.eigvalsh(c2 * f["HW"] @ f["HW"].T))[::-1]
+    mu = np.sort(np.linalg.eigvalsh(c2 * f["HB"] @ f["HB"].T))[::-1]
+    lo = sum(max(math.exp(mu[d - t + i] - nu[0]), math.exp(mu[d - 1] - nu[t - i - 1])) for i in range(t))
+    hi = sum(min(math.exp(mu[i] - nu[d - 1]), math.exp(mu[0] - nu[d - 1 - i])) for i in range(t))
+    assert lo * (1 - 1e-12) <= rho <= hi * (1 + 1e-12)
+
+
+def test_brute_force_tiny_cholesky_route():
+    for d, k, nj, seed in [(6, 2, 2, 16), (8, 3, 2, 17)]:
+        p, f, c2 = _random_problem(d, k, nj, seed)
+        t = k - 1
+        a = O.eda_dense(f["HW"], f["HB"], t, c2)
+        b = O.eda_cholesky_route(f["HW"], f["HB"], t, c2)
+        j = O.eda_dense(f["HW"], f["HB"], t, c2, route="jacobi")
+        assert np.allclose(a["lam"], b["lam"], rtol=1e-13, atol=0)
+        assert np.allclose(a["lam"], j["lam"], rtol=1e-13, atol=0)
+        assert O.sin_angle(a["V"], b["V"]) < 1e-11
+        assert O.sin_angle(a["V"], j["V"]) < 1e-11
+        # the generalized eigenvectors satisfy exp(c2 S_B) x = lambda exp(c2 S_W) x
+        EW = O.expm_taylor(c2 * f["HW"] @ f["HW"].T)
+        EB = O.expm_taylor(c2 * f["HB"] @ f["HB"].T)
+        for i in range(t):
+            x = a["Xt"][:, i]
+            r = EB @ x - a["lam_t"][i] * (EW @ x)
+            assert np.linalg.norm(r) < 1e-12 * a["lam_t"][i] * np.linalg.norm(EW @ x)
+
+
+@pytest.mark.parametrize("d", [64, 256])
+def test_tier_a_equals_tier_b(d):
+    p, f, c2 = _random_problem(d, 6, 4, seed=18 + d, tau=10.0)
+    t = 5
+    a = O.eda_dense(f["HW"], f["HB"], t, c2)
+    b = O.eda_projected(f["HW"], f["HB"], t, c2)
+    assert np.allclose(a["lam"], b["lam"], rtol=1e-11, atol=0)
+    assert O.sin_angle(a["V"], b["V"]) < 1e-9
+
+
+def test_scale_invariance():
+    p = synth.gaussian_clusters(d=32, k=4, n_per_class=3, seed=19)
+    a = O.eda(p.X, p.labels, p.k, 3, tau=5.0)
+    b = O.eda(3.0 * p.X, p.labels, p.k, 3, tau=5.0)
+    assert abs(b["c2"] * 9.0 - a["c2"]) < 1e-14 * a["c2"]
+    assert np.allclose(a["lam_t"], b["lam_t"], rtol=1e-12, atol=0)
+    assert O.sin_angle(a["V"], b["V"]) < 1e-10
+
+
+# ---------------------------------------------------------------- Section 3.3 / 4
+
+def test_nn_classify_brute_force():
+    Ptr = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 2.0], [1.0, 0.0]])
+    ytr = np.array([0, 1, 2, 3])
+    Pte = np.array([[0.9, 0.1], [0.5, 0.0], [0.0, 1.6]])
+    pred, dmin, margin = O.nn_classify(Ptr, ytr, Pte)
+    assert pred.tolist() == [1, 0, 2]      # (0.5, 0) ties samples 0 and 1 -> smaller index
+    assert abs(dmin[0] - math.hypot(0.1, 0.1)) < 1e-15
+    assert margin[1] == 0.0
+
+
+def test_theorem_3_8_distance_bound():
+    rng = np.random.default_rng(20)
+    d, t = 30, 4
+    V = O.orth(rng.standard_normal((d, t)))
+    Vt = O.orth(V + 1e-3 * rng.standard_normal((d, t)))
+    s = O.sin_angle(V, Vt)
+    c = math.sqrt(max(1 - s * s, 0.0))
+    for _ in range(50):
+        x = rng.standard_normal(d); x /= np.linalg.norm(x)
+        y = rng.standard_normal(d); y /= np.linalg.norm(y)
+        dd = np.linalg.norm(V.T @ (x - y))
+        dt = np.linalg.norm(Vt.T @ (x - y))
+        assert (dt - 2 * s) / c <= dd + 1e-14
+        assert dd <= dt * c + 2 * s + 1e-14
