@@ -1,0 +1,161 @@
+/*
+ * eda.h - C ABI of the GB300 (sm_103a) library for exponential discriminant
+ * analysis (EDA): the t dominant eigenpairs of the pencil
+ *     exp(c^2 S_B) x = lambda exp(c^2 S_W) x                       (Eq. 2.02)
+ * solved in the symmetric form M y = lambda y with
+ *     M = exp(-c^2 S_W / 2) exp(c^2 S_B) exp(-c^2 S_W / 2)        (Eq. 3.2, eqn315)
+ * by block Lanczos (Algorithm 3), where S_W = H_W H_W^T and S_B = H_B H_B^T
+ * (Eq. eqn1, eqn2) are never formed: every exponential is applied through
+ * Theorem 3.1 as
+ *     exp(alpha H H^T) X = X + H K(alpha) (H^T X),
+ *     K(alpha) = alpha phi(alpha H^T H),  phi(z) = (e^z - 1) / z.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers are DEVICE pointers unless a comment says otherwise. The caller
+ *    owns every input and output buffer; the library owns the handle and the
+ *    device memory behind it (factors, Gram matrices, operators, workspaces).
+ *  - Matrices are column-major. A d x n sample block has one sample per
+ *    column, each sample contiguous, leading dimension ld >= d.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is issued on it in order. Calls that return results to the
+ *    host (eda_build, eda_solve) synchronise that stream before returning.
+ *  - Every call returns an eda_status; no call aborts, traps or exits. On a
+ *    CUDA error the code is EDA_ERR_CUDA and eda_last_cuda_error() tells which.
+ *  - Handles are not thread-safe: one handle is used by one host thread at a time.
+ */
+#ifndef EDA_GB300_H
+#define EDA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EDA_OK = 0,
+    EDA_ERR_INVALID_ARG = -1,    /* a size, pointer, enum or tolerance is out of range      */
+    EDA_ERR_BAD_LABELS = -2,     /* a label outside [0, k) or a class with no sample          */
+    EDA_ERR_NONFINITE = -3,      /* NaN/Inf in the input, a Gram matrix or a residual         */
+    EDA_ERR_OOM = -4,            /* device allocation failed                                 */
+    EDA_ERR_CUDA = -5,           /* a CUDA call failed; see eda_last_cuda_error()              */
+    EDA_ERR_TIMEOUT = -6,        /* a bounded device wait (grid barrier) gave up              */
+    EDA_ERR_BREAKDOWN = -7,      /* Krylov block lost rank and could not be refilled          */
+    EDA_ERR_NOT_CONVERGED = -8   /* outputs hold the best Ritz pairs; see eda_solve_info      */
+} eda_status;
+
+typedef enum {
+    EDA_F64 = 0,                 /* IEEE double                                              */
+    EDA_F32 = 1,                 /* IEEE single                                              */
+    EDA_BF16 = 2,                /* bfloat16 storage, FP32 accumulation                      */
+    EDA_BF16X2 = 3               /* hi + lo bfloat16 split of an FP32 value                  */
+} eda_prec;
+
+typedef enum {
+    EDA_OP_SW = 0,               /* Y = exp(alpha S_W) X                                     */
+    EDA_OP_SB = 1,               /* Y = exp(alpha S_B) X                                     */
+    EDA_OP_M = 2                 /* Y = M X with the handle's c^2 (alpha ignored)            */
+} eda_op;
+
+typedef struct {
+    int32_t prec;                /* eda_prec of the Krylov sweeps (EDA_F64 = plain FP64)     */
+    int32_t block_b;             /* block size b of block Lanczos (>= 1)                     */
+    int32_t m_max;               /* max basis columns; <= 0 selects n + k + b (exact end)    */
+    int32_t check_every;         /* Rayleigh-Ritz convergence check every this many blocks   */
+    double tau;                  /* scale target: c^2 = tau / max(lmax(G_W), lmax(G_B))      */
+    double c2;                   /* explicit c^2 when > 0 (tau is then ignored)              */
+    uint64_t seed;               /* seed of the counter-based start block / refill vectors  */
+    int32_t true_residuals;      /* 1: eda_solve also reports true FP64 residuals            */
+    int32_t reserved[7];
+} eda_config;
+
+typedef struct {
+    int32_t converged;           /* number of the t wanted pairs with rel-res <= tol          */
+    int32_t iters;               /* block Lanczos steps taken                                */
+    int32_t mapplies;            /* M-applies, counted in d x b blocks                       */
+    int32_t basis_cols;          /* final basis width m                                      */
+    int32_t refills;             /* rank-deficient columns replaced by fresh random vectors  */
+    int32_t checks;              /* Rayleigh-Ritz checks performed                            */
+    double c2, lmax_w, lmax_b;   /* scale and the two largest Gram eigenvalues               */
+    double max_relres_est;       /* max_i ||B_{m+1} S_{m,i}|| / theta_i over the t pairs      */
+    double max_relres_true;      /* max_i ||M y_i - theta_i y_i|| / theta_i (if requested)   */
+    double ms_solve;             /* device time of the whole eda_solve call                   */
+    double* relres;              /* HOST pointer, t entries, filled when non-NULL            */
+} eda_solve_info;
+
+typedef struct eda_ctx* eda_handle;
+
+/* Fill *cfg with defaults: F64, b = 8, m_max = 0 (n + k + b), check_every = 1,
+ * tau = 10, c2 = 0, seed = 1, true_residuals = 0. */
+int eda_config_default(eda_config* cfg);
+
+/* Build a handle from labelled samples (Section 1; Algorithm 2 step 1 with the
+ * Gram/eigen form of steps 2-4).
+ *   X       : d x n samples, x_dtype EDA_F64 or EDA_F32, leading dimension ldx >= d.
+ *   labels  : n int32 class ids in [0, k).
+ * Steps on the device: stable class segmentation; centroids mu_j, mu in a
+ * fixed order (bit-exact FP64); H_W (d x n, class-major columns, input order
+ * within a class) and H_B (d x k, columns sqrt(n_j)(mu_j - mu)); Gram
+ * matrices G_W = H_W^T H_W, G_B = H_B^T H_B in FP64; their symmetric
+ * eigendecompositions; c^2; and K(alpha) for alpha = -c^2/2 (W) and +c^2 (B).
+ * Errors: INVALID_ARG (d < 1, n < 2, k < 1, k > n, ldx < d), BAD_LABELS,
+ * NONFINITE (X has NaN/Inf), OOM, CUDA. *out is set only on EDA_OK.
+ * X and labels are read only during the call (stream-ordered). */
+int eda_build(const void* X, int32_t x_dtype, int64_t d, int64_t n, int64_t ldx,
+              const int32_t* labels, int32_t k, const eda_config* cfg, void* stream,
+              eda_handle* out);
+
+/* Build a handle from given factors (H_W: d x n, H_B: d x kb, FP64, ld = d).
+ * No segmentation or centroid step; everything from the Gram on is as in
+ * eda_build. Used for closed-form checks (commuting diagonal factors). */
+int eda_build_from_factors(const double* HW, int64_t n, const double* HB, int64_t kb, int64_t d,
+                           const eda_config* cfg, void* stream, eda_handle* out);
+
+/* Y = exp(alpha H H^T) X for op SW (H = H_W) or SB (H = H_B), or Y = M X for
+ * op M (Theorem 3.1; Algorithm 2 steps 6L-12L for M). X, Y: d x b, leading
+ * dimension ldx, io_dtype EDA_F64. X and Y must not overlap. */
+int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y,
+                  int64_t ldx, int32_t b, int32_t io_dtype, void* stream);
+
+/* The t dominant eigenpairs (Algorithm 3, steps 5-6).
+ *   V0     : optional d x b0 start block (NULL: seeded counter-based Gaussian block).
+ *   V      : d x t output, orthonormal basis of the t generalized eigenvectors
+ *            x_i = exp(-c^2 S_W / 2) y_i (Eq. eqn311), orthonormalised.
+ *   lambda : t output eigenvalues, descending.
+ *   Y      : optional d x t output, the orthonormal Ritz vectors y_i of M.
+ * tol is the relative residual ||M y - theta y|| <= tol * theta of each of the t
+ * pairs (Remark 3.4). Returns EDA_ERR_NOT_CONVERGED (outputs still written)
+ * when the basis limit is reached first. */
+int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0,
+              double* V, double* lambda, double* Y, eda_solve_info* info, void* stream);
+
+/* P = V^T Xq (t x m, column-major, ld t): the projected samples of the
+ * nearest-neighbour classifier (Section 3.3, d_ij = ||V^T (x_i - y_j)||).
+ * V: d x t (ld d); Xq: d x m (EDA_F64 or EDA_F32, ld ldq). */
+int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_t xq_dtype,
+                int64_t m, int64_t ldq, double* P, void* stream);
+
+/* Copy out build results into caller device buffers (any pointer may be NULL):
+ * HW d x n, HB d x k, counts k, perm n, GW n x n, GB k x k, KW n x n
+ * (alpha = -c^2/2), KB k x k (alpha = c^2), evals_w n, evals_b k (ascending). */
+int eda_get_factors(eda_handle h, double* HW, double* HB, int32_t* counts, int32_t* perm,
+                    double* GW, double* GB, double* KW, double* KB, double* evals_w,
+                    double* evals_b, void* stream);
+
+/* Host-side scalars of a built handle. Any pointer may be NULL. */
+int eda_get_dims(eda_handle h, int64_t* d, int64_t* n, int32_t* k, double* c2,
+                 double* lmax_w, double* lmax_b);
+
+void eda_destroy(eda_handle h);
+const char* eda_strerror(int status);
+/* The last CUDA error code seen by any call of this thread (0 = none) and its name. */
+int eda_last_cuda_error(void);
+const char* eda_last_cuda_error_string(void);
+
+/* Number of this library's kernels launched so far by the calling process. */
+uint64_t eda_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDA_GB300_H */

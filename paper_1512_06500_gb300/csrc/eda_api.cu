@@ -1,0 +1,420 @@
+// C ABI: handle lifetime, the build step (Section 1 and Algorithm 2 steps 1-4 in Gram/eigen
+// form), exp-vector products (Theorem 3.1, Algorithm 2 steps 6L-12L) and projection.
+#include "eda_internal.cuh"
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace eda {
+
+namespace {
+thread_local int g_last_cuda_error = 0;
+uint64_t g_launches = 0;
+}  // namespace
+
+void note_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
+
+int ensure_workspace(eda_ctx* h, size_t bytes) {
+    if (h->ws_bytes >= bytes) return EDA_OK;
+    if (h->ws) {
+        EDA_CUDA_TRY(cudaFree(h->ws));
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    void* p = nullptr;
+    EDA_CUDA_TRY(cudaMalloc(&p, bytes));
+    h->ws = p;
+    h->ws_bytes = bytes;
+    return EDA_OK;
+}
+uint64_t& launch_counter() { return g_launches; }
+
+// Solve-side entry points implemented in lanczos.cu.
+int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* V, double* lambda, double* Y,
+               eda_solve_info* info, cudaStream_t s);
+int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t ldy, double* tmp, double* P,
+            double* Q, double* partial, size_t partial_cap, cudaStream_t s);
+
+namespace {
+
+constexpr double kSigRel = 32.0;   // eigenvalues <= kSigRel * n * eps * lambda_max are the Gram's null space
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int read_status(eda_ctx* h, cudaStream_t s, int* out) {
+    EDA_CUDA_TRY(cudaMemcpyAsync(out, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaStreamSynchronize(s));
+    return EDA_OK;
+}
+
+int status_to_code(int st) {
+    if (st & ST_TIMEOUT) return EDA_ERR_TIMEOUT;
+    if (st & ST_NONFINITE) return EDA_ERR_NONFINITE;
+    if (st & (ST_BADLABEL | ST_EMPTYCLASS)) return EDA_ERR_BAD_LABELS;
+    return EDA_OK;
+}
+
+// Allocate the handle's device block: factors, Grams, eigenpairs, operators, status, barrier.
+int alloc_handle(eda_ctx* h, bool with_labels) {
+    const size_t d = h->d, n = h->n, k = h->k;
+    const size_t N = std::max(n, k);
+    size_t bytes = 0;
+    auto add = [&](size_t b) { bytes += align256(b); };
+    add(d * n * 8);           // HW
+    add(d * k * 8);           // HB
+    if (with_labels) {
+        add(k * 4);           // counts
+        add((k + 1) * 4);     // offsets
+        add(n * 4);           // perm
+        add(k * d * 8);       // mu_j
+        add(d * 8);           // mu
+    }
+    add(n * n * 8);           // GW
+    add(k * k * 8);           // GB
+    add(n * 8);               // evals_w
+    add(k * 8);               // evals_b
+    add(n * n * 8);           // evecs_w
+    add(k * k * 8);           // evecs_b
+    add(n * n * 8);           // KW
+    add(k * k * 8);           // KB
+    add(256);                 // status
+    add(256);                 // barrier
+    // build scratch: eigensolver workspace + gram partials + phi/Newton-Schulz temporaries
+    const size_t pcap = std::max<size_t>(1u << 19, N * N);
+    add(symeig_work_bytes((int)N, (int)N));
+    add(pcap * 8);
+    add(3 * N * N * 8 + 256);
+    h->block_bytes = bytes + 4096;
+    void* p = nullptr;
+    EDA_CUDA_TRY(cudaMalloc(&p, h->block_bytes));
+    h->block = p;
+    Arena a{static_cast<char*>(p), h->block_bytes, 0};
+    h->HW = a.take<double>(d * n);
+    h->HB = a.take<double>(d * k);
+    if (with_labels) {
+        h->counts = a.take<int32_t>(k);
+        h->offsets = a.take<int32_t>(k + 1);
+        h->perm = a.take<int32_t>(n);
+        h->mu_j = a.take<double>(k * d);
+        h->mu = a.take<double>(d);
+    }
+    h->GW = a.take<double>(n * n);
+    h->GB = a.take<double>(k * k);
+    h->evals_w = a.take<double>(n);
+    h->evals_b = a.take<double>(k);
+    h->evecs_w = a.take<double>(n * n);
+    h->evecs_b = a.take<double>(k * k);
+    h->KW = a.take<double>(n * n);
+    h->KB = a.take<double>(k * k);
+    h->status = a.take<int>(64);
+    unsigned* bar = a.take<unsigned>(64);
+    h->bar = GridBarrier{bar, bar + 32};
+    h->build_arena_off = a.used;
+    if (!h->KB || !bar) return EDA_ERR_OOM;
+    EDA_CUDA_TRY(cudaMemset(h->status, 0, 256));
+    EDA_CUDA_TRY(cudaMemset(bar, 0, 256));
+    return EDA_OK;
+}
+
+// Eigenpairs of one Gram G (m x m): all eigenvalues, vectors for the significant ones, and
+// K(alpha). Returns lambda_max and the number of significant eigenpairs.
+int gram_eigen(eda_ctx* h, int m, double* G, double* evals, double* evecs, Arena& scratch, double* part, size_t pcap,
+               double* lmax, int* nsig, cudaStream_t s) {
+    if (m <= 0) {
+        *lmax = 0.0;
+        *nsig = 0;
+        return EDA_OK;
+    }
+    SymEigWork ws{};
+    EDA_TRY(symeig_work_carve(scratch, m, m, h->bar, &ws));
+    EDA_TRY(symeig_values(m, G, m, 0, m - 1, evals, &ws, h->status, s));
+    std::vector<double> w(m);
+    EDA_CUDA_TRY(cudaMemcpyAsync(w.data(), evals, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaStreamSynchronize(s));
+    int st = 0;
+    EDA_TRY(read_status(h, s, &st));
+    if (int c = status_to_code(st)) return c;
+    for (double v : w)
+        if (!std::isfinite(v)) return EDA_ERR_NONFINITE;
+    *lmax = std::max(w[m - 1], 0.0);
+    const double thr = kSigRel * m * DBL_EPSILON * *lmax;
+    int first = 0;
+    while (first < m && !(w[first] > thr)) ++first;
+    *nsig = m - first;
+    if (*nsig > 0) {
+        EDA_TRY(symeig_vectors(m, *nsig, evals + first, evecs, m, &ws, h->cfg.seed, 1e-7, s));
+        double* tmp = scratch.take<double>(3 * (size_t)m * m + 64);
+        if (!tmp) return EDA_ERR_OOM;
+        EDA_TRY(newton_schulz_f64(m, *nsig, evecs, m, 1, tmp, part, pcap, s));
+    }
+    h->nsig_first = first;   // only meaningful for the last call; the callers store their own copy
+    return EDA_OK;
+}
+
+// Everything after H_W, H_B exist: Grams, eigenpairs, c^2, K operators.
+int finish_build(eda_ctx* h, cudaStream_t s) {
+    const int n = (int)h->n, k = h->k;
+    const int64_t d = h->d;
+    Arena scratch{static_cast<char*>(h->block), h->block_bytes, h->build_arena_off};
+    const size_t N = std::max<int64_t>(n, k);
+    const size_t pcap = std::max<size_t>(1u << 19, N * N);
+    double* part = scratch.take<double>(pcap);
+    if (!part) return EDA_ERR_OOM;
+    EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
+    EDA_TRY(symmetrize_f64(n, h->GW, n, s));
+    EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, part, pcap, s));
+    EDA_TRY(symmetrize_f64(k, h->GB, k, s));
+    EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
+    EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));
+    const size_t mark = scratch.used;
+    int nsw = 0, nsb = 0;
+    EDA_TRY(gram_eigen(h, n, h->GW, h->evals_w, h->evecs_w, scratch, part, pcap, &h->lmax_w, &nsw, s));
+    const int first_w = h->nsig_first;
+    scratch.used = mark;
+    EDA_TRY(gram_eigen(h, k, h->GB, h->evals_b, h->evecs_b, scratch, part, pcap, &h->lmax_b, &nsb, s));
+    const int first_b = h->nsig_first;
+    scratch.used = mark;
+    h->nsig_w = nsw;
+    h->nsig_b = nsb;
+    if (h->cfg.c2 > 0.0) {
+        h->c2 = h->cfg.c2;
+    } else {
+        const double m = std::max(h->lmax_w, h->lmax_b);
+        if (!(m > 0.0)) return EDA_ERR_INVALID_ARG;   // both scatter matrices vanish
+        h->c2 = h->cfg.tau / m;
+    }
+    double* tmp = scratch.take<double>(N * N + 64);
+    if (!tmp) return EDA_ERR_OOM;
+    EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
+    EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
+    int st = 0;
+    EDA_TRY(read_status(h, s, &st));
+    return status_to_code(st);
+}
+
+bool valid_cfg(const eda_config& c) {
+    return c.block_b >= 1 && c.check_every >= 1 && (c.c2 > 0.0 || c.tau > 0.0) &&
+           (c.prec == EDA_F64 || c.prec == EDA_F32 || c.prec == EDA_BF16 || c.prec == EDA_BF16X2);
+}
+
+}  // namespace
+}  // namespace eda
+
+using namespace eda;
+
+extern "C" {
+
+int eda_config_default(eda_config* cfg) {
+    if (!cfg) return EDA_ERR_INVALID_ARG;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->prec = EDA_F64;
+    cfg->block_b = 8;
+    cfg->m_max = 0;
+    cfg->check_every = 1;
+    cfg->tau = 10.0;
+    cfg->c2 = 0.0;
+    cfg->seed = 1;
+    cfg->true_residuals = 0;
+    return EDA_OK;
+}
+
+int eda_build(const void* X, int32_t x_dtype, int64_t d, int64_t n, int64_t ldx, const int32_t* labels, int32_t k,
+              const eda_config* cfg, void* stream, eda_handle* out) {
+    if (!out || !X || !labels || d < 1 || n < 2 || k < 1 || k > n || ldx < d || n > (1 << 20) || k > 12288)
+        return EDA_ERR_INVALID_ARG;
+    if (x_dtype != EDA_F64 && x_dtype != EDA_F32) return EDA_ERR_INVALID_ARG;
+    eda_config c;
+    if (cfg) c = *cfg;
+    else eda_config_default(&c);
+    if (!valid_cfg(c)) return EDA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    eda_ctx* h = new (std::nothrow) eda_ctx();
+    if (!h) return EDA_ERR_OOM;
+    h->d = d;
+    h->n = n;
+    h->k = k;
+    h->cfg = c;
+    int rc = alloc_handle(h, true);
+    if (rc == EDA_OK) rc = segment_labels(labels, (int)n, k, h->counts, h->offsets, h->perm, h->status, s);
+    if (rc == EDA_OK) {
+        int st = 0;
+        rc = read_status(h, s, &st);
+        if (rc == EDA_OK) rc = status_to_code(st);
+    }
+    if (rc == EDA_OK)
+        rc = build_factors(X, x_dtype, d, (int)n, ldx, k, labels, h->counts, h->offsets, h->perm, h->mu_j, h->mu,
+                           h->HW, h->HB, h->status, s);
+    if (rc == EDA_OK) {
+        int st = 0;
+        rc = read_status(h, s, &st);
+        if (rc == EDA_OK) rc = status_to_code(st);
+    }
+    if (rc == EDA_OK) rc = finish_build(h, s);
+    if (rc != EDA_OK) {
+        eda_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return EDA_OK;
+}
+
+int eda_build_from_factors(const double* HW, int64_t n, const double* HB, int64_t kb, int64_t d,
+                           const eda_config* cfg, void* stream, eda_handle* out) {
+    if (!out || !HW || !HB || d < 1 || n < 1 || kb < 1 || n > (1 << 20) || kb > (1 << 20)) return EDA_ERR_INVALID_ARG;
+    eda_config c;
+    if (cfg) c = *cfg;
+    else eda_config_default(&c);
+    if (!valid_cfg(c)) return EDA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    eda_ctx* h = new (std::nothrow) eda_ctx();
+    if (!h) return EDA_ERR_OOM;
+    h->d = d;
+    h->n = n;
+    h->k = (int32_t)kb;
+    h->cfg = c;
+    int rc = alloc_handle(h, false);
+    if (rc == EDA_OK) rc = copy_mat_f64(d, (int)n, HW, d, h->HW, d, s);
+    if (rc == EDA_OK) rc = copy_mat_f64(d, (int)kb, HB, d, h->HB, d, s);
+    if (rc == EDA_OK) rc = check_finite_f64(d, (int)n, h->HW, d, h->status, s);
+    if (rc == EDA_OK) rc = check_finite_f64(d, (int)kb, h->HB, d, h->status, s);
+    if (rc == EDA_OK) rc = finish_build(h, s);
+    if (rc != EDA_OK) {
+        eda_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return EDA_OK;
+}
+
+int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y, int64_t ldx, int32_t b,
+                  int32_t io_dtype, void* stream) {
+    if (!h || !X || !Y || b < 1 || ldx < h->d || io_dtype != EDA_F64) return EDA_ERR_INVALID_ARG;
+    if (op != EDA_OP_SW && op != EDA_OP_SB && op != EDA_OP_M) return EDA_ERR_INVALID_ARG;
+    const char* xb = static_cast<const char*>(X);
+    const char* yb = static_cast<const char*>(Y);
+    const size_t span = ((size_t)(b - 1) * ldx + h->d) * sizeof(double);
+    if (xb < yb + span && yb < xb + span) return EDA_ERR_INVALID_ARG;   // X and Y overlap
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t d = h->d;
+    const int N = (int)std::max<int64_t>(h->n, h->k);
+    // temporaries: P, Q (N x b), split-K partials, and one d x b block for op M
+    const size_t pcap = std::max<size_t>(1u << 19, (size_t)N * b);
+    const size_t need = align256((size_t)N * b * 8) * 2 + align256(pcap * 8) + align256((size_t)d * b * 8) + 4096;
+    EDA_TRY(eda::ensure_workspace(h, need));
+    Arena a{static_cast<char*>(h->ws), h->ws_bytes, 0};
+    double* P = a.take<double>((size_t)N * b);
+    double* Q = a.take<double>((size_t)N * b);
+    double* part = a.take<double>(pcap);
+    double* tmp = a.take<double>((size_t)d * b);
+    const double* x = static_cast<const double*>(X);
+    double* y = static_cast<double*>(Y);
+    if (op == EDA_OP_M) return m_apply(h, b, x, ldx, y, ldx, tmp, P, Q, part, pcap, s);
+    // K(alpha) for the requested alpha: rebuild from the stored eigenpairs when alpha differs
+    const bool isW = (op == EDA_OP_SW);
+    const int m = isW ? (int)h->n : h->k;
+    const double stored = isW ? -0.5 * h->c2 : h->c2;
+    const double* K = isW ? h->KW : h->KB;
+    if (alpha != stored) {
+        if (!h->kblock) {
+            void* kb = nullptr;
+            EDA_CUDA_TRY(cudaMalloc(&kb, 2 * align256((size_t)N * N * 8)));
+            h->kblock = kb;
+            h->Kalpha = static_cast<double*>(kb);
+            h->Kalpha_tmp = reinterpret_cast<double*>(static_cast<char*>(kb) + align256((size_t)N * N * 8));
+        }
+        double* Kx = h->Kalpha;
+        double* t2 = h->Kalpha_tmp;
+        const int ns = isW ? h->nsig_w : h->nsig_b;
+        const double* lam = (isW ? h->evals_w : h->evals_b) + (m - ns);
+        EDA_TRY(phi_operator(m, ns, lam, isW ? h->evecs_w : h->evecs_b, m, alpha, Kx, t2, s));
+        K = Kx;
+    }
+    ExpOp eo{isW ? h->HW : h->HB, K, m};
+    return exp_apply_f64(d, eo, b, x, ldx, y, ldx, P, Q, part, pcap, s);
+}
+
+int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0, double* V, double* lambda, double* Y,
+              eda_solve_info* info, void* stream) {
+    if (!h || !V || !lambda || t < 1 || !(tol > 0.0) || (V0 && b0 < 1)) return EDA_ERR_INVALID_ARG;
+    return solve_impl(h, t, tol, V0, b0, V, lambda, Y, info, static_cast<cudaStream_t>(stream));
+}
+
+int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_t xq_dtype, int64_t m, int64_t ldq,
+                double* P, void* stream) {
+    if (!h || !V || !Xq || !P || t < 1 || m < 0 || ldq < h->d) return EDA_ERR_INVALID_ARG;
+    if (xq_dtype != EDA_F64) return EDA_ERR_INVALID_ARG;
+    if (m == 0) return EDA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t pcap = std::max<size_t>(1u << 19, (size_t)t * m);
+    EDA_TRY(eda::ensure_workspace(h, align256(pcap * 8) + 4096));
+    double* part = static_cast<double*>(h->ws);
+    return gemm_tn_f64(h->d, t, (int)m, 1.0, V, h->d, static_cast<const double*>(Xq), ldq, 0.0, P, t, part, pcap, s);
+}
+
+int eda_get_factors(eda_handle h, double* HW, double* HB, int32_t* counts, int32_t* perm, double* GW, double* GB,
+                    double* KW, double* KB, double* evals_w, double* evals_b, void* stream) {
+    if (!h) return EDA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t d = h->d, n = h->n, k = h->k;
+    auto cp = [&](void* dst, const void* src, size_t bytes) -> int {
+        if (!dst) return EDA_OK;
+        if (!src) return EDA_ERR_INVALID_ARG;
+        EDA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+        return EDA_OK;
+    };
+    EDA_TRY(cp(HW, h->HW, d * n * 8));
+    EDA_TRY(cp(HB, h->HB, d * k * 8));
+    EDA_TRY(cp(counts, h->counts, k * 4));
+    EDA_TRY(cp(perm, h->perm, n * 4));
+    EDA_TRY(cp(GW, h->GW, n * n * 8));
+    EDA_TRY(cp(GB, h->GB, k * k * 8));
+    EDA_TRY(cp(KW, h->KW, n * n * 8));
+    EDA_TRY(cp(KB, h->KB, k * k * 8));
+    EDA_TRY(cp(evals_w, h->evals_w, n * 8));
+    EDA_TRY(cp(evals_b, h->evals_b, k * 8));
+    return EDA_OK;
+}
+
+int eda_get_dims(eda_handle h, int64_t* d, int64_t* n, int32_t* k, double* c2, double* lmax_w, double* lmax_b) {
+    if (!h) return EDA_ERR_INVALID_ARG;
+    if (d) *d = h->d;
+    if (n) *n = h->n;
+    if (k) *k = h->k;
+    if (c2) *c2 = h->c2;
+    if (lmax_w) *lmax_w = h->lmax_w;
+    if (lmax_b) *lmax_b = h->lmax_b;
+    return EDA_OK;
+}
+
+void eda_destroy(eda_handle h) {
+    if (!h) return;
+    if (h->ws) cudaFree(h->ws);
+    if (h->kblock) cudaFree(h->kblock);
+    if (h->block) cudaFree(h->block);
+    delete h;
+}
+
+const char* eda_strerror(int status) {
+    switch (status) {
+        case EDA_OK: return "success";
+        case EDA_ERR_INVALID_ARG: return "invalid argument";
+        case EDA_ERR_BAD_LABELS: return "label outside [0, k) or empty class";
+        case EDA_ERR_NONFINITE: return "non-finite value in input or intermediate";
+        case EDA_ERR_OOM: return "device allocation failed";
+        case EDA_ERR_CUDA: return "CUDA error (see eda_last_cuda_error)";
+        case EDA_ERR_TIMEOUT: return "bounded device wait gave up";
+        case EDA_ERR_BREAKDOWN: return "Krylov block lost rank and could not be refilled";
+        case EDA_ERR_NOT_CONVERGED: return "not converged within the basis limit";
+        default: return "unknown status";
+    }
+}
+
+int eda_last_cuda_error(void) { return g_last_cuda_error; }
+const char* eda_last_cuda_error_string(void) { return cudaGetErrorString((cudaError_t)g_last_cuda_error); }
+uint64_t eda_kernel_launches(void) { return g_launches; }
+
+}  // extern "C"

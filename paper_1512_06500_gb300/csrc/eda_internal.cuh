@@ -1,0 +1,187 @@
+// Internal declarations shared by the CUDA translation units of the EDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+
+#include "../../include/eda.h"
+
+namespace eda {
+
+// ---------------------------------------------------------------- errors
+void note_cuda_error(cudaError_t e);
+uint64_t& launch_counter();
+
+#define EDA_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t e__ = (expr);                                 \
+        if (e__ != cudaSuccess) {                                 \
+            ::eda::note_cuda_error(e__);                          \
+            return e__ == cudaErrorMemoryAllocation ? EDA_ERR_OOM \
+                                                    : EDA_ERR_CUDA; \
+        }                                                         \
+    } while (0)
+
+#define EDA_TRY(expr)                    \
+    do {                                 \
+        int s__ = (expr);                \
+        if (s__ != EDA_OK) return s__;   \
+    } while (0)
+
+// After a kernel launch: count it and surface launch-configuration errors.
+#define EDA_LAUNCHED()                                \
+    do {                                              \
+        ::eda::launch_counter()++;                    \
+        EDA_CUDA_TRY(cudaPeekAtLastError());          \
+    } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Device status word bits (written by kernels, read by the host).
+enum : int {
+    ST_TIMEOUT = 1,       // a bounded grid-barrier wait gave up
+    ST_NONFINITE = 2,     // NaN/Inf met
+    ST_BADLABEL = 4,      // a label outside [0, k)
+    ST_EMPTYCLASS = 8,    // a class without samples
+    ST_RANKLOSS = 16,     // Cholesky pivot below the rank threshold
+};
+
+// ---------------------------------------------------------------- workspace
+// A stream-ordered bump allocator over one device block owned by the handle.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    template <class T> T* take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        if (off + count * sizeof(T) > cap) return nullptr;
+        used = off + count * sizeof(T);
+        return reinterpret_cast<T*>(base + off);
+    }
+    void reset() { used = 0; }
+};
+
+// Grid barrier state in device memory (zeroed at allocation).
+struct GridBarrier {
+    unsigned int* count;
+    unsigned int* gen;
+};
+
+// ---------------------------------------------------------------- dense FP64 ops
+// C (m x p) = alpha * A^T B (+ beta * C), A: d x m (lda), B: d x p (ldb), reduction over d split
+// across CTAs with a fixed-order second pass (deterministic). partial: >= splits * m * p doubles.
+int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda,
+                const double* B, int64_t ldb, double beta, double* C, int ldc,
+                double* partial, size_t partial_cap, cudaStream_t s);
+// C (d x p) = beta * C0 + alpha * A B, A: d x m (lda), B: m x p (ldb); C may equal C0 (same ld).
+int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda,
+                const double* B, int ldb, double beta, const double* C0, int64_t ldc0,
+                double* C, int64_t ldc, cudaStream_t s);
+// Small dense C (m x p) = alpha * op(A) op(B) + beta * C with op = N or T (all column-major).
+int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const double* A, int lda,
+                   const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
+// In-place upper Cholesky of a b x b SPD matrix G = R^T R (R stored in the upper triangle, the
+// strict lower triangle zeroed) and Rinv = R^{-1} (b x b, ld b). A pivot (squared) at or below
+// max(rank_tol * max diag, piv_min2) marks rank loss: that row of R and of Rinv is set to zero
+// and ST_RANKLOSS is or-ed into *status; lost pivots are listed in lost[0..], lost[b] = count.
+int chol_inv_small(int b, double* G, int ldg, double* Rinv, double rank_tol, double piv_min2,
+                   int* status, int* lost, cudaStream_t s);
+// Copy / scale / symmetrise helpers.
+int copy_mat_f64(int64_t rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb,
+                 cudaStream_t s);
+int symmetrize_f64(int m, double* A, int lda, cudaStream_t s);
+int fill_gaussian_f64(int64_t rows, int cols, double* A, int64_t lda, uint64_t seed,
+                      uint64_t stream_id, cudaStream_t s);
+int col_norms_f64(int64_t rows, int cols, const double* A, int64_t lda, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- symmetric eigensolver
+struct SymEigWork {
+    double* A;        // n x n copy (destroyed)
+    double* dgl;      // n diagonal
+    double* eoff;     // n off-diagonal
+    double* tau;      // n Householder scalars
+    double* vbuf;     // 4 * n scratch vectors for the tridiagonal reduction
+    double* partial;  // per-CTA partial sums (2 * max_ctas)
+    double* lu;       // 5 * n * nv inverse-iteration factors
+    GridBarrier bar;
+    int max_ctas;
+};
+size_t symeig_work_bytes(int n, int nv);
+int symeig_work_carve(Arena& a, int n, int nv, GridBarrier bar, SymEigWork* w);
+// Eigenpairs with ascending indices il..iu (0-based) of the symmetric n x n A (lda). Eigenvalues go
+// to w (iu-il+1, ascending), eigenvectors to Z (n x (iu-il+1), ldz) when Z != NULL. Runs of
+// eigenvalues whose gaps are <= cluster_rel * max|w| get explicit Gram-Schmidt.
+int symeig_f64(int n, const double* A, int lda, int il, int iu, double* w, double* Z, int ldz,
+               SymEigWork* ws, int* status, uint64_t seed, double cluster_rel, cudaStream_t s);
+// The two halves of symeig_f64: reduction + eigenvalues, then eigenvectors of nv eigenvalues w
+// (any subset, ascending) reusing the reduction left in ws.
+int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, SymEigWork* ws,
+                  int* status, cudaStream_t s);
+int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, uint64_t seed,
+                   double cluster_rel, cudaStream_t s);
+// Orthonormalise the columns of Z (n x nv) against each other by Newton-Schulz steps
+// Z <- Z (3 I - Z^T Z) / 2; tmp holds 2 * nv * nv + n * nv doubles.
+int newton_schulz_f64(int n, int nv, double* Z, int ldz, int steps, double* tmp, double* partial,
+                      size_t partial_cap, cudaStream_t s);
+
+// ---------------------------------------------------------------- build kernels
+int segment_labels(const int32_t* labels, int n, int k, int32_t* counts, int32_t* offsets,
+                   int32_t* perm, int* status, cudaStream_t s);
+int build_factors(const void* X, int x_dtype, int64_t d, int n, int64_t ldx, int k,
+                  const int32_t* labels, const int32_t* counts, const int32_t* offsets,
+                  const int32_t* perm, double* mu_j, double* mu, double* HW, double* HB,
+                  int* status, cudaStream_t s);
+int check_finite_f64(int64_t rows, int cols, const double* A, int64_t lda, int* status, cudaStream_t s);
+// K = alpha I + W_s diag(alpha (phi(alpha lam_s) - 1)) W_s^T over the ns significant eigenpairs
+// (lam_s, W_s) of the Gram; equal to alpha W diag(phi(alpha lam)) W^T because sum_i w_i w_i^T = I
+// and phi(0) = 1. tmp: n * ns doubles.
+int phi_operator(int n, int ns, const double* lam, const double* W, int ldw, double alpha,
+                 double* K, double* tmp, cudaStream_t s);
+
+// ---------------------------------------------------------------- exp-apply
+struct ExpOp {
+    const double* H;  // d x m (ld d)
+    const double* K;  // m x m
+    int m;
+};
+// Y = X + H K (H^T X) for a d x b block (FP64 sweeps).
+int exp_apply_f64(int64_t d, const ExpOp& op, int b, const double* X, int64_t ldx, double* Y,
+                  int64_t ldy, double* P, double* Q, double* partial, size_t partial_cap,
+                  cudaStream_t s);
+
+}  // namespace eda
+
+// The handle.
+struct eda_ctx {
+    int64_t d = 0, n = 0;
+    int32_t k = 0;          // number of columns of H_B
+    eda_config cfg{};
+    double c2 = 0, lmax_w = 0, lmax_b = 0;
+    // owned device memory
+    void* block = nullptr;  // one allocation for everything below
+    size_t block_bytes = 0;
+    double *HW = nullptr, *HB = nullptr;
+    int32_t *counts = nullptr, *offsets = nullptr, *perm = nullptr;
+    double *mu_j = nullptr, *mu = nullptr;
+    double *GW = nullptr, *GB = nullptr;
+    double *evals_w = nullptr, *evals_b = nullptr;
+    double *evecs_w = nullptr, *evecs_b = nullptr;
+    double *KW = nullptr, *KB = nullptr;   // K(-c^2/2) for H_W, K(c^2) for H_B
+    int* status = nullptr;                 // device status word
+    eda::GridBarrier bar{};
+    size_t build_arena_off = 0;            // start of the build scratch inside `block`
+    int nsig_first = 0;                    // scratch result of the last Gram eigensolve
+    int nsig_w = 0, nsig_b = 0;            // significant eigenpairs kept for K_W, K_B
+    // K(alpha) for an alpha other than the stored ones (allocated on first use)
+    void* kblock = nullptr;
+    double *Kalpha = nullptr, *Kalpha_tmp = nullptr;
+    // solve workspace (grown on demand)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace eda {
+// Grow the handle's solve workspace to at least `bytes` (contents are not preserved).
+int ensure_workspace(eda_ctx* h, size_t bytes);
+}  // namespace eda

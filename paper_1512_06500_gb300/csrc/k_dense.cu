@@ -1,0 +1,353 @@
+// FP64 dense building blocks of the Krylov solver: tall-skinny products with a deterministic
+// split-K reduction, small products, Cholesky with inverse, and seeded Gaussian blocks.
+#include "eda_internal.cuh"
+
+#include <cmath>
+
+namespace eda {
+
+namespace {
+
+constexpr int TN_KB = 32;       // rows of A/B staged per pass
+constexpr int TN_TM = 32;       // output tile rows
+constexpr int TN_THREADS = 256;
+
+// partial[s][j][i] = sum over rows r of split s of A[r, i0+i] * B[r, j0+j]
+template <int TP>
+__global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m, int p, const double* __restrict__ A,
+                                                                int64_t lda, const double* __restrict__ B, int64_t ldb,
+                                                                int64_t rows_per_split, double* __restrict__ partial) {
+    __shared__ double As[TN_KB][TN_TM + 1];
+    __shared__ double Bs[TN_KB][TP + 1];
+    const int i0 = blockIdx.x * TN_TM;
+    const int j0 = blockIdx.y * TP;
+    const int s = blockIdx.z;
+    const int64_t r_begin = (int64_t)s * rows_per_split;
+    const int64_t r_end = min(d, r_begin + rows_per_split);
+    // thread -> outputs: TM*TP outputs over 256 threads
+    constexpr int OUT = TN_TM * TP / TN_THREADS;      // 1 (TP=8), 2 (TP=16), 4 (TP=32)
+    constexpr int TPT = (TP >= 16) ? 2 : 1;           // columns per thread
+    constexpr int TMT = OUT / TPT;                    // rows per thread
+    const int tx = threadIdx.x % (TN_TM / TMT);       // row group
+    const int ty = threadIdx.x / (TN_TM / TMT);       // column group
+    double acc[TMT][TPT];
+#pragma unroll
+    for (int a = 0; a < TMT; ++a)
+#pragma unroll
+        for (int b = 0; b < TPT; ++b) acc[a][b] = 0.0;
+
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += TN_KB) {
+        // stage A rows r0..r0+KB of columns i0..i0+TM (coalesced along rows)
+        for (int e = threadIdx.x; e < TN_KB * TN_TM; e += TN_THREADS) {
+            const int rr = e % TN_KB, cc = e / TN_KB;
+            const int64_t r = r0 + rr;
+            const int c = i0 + cc;
+            As[rr][cc] = (r < r_end && c < m) ? A[(int64_t)c * lda + r] : 0.0;
+        }
+        for (int e = threadIdx.x; e < TN_KB * TP; e += TN_THREADS) {
+            const int rr = e % TN_KB, cc = e / TN_KB;
+            const int64_t r = r0 + rr;
+            const int c = j0 + cc;
+            Bs[rr][cc] = (r < r_end && c < p) ? B[(int64_t)c * ldb + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < TN_KB; ++rr) {
+            double av[TMT], bv[TPT];
+#pragma unroll
+            for (int a = 0; a < TMT; ++a) av[a] = As[rr][tx + a * (TN_TM / TMT)];
+#pragma unroll
+            for (int b = 0; b < TPT; ++b) bv[b] = Bs[rr][ty + b * (TP / TPT)];
+#pragma unroll
+            for (int a = 0; a < TMT; ++a)
+#pragma unroll
+                for (int b = 0; b < TPT; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+    double* out = partial + (int64_t)s * m * p;
+#pragma unroll
+    for (int a = 0; a < TMT; ++a)
+#pragma unroll
+        for (int b = 0; b < TPT; ++b) {
+            const int i = i0 + tx + a * (TN_TM / TMT);
+            const int j = j0 + ty + b * (TP / TPT);
+            if (i < m && j < p) out[(int64_t)j * m + i] = acc[a][b];
+        }
+}
+
+// C[i, j] = alpha * sum_s partial[s][j][i] + beta * C[i, j], splits summed in order.
+__global__ void k_gemm_tn_reduce(int m, int p, int splits, const double* __restrict__ partial, double alpha,
+                                 double beta, double* __restrict__ C, int ldc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * p) return;
+    const int i = (int)(e % m), j = (int)(e / m);
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) acc += partial[(int64_t)s * m * p + e];
+    double v = alpha * acc;
+    if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
+    C[(int64_t)j * ldc + i] = v;
+}
+
+// C[r, c] = beta * C0[r, c] + alpha * sum_l A[r, l] B[l, c]; thread per (row, PC columns).
+template <int PC>
+__global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double alpha, const double* __restrict__ A,
+                                                 int64_t lda, const double* __restrict__ B, int ldb, double beta,
+                                                 const double* C0, int64_t ldc0, double* C, int64_t ldc) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c0 = blockIdx.y * PC;
+    if (r >= d) return;
+    double acc[PC];
+#pragma unroll
+    for (int c = 0; c < PC; ++c) acc[c] = 0.0;
+    for (int l = 0; l < m; ++l) {
+        const double a = A[(int64_t)l * lda + r];
+#pragma unroll
+        for (int c = 0; c < PC; ++c)
+            if (c0 + c < p) acc[c] = fma(a, __ldg(B + (int64_t)(c0 + c) * ldb + l), acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < PC; ++c) {
+        if (c0 + c >= p) break;
+        double v = alpha * acc[c];
+        if (beta != 0.0) v = fma(beta, C0[(int64_t)(c0 + c) * ldc0 + r], v);
+        C[(int64_t)(c0 + c) * ldc + r] = v;
+    }
+}
+
+__global__ void k_gemm_small(bool ta, bool tb, int m, int p, int kk, double alpha, const double* __restrict__ A,
+                             int lda, const double* __restrict__ B, int ldb, double beta, double* __restrict__ C,
+                             int ldc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= m || j >= p) return;
+    double acc = 0.0;
+    for (int l = 0; l < kk; ++l) {
+        const double a = ta ? A[(int64_t)i * lda + l] : A[(int64_t)l * lda + i];
+        const double b = tb ? B[(int64_t)l * ldb + j] : B[(int64_t)j * ldb + l];
+        acc = fma(a, b, acc);
+    }
+    double v = alpha * acc;
+    if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
+    C[(int64_t)j * ldc + i] = v;
+}
+
+// Single-CTA right-looking upper Cholesky G = R^T R with rank detection, then R^{-1}.
+__global__ void k_chol_inv(int b, double* G, int ldg, double* Rinv, double rank_tol, double piv_min2, int* status,
+                           int* lost) {
+    __shared__ double maxdiag;
+    __shared__ int nlost;
+    __shared__ double piv;
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        bool bad = false;
+        for (int j = 0; j < b; ++j) {
+            const double g = G[(int64_t)j * ldg + j];
+            if (!isfinite(g)) bad = true;
+            mx = fmax(mx, fabs(g));
+        }
+        maxdiag = mx;
+        nlost = 0;
+        if (bad) atomicOr(status, ST_NONFINITE);
+    }
+    __syncthreads();
+    const double thr = fmax(rank_tol * maxdiag, piv_min2);
+    for (int j = 0; j < b; ++j) {
+        if (threadIdx.x == 0) {
+            const double g = G[(int64_t)j * ldg + j];
+            if (!(g > thr) || maxdiag == 0.0) {
+                piv = 0.0;
+                if (lost) lost[nlost] = j;
+                nlost++;
+                atomicOr(status, ST_RANKLOSS);
+            } else {
+                piv = sqrt(g);
+            }
+            G[(int64_t)j * ldg + j] = piv;
+        }
+        __syncthreads();
+        const double rjj = piv;
+        // row j of R: G[j, c] / r_jj for c > j (upper triangle, column-major: G[c*ldg + j])
+        for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) {
+            const double v = (rjj > 0.0) ? G[(int64_t)c * ldg + j] / rjj : 0.0;
+            G[(int64_t)c * ldg + j] = v;
+        }
+        __syncthreads();
+        // trailing update of the upper triangle: G[c1, c2] -= R[j, c1] R[j, c2], j < c1 <= c2
+        const int rem = b - j - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int c1 = j + 1 + e % rem, c2 = j + 1 + e / rem;
+            if (c1 <= c2) G[(int64_t)c2 * ldg + c1] -= G[(int64_t)c1 * ldg + j] * G[(int64_t)c2 * ldg + j];
+        }
+        __syncthreads();
+    }
+    // zero the strict lower triangle
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int r = e % b, c = e / b;
+        if (r > c) G[(int64_t)c * ldg + r] = 0.0;
+    }
+    __syncthreads();
+    // Rinv by back substitution, one column per thread
+    for (int c = threadIdx.x; c < b; c += blockDim.x) {
+        for (int i = b - 1; i >= 0; --i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            if (i > c) v = 0.0;
+            else {
+                for (int l = i + 1; l <= c; ++l) v -= G[(int64_t)l * ldg + i] * Rinv[(int64_t)c * b + l];
+                const double rii = G[(int64_t)i * ldg + i];
+                v = (rii > 0.0) ? v / rii : 0.0;
+            }
+            Rinv[(int64_t)c * b + i] = v;
+        }
+    }
+    if (threadIdx.x == 0 && lost) lost[b] = nlost;
+}
+
+__global__ void k_copy(int64_t rows, int cols, const double* __restrict__ A, int64_t lda, double* __restrict__ B,
+                       int64_t ldb) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * cols) return;
+    const int64_t r = e % rows, c = e / rows;
+    B[c * ldb + r] = A[c * lda + r];
+}
+
+__global__ void k_symmetrize(int m, double* A, int lda) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int r = (int)(e % m), c = (int)(e / m);
+    if (r < c) {
+        const double v = 0.5 * (A[(int64_t)c * lda + r] + A[(int64_t)r * lda + c]);
+        A[(int64_t)c * lda + r] = v;
+        A[(int64_t)r * lda + c] = v;
+    }
+}
+
+// splitmix64 finaliser (Steele, Lea and Flood, 2014) as a counter-based generator.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_fill_gaussian(int64_t rows, int cols, double* A, int64_t lda, uint64_t seed, uint64_t sid) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * cols) return;
+    const int64_t r = e % rows, c = e / rows;
+    const uint64_t h1 = mix64(seed ^ mix64(sid * 0x100000001B3ull + (uint64_t)e));
+    const uint64_t h2 = mix64(h1 + 0x632BE59BD9B4E019ull);
+    const double u1 = ((h1 >> 11) + 1) * (1.0 / 9007199254740993.0);   // (0, 1]
+    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);         // [0, 1)
+    A[c * lda + r] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);            // Box-Muller
+}
+
+__global__ void k_col_norms(int64_t rows, const double* __restrict__ A, int64_t lda, double* out) {
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double v = A[(int64_t)c * lda + r];
+        acc = fma(v, v, acc);
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        out[c] = sqrt(s);
+    }
+}
+
+}  // namespace
+
+int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                double beta, double* C, int ldc, double* partial, size_t partial_cap, cudaStream_t s) {
+    if (m <= 0 || p <= 0) return EDA_OK;
+    const int TP = p <= 8 ? 8 : (p <= 16 ? 16 : 32);
+    const int tiles = ceil_div(m, TN_TM) * ceil_div(p, TP);
+    int splits = std::max(1, ceil_div(2 * 152, tiles));
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, (d + 63) / 64));
+    while (splits > 1 && (size_t)splits * m * p > partial_cap) --splits;
+    if ((size_t)splits * m * p > partial_cap) return EDA_ERR_INVALID_ARG;
+    int64_t rows = (d + splits - 1) / splits;
+    rows = (rows + TN_KB - 1) / TN_KB * TN_KB;
+    splits = (int)std::max<int64_t>(1, (d + rows - 1) / rows);
+    dim3 grid(ceil_div(m, TN_TM), ceil_div(p, TP), splits);
+    if (d > 0) {
+        if (TP == 8) k_gemm_tn_partial<8><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        else if (TP == 16) k_gemm_tn_partial<16><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        else k_gemm_tn_partial<32><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        EDA_LAUNCHED();
+    } else {
+        splits = 0;
+    }
+    const int64_t tot = (int64_t)m * p;
+    k_gemm_tn_reduce<<<ceil_div(tot, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int ldb,
+                double beta, const double* C0, int64_t ldc0, double* C, int64_t ldc, cudaStream_t s) {
+    if (d <= 0 || p <= 0) return EDA_OK;
+    const int rowblocks = ceil_div(d, 128);
+    int pc = 8;
+    while (pc > 1 && (int64_t)rowblocks * ceil_div(p, pc) < 2 * 152) pc >>= 1;
+    dim3 grid(rowblocks, ceil_div(p, pc));
+    switch (pc) {
+        case 8: k_gemm_nn<8><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
+        case 4: k_gemm_nn<4><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
+        case 2: k_gemm_nn<2><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
+        default: k_gemm_nn<1><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
+    }
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const double* A, int lda, const double* B,
+                   int ldb, double beta, double* C, int ldc, cudaStream_t s) {
+    if (m <= 0 || p <= 0) return EDA_OK;
+    dim3 blk(16, 16), grid(ceil_div(m, 16), ceil_div(p, 16));
+    k_gemm_small<<<grid, blk, 0, s>>>(ta, tb, m, p, kk, alpha, A, lda, B, ldb, beta, C, ldc);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+int chol_inv_small(int b, double* G, int ldg, double* Rinv, double rank_tol, double piv_min2, int* status, int* lost,
+                   cudaStream_t s) {
+    k_chol_inv<<<1, 256, 0, s>>>(b, G, ldg, Rinv, rank_tol, piv_min2, status, lost);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+int copy_mat_f64(int64_t rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return EDA_OK;
+    k_copy<<<ceil_div(rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, B, ldb);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+int symmetrize_f64(int m, double* A, int lda, cudaStream_t s) {
+    if (m <= 1) return EDA_OK;
+    k_symmetrize<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, A, lda);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+int fill_gaussian_f64(int64_t rows, int cols, double* A, int64_t lda, uint64_t seed, uint64_t stream_id,
+                      cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return EDA_OK;
+    k_fill_gaussian<<<ceil_div(rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, seed, stream_id);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+int col_norms_f64(int64_t rows, int cols, const double* A, int64_t lda, double* out, cudaStream_t s) {
+    if (cols <= 0) return EDA_OK;
+    k_col_norms<<<cols, 256, 0, s>>>(rows, A, lda, out);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+}  // namespace eda

@@ -1,0 +1,81 @@
+"""The C ABI library builds, loads and exports every symbol include/eda.h declares (no GPU needed).
+
+Calls made here never reach the device: argument validation rejects them first, and
+eda_strerror / eda_config_default are host-only.
+"""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "eda.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eda_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1512_06500_gb300 import build_lib, eda
+    path = build_lib.build()
+    return eda.load(path), path
+
+
+def test_header_matches_binding_list(lib):
+    from paper_1512_06500_gb300 import eda
+    assert _declared() == sorted(eda.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    _, path = lib
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [s for s in _declared() if s not in syms]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    from paper_1512_06500_gb300 import eda
+    L, _ = lib
+    assert L.eda_strerror(0) == b"success"
+    assert L.eda_strerror(-8).startswith(b"not converged")
+    c = eda.config()
+    assert (c.prec, c.block_b, c.m_max, c.check_every, c.tau, c.c2) == (0, 8, 0, 1, 10.0, 0.0)
+
+
+def test_invalid_arguments_rejected_before_device_work(lib):
+    from paper_1512_06500_gb300 import eda
+    L, _ = lib
+    h = ctypes.c_void_p()
+    c = eda.config()
+    # null sample pointer, zero dimension, k > n
+    assert L.eda_build(None, 0, 10, 5, 10, None, 2, ctypes.byref(c), None, ctypes.byref(h)) == -1
+    assert L.eda_build(ctypes.c_void_p(16), 0, 0, 5, 10, ctypes.c_void_p(16), 2, ctypes.byref(c), None,
+                       ctypes.byref(h)) == -1
+    assert L.eda_build(ctypes.c_void_p(16), 0, 10, 5, 10, ctypes.c_void_p(16), 6, ctypes.byref(c), None,
+                       ctypes.byref(h)) == -1
+    bad = eda.config(block_b=0)
+    assert L.eda_build(ctypes.c_void_p(16), 0, 10, 5, 10, ctypes.c_void_p(16), 2, ctypes.byref(bad), None,
+                       ctypes.byref(h)) == -1
+    assert L.eda_solve(None, 3, 1e-6, None, 0, None, None, None, None, None) == -1
+    assert L.eda_apply_exp(None, 0, 1.0, None, None, 10, 1, 0, None) == -1
+    L.eda_destroy(None)
+
+
+def test_product_path_has_no_oracle_or_cpu_fallback():
+    # the package and the library sources never reference the oracle
+    pkg = os.path.join(ROOT, "paper_1512_06500_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
