@@ -155,6 +155,17 @@ const char* eda_last_cuda_error_string(void);
 /* Number of this library's kernels launched so far by the calling process. */
 uint64_t eda_kernel_launches(void);
 
+/* Region timers (off by default). When enabled, the library records a CUDA event pair on the
+ * launching stream around each call of a named region: "exp_apply_w" / "exp_apply_b" (one
+ * Theorem 3.1 product with H_W / H_B),
+ * "m_apply" (three products), "tridiag" (Householder reduction), "symeig" (a full small
+ * eigensolve), "gram" (the two Gram products of the build), "rr" (one Rayleigh-Ritz check),
+ * "reorth" (one CGS2 pass pair). eda_profile_read synchronises the pending events of a region
+ * and returns its accumulated device time in ms and its call count (0, 0 for unknown names). */
+int eda_profile_enable(int on);
+int eda_profile_reset(void);
+int eda_profile_read(const char* region, double* total_ms, int64_t* calls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -164,10 +164,13 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     const size_t pcap = std::max<size_t>(1u << 19, N * N);
     double* part = scratch.take<double>(pcap);
     if (!part) return EDA_ERR_OOM;
-    EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
-    EDA_TRY(symmetrize_f64(n, h->GW, n, s));
-    EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, part, pcap, s));
-    EDA_TRY(symmetrize_f64(k, h->GB, k, s));
+    {
+        ProfScope prof("gram", s);
+        EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
+        EDA_TRY(symmetrize_f64(n, h->GW, n, s));
+        EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, part, pcap, s));
+        EDA_TRY(symmetrize_f64(k, h->GB, k, s));
+    }
     EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
     EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));
     const size_t mark = scratch.used;
@@ -333,7 +336,7 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
         EDA_TRY(phi_operator(m, ns, lam, isW ? h->evecs_w : h->evecs_b, m, alpha, Kx, t2, s));
         K = Kx;
     }
-    ExpOp eo{isW ? h->HW : h->HB, K, m};
+    ExpOp eo{isW ? h->HW : h->HB, K, m, isW ? "exp_apply_w" : "exp_apply_b"};
     return exp_apply_f64(d, eo, b, x, ldx, y, ldx, P, Q, part, pcap, s);
 }
 

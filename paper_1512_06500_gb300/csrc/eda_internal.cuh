@@ -48,6 +48,21 @@ enum : int {
     ST_RANKLOSS = 16,     // Cholesky pivot below the rank threshold
 };
 
+// ---------------------------------------------------------------- region timers
+// Records a CUDA event pair around its scope on stream s when profiling is enabled.
+class ProfScope {
+  public:
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    const char* name_;
+    cudaStream_t s_;
+    cudaEvent_t e0_ = nullptr;
+};
+
 // ---------------------------------------------------------------- workspace
 // A stream-ordered bump allocator over one device block owned by the handle.
 struct Arena {
@@ -144,6 +159,7 @@ struct ExpOp {
     const double* H;  // d x m (ld d)
     const double* K;  // m x m
     int m;
+    const char* tag;  // region-timer name
 };
 // Y = X + H K (H^T X) for a d x b block (FP64 sweeps).
 int exp_apply_f64(int64_t d, const ExpOp& op, int b, const double* X, int64_t ldx, double* Y,

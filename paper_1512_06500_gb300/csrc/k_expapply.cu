@@ -8,6 +8,7 @@ namespace eda {
 
 int exp_apply_f64(int64_t d, const ExpOp& op, int b, const double* X, int64_t ldx, double* Y, int64_t ldy,
                   double* P, double* Q, double* partial, size_t partial_cap, cudaStream_t s) {
+    ProfScope prof(op.tag ? op.tag : "exp_apply", s);
     const int m = op.m;
     // sweep 1: P = H^T X (m x b), split over d with a fixed-order reduction
     EDA_TRY(gemm_tn_f64(d, m, b, 1.0, op.H, d, X, ldx, 0.0, P, m, partial, partial_cap, s));

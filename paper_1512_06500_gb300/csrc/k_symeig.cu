@@ -406,6 +406,7 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     double* pglob = ws->vbuf;
     EDA_CUDA_TRY(cudaMemsetAsync(ws->bar.count, 0, sizeof(unsigned), s));
     {
+        ProfScope prof("tridiag", s);
         int nn = n;
         double* a0 = ws->A;
         double* a1 = HV;
@@ -442,6 +443,7 @@ int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWor
 
 int symeig_f64(int n, const double* A, int lda, int il, int iu, double* w, double* Z, int ldz, SymEigWork* ws,
                int* status, uint64_t seed, double cluster_rel, cudaStream_t s) {
+    ProfScope prof("symeig", s);
     EDA_TRY(symeig_values(n, A, lda, il, iu, w, ws, status, s));
     if (!Z) return EDA_OK;
     return symeig_vectors(n, iu - il + 1, w, Z, ldz, ws, seed, cluster_rel, s);

@@ -97,6 +97,7 @@ int cholqr_pass(int64_t d, int b, double* X, int64_t ldx, double* Rm, double* Ri
 int cgs2(int64_t d, int cols, int b, const double* V, double* X, int64_t ldx, double* Cfirst, double* C2,
          SolveWs& w, cudaStream_t s) {
     if (cols <= 0) return EDA_OK;
+    ProfScope prof("reorth", s);
     EDA_TRY(gemm_tn_f64(d, cols, b, 1.0, V, d, X, ldx, 0.0, Cfirst, cols, w.part, w.pcap, s));
     EDA_TRY(gemm_nn_f64(d, cols, b, -1.0, V, d, Cfirst, cols, 1.0, X, ldx, X, ldx, s));
     EDA_TRY(gemm_tn_f64(d, cols, b, 1.0, V, d, X, ldx, 0.0, C2, cols, w.part, w.pcap, s));
@@ -109,9 +110,10 @@ int cgs2(int64_t d, int cols, int b, const double* V, double* X, int64_t ldx, do
 // Y = M X = E_W^{-1/2} E_B E_W^{-1/2} X, the three products (iii)-(v) of Eq. (320).
 int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t ldy, double* tmp, double* P,
             double* Q, double* partial, size_t partial_cap, cudaStream_t s) {
+    ProfScope prof("m_apply", s);
     const int64_t d = h->d;
-    const ExpOp W{h->HW, h->KW, (int)h->n};
-    const ExpOp B{h->HB, h->KB, h->k};
+    const ExpOp W{h->HW, h->KW, (int)h->n, "exp_apply_w"};
+    const ExpOp B{h->HB, h->KB, h->k, "exp_apply_b"};
     EDA_TRY(exp_apply_f64(d, W, b, X, ldx, tmp, d, P, Q, partial, partial_cap, s));
     EDA_TRY(exp_apply_f64(d, B, b, tmp, d, Y, ldy, P, Q, partial, partial_cap, s));
     EDA_TRY(exp_apply_f64(d, W, b, Y, ldy, tmp, d, P, Q, partial, partial_cap, s));
@@ -271,6 +273,7 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
         if ((cols >= t + 1 && iters % h->cfg.check_every == 0) || (last && cols >= t)) {
             ++checks;
             rr_cols = cols;
+            ProfScope prof("rr", s);
             EDA_TRY(symeig_f64(cols, w.T, m_max, cols - t, cols - 1, w.theta, w.S, cols, &w.eig, h->status,
                                h->cfg.seed + 7, 1e-7, s));
             if (exhausted) {
@@ -315,7 +318,7 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
     EDA_CUDA_TRY(cudaMemcpyAsync(lambda, w.lamd, t * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (Yout) EDA_CUDA_TRY(cudaMemcpyAsync(Yout, w.Ydesc, (size_t)d * t * 8, cudaMemcpyDeviceToDevice, s));
     // x = exp(-c^2 S_W / 2) y
-    const ExpOp Wop{h->HW, h->KW, n};
+    const ExpOp Wop{h->HW, h->KW, n, "exp_apply_w"};
     EDA_TRY(exp_apply_f64(d, Wop, t, w.Ydesc, d, w.Xt, d, w.P, w.Q, w.part, w.pcap, s));
     // V = orth(X_t): CholQR2
     {

@@ -33,6 +33,7 @@ EXPORTS = [
     "eda_config_default", "eda_build", "eda_build_from_factors", "eda_apply_exp", "eda_solve",
     "eda_project", "eda_get_factors", "eda_get_dims", "eda_destroy", "eda_strerror",
     "eda_last_cuda_error", "eda_last_cuda_error_string", "eda_kernel_launches",
+    "eda_profile_enable", "eda_profile_reset", "eda_profile_read",
 ]
 
 
@@ -94,6 +95,9 @@ def load(path: str | None = None):
         "eda_last_cuda_error": ([], ctypes.c_int),
         "eda_last_cuda_error_string": ([], ctypes.c_char_p),
         "eda_kernel_launches": ([], ctypes.c_uint64),
+        "eda_profile_enable": ([ctypes.c_int], ctypes.c_int),
+        "eda_profile_reset": ([], ctypes.c_int),
+        "eda_profile_read": ([ctypes.c_char_p, P(f64), P(i64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -145,6 +149,21 @@ def config(**kw) -> Config:
 
 def kernel_launches() -> int:
     return int(load().eda_kernel_launches())
+
+
+def profile_enable(on=True):
+    _check(load().eda_profile_enable(1 if on else 0), "eda_profile_enable")
+
+
+def profile_reset():
+    _check(load().eda_profile_reset(), "eda_profile_reset")
+
+
+def profile_read(region: str):
+    """(total device ms, calls) of a library region since the last reset."""
+    ms, calls = ctypes.c_double(), ctypes.c_int64()
+    _check(load().eda_profile_read(region.encode(), ctypes.byref(ms), ctypes.byref(calls)), "eda_profile_read")
+    return ms.value, calls.value
 
 
 class Handle:
