@@ -135,6 +135,23 @@ int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0,
 int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_t xq_dtype,
                 int64_t m, int64_t ldq, double* P, void* stream);
 
+/* Y = X + H K (H^T X) for a caller-supplied operator, allocating no device memory.
+ * The paper has no counterpart: this is for callers that must not allocate, such as code
+ * embedded in a host framework that owns a fixed device-memory budget, or latency-critical
+ * loops where cudaMalloc/cudaFree (which may synchronise the device) cannot be used.
+ *   H : d x m, K : m x m (for exp(alpha H H^T) pass K = alpha phi(alpha H^T H), e.g. the KW or
+ *       KB matrices returned by eda_get_factors), X, Y : d x b, all FP64, leading dimension ld
+ *       (H uses ld = d). X and Y must not overlap.
+ * Temporaries live in one fixed 4 MiB device array inside the library (held on every GPU that
+ * loads it until the process exits): m * b must not exceed 174762 (2^19 / 3 doubles), larger
+ * sizes return EDA_ERR_INVALID_ARG before any device work. The first call on a device looks up
+ * that array's device address with the device current; make that first call before any stream
+ * capture. All calls share the array, so calls whose work overlaps on the GPU (different
+ * streams, or other host threads) race and must be serialised by the caller. Nothing carries
+ * over between calls: every scratch value read is written earlier in the same call. */
+int eda_lowrank_exp_apply_noalloc(const double* H, int64_t d, int32_t m, const double* K,
+                                  const double* X, double* Y, int64_t ld, int32_t b, void* stream);
+
 /* Copy out build results into caller device buffers (any pointer may be NULL):
  * HW d x n, HB d x k, counts k, perm n, GW n x n, GB k x k, KW n x n
  * (alpha = -c^2/2), KB k x k (alpha = c^2), evals_w n, evals_b k (ascending). */

@@ -34,6 +34,7 @@ EXPORTS = [
     "eda_project", "eda_get_factors", "eda_get_dims", "eda_destroy", "eda_strerror",
     "eda_last_cuda_error", "eda_last_cuda_error_string", "eda_kernel_launches",
     "eda_profile_enable", "eda_profile_reset", "eda_profile_read",
+    "eda_lowrank_exp_apply_noalloc",
 ]
 
 
@@ -98,6 +99,7 @@ def load(path: str | None = None):
         "eda_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "eda_profile_reset": ([], ctypes.c_int),
         "eda_profile_read": ([ctypes.c_char_p, P(f64), P(i64)], ctypes.c_int),
+        "eda_lowrank_exp_apply_noalloc": ([vp, i64, i32, vp, vp, vp, i64, i32, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -291,3 +293,19 @@ def build_from_factors(HW, HB, cfg: Config | None = None, stream=None) -> Handle
     _check(load().eda_build_from_factors(_ptr(HW), n, _ptr(HB), kb, d, ctypes.byref(c), _stream(stream),
                                          ctypes.byref(h)), "eda_build_from_factors")
     return Handle(h, HW.device)
+
+
+def lowrank_exp_apply_noalloc(H, K, X, out=None, stream=None):
+    """Y = X + H K (H^T X) without any device allocation (fixed library scratch).
+
+    H: (m, d) float64 CUDA tensor (column-major d x m), K: (m, m), X: (b, d). The library
+    rejects m * b above 174762 with EDA_ERR_INVALID_ARG.
+    """
+    for t, nm in ((H, "H"), (K, "K"), (X, "X")):
+        _need_cuda(t, nm, torch.float64)
+    m, d = H.shape
+    b = X.shape[0]
+    Y = out if out is not None else torch.empty_like(X)
+    _check(load().eda_lowrank_exp_apply_noalloc(_ptr(H), d, m, _ptr(K), _ptr(X), _ptr(Y), d, b, _stream(stream)),
+           "eda_lowrank_exp_apply_noalloc")
+    return Y
