@@ -202,8 +202,8 @@ def run_gpu(args, rank, world, local_rank):
         ms = float(t.item())
 
     # ---- roofline of the exp-apply (Theorem 3.1 product) measured inside the timed region ----
-    regions = {r: eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b", "m_apply", "tridiag", "symeig",
-                                                  "gram", "rr", "reorth")}
+    regions = {r: eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b", "m_apply", "tridiag", "bisect",
+                                                  "invit", "backtransform", "symeig", "gram", "rr", "reorth")}
     d, n, k, b = p.d, p.n, p.k, c["b"]
     ew_ms, ew_calls = regions["exp_apply_w"]
     # Lanczos-block calls have width b; the recovery call has width t. Count FLOPs per call exactly:

@@ -308,7 +308,8 @@ int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t 
 int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const double* A, int lda, const double* B,
                    int ldb, double beta, double* C, int ldc, cudaStream_t s) {
     if (m <= 0 || p <= 0) return EDA_OK;
-    dim3 blk(16, 16), grid(ceil_div(m, 16), ceil_div(p, 16));
+    // one warp per CTA (32 rows of one column): FP64 work spreads over all SMs
+    dim3 blk(32, 1), grid(ceil_div(m, 32), p);
     k_gemm_small<<<grid, blk, 0, s>>>(ta, tb, m, p, kk, alpha, A, lda, B, ldb, beta, C, ldc);
     EDA_LAUNCHED();
     return EDA_OK;

@@ -10,6 +10,8 @@
 // stored reflectors. Callers add a Newton-Schulz step for orthogonality across near clusters.
 #include "eda_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -59,15 +61,18 @@ __device__ void grid_sync(GridBarrier bar, int* status) {
 }
 
 __device__ double block_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) red[w] = v;
     __syncthreads();
-    double s = 0.0;
+    // pairwise tree over the warps: the same fixed order in every thread and every CTA
     const int nw = blockDim.x >> 5;
-    for (int i = 0; i < nw; ++i) s += red[i];   // same fixed order in every thread and CTA
-    return s;
+    if (nw == 4) return (red[0] + red[1]) + (red[2] + red[3]);
+    if (nw == 8) return ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+    double sacc = 0.0;
+    for (int i = 0; i < nw; ++i) sacc += red[i];
+    return sacc;
 }
 
 // Householder tridiagonalisation of the full symmetric n x n matrix A (ld n), in place.
@@ -157,61 +162,340 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag(int n, double* A, doubl
     }
 }
 
-// Number of eigenvalues of the tridiagonal (dgl, e2 = squared off-diagonal) below x.
-__device__ int sturm_count(int n, const double* dgl, const double* e2, double x, double pivmin) {
+constexpr int CT_THREADS = 128;
+
+// Reflector of column j (entries a[i], i > j) formed by the CTA that owns the column and
+// published in its shared memory: vpub[i] for i > j, vpub[n] = tau, vpub[n + 1] = beta.
+__device__ void make_reflector(int j, int n, const double* a, double* vpub, double* HV, double* eoff, double* tau,
+                               double* red) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int i0 = j + 1;
+    double ss = 0.0;
+    for (int i = i0 + 1 + tid; i < n; i += bd) ss = fma(a[i], a[i], ss);
+    ss = block_sum(ss, red);
+    const double alpha = a[i0];
+    double beta, tj, scal;
+    if (ss == 0.0) {
+        beta = alpha;
+        tj = 0.0;
+        scal = 0.0;
+    } else {
+        // beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta, scal = 1 / (alpha - beta)
+        const double nrm2 = fma(alpha, alpha, ss);
+        const double rn = rsqrt(nrm2);
+        const double sg = (alpha >= 0.0) ? 1.0 : -1.0;
+        beta = -sg * nrm2 * rn;
+        tj = fma(sg * alpha, rn, 1.0);
+        scal = 1.0 / (alpha - beta);
+    }
+    for (int i = tid; i < n; i += bd) {
+        const double val = (i < i0) ? 0.0 : ((i == i0) ? 1.0 : a[i] * scal);
+        if (i >= i0) vpub[i] = val;
+        HV[(int64_t)j * n + i] = val;
+    }
+    if (tid == 0) {
+        vpub[n] = tj;
+        vpub[n + 1] = beta;
+        eoff[j] = beta;
+        tau[j] = tj;
+    }
+}
+
+// Householder tridiagonalisation on one thread-block cluster (C <= 16 CTAs). Column c of the
+// symmetric matrix is owned by CTA c % C and kept in its shared memory (or, for large n, in a
+// global slab of that CTA). Per column j: after a cluster barrier every CTA reads the reflector
+// that the owner of column j published, forms its partial p over the columns it owns; after a
+// second barrier every CTA sums the partials of all CTAs (distributed shared memory, fixed
+// pairwise order), forms w and updates its columns. The owner of column j + 1 updates that
+// column first and publishes reflector j + 1 while the other CTAs are still updating
+// (look-ahead), so the reflector's FP64 latency chain is off the critical path.
+template <int C>
+__global__ void __launch_bounds__(CT_THREADS) k_tridiag_cluster(int n, const double* __restrict__ Ain, int lda,
+                                                                double* Aglob, int in_smem, double* HV, double* dgl,
+                                                                double* eoff, double* tau) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    extern __shared__ double sm[];
+    __shared__ double red[32];
+    const int ncl = (n + C - 1) / C;
+    double* vbuf = sm;                 // n: reflector (local copy)
+    double* vpub = sm + n;             // n + 2: reflector published by the owner, then tau, beta
+    double* ppart = sm + 2 * n + 2;    // n: this CTA's partial p
+    double* pw = sm + 3 * n + 2;       // n: full p, then w
+    double* Aloc = in_smem ? (sm + 4 * n + 2) : (Aglob + (size_t)rank * ncl * n);
+    const int tid = threadIdx.x, bd = blockDim.x;
+
+    for (int q = 0; q < ncl; ++q) {
+        const int c = q * C + rank;
+        if (c >= n) break;
+        for (int i = tid; i < n; i += bd)
+            Aloc[(size_t)q * n + i] = 0.5 * (Ain[(int64_t)c * lda + i] + Ain[(int64_t)i * lda + c]);
+    }
+    __syncthreads();
+    if (n >= 3 && rank == 0) make_reflector(0, n, Aloc, vpub, HV, eoff, tau, red);
+
+    for (int j = 0; j + 2 < n; ++j) {
+        const int i0 = j + 1;
+        const int owner = j % C;
+        const int next = j + 1;
+        const bool own_next = (next + 2 < n) && (next % C == rank);
+        cluster.sync();                                   // reflector j published
+        const double* rv = cluster.map_shared_rank(vpub, owner);
+        const double tj = rv[n];
+        if (tj == 0.0) {                                  // same decision in every CTA
+            __syncthreads();
+            if (own_next) make_reflector(next, n, Aloc + (size_t)(next / C) * n, vpub, HV, eoff, tau, red);
+            continue;
+        }
+        for (int i = i0 + tid; i < n; i += bd) vbuf[i] = rv[i];
+        __syncthreads();
+        const int q0 = (i0 - rank + C - 1) / C;           // first owned column >= i0
+        for (int i = i0 + tid; i < n; i += bd) {
+            double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+            int q = q0;
+            for (; q + 3 < ncl; q += 4) {
+                const int c0 = q * C + rank;
+                if (c0 + 3 * C >= n) break;
+                const double* a = Aloc + (size_t)q * n + i;
+                acc0 = fma(a[0], vbuf[c0], acc0);
+                acc1 = fma(a[n], vbuf[c0 + C], acc1);
+                acc2 = fma(a[2 * n], vbuf[c0 + 2 * C], acc2);
+                acc3 = fma(a[3 * n], vbuf[c0 + 3 * C], acc3);
+            }
+            for (; q < ncl; ++q) {
+                const int c = q * C + rank;
+                if (c >= n) break;
+                acc0 = fma(Aloc[(size_t)q * n + i], vbuf[c], acc0);
+            }
+            ppart[i] = (acc0 + acc1) + (acc2 + acc3);
+        }
+        cluster.sync();                                   // partial products published
+        for (int i = i0 + tid; i < n; i += bd) {
+            double t[C];
+#pragma unroll
+            for (int r = 0; r < C; ++r) t[r] = cluster.map_shared_rank(ppart, r)[i];
+#pragma unroll
+            for (int wd = 1; wd < C; wd <<= 1)
+#pragma unroll
+                for (int r = 0; r + wd < C; r += 2 * wd) t[r] += t[r + wd];
+            pw[i] = tj * t[0];
+        }
+        __syncthreads();
+        double pv = 0.0;
+        for (int i = i0 + tid; i < n; i += bd) pv = fma(pw[i], vbuf[i], pv);
+        pv = block_sum(pv, red);
+        const double kk = 0.5 * tj * pv;
+        for (int i = i0 + tid; i < n; i += bd) pw[i] = fma(-kk, vbuf[i], pw[i]);
+        __syncthreads();
+        if (own_next) {
+            double* col = Aloc + (size_t)(next / C) * n;
+            const double vc = vbuf[next], wc = pw[next];
+            for (int i = i0 + tid; i < n; i += bd) col[i] -= fma(vbuf[i], wc, pw[i] * vc);
+            __syncthreads();
+            make_reflector(next, n, col, vpub, HV, eoff, tau, red);
+        }
+        {
+            const int qskip = own_next ? next / C : -1;
+            int qend = ncl;
+            while (qend > q0 && (qend - 1) * C + rank >= n) --qend;
+            for (int i = i0 + tid; i < n; i += bd) {
+                const double vi = vbuf[i], wi = pw[i];
+                int q = q0;
+                for (; q + 3 < qend; q += 4) {
+                    double* c0 = Aloc + (size_t)q * n + i;
+                    const int cc = q * C + rank;
+                    const double a0 = c0[0], a1 = c0[n], a2 = c0[2 * n], a3 = c0[3 * n];
+                    const double r0 = a0 - fma(vi, pw[cc], wi * vbuf[cc]);
+                    const double r1 = a1 - fma(vi, pw[cc + C], wi * vbuf[cc + C]);
+                    const double r2 = a2 - fma(vi, pw[cc + 2 * C], wi * vbuf[cc + 2 * C]);
+                    const double r3 = a3 - fma(vi, pw[cc + 3 * C], wi * vbuf[cc + 3 * C]);
+                    if (q != qskip) c0[0] = r0;
+                    if (q + 1 != qskip) c0[n] = r1;
+                    if (q + 2 != qskip) c0[2 * n] = r2;
+                    if (q + 3 != qskip) c0[3 * n] = r3;
+                }
+                for (; q < qend; ++q) {
+                    if (q == qskip) continue;
+                    const int cc = q * C + rank;
+                    double* c0 = Aloc + (size_t)q * n + i;
+                    c0[0] -= fma(vi, pw[cc], wi * vbuf[cc]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int q = 0; q < ncl; ++q) {
+        const int c = q * C + rank;
+        if (c >= n) break;
+        if (tid == 0) {
+            dgl[c] = Aloc[(size_t)q * n + c];
+            if (c == n - 2) eoff[c] = Aloc[(size_t)q * n + c + 1];
+        }
+    }
+    if (rank == 0) {
+        for (int jj = (n >= 2 ? n - 2 : 0); jj < n; ++jj) {
+            if (tid == 0) tau[jj] = 0.0;
+            for (int i = tid; i < n; i += bd) HV[(int64_t)jj * n + i] = 0.0;
+        }
+        if (tid == 0) eoff[n - 1] = 0.0;
+    }
+    cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// Number of eigenvalues below x of the tridiagonal with diagonal d and squared off-diagonal e2, in
+// single precision (ratio form q_i = (d_i - x) - e2_{i-1} / q_{i-1}, small pivots replaced).
+__device__ __forceinline__ int sturm_count_f32(int n, const float* d, const float* e2, float x, float pivmin) {
     int cnt = 0;
-    double q = dgl[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0);
+    float q = d[0] - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.f);
     for (int i = 1; i < n; ++i) {
-        q = (dgl[i] - x) - e2[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += (q < 0.0);
+        q = (d[i] - x) - __fdividef(e2[i - 1], q);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += (q < 0.f);
     }
     return cnt;
 }
 
-// One warp per wanted eigenvalue (ascending index il + warp id): 33-way multisection.
-__global__ void k_bisect(int n, const double* dgl, const double* eoff, double* e2, int il, int nw, double* w) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// The same count in double precision without divisions, for two shifts at once (independent
+// chains hide the FP64 latency): the leading principal minors p_i = det(T_i - x I) obey
+// p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}, and the number of sign changes along
+// p_0 = 1, p_1, ..., p_n is the number of eigenvalues below x (Sturm). Sign tests use the sign
+// bit (integer pipe); an exact zero takes the sign opposite to its predecessor (a sign change,
+// as a zero pivot does in the ratio form); every fourth step the pair (p_{i-1}, p_i) is rescaled
+// by a power of two when its exponent drifts, which keeps every sign and ratio exact.
+__device__ __forceinline__ double fix_zero(double p, double prev) {
+    const int hi = __double2hiint(p), lo = __double2loint(p);
+    if (((hi & 0x7fffffff) | lo) != 0) return p;
+    return __hiloint2double((~__double2hiint(prev) & 0x80000000) | 0x00100000, 0);   // -sign(prev) * DBL_MIN
+}
+
+__device__ __forceinline__ void rescale_pair(double& pc, double& pm) {
+    const int ex = (__double2hiint(pc) >> 20) & 0x7ff;
+    if (ex > 1023 + 480 || ex < 1023 - 480) {
+        const double sc = __hiloint2double((2046 - ex) << 20, 0);   // 2^(1023 - ex)
+        pc *= sc;
+        pm *= sc;
+    }
+}
+
+__device__ __forceinline__ void sturm_count2_f64(int n, const double* d, const double* e2, double x0, double x1,
+                                                 int& c0, int& c1) {
+    double pm0 = 1.0, pm1 = 1.0;
+    double pc0 = fix_zero(d[0] - x0, 1.0), pc1 = fix_zero(d[0] - x1, 1.0);
+    c0 = (int)((unsigned)__double2hiint(pc0) >> 31);
+    c1 = (int)((unsigned)__double2hiint(pc1) >> 31);
+    for (int i = 1; i < n; ++i) {
+        const double di = d[i], ei = e2[i - 1];
+        const double pn0 = fix_zero(fma(di - x0, pc0, -ei * pm0), pc0);
+        const double pn1 = fix_zero(fma(di - x1, pc1, -ei * pm1), pc1);
+        c0 += (int)(((unsigned)__double2hiint(pn0) ^ (unsigned)__double2hiint(pc0)) >> 31);
+        c1 += (int)(((unsigned)__double2hiint(pn1) ^ (unsigned)__double2hiint(pc1)) >> 31);
+        pm0 = pc0;
+        pc0 = pn0;
+        pm1 = pc1;
+        pc1 = pn1;
+        if ((i & 3) == 0) {
+            rescale_pair(pc0, pm0);
+            rescale_pair(pc1, pm1);
+        }
+    }
+}
+
+// One warp per wanted eigenvalue (ascending index il + warp id). The tridiagonal is scaled by
+// 1 / ||T||; 33-way multisection first on single-precision counts (fast) until the interval is
+// 1e-5 wide, then, after widening it by that margin (far above the single-precision backward
+// error of the count, about 1e-6), on double-precision counts down to ~eps.
+__global__ void __launch_bounds__(32) k_bisect(int n, const double* __restrict__ dgl, const double* __restrict__ eoff,
+                                                int il, int nw, double* w) {
+    extern __shared__ double smb[];
+    double* d64 = smb;                                     // n
+    double* e264 = smb + n;                                // n
+    float* d32 = reinterpret_cast<float*>(smb + 2 * n);    // n
+    float* e232 = d32 + n;                                 // n
+    __shared__ double s_tnorm;
     const int lane = threadIdx.x & 31;
+    // ||T||_inf by the CTA
+    if (threadIdx.x < 32) {
+        double m = 0.0;
+        for (int i = lane; i < n; i += 32) {
+            const double r = fabs(dgl[i]) + ((i > 0) ? fabs(eoff[i - 1]) : 0.0) + ((i + 1 < n) ? fabs(eoff[i]) : 0.0);
+            m = fmax(m, r);
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_tnorm = (m > 0.0) ? m : 1.0;
+    }
+    __syncthreads();
+    const double tn = s_tnorm, itn = 1.0 / tn;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double di = dgl[i] * itn;
+        const double ei = (i + 1 < n) ? eoff[i] * itn : 0.0;
+        d64[i] = di;
+        e264[i] = ei * ei;
+        d32[i] = (float)di;
+        e232[i] = (float)(ei * ei);
+    }
+    __syncthreads();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= nw) return;
     const int idx = il + gw;
-    // Gershgorin interval and pivmin, computed by the warp
-    double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
-    for (int i = lane; i < n; i += 32) {
-        const double el = (i > 0) ? fabs(eoff[i - 1]) : 0.0;
-        const double er = (i + 1 < n) ? fabs(eoff[i]) : 0.0;
-        lo = fmin(lo, dgl[i] - el - er);
-        hi = fmax(hi, dgl[i] + el + er);
-        if (i + 1 < n) emax = fmax(emax, er * er);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    }
-    const double tnorm = fmax(fabs(lo), fabs(hi));
-    const double pivmin = DBL_MIN * fmax(1.0, emax);
-    lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
-    hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
-    for (int round = 0; round < 24; ++round) {
-        const double width = hi - lo;
-        if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) || width <= 0.05 * DBL_EPSILON * tnorm) break;
-        const double x = lo + (lane + 1) * (width / 33.0);
-        const int cnt = sturm_count(n, dgl, e2, x, pivmin);
+    // scaled Gershgorin interval is inside [-1, 1]
+    float lo = -1.0f - 1e-6f, hi = 1.0f + 1e-6f;
+    const float piv32 = 1e-30f;
+    for (int round = 0; round < 8 && hi - lo > 1e-5f; ++round) {
+        const float step = (hi - lo) / 33.f;
+        const float x = lo + (lane + 1) * step;
+        const int cnt = sturm_count_f32(n, d32, e232, x, piv32);
         const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
         if (above == 0u) {
             lo = __shfl_sync(0xffffffffu, x, 31);
         } else {
             const int l = __ffs(above) - 1;
-            const double xl = __shfl_sync(0xffffffffu, x, l);
-            const double xp = __shfl_sync(0xffffffffu, x, l > 0 ? l - 1 : 0);
+            const float xl = __shfl_sync(0xffffffffu, x, l);
+            const float xp = __shfl_sync(0xffffffffu, x, l > 0 ? l - 1 : 0);
             if (l > 0) lo = xp;
             hi = xl;
         }
     }
-    if (lane == 0) w[gw] = 0.5 * (lo + hi);
+    double dlo = (double)lo - 1e-5, dhi = (double)hi + 1e-5;
+    // confirm the bracket in double precision; fall back to the full interval if it fails
+    {
+        int clo = 0, chi = 0;
+        if (lane == 0) sturm_count2_f64(n, d64, e264, dlo, dhi, clo, chi);
+        clo = __shfl_sync(0xffffffffu, clo, 0);
+        chi = __shfl_sync(0xffffffffu, chi, 0);
+        if (!(clo <= idx && chi > idx)) {
+            dlo = -1.0 - 1e-12;
+            dhi = 1.0 + 1e-12;
+        }
+    }
+    for (int round = 0; round < 24; ++round) {
+        const double width = dhi - dlo;
+        if (width <= 2.0 * DBL_EPSILON * fmax(fabs(dlo), fabs(dhi)) || width <= 0.5 * DBL_EPSILON) break;
+        const double step = width / 65.0;
+        const double x0 = dlo + (2 * lane + 1) * step, x1 = dlo + (2 * lane + 2) * step;
+        int c0, c1;
+        sturm_count2_f64(n, d64, e264, x0, x1, c0, c1);
+        const unsigned above = __ballot_sync(0xffffffffu, c0 > idx || c1 > idx);
+        if (above == 0u) {
+            dlo = __shfl_sync(0xffffffffu, x1, 31);
+        } else {
+            const int l = __ffs(above) - 1;
+            const bool first = __shfl_sync(0xffffffffu, c0 > idx, l);
+            const double a0 = __shfl_sync(0xffffffffu, x0, l);
+            const double a1 = __shfl_sync(0xffffffffu, x1, l);
+            const double pl = __shfl_sync(0xffffffffu, x1, l > 0 ? l - 1 : 0);
+            if (first) {
+                if (l > 0) dlo = pl;
+                dhi = a0;
+            } else {
+                dlo = a0;
+                dhi = a1;
+            }
+        }
+    }
+    if (lane == 0) w[gw] = 0.5 * (dlo + dhi) * tn;
 }
 
 __global__ void k_square_off(int n, const double* eoff, double* e2) {
@@ -227,82 +511,77 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // Inverse iteration, one thread per eigenvector; factor arrays laid out [array][i][q] so that
-// the threads of a warp touch consecutive addresses. Output: Zt[i][q] (n x nv, row stride nv).
-__global__ void k_invit(int n, int nv, const double* dgl, const double* eoff, const double* lam, double* lu,
-                        double* Zt, uint64_t seed) {
+// the threads of a warp touch consecutive addresses. Gaussian elimination with partial pivoting
+// of T - lambda I takes one reciprocal per row (of the pivot); the two triangular solves carry
+// the running entries in registers, so the sequential chains never wait on memory.
+// Output: Zt[i][q] (n x nv, row stride nv).
+__global__ void k_invit(int n, int nv, const double* __restrict__ dgl, const double* __restrict__ eoff,
+                        const double* __restrict__ lam, double* lu, double* Zt, uint64_t seed) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nv) return;
     const int64_t S = nv;
-    double* DL = lu;
-    double* D = lu + (int64_t)n * S;
-    double* DU = lu + 2 * (int64_t)n * S;
-    double* DU2 = lu + 3 * (int64_t)n * S;
-    double* PIV = lu + 4 * (int64_t)n * S;     // 0 / 1 flags stored as doubles
+    double* DL = lu;                           // multipliers
+    double* RD = lu + (int64_t)n * S;          // reciprocal pivots
+    double* DU = lu + 2 * (int64_t)n * S;      // first superdiagonal of U
+    double* DU2 = lu + 3 * (int64_t)n * S;     // second superdiagonal of U
+    double* PIV = lu + 4 * (int64_t)n * S;     // 1.0 where rows i and i+1 were interchanged
     double* x = Zt;
     const double l = lam[q];
     double tnorm = 0.0;
     for (int i = 0; i < n; ++i)
         tnorm = fmax(tnorm, fabs(dgl[i]) + ((i > 0) ? fabs(eoff[i - 1]) : 0.0) + ((i + 1 < n) ? fabs(eoff[i]) : 0.0));
     const double tiny = fmax(DBL_EPSILON * tnorm, DBL_MIN);
-    for (int i = 0; i < n; ++i) {
-        D[i * S + q] = dgl[i] - l;
-        if (i + 1 < n) {
-            DL[i * S + q] = eoff[i];
-            DU[i * S + q] = eoff[i];
-        }
-        DU2[i * S + q] = 0.0;
-        PIV[i * S + q] = 0.0;
-    }
-    // Gaussian elimination with partial pivoting on T - lambda I
+    double dcur = dgl[0] - l;
+    double ucur = (n > 1) ? eoff[0] : 0.0;
     for (int i = 0; i + 1 < n; ++i) {
-        const double di = D[i * S + q], dli = DL[i * S + q];
-        if (fabs(di) >= fabs(dli)) {
-            const double dd = (di == 0.0) ? tiny : di;
-            D[i * S + q] = dd;
-            const double f = dli / dd;
-            DL[i * S + q] = f;
-            D[(i + 1) * S + q] -= f * DU[i * S + q];
-        } else {
-            const double f = di / dli;
-            D[i * S + q] = dli;
-            DL[i * S + q] = f;
-            const double tmp = DU[i * S + q];
-            DU[i * S + q] = D[(i + 1) * S + q];
-            D[(i + 1) * S + q] = tmp - f * D[(i + 1) * S + q];
-            if (i + 2 < n) {
-                DU2[i * S + q] = DU[(i + 1) * S + q];
-                DU[(i + 1) * S + q] = -f * DU[(i + 1) * S + q];
-            }
-            PIV[i * S + q] = 1.0;
-        }
+        const double sub = eoff[i];                    // T[i+1, i]
+        const double dnext = dgl[i + 1] - l;
+        const double unext = (i + 2 < n) ? eoff[i + 1] : 0.0;
+        const bool swap = fabs(dcur) < fabs(sub);
+        const double piv = swap ? sub : ((dcur == 0.0) ? tiny : dcur);
+        const double r = 1.0 / piv;
+        const double f = (swap ? dcur : sub) * r;
+        RD[i * S + q] = r;
+        DL[i * S + q] = f;
+        DU[i * S + q] = swap ? dnext : ucur;
+        DU2[i * S + q] = swap ? unext : 0.0;
+        PIV[i * S + q] = swap ? 1.0 : 0.0;
+        const double nd = swap ? (ucur - f * dnext) : (dnext - f * ucur);
+        ucur = swap ? -f * unext : unext;
+        dcur = nd;
     }
-    if (D[(int64_t)(n - 1) * S + q] == 0.0) D[(int64_t)(n - 1) * S + q] = tiny;
+    RD[(int64_t)(n - 1) * S + q] = 1.0 / ((dcur == 0.0) ? tiny : dcur);
     // random start in [-1, 1]
     for (int i = 0; i < n; ++i) {
         const uint64_t h = mix64(seed ^ mix64(((uint64_t)q << 32) + (uint64_t)i + 0x5851F42D4C957F2Dull));
         x[i * S + q] = 2.0 * ((h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
     }
-    for (int it = 0; it < 3; ++it) {
-        // forward: L^{-1} P b
+    for (int it = 0; it < 2; ++it) {
+        // forward: L^{-1} P b, the running entry carried in a register
+        double carry = x[q];
         for (int i = 0; i + 1 < n; ++i) {
             const double f = DL[i * S + q];
-            if (PIV[i * S + q] == 0.0) {
-                x[(i + 1) * S + q] -= f * x[i * S + q];
+            const double nxt = x[(i + 1) * S + q];
+            if (PIV[i * S + q] != 0.0) {
+                x[i * S + q] = nxt;
+                carry = carry - f * nxt;
             } else {
-                const double t0 = x[i * S + q];
-                x[i * S + q] = x[(i + 1) * S + q];
-                x[(i + 1) * S + q] = t0 - f * x[i * S + q];
+                x[i * S + q] = carry;
+                carry = nxt - f * carry;
             }
         }
-        // back: U^{-1}
-        double mx = 0.0;
+        x[(int64_t)(n - 1) * S + q] = carry;
+        // back: U^{-1}, carrying the two previous solution entries
+        double v1 = 0.0, v2 = 0.0, mx = 0.0;
         for (int i = n - 1; i >= 0; --i) {
             double v = x[i * S + q];
-            if (i + 1 < n) v -= DU[i * S + q] * x[(i + 1) * S + q];
-            if (i + 2 < n) v -= DU2[i * S + q] * x[(i + 2) * S + q];
-            v /= D[i * S + q];
+            if (i + 1 < n) v -= DU[i * S + q] * v1;
+            if (i + 2 < n) v -= DU2[i * S + q] * v2;
+            v *= RD[i * S + q];
             x[i * S + q] = v;
             mx = fmax(mx, fabs(v));
+            v2 = v1;
+            v1 = v;
         }
         const double sc = (mx > 0.0 && isfinite(mx)) ? 1.0 / mx : 0.0;
         for (int i = 0; i < n; ++i) x[i * S + q] *= sc;
@@ -321,23 +600,64 @@ __global__ void k_transpose_out(int n, int nv, const double* Zt, double* Z, int 
     Z[(int64_t)q * ldz + i] = Zt[(int64_t)i * nv + q];
 }
 
-// Z <- H_0 H_1 ... H_{n-3} Z; each CTA owns 8 columns, the reflector is staged in shared memory.
-__global__ void k_backtransform(int n, int nv, const double* HV, const double* tau, double* Z, int ldz) {
-    extern __shared__ double u[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int col = blockIdx.x * (blockDim.x >> 5) + warp;
+// Z <- H_0 H_1 ... H_{n-3} Z, one warp per column of Z; reflector j is read from HV (row j,
+// contiguous, zero above j + 1) through the read-only cache.
+__global__ void k_backtransform(int n, int nv, const double* __restrict__ HV, const double* __restrict__ tau,
+                                double* Z, int ldz) {
+    const int lane = threadIdx.x & 31;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (col >= nv) return;
+    double* z = Z + (int64_t)col * ldz;
     for (int j = n - 3; j >= 0; --j) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = HV[(int64_t)j * n + i];
-        __syncthreads();
-        const double tj = tau[j];
-        if (col >= nv || tj == 0.0) continue;
-        double* z = Z + (int64_t)col * ldz;
+        const double tj = __ldg(tau + j);
+        if (tj == 0.0) continue;
+        const double* u = HV + (int64_t)j * n;
         double dot = 0.0;
-        for (int i = j + 1 + lane; i < n; i += 32) dot = fma(u[i], z[i], dot);
+        for (int i = j + 1 + lane; i < n; i += 32) dot = fma(__ldg(u + i), z[i], dot);
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
         const double f = tj * dot;
-        for (int i = j + 1 + lane; i < n; i += 32) z[i] = fma(-f, u[i], z[i]);
+        for (int i = j + 1 + lane; i < n; i += 32) z[i] = fma(-f, __ldg(u + i), z[i]);
+    }
+}
+
+// The same with the column held in registers (NPL entries per lane, n <= 32 * NPL), so that the
+// chain of reflectors never waits on memory.
+template <int NPL>
+__global__ void __launch_bounds__(32) k_backtransform_reg(int n, int nv, const double* __restrict__ HV,
+                                                          const double* __restrict__ tau, double* Z, int ldz) {
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.x;
+    if (col >= nv) return;
+    double* zc = Z + (int64_t)col * ldz;
+    double z[NPL];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+        const int i = lane + 32 * k;
+        z[k] = (i < n) ? zc[i] : 0.0;
+    }
+    for (int j = n - 3; j >= 0; --j) {
+        const double tj = __ldg(tau + j);
+        if (tj == 0.0) continue;
+        const double* u = HV + (int64_t)j * n;     // zero for i <= j
+        double uu[NPL];
+        double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            const int i = lane + 32 * k;
+            uu[k] = (i < n) ? __ldg(u + i) : 0.0;
+            if (k & 1) d1 = fma(uu[k], z[k], d1);
+            else d0 = fma(uu[k], z[k], d0);
+        }
+        double dot = d0 + d1;
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        const double f = tj * dot;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) z[k] = fma(-f, uu[k], z[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+        const int i = lane + 32 * k;
+        if (i < n) zc[i] = z[k];
     }
 }
 
@@ -358,7 +678,7 @@ size_t symeig_work_bytes(int n, int nv) {
     const size_t nn = (size_t)n * n;
     size_t b = 0;
     auto add = [&](size_t cnt) { b += ((cnt * sizeof(double) + 255) / 256) * 256; };
-    add(nn);            // A
+    add(nn + 16 * (size_t)n);   // A (the cluster path keeps up to n + 16 columns of n)
     add(nn);            // HV
     add(n);             // d
     add(n);             // e
@@ -370,7 +690,7 @@ size_t symeig_work_bytes(int n, int nv) {
 
 int symeig_work_carve(Arena& a, int n, int nv, GridBarrier bar, SymEigWork* w) {
     const size_t nn = (size_t)n * n;
-    w->A = a.take<double>(nn);
+    w->A = a.take<double>(nn + 16 * (size_t)n);
     w->partial = a.take<double>(nn);      // HV
     w->dgl = a.take<double>(n);
     w->eoff = a.take<double>(n);
@@ -383,14 +703,91 @@ int symeig_work_carve(Arena& a, int n, int nv, GridBarrier bar, SymEigWork* w) {
     return EDA_OK;
 }
 
+constexpr int kClusterMaxN = 512;
+
+// Launch k_tridiag_cluster<C> on one cluster of C CTAs (a power of two, 16 only when the device
+// accepts that non-portable cluster size with the needed shared memory).
+template <int C>
+int launch_tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_t s, bool probe_only,
+                           bool* fits) {
+    auto kern = k_tridiag_cluster<C>;
+    static size_t smem_set = 0;
+    static bool attrs = false;
+    if (!attrs) {
+        attrs = true;
+        if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaGetLastError();
+    }
+    const int ncl = (n + C - 1) / C;
+    const size_t vec_bytes = (4 * (size_t)n + 2) * sizeof(double);
+    const size_t a_bytes = (size_t)ncl * n * sizeof(double);
+    const int in_smem = (vec_bytes + a_bytes <= 200 * 1024) ? 1 : 0;
+    const size_t smem = vec_bytes + (in_smem ? a_bytes : 0);
+    if (smem > smem_set) {
+        EDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)std::max<size_t>(smem, 48 * 1024)));
+        smem_set = std::max<size_t>(smem, 48 * 1024);
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(CT_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (probe_only) {
+        int nclusters = 0;
+        *fits = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1;
+        cudaGetLastError();
+        return EDA_OK;
+    }
+    ProfScope prof("tridiag", s);
+    EDA_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, n, A, lda, ws->A, in_smem, ws->partial, ws->dgl, ws->eoff, ws->tau));
+    launch_counter()++;
+    return EDA_OK;
+}
+
+int launch_tridiag_c(int C, int n, const double* A, int lda, SymEigWork* ws, cudaStream_t s, bool probe_only,
+                     bool* fits) {
+    switch (C) {
+        case 16: return launch_tridiag_cluster<16>(n, A, lda, ws, s, probe_only, fits);
+        case 8: return launch_tridiag_cluster<8>(n, A, lda, ws, s, probe_only, fits);
+        case 4: return launch_tridiag_cluster<4>(n, A, lda, ws, s, probe_only, fits);
+        case 2: return launch_tridiag_cluster<2>(n, A, lda, ws, s, probe_only, fits);
+        default: return launch_tridiag_cluster<1>(n, A, lda, ws, s, probe_only, fits);
+    }
+}
+
+int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_t s) {
+    static int chosen_C[kClusterMaxN + 1] = {};   // cluster size that passed the occupancy check, per n
+    if (!chosen_C[n]) {
+        int want = 2;
+        if (n > 64) {
+            want = 1;
+            while (want < 16 && want * 2 * 12 <= n) want *= 2;
+        }
+        int C = want;
+        for (; C > 1; C /= 2) {
+            bool fits = false;
+            EDA_TRY(launch_tridiag_c(C, n, A, lda, ws, s, true, &fits));
+            if (fits) break;
+        }
+        chosen_C[n] = C;
+    }
+    return launch_tridiag_c(chosen_C[n], n, A, lda, ws, s, false, nullptr);
+}
+
 int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, SymEigWork* ws, int* status,
                   cudaStream_t s) {
     if (n <= 0 || il < 0 || iu >= n || il > iu) return EDA_ERR_INVALID_ARG;
     const int nv = iu - il + 1;
     double* HV = ws->partial;
-    k_copy_sq<<<ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, A, lda, ws->A);
-    EDA_LAUNCHED();
-    // ---- tridiagonal reduction: cooperative launch ----
+    // ---- tridiagonal reduction: one cluster for small n, a cooperative grid otherwise ----
     int dev = 0;
     EDA_CUDA_TRY(cudaGetDevice(&dev));
     int sms = 0;
@@ -399,12 +796,17 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     if (smem > 48 * 1024) {
         EDA_CUDA_TRY(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
+    if (n <= kClusterMaxN) {
+        EDA_TRY(tridiag_cluster(n, A, lda, ws, s));
+    } else {
     int per_sm = 0;
     EDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, TRI_THREADS, smem));
     int ctas = std::max(1, std::min(n / 16, sms));
     ctas = std::min(ctas, std::max(1, per_sm * sms));
     double* pglob = ws->vbuf;
     EDA_CUDA_TRY(cudaMemsetAsync(ws->bar.count, 0, sizeof(unsigned), s));
+    k_copy_sq<<<ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, A, lda, ws->A);
+    EDA_LAUNCHED();
     {
         ProfScope prof("tridiag", s);
         int nn = n;
@@ -420,12 +822,18 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
         EDA_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(ctas), dim3(TRI_THREADS), args, smem, s));
         launch_counter()++;
     }
+    }
     // ---- eigenvalues ----
-    double* e2 = ws->vbuf + n;
-    k_square_off<<<ceil_div(n, 256), 256, 0, s>>>(n, ws->eoff, e2);
-    EDA_LAUNCHED();
-    k_bisect<<<ceil_div((int64_t)nv * 32, 256), 256, 0, s>>>(n, ws->dgl, ws->eoff, e2, il, nv, w);
-    EDA_LAUNCHED();
+    const size_t bsm = 3 * (size_t)n * sizeof(double);
+    if (bsm > 48 * 1024) {
+        EDA_CUDA_TRY(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+    }
+    {
+        ProfScope prof("bisect", s);
+        // one warp per CTA: the FP64 pipe of one SM is narrow, so the warps are spread over SMs
+        k_bisect<<<nv, 32, bsm, s>>>(n, ws->dgl, ws->eoff, il, nv, w);
+        EDA_LAUNCHED();
+    }
     return EDA_OK;
 }
 
@@ -434,8 +842,11 @@ int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWor
     if (nv <= 0) return EDA_OK;
     double* lu = ws->lu;
     double* Zt = ws->lu + 5 * (size_t)n * nv;
-    k_invit<<<ceil_div(nv, 64), 64, 0, s>>>(n, nv, ws->dgl, ws->eoff, w, lu, Zt, seed);
-    EDA_LAUNCHED();
+    {
+        ProfScope prof("invit", s);
+        k_invit<<<ceil_div(nv, 32), 32, 0, s>>>(n, nv, ws->dgl, ws->eoff, w, lu, Zt, seed);
+        EDA_LAUNCHED();
+    }
     k_transpose_out<<<ceil_div((int64_t)n * nv, 256), 256, 0, s>>>(n, nv, Zt, Z, ldz);
     EDA_LAUNCHED();
     return symeig_finish_vectors(n, nv, w, Z, ldz, ws, cluster_rel, s);
@@ -497,11 +908,12 @@ int symeig_finish_vectors(int n, int nv, const double* w, double* Z, int ldz, Sy
     k_cluster_mgs_dev<<<ceil_div((int64_t)nv * 32, 256), 256, 0, s>>>(n, nv, w, ctol, Z, ldz);
     EDA_LAUNCHED();
     if (n >= 3) {
-        const size_t smem = (size_t)n * sizeof(double);
-        if (smem > 48 * 1024) {
-            EDA_CUDA_TRY(cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        }
-        k_backtransform<<<ceil_div(nv, 8), 256, smem, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
+
+        ProfScope prof("backtransform", s);
+        if (n <= 256) k_backtransform_reg<8><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
+        else if (n <= 512) k_backtransform_reg<16><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
+        else if (n <= 1024) k_backtransform_reg<32><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
+        else k_backtransform<<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
         EDA_LAUNCHED();
     }
     return EDA_OK;

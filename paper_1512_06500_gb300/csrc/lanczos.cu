@@ -223,6 +223,12 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
     std::vector<double> relres_h(t), theta_h(t);
     double max_rel = INFINITY;
     int conv_count = 0;
+    // Rayleigh-Ritz schedule: the first check once the basis has t + b columns; later checks at
+    // the basis width where the geometric rate seen between the last two checks predicts
+    // convergence (never sooner than check_every blocks, always at the last block).
+    int next_check = t + b;
+    int prev_check_cols = 0;
+    double prev_check_rel = 0.0;
     int rr_cols = 0;         // size of T used by the last Rayleigh-Ritz
 
     while (true) {
@@ -270,7 +276,7 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
         }
         // Rayleigh-Ritz on the leading cols x cols block when due
         const bool last = exhausted || !room;
-        if ((cols >= t + 1 && iters % h->cfg.check_every == 0) || (last && cols >= t)) {
+        if ((cols >= next_check && cols >= t + 1) || (last && cols >= t)) {
             ++checks;
             rr_cols = cols;
             ProfScope prof("rr", s);
@@ -292,6 +298,18 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
                 max_rel = std::max(max_rel, relres_h[i]);
             }
             if (conv_count == t) converged = true;
+            // schedule the next check
+            int gap = b * h->cfg.check_every;
+            if (prev_check_cols > 0 && max_rel > 0.0 && prev_check_rel > 0.0 && max_rel < prev_check_rel &&
+                std::isfinite(max_rel)) {
+                const double blocks = (double)(cols - prev_check_cols) / b;
+                const double rate = std::pow(max_rel / prev_check_rel, 1.0 / blocks);   // per block
+                const double need = std::log(tol / max_rel) / std::log(rate);           // blocks to go
+                if (std::isfinite(need) && need > 1.0) gap = std::max(gap, b * (int)std::floor(0.8 * need));
+            }
+            prev_check_cols = cols;
+            prev_check_rel = max_rel;
+            next_check = cols + gap;
         }
         if (converged || last) break;
         // T gets the off-diagonal block B_{j+1} (rows cols.., columns j0..)
