@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m
         }
 }
 
-// C[i, j] = alpha * sum_s partial[s][j][i] + beta * C[i, j], splits summed in order.
+// C[i, j] = alpha * sum_s partial[s][j][i] + beta * C[i, j]. Small split counts: one thread per
+// output, splits summed in order. Large split counts: one warp per output, lane l sums splits
+// l, l + 32, ... in order, then a fixed butterfly across lanes (deterministic either way).
 __global__ void k_gemm_tn_reduce(int m, int p, int splits, const double* __restrict__ partial, double alpha,
                                  double beta, double* __restrict__ C, int ldc) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,29 +91,124 @@ __global__ void k_gemm_tn_reduce(int m, int p, int splits, const double* __restr
     C[(int64_t)j * ldc + i] = v;
 }
 
-// C[r, c] = beta * C0[r, c] + alpha * sum_l A[r, l] B[l, c]; thread per (row, PC columns).
-template <int PC>
+__global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const double* __restrict__ partial, double alpha,
+                                      double beta, double* __restrict__ C, int ldc) {
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= (int64_t)m * p) return;
+    const int i = (int)(e % m), j = (int)(e / m);
+    const int64_t mp = (int64_t)m * p;
+    double a0 = 0.0, a1 = 0.0;
+    int s = lane;
+    for (; s + 32 < splits; s += 64) {
+        a0 += partial[(int64_t)s * mp + e];
+        a1 += partial[(int64_t)(s + 32) * mp + e];
+    }
+    if (s < splits) a0 += partial[(int64_t)s * mp + e];
+    double acc = a0 + a1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        double v = alpha * acc;
+        if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
+        C[(int64_t)j * ldc + i] = v;
+    }
+}
+
+// C[r, c] = beta * C0[r, c] + alpha * sum_l A[r, l] B[l, c] for tall A (d x m) and small B
+// (m x p). A CTA owns 32 rows and NC columns; its four warps (one per SM sub-partition, each of
+// which has its own narrow FP64 unit) split the inner dimension into quarters, each thread
+// keeps NC independent accumulators, the slice of B sits in shared memory, and the partial sums
+// of the quarters are added in a fixed order at the end.
+template <int NC>
 __global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double alpha, const double* __restrict__ A,
                                                  int64_t lda, const double* __restrict__ B, int ldb, double beta,
                                                  const double* C0, int64_t ldc0, double* C, int64_t ldc) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c0 = blockIdx.y * PC;
-    if (r >= d) return;
-    double acc[PC];
+    constexpr int LCH = 256;                 // rows of B staged per pass
+    __shared__ double Bs[LCH][NC];
+    __shared__ double red[3][32][NC];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+    const int c0 = blockIdx.y * NC;
+    const int nc = min(NC, p - c0);
+    double acc[NC];
 #pragma unroll
-    for (int c = 0; c < PC; ++c) acc[c] = 0.0;
-    for (int l = 0; l < m; ++l) {
-        const double a = A[(int64_t)l * lda + r];
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    const bool live = r < d;
+    const double* Ar = A + (live ? r : 0);
+    for (int l0 = 0; l0 < m; l0 += LCH) {
+        const int lc = min(LCH, m - l0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < lc * NC; e += blockDim.x) {
+            const int l = e / NC, c = e % NC;
+            Bs[l][c] = (c < nc) ? B[(int64_t)(c0 + c) * ldb + l0 + l] : 0.0;
+        }
+        __syncthreads();
+        const int q = (lc + 3) / 4;
+        const int lb = w * q, le = min(lc, lb + q);
+        int l = lb;
+        for (; l + 3 < le; l += 4) {
+            double a[4];
 #pragma unroll
-        for (int c = 0; c < PC; ++c)
-            if (c0 + c < p) acc[c] = fma(a, __ldg(B + (int64_t)(c0 + c) * ldb + l), acc[c]);
+            for (int u = 0; u < 4; ++u) a[u] = live ? Ar[(int64_t)(l0 + l + u) * lda] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[c] = fma(a[u], Bs[l + u][c], acc[c]);
+        }
+        for (; l < le; ++l) {
+            const double a0 = live ? Ar[(int64_t)(l0 + l) * lda] : 0.0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = fma(a0, Bs[l][c], acc[c]);
+        }
     }
+    if (w > 0) {
 #pragma unroll
-    for (int c = 0; c < PC; ++c) {
-        if (c0 + c >= p) break;
-        double v = alpha * acc[c];
+        for (int c = 0; c < NC; ++c) red[w - 1][lane][c] = acc[c];
+    }
+    __syncthreads();
+    if (w > 0 || !live) return;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if (c >= nc) break;
+        const double sum = (acc[c] + red[0][lane][c]) + (red[1][lane][c] + red[2][lane][c]);
+        double v = alpha * sum;
         if (beta != 0.0) v = fma(beta, C0[(int64_t)(c0 + c) * ldc0 + r], v);
         C[(int64_t)(c0 + c) * ldc + r] = v;
+    }
+}
+
+// Small C (m x p) = alpha A B + beta C (both operands untransposed) with a long inner dimension:
+// CTA = 4 warps for one (32-row block, column); warp w sums its quarter of the inner dimension
+// with four independent chains, the quarters are added in a fixed order through shared memory.
+__global__ void __launch_bounds__(128) k_gemm_small_nn_splitk(int m, int p, int kk, double alpha,
+                                                              const double* __restrict__ A, int lda,
+                                                              const double* __restrict__ B, int ldb, double beta,
+                                                              double* __restrict__ C, int ldc) {
+    __shared__ double part[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const int j = blockIdx.y;
+    const int q = (kk + 3) / 4;
+    const int lb = w * q, le = min(kk, lb + q);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (i < m) {
+        const double* Bj = B + (int64_t)j * ldb;
+        int l = lb;
+        for (; l + 3 < le; l += 4) {
+            a0 = fma(A[(int64_t)l * lda + i], Bj[l], a0);
+            a1 = fma(A[(int64_t)(l + 1) * lda + i], Bj[l + 1], a1);
+            a2 = fma(A[(int64_t)(l + 2) * lda + i], Bj[l + 2], a2);
+            a3 = fma(A[(int64_t)(l + 3) * lda + i], Bj[l + 3], a3);
+        }
+        for (; l < le; ++l) a0 = fma(A[(int64_t)l * lda + i], Bj[l], a0);
+    }
+    part[w][lane] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (w == 0 && i < m) {
+        const double acc = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
+        double v = alpha * acc;
+        if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
+        C[(int64_t)j * ldc + i] = v;
     }
 }
 
@@ -121,13 +218,27 @@ __global__ void k_gemm_small(bool ta, bool tb, int m, int p, int kk, double alph
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= m || j >= p) return;
-    double acc = 0.0;
-    for (int l = 0; l < kk; ++l) {
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    int l = 0;
+    for (; l + 3 < kk; l += 4) {
+        if (ta) {
+            acc0 = fma(A[(int64_t)i * lda + l], tb ? B[(int64_t)l * ldb + j] : B[(int64_t)j * ldb + l], acc0);
+            acc1 = fma(A[(int64_t)i * lda + l + 1], tb ? B[(int64_t)(l + 1) * ldb + j] : B[(int64_t)j * ldb + l + 1], acc1);
+            acc2 = fma(A[(int64_t)i * lda + l + 2], tb ? B[(int64_t)(l + 2) * ldb + j] : B[(int64_t)j * ldb + l + 2], acc2);
+            acc3 = fma(A[(int64_t)i * lda + l + 3], tb ? B[(int64_t)(l + 3) * ldb + j] : B[(int64_t)j * ldb + l + 3], acc3);
+        } else {
+            acc0 = fma(A[(int64_t)l * lda + i], tb ? B[(int64_t)l * ldb + j] : B[(int64_t)j * ldb + l], acc0);
+            acc1 = fma(A[(int64_t)(l + 1) * lda + i], tb ? B[(int64_t)(l + 1) * ldb + j] : B[(int64_t)j * ldb + l + 1], acc1);
+            acc2 = fma(A[(int64_t)(l + 2) * lda + i], tb ? B[(int64_t)(l + 2) * ldb + j] : B[(int64_t)j * ldb + l + 2], acc2);
+            acc3 = fma(A[(int64_t)(l + 3) * lda + i], tb ? B[(int64_t)(l + 3) * ldb + j] : B[(int64_t)j * ldb + l + 3], acc3);
+        }
+    }
+    for (; l < kk; ++l) {
         const double a = ta ? A[(int64_t)i * lda + l] : A[(int64_t)l * lda + i];
         const double b = tb ? B[(int64_t)l * ldb + j] : B[(int64_t)j * ldb + l];
-        acc = fma(a, b, acc);
+        acc0 = fma(a, b, acc0);
     }
-    double v = alpha * acc;
+    double v = alpha * ((acc0 + acc1) + (acc2 + acc3));
     if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
     C[(int64_t)j * ldc + i] = v;
 }
@@ -283,7 +394,10 @@ int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t 
         splits = 0;
     }
     const int64_t tot = (int64_t)m * p;
-    k_gemm_tn_reduce<<<ceil_div(tot, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
+    if (splits >= 16 && tot <= 65536)
+        k_gemm_tn_reduce_warp<<<ceil_div(tot * 32, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
+    else
+        k_gemm_tn_reduce<<<ceil_div(tot, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
     EDA_LAUNCHED();
     return EDA_OK;
 }
@@ -291,15 +405,16 @@ int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t 
 int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int ldb,
                 double beta, const double* C0, int64_t ldc0, double* C, int64_t ldc, cudaStream_t s) {
     if (d <= 0 || p <= 0) return EDA_OK;
-    const int rowblocks = ceil_div(d, 128);
-    int pc = 8;
-    while (pc > 1 && (int64_t)rowblocks * ceil_div(p, pc) < 2 * 152) pc >>= 1;
-    dim3 grid(rowblocks, ceil_div(p, pc));
-    switch (pc) {
-        case 8: k_gemm_nn<8><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
-        case 4: k_gemm_nn<4><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
-        case 2: k_gemm_nn<2><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
-        default: k_gemm_nn<1><<<grid, 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc); break;
+    const int rowblocks = ceil_div(d, 32);
+    // columns per thread: as many as possible while at least ~one CTA per SM stays busy
+    if (p >= 6 && (int64_t)rowblocks * ceil_div(p, 8) >= 120) {
+        k_gemm_nn<8><<<dim3(rowblocks, ceil_div(p, 8)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+    } else if (p >= 3 && (int64_t)rowblocks * ceil_div(p, 4) >= 120) {
+        k_gemm_nn<4><<<dim3(rowblocks, ceil_div(p, 4)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+    } else if (p >= 2) {
+        k_gemm_nn<2><<<dim3(rowblocks, ceil_div(p, 2)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+    } else {
+        k_gemm_nn<1><<<dim3(rowblocks, p), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     }
     EDA_LAUNCHED();
     return EDA_OK;
@@ -308,6 +423,11 @@ int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t 
 int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const double* A, int lda, const double* B,
                    int ldb, double beta, double* C, int ldc, cudaStream_t s) {
     if (m <= 0 || p <= 0) return EDA_OK;
+    if (!ta && !tb && kk >= 64) {
+        k_gemm_small_nn_splitk<<<dim3(ceil_div(m, 32), p), 128, 0, s>>>(m, p, kk, alpha, A, lda, B, ldb, beta, C, ldc);
+        EDA_LAUNCHED();
+        return EDA_OK;
+    }
     // one warp per CTA (32 rows of one column): FP64 work spreads over all SMs
     dim3 blk(32, 1), grid(ceil_div(m, 32), p);
     k_gemm_small<<<grid, blk, 0, s>>>(ta, tb, m, p, kk, alpha, A, lda, B, ldb, beta, C, ldc);
