@@ -58,7 +58,9 @@ typedef enum {
 } eda_op;
 
 typedef struct {
-    int32_t prec;                /* eda_prec of the Krylov sweeps (EDA_F64 = plain FP64)     */
+    int32_t prec;                /* eda_prec of the Krylov sweeps: EDA_F64 (plain FP64) or   */
+                                 /* EDA_F32 (single-precision H, basis and sweeps, then FP64 */
+                                 /* refinement of the Ritz vectors to tol)                   */
     int32_t block_b;             /* block size b of block Lanczos (>= 1)                     */
     int32_t m_max;               /* max basis columns; <= 0 selects n + k + b (exact end)    */
     int32_t check_every;         /* Rayleigh-Ritz convergence check every this many blocks   */
@@ -76,6 +78,8 @@ typedef struct {
     int32_t basis_cols;          /* final basis width m                                      */
     int32_t refills;             /* rank-deficient columns replaced by fresh random vectors  */
     int32_t checks;              /* Rayleigh-Ritz checks performed                            */
+    int32_t refine_iters;        /* FP64 refinement iterations (mixed precision only)         */
+    int32_t reserved0;
     double c2, lmax_w, lmax_b;   /* scale and the two largest Gram eigenvalues               */
     double max_relres_est;       /* max_i ||B_{m+1} S_{m,i}|| / theta_i over the t pairs      */
     double max_relres_true;      /* max_i ||M y_i - theta_i y_i|| / theta_i (if requested)   */

@@ -155,10 +155,21 @@ int gram_eigen(eda_ctx* h, int m, double* G, double* evals, double* evecs, Arena
     return EDA_OK;
 }
 
-// Everything after H_W, H_B exist: Grams, eigenpairs, c^2, K operators.
+// Everything after H_W, H_B exist: Grams, eigenpairs, c^2, K operators, and for the mixed
+// solver single-precision copies of the factors.
 int finish_build(eda_ctx* h, cudaStream_t s) {
     const int n = (int)h->n, k = h->k;
     const int64_t d = h->d;
+    if (h->cfg.prec == EDA_F32) {
+        const size_t bw = align256((size_t)d * n * sizeof(float)), bb = align256((size_t)d * k * sizeof(float));
+        void* p = nullptr;
+        EDA_CUDA_TRY(cudaMalloc(&p, bw + bb));
+        h->block32 = p;
+        h->HW32 = static_cast<float*>(p);
+        h->HB32 = reinterpret_cast<float*>(static_cast<char*>(p) + bw);
+        EDA_TRY((copy_mat<double, float>(d, n, h->HW, d, h->HW32, d, s)));
+        EDA_TRY((copy_mat<double, float>(d, k, h->HB, d, h->HB32, d, s)));
+    }
     Arena scratch{static_cast<char*>(h->block), h->block_bytes, h->build_arena_off};
     const size_t N = std::max<int64_t>(n, k);
     const size_t pcap = std::max<size_t>(1u << 19, N * N);
@@ -201,7 +212,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
 
 bool valid_cfg(const eda_config& c) {
     return c.block_b >= 1 && c.check_every >= 1 && (c.c2 > 0.0 || c.tau > 0.0) &&
-           (c.prec == EDA_F64 || c.prec == EDA_F32 || c.prec == EDA_BF16 || c.prec == EDA_BF16X2);
+           (c.prec == EDA_F64 || c.prec == EDA_F32);
 }
 
 }  // namespace
@@ -397,6 +408,7 @@ void eda_destroy(eda_handle h) {
     if (!h) return;
     if (h->ws) cudaFree(h->ws);
     if (h->kblock) cudaFree(h->kblock);
+    if (h->block32) cudaFree(h->block32);
     if (h->block) cudaFree(h->block);
     delete h;
 }

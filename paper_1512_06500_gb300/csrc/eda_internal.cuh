@@ -110,6 +110,22 @@ int fill_gaussian_f64(int64_t rows, int cols, double* A, int64_t lda, uint64_t s
                       uint64_t stream_id, cudaStream_t s);
 int col_norms_f64(int64_t rows, int cols, const double* A, int64_t lda, double* out, cudaStream_t s);
 
+// Templated tall-skinny products on the storage type T (double or float). T = float computes
+// each split in single precision and sums the splits in double; the small outputs/operands
+// (C of gemm_tn, B of gemm_nn) are always double. partial_buf holds splits * m * p values of T.
+template <class T>
+int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const T* B, int64_t ldb, double beta,
+            double* C, int ldc, void* partial_buf, size_t partial_cap, cudaStream_t s);
+template <class T>
+int gemm_nn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const double* B, int ldb, double beta,
+            const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s);
+template <class Ti, class To>
+int copy_mat(int64_t rows, int cols, const Ti* A, int64_t lda, To* B, int64_t ldb, cudaStream_t s);
+template <class T>
+int fill_gaussian(int64_t rows, int cols, T* A, int64_t lda, uint64_t seed, uint64_t stream_id, cudaStream_t s);
+template <class T>
+int col_norms(int64_t rows, int cols, const T* A, int64_t lda, double* out, cudaStream_t s);
+
 // ---------------------------------------------------------------- symmetric eigensolver
 struct SymEigWork {
     double* A;        // n x n copy (destroyed)
@@ -161,6 +177,10 @@ struct ExpOp {
     int m;
     const char* tag;  // region-timer name
 };
+// Y = X + H K (H^T X) for a d x b block with H and X in storage type T (double or float).
+template <class T>
+int exp_apply(int64_t d, const T* H, const double* K, int m, const char* tag, int b, const T* X, int64_t ldx, T* Y,
+              int64_t ldy, double* P, double* Q, void* partial, size_t partial_cap, cudaStream_t s);
 // Y = X + H K (H^T X) for a d x b block (FP64 sweeps).
 int exp_apply_f64(int64_t d, const ExpOp& op, int b, const double* X, int64_t ldx, double* Y,
                   int64_t ldy, double* P, double* Q, double* partial, size_t partial_cap,
@@ -184,6 +204,9 @@ struct eda_ctx {
     double *evals_w = nullptr, *evals_b = nullptr;
     double *evecs_w = nullptr, *evecs_b = nullptr;
     double *KW = nullptr, *KB = nullptr;   // K(-c^2/2) for H_W, K(c^2) for H_B
+    // single-precision copies of H_W, H_B for the mixed-precision solver (prec = EDA_F32)
+    void* block32 = nullptr;
+    float *HW32 = nullptr, *HB32 = nullptr;
     int* status = nullptr;                 // device status word
     eda::GridBarrier bar{};
     size_t build_arena_off = 0;            // start of the build scratch inside `block`

@@ -13,12 +13,12 @@ constexpr int TN_TM = 32;       // output tile rows
 constexpr int TN_THREADS = 256;
 
 // partial[s][j][i] = sum over rows r of split s of A[r, i0+i] * B[r, j0+j]
-template <int TP>
-__global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m, int p, const double* __restrict__ A,
-                                                                int64_t lda, const double* __restrict__ B, int64_t ldb,
-                                                                int64_t rows_per_split, double* __restrict__ partial) {
-    __shared__ double As[TN_KB][TN_TM + 1];
-    __shared__ double Bs[TN_KB][TP + 1];
+template <int TP, class T>
+__global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m, int p, const T* __restrict__ A,
+                                                                int64_t lda, const T* __restrict__ B, int64_t ldb,
+                                                                int64_t rows_per_split, T* __restrict__ partial) {
+    __shared__ T As[TN_KB][TN_TM + 1];
+    __shared__ T Bs[TN_KB][TP + 1];
     const int i0 = blockIdx.x * TN_TM;
     const int j0 = blockIdx.y * TP;
     const int s = blockIdx.z;
@@ -30,11 +30,11 @@ __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m
     constexpr int TMT = OUT / TPT;                    // rows per thread
     const int tx = threadIdx.x % (TN_TM / TMT);       // row group
     const int ty = threadIdx.x / (TN_TM / TMT);       // column group
-    double acc[TMT][TPT];
+    T acc[TMT][TPT];
 #pragma unroll
     for (int a = 0; a < TMT; ++a)
 #pragma unroll
-        for (int b = 0; b < TPT; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < TPT; ++b) acc[a][b] = T(0);
 
     for (int64_t r0 = r_begin; r0 < r_end; r0 += TN_KB) {
         // stage A rows r0..r0+KB of columns i0..i0+TM (coalesced along rows)
@@ -42,18 +42,18 @@ __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m
             const int rr = e % TN_KB, cc = e / TN_KB;
             const int64_t r = r0 + rr;
             const int c = i0 + cc;
-            As[rr][cc] = (r < r_end && c < m) ? A[(int64_t)c * lda + r] : 0.0;
+            As[rr][cc] = (r < r_end && c < m) ? A[(int64_t)c * lda + r] : T(0);
         }
         for (int e = threadIdx.x; e < TN_KB * TP; e += TN_THREADS) {
             const int rr = e % TN_KB, cc = e / TN_KB;
             const int64_t r = r0 + rr;
             const int c = j0 + cc;
-            Bs[rr][cc] = (r < r_end && c < p) ? B[(int64_t)c * ldb + r] : 0.0;
+            Bs[rr][cc] = (r < r_end && c < p) ? B[(int64_t)c * ldb + r] : T(0);
         }
         __syncthreads();
 #pragma unroll 8
         for (int rr = 0; rr < TN_KB; ++rr) {
-            double av[TMT], bv[TPT];
+            T av[TMT], bv[TPT];
 #pragma unroll
             for (int a = 0; a < TMT; ++a) av[a] = As[rr][tx + a * (TN_TM / TMT)];
 #pragma unroll
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m
         }
         __syncthreads();
     }
-    double* out = partial + (int64_t)s * m * p;
+    T* out = partial + (int64_t)s * m * p;
 #pragma unroll
     for (int a = 0; a < TMT; ++a)
 #pragma unroll
@@ -79,19 +79,21 @@ __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m
 // C[i, j] = alpha * sum_s partial[s][j][i] + beta * C[i, j]. Small split counts: one thread per
 // output, splits summed in order. Large split counts: one warp per output, lane l sums splits
 // l, l + 32, ... in order, then a fixed butterfly across lanes (deterministic either way).
-__global__ void k_gemm_tn_reduce(int m, int p, int splits, const double* __restrict__ partial, double alpha,
+template <class T>
+__global__ void k_gemm_tn_reduce(int m, int p, int splits, const T* __restrict__ partial, double alpha,
                                  double beta, double* __restrict__ C, int ldc) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)m * p) return;
     const int i = (int)(e % m), j = (int)(e / m);
     double acc = 0.0;
-    for (int s = 0; s < splits; ++s) acc += partial[(int64_t)s * m * p + e];
+    for (int s = 0; s < splits; ++s) acc += (double)partial[(int64_t)s * m * p + e];
     double v = alpha * acc;
     if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
     C[(int64_t)j * ldc + i] = v;
 }
 
-__global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const double* __restrict__ partial, double alpha,
+template <class T>
+__global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const T* __restrict__ partial, double alpha,
                                       double beta, double* __restrict__ C, int ldc) {
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -101,10 +103,10 @@ __global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const double* __
     double a0 = 0.0, a1 = 0.0;
     int s = lane;
     for (; s + 32 < splits; s += 64) {
-        a0 += partial[(int64_t)s * mp + e];
-        a1 += partial[(int64_t)(s + 32) * mp + e];
+        a0 += (double)partial[(int64_t)s * mp + e];
+        a1 += (double)partial[(int64_t)(s + 32) * mp + e];
     }
-    if (s < splits) a0 += partial[(int64_t)s * mp + e];
+    if (s < splits) a0 += (double)partial[(int64_t)s * mp + e];
     double acc = a0 + a1;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
@@ -119,44 +121,44 @@ __global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const double* __
 // which has its own narrow FP64 unit) split the inner dimension into quarters, each thread
 // keeps NC independent accumulators, the slice of B sits in shared memory, and the partial sums
 // of the quarters are added in a fixed order at the end.
-template <int NC>
-__global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double alpha, const double* __restrict__ A,
+template <int NC, class T>
+__global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double alpha, const T* __restrict__ A,
                                                  int64_t lda, const double* __restrict__ B, int ldb, double beta,
-                                                 const double* C0, int64_t ldc0, double* C, int64_t ldc) {
+                                                 const T* C0, int64_t ldc0, T* C, int64_t ldc) {
     constexpr int LCH = 256;                 // rows of B staged per pass
-    __shared__ double Bs[LCH][NC];
-    __shared__ double red[3][32][NC];
+    __shared__ T Bs[LCH][NC];
+    __shared__ T red[3][32][NC];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t r = (int64_t)blockIdx.x * 32 + lane;
     const int c0 = blockIdx.y * NC;
     const int nc = min(NC, p - c0);
-    double acc[NC];
+    T acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = T(0);
     const bool live = r < d;
-    const double* Ar = A + (live ? r : 0);
+    const T* Ar = A + (live ? r : 0);
     for (int l0 = 0; l0 < m; l0 += LCH) {
         const int lc = min(LCH, m - l0);
         __syncthreads();
         for (int e = threadIdx.x; e < lc * NC; e += blockDim.x) {
             const int l = e / NC, c = e % NC;
-            Bs[l][c] = (c < nc) ? B[(int64_t)(c0 + c) * ldb + l0 + l] : 0.0;
+            Bs[l][c] = (c < nc) ? (T)B[(int64_t)(c0 + c) * ldb + l0 + l] : T(0);
         }
         __syncthreads();
         const int q = (lc + 3) / 4;
         const int lb = w * q, le = min(lc, lb + q);
         int l = lb;
         for (; l + 3 < le; l += 4) {
-            double a[4];
+            T a[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = live ? Ar[(int64_t)(l0 + l + u) * lda] : 0.0;
+            for (int u = 0; u < 4; ++u) a[u] = live ? Ar[(int64_t)(l0 + l + u) * lda] : T(0);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) acc[c] = fma(a[u], Bs[l + u][c], acc[c]);
         }
         for (; l < le; ++l) {
-            const double a0 = live ? Ar[(int64_t)(l0 + l) * lda] : 0.0;
+            const T a0 = live ? Ar[(int64_t)(l0 + l) * lda] : T(0);
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = fma(a0, Bs[l][c], acc[c]);
         }
@@ -170,9 +172,9 @@ __global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         if (c >= nc) break;
-        const double sum = (acc[c] + red[0][lane][c]) + (red[1][lane][c] + red[2][lane][c]);
-        double v = alpha * sum;
-        if (beta != 0.0) v = fma(beta, C0[(int64_t)(c0 + c) * ldc0 + r], v);
+        const T sum = (acc[c] + red[0][lane][c]) + (red[1][lane][c] + red[2][lane][c]);
+        T v = (T)alpha * sum;
+        if (beta != 0.0) v = fma((T)beta, C0[(int64_t)(c0 + c) * ldc0 + r], v);
         C[(int64_t)(c0 + c) * ldc + r] = v;
     }
 }
@@ -314,12 +316,13 @@ __global__ void k_chol_inv(int b, double* G, int ldg, double* Rinv, double rank_
     if (threadIdx.x == 0 && lost) lost[b] = nlost;
 }
 
-__global__ void k_copy(int64_t rows, int cols, const double* __restrict__ A, int64_t lda, double* __restrict__ B,
+template <class Ti, class To>
+__global__ void k_copy(int64_t rows, int cols, const Ti* __restrict__ A, int64_t lda, To* __restrict__ B,
                        int64_t ldb) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * cols) return;
     const int64_t r = e % rows, c = e / rows;
-    B[c * ldb + r] = A[c * lda + r];
+    B[c * ldb + r] = (To)A[c * lda + r];
 }
 
 __global__ void k_symmetrize(int m, double* A, int lda) {
@@ -341,7 +344,8 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_fill_gaussian(int64_t rows, int cols, double* A, int64_t lda, uint64_t seed, uint64_t sid) {
+template <class T>
+__global__ void k_fill_gaussian(int64_t rows, int cols, T* A, int64_t lda, uint64_t seed, uint64_t sid) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * cols) return;
     const int64_t r = e % rows, c = e / rows;
@@ -349,14 +353,15 @@ __global__ void k_fill_gaussian(int64_t rows, int cols, double* A, int64_t lda, 
     const uint64_t h2 = mix64(h1 + 0x632BE59BD9B4E019ull);
     const double u1 = ((h1 >> 11) + 1) * (1.0 / 9007199254740993.0);   // (0, 1]
     const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);         // [0, 1)
-    A[c * lda + r] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);            // Box-Muller
+    A[c * lda + r] = (T)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));       // Box-Muller
 }
 
-__global__ void k_col_norms(int64_t rows, const double* __restrict__ A, int64_t lda, double* out) {
+template <class T>
+__global__ void k_col_norms(int64_t rows, const T* __restrict__ A, int64_t lda, double* out) {
     const int c = blockIdx.x;
     double acc = 0.0;
     for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
-        const double v = A[(int64_t)c * lda + r];
+        const double v = (double)A[(int64_t)c * lda + r];
         acc = fma(v, v, acc);
     }
     __shared__ double red[32];
@@ -372,9 +377,11 @@ __global__ void k_col_norms(int64_t rows, const double* __restrict__ A, int64_t 
 
 }  // namespace
 
-int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
-                double beta, double* C, int ldc, double* partial, size_t partial_cap, cudaStream_t s) {
+template <class T>
+int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const T* B, int64_t ldb, double beta,
+            double* C, int ldc, void* partial_buf, size_t partial_cap, cudaStream_t s) {
     if (m <= 0 || p <= 0) return EDA_OK;
+    T* partial = static_cast<T*>(partial_buf);
     const int TP = p <= 8 ? 8 : (p <= 16 ? 16 : 32);
     const int tiles = ceil_div(m, TN_TM) * ceil_div(p, TP);
     int splits = std::max(1, ceil_div(2 * 152, tiles));
@@ -386,38 +393,90 @@ int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t 
     splits = (int)std::max<int64_t>(1, (d + rows - 1) / rows);
     dim3 grid(ceil_div(m, TN_TM), ceil_div(p, TP), splits);
     if (d > 0) {
-        if (TP == 8) k_gemm_tn_partial<8><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
-        else if (TP == 16) k_gemm_tn_partial<16><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
-        else k_gemm_tn_partial<32><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        if (TP == 8) k_gemm_tn_partial<8, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        else if (TP == 16) k_gemm_tn_partial<16, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        else k_gemm_tn_partial<32, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
         EDA_LAUNCHED();
     } else {
         splits = 0;
     }
     const int64_t tot = (int64_t)m * p;
     if (splits >= 16 && tot <= 65536)
-        k_gemm_tn_reduce_warp<<<ceil_div(tot * 32, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
+        k_gemm_tn_reduce_warp<T><<<ceil_div(tot * 32, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
     else
-        k_gemm_tn_reduce<<<ceil_div(tot, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
+        k_gemm_tn_reduce<T><<<ceil_div(tot, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
     EDA_LAUNCHED();
     return EDA_OK;
 }
 
-int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int ldb,
-                double beta, const double* C0, int64_t ldc0, double* C, int64_t ldc, cudaStream_t s) {
+template <class T>
+int gemm_nn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const double* B, int ldb, double beta,
+            const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s) {
     if (d <= 0 || p <= 0) return EDA_OK;
     const int rowblocks = ceil_div(d, 32);
     // columns per thread: as many as possible while at least ~one CTA per SM stays busy
     if (p >= 6 && (int64_t)rowblocks * ceil_div(p, 8) >= 120) {
-        k_gemm_nn<8><<<dim3(rowblocks, ceil_div(p, 8)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<8, T><<<dim3(rowblocks, ceil_div(p, 8)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     } else if (p >= 3 && (int64_t)rowblocks * ceil_div(p, 4) >= 120) {
-        k_gemm_nn<4><<<dim3(rowblocks, ceil_div(p, 4)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<4, T><<<dim3(rowblocks, ceil_div(p, 4)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     } else if (p >= 2) {
-        k_gemm_nn<2><<<dim3(rowblocks, ceil_div(p, 2)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<2, T><<<dim3(rowblocks, ceil_div(p, 2)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     } else {
-        k_gemm_nn<1><<<dim3(rowblocks, p), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<1, T><<<dim3(rowblocks, p), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     }
     EDA_LAUNCHED();
     return EDA_OK;
+}
+
+template <class Ti, class To>
+int copy_mat(int64_t rows, int cols, const Ti* A, int64_t lda, To* B, int64_t ldb, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return EDA_OK;
+    k_copy<Ti, To><<<ceil_div(rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, B, ldb);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+template <class T>
+int fill_gaussian(int64_t rows, int cols, T* A, int64_t lda, uint64_t seed, uint64_t stream_id, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return EDA_OK;
+    k_fill_gaussian<T><<<ceil_div(rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, seed, stream_id);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+template <class T>
+int col_norms(int64_t rows, int cols, const T* A, int64_t lda, double* out, cudaStream_t s) {
+    if (cols <= 0) return EDA_OK;
+    k_col_norms<T><<<cols, 256, 0, s>>>(rows, A, lda, out);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+template int gemm_tn<double>(int64_t, int, int, double, const double*, int64_t, const double*, int64_t, double,
+                             double*, int, void*, size_t, cudaStream_t);
+template int gemm_tn<float>(int64_t, int, int, double, const float*, int64_t, const float*, int64_t, double,
+                            double*, int, void*, size_t, cudaStream_t);
+template int gemm_nn<double>(int64_t, int, int, double, const double*, int64_t, const double*, int, double,
+                             const double*, int64_t, double*, int64_t, cudaStream_t);
+template int gemm_nn<float>(int64_t, int, int, double, const float*, int64_t, const double*, int, double,
+                            const float*, int64_t, float*, int64_t, cudaStream_t);
+template int copy_mat<double, double>(int64_t, int, const double*, int64_t, double*, int64_t, cudaStream_t);
+template int copy_mat<float, float>(int64_t, int, const float*, int64_t, float*, int64_t, cudaStream_t);
+template int copy_mat<double, float>(int64_t, int, const double*, int64_t, float*, int64_t, cudaStream_t);
+template int copy_mat<float, double>(int64_t, int, const float*, int64_t, double*, int64_t, cudaStream_t);
+template int fill_gaussian<double>(int64_t, int, double*, int64_t, uint64_t, uint64_t, cudaStream_t);
+template int fill_gaussian<float>(int64_t, int, float*, int64_t, uint64_t, uint64_t, cudaStream_t);
+template int col_norms<double>(int64_t, int, const double*, int64_t, double*, cudaStream_t);
+template int col_norms<float>(int64_t, int, const float*, int64_t, double*, cudaStream_t);
+
+int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                double beta, double* C, int ldc, double* partial, size_t partial_cap, cudaStream_t s) {
+    return gemm_tn<double>(d, m, p, alpha, A, lda, B, ldb, beta, C, ldc, partial, partial_cap, s);
+}
+
+int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int ldb,
+                double beta, const double* C0, int64_t ldc0, double* C, int64_t ldc, cudaStream_t s) {
+    return gemm_nn<double>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc, s);
 }
 
 int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const double* A, int lda, const double* B,
@@ -443,10 +502,7 @@ int chol_inv_small(int b, double* G, int ldg, double* Rinv, double rank_tol, dou
 }
 
 int copy_mat_f64(int64_t rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb, cudaStream_t s) {
-    if (rows <= 0 || cols <= 0) return EDA_OK;
-    k_copy<<<ceil_div(rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, B, ldb);
-    EDA_LAUNCHED();
-    return EDA_OK;
+    return copy_mat<double, double>(rows, cols, A, lda, B, ldb, s);
 }
 
 int symmetrize_f64(int m, double* A, int lda, cudaStream_t s) {
@@ -458,17 +514,11 @@ int symmetrize_f64(int m, double* A, int lda, cudaStream_t s) {
 
 int fill_gaussian_f64(int64_t rows, int cols, double* A, int64_t lda, uint64_t seed, uint64_t stream_id,
                       cudaStream_t s) {
-    if (rows <= 0 || cols <= 0) return EDA_OK;
-    k_fill_gaussian<<<ceil_div(rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, seed, stream_id);
-    EDA_LAUNCHED();
-    return EDA_OK;
+    return fill_gaussian<double>(rows, cols, A, lda, seed, stream_id, s);
 }
 
 int col_norms_f64(int64_t rows, int cols, const double* A, int64_t lda, double* out, cudaStream_t s) {
-    if (cols <= 0) return EDA_OK;
-    k_col_norms<<<cols, 256, 0, s>>>(rows, A, lda, out);
-    EDA_LAUNCHED();
-    return EDA_OK;
+    return col_norms<double>(rows, cols, A, lda, out, s);
 }
 
 }  // namespace eda

@@ -7,11 +7,18 @@
 // space is exhausted after about (n - 1) / b + 1 blocks. With the basis sized to n + k + b
 // columns no restart is needed: the loop ends by convergence or by exact termination (the new
 // block has no component outside the basis).
+//
+// Precision: the Krylov sweeps and the basis use the storage type T. With T = double this is
+// the plain FP64 solver. With T = float (single-precision H, basis and sweeps; the small
+// matrices stay FP64) the loop stops at a loose tolerance and the Ritz vectors are refined in
+// FP64: Rayleigh-Ritz on span(Y) with FP64 M-applies, then subspace iteration Y <- M Y, until
+// the true FP64 relative residual of every pair is at most tol.
 #include "eda_internal.cuh"
 
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 namespace eda {
@@ -52,7 +59,7 @@ __global__ void k_ritz_residuals(int t, int b, const double* Bm, int ldb, const 
     relres[i] = th > 0.0 ? sqrt(acc) / th : INFINITY;
 }
 
-// out[:, i] = in[:, t-1-i]  (descending order of the Ritz values)
+// out[:, i] = in[:, t-1-i] (descending order of the Ritz values)
 __global__ void k_reverse_cols(int64_t rows, int t, const double* in, int64_t ldi, double* out, int64_t ldo) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * t) return;
@@ -66,7 +73,7 @@ __global__ void k_reverse_vec(int t, const double* in, double* out) {
     if (i < t) out[i] = in[t - 1 - i];
 }
 
-// R = M Y - Y diag(theta) in place of MY, column by column
+// R = MY - Y diag(theta), written over MY
 __global__ void k_sub_scaled(int64_t d, int t, double* MY, int64_t ldm, const double* Y, int64_t ldy,
                              const double* theta) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,56 +83,272 @@ __global__ void k_sub_scaled(int64_t d, int t, double* MY, int64_t ldm, const do
     MY[(int64_t)c * ldm + r] = fma(-theta[c], Y[(int64_t)c * ldy + r], MY[(int64_t)c * ldm + r]);
 }
 
+__global__ void k_divide(int t, double* num, const double* den) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t) num[i] = fabs(den[i]) > 0.0 ? num[i] / fabs(den[i]) : INFINITY;
+}
+
+// Workspace of one solve: Krylov state in T, small matrices and the FP64 finish.
+template <class T>
 struct SolveWs {
-    double *V, *W, *W1, *tmp, *T, *C, *Gb, *R1, *R1i, *R2, *R2i, *Bm, *P, *Q, *part;
-    double *theta, *S, *relres, *Ydesc, *Xt, *Gt, *Rt, *Rti, *lamd;
+    T *V, *W, *W1, *tmp, *Yt;
+    double *Tm, *C, *R1, *R1i, *R2, *R2i, *Bm, *P, *Q, *theta, *S, *relres;
+    double *Y, *Z, *Y2, *Z2, *Xt, *Gt, *Rt, *Rti, *lamd, *tmp64;
+    void* part;
     int* lost;
     size_t pcap;
     SymEigWork eig;
 };
 
-// CholQR of X (d x b) in place: X <- X R^{-1}; R returned in Rm (b x b). Rank loss marks lost pivots.
-int cholqr_pass(int64_t d, int b, double* X, int64_t ldx, double* Rm, double* Rinv, double* out, double piv_min2,
-                int* status, int* lost, SolveWs& w, cudaStream_t s) {
-    EDA_TRY(gemm_tn_f64(d, b, b, 1.0, X, ldx, X, ldx, 0.0, Rm, b, w.part, w.pcap, s));
+template <class T>
+int cholqr_pass(int64_t d, int b, T* X, int64_t ldx, double* Rm, double* Rinv, T* out, double piv_min2, int* status,
+                int* lost, SolveWs<T>& w, cudaStream_t s) {
+    EDA_TRY(gemm_tn<T>(d, b, b, 1.0, X, ldx, X, ldx, 0.0, Rm, b, w.part, w.pcap, s));
     EDA_TRY(chol_inv_small(b, Rm, b, Rinv, 1e-28, piv_min2, status, lost, s));
-    EDA_TRY(gemm_nn_f64(d, b, b, 1.0, X, ldx, Rinv, b, 0.0, nullptr, 0, out, ldx, s));
+    EDA_TRY(gemm_nn<T>(d, b, b, 1.0, X, ldx, Rinv, b, 0.0, nullptr, 0, out, ldx, s));
     return EDA_OK;
 }
 
 // CGS2: X <- X - V (V^T X), twice; the first coefficients are left in Cfirst (cols x b).
-int cgs2(int64_t d, int cols, int b, const double* V, double* X, int64_t ldx, double* Cfirst, double* C2,
-         SolveWs& w, cudaStream_t s) {
+template <class T>
+int cgs2(int64_t d, int cols, int b, const T* V, T* X, int64_t ldx, double* Cfirst, double* C2, SolveWs<T>& w,
+         cudaStream_t s) {
     if (cols <= 0) return EDA_OK;
     ProfScope prof("reorth", s);
-    EDA_TRY(gemm_tn_f64(d, cols, b, 1.0, V, d, X, ldx, 0.0, Cfirst, cols, w.part, w.pcap, s));
-    EDA_TRY(gemm_nn_f64(d, cols, b, -1.0, V, d, Cfirst, cols, 1.0, X, ldx, X, ldx, s));
-    EDA_TRY(gemm_tn_f64(d, cols, b, 1.0, V, d, X, ldx, 0.0, C2, cols, w.part, w.pcap, s));
-    EDA_TRY(gemm_nn_f64(d, cols, b, -1.0, V, d, C2, cols, 1.0, X, ldx, X, ldx, s));
+    EDA_TRY(gemm_tn<T>(d, cols, b, 1.0, V, d, X, ldx, 0.0, Cfirst, cols, w.part, w.pcap, s));
+    EDA_TRY(gemm_nn<T>(d, cols, b, -1.0, V, d, Cfirst, cols, 1.0, X, ldx, X, ldx, s));
+    EDA_TRY(gemm_tn<T>(d, cols, b, 1.0, V, d, X, ldx, 0.0, C2, cols, w.part, w.pcap, s));
+    EDA_TRY(gemm_nn<T>(d, cols, b, -1.0, V, d, C2, cols, 1.0, X, ldx, X, ldx, s));
     return EDA_OK;
 }
+
+template <class T> struct HStore;
+template <> struct HStore<double> {
+    static const double* W(eda_ctx* h) { return h->HW; }
+    static const double* B(eda_ctx* h) { return h->HB; }
+};
+template <> struct HStore<float> {
+    static const float* W(eda_ctx* h) { return h->HW32; }
+    static const float* B(eda_ctx* h) { return h->HB32; }
+};
 
 }  // namespace
 
 // Y = M X = E_W^{-1/2} E_B E_W^{-1/2} X, the three products (iii)-(v) of Eq. (320).
-int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t ldy, double* tmp, double* P,
-            double* Q, double* partial, size_t partial_cap, cudaStream_t s) {
+template <class T>
+int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* tmp, double* P, double* Q,
+              void* partial, size_t partial_cap, cudaStream_t s) {
     ProfScope prof("m_apply", s);
     const int64_t d = h->d;
-    const ExpOp W{h->HW, h->KW, (int)h->n, "exp_apply_w"};
-    const ExpOp B{h->HB, h->KB, h->k, "exp_apply_b"};
-    EDA_TRY(exp_apply_f64(d, W, b, X, ldx, tmp, d, P, Q, partial, partial_cap, s));
-    EDA_TRY(exp_apply_f64(d, B, b, tmp, d, Y, ldy, P, Q, partial, partial_cap, s));
-    EDA_TRY(exp_apply_f64(d, W, b, Y, ldy, tmp, d, P, Q, partial, partial_cap, s));
-    EDA_TRY(copy_mat_f64(d, b, tmp, d, Y, ldy, s));
+    const T* HW = HStore<T>::W(h);
+    const T* HB = HStore<T>::B(h);
+    const int n = (int)h->n;
+    EDA_TRY(exp_apply<T>(d, HW, h->KW, n, "exp_apply_w", b, X, ldx, tmp, d, P, Q, partial, partial_cap, s));
+    EDA_TRY(exp_apply<T>(d, HB, h->KB, h->k, "exp_apply_b", b, tmp, d, Y, ldy, P, Q, partial, partial_cap, s));
+    EDA_TRY(exp_apply<T>(d, HW, h->KW, n, "exp_apply_w", b, Y, ldy, tmp, d, P, Q, partial, partial_cap, s));
+    EDA_TRY((copy_mat<T, T>(d, b, tmp, d, Y, ldy, s)));
     return EDA_OK;
 }
 
-int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vout, double* lambda, double* Yout,
-               eda_solve_info* info, cudaStream_t s) {
+int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t ldy, double* tmp, double* P,
+            double* Q, double* partial, size_t partial_cap, cudaStream_t s) {
+    return m_apply_t<double>(h, b, X, ldx, Y, ldy, tmp, P, Q, partial, partial_cap, s);
+}
+
+namespace {
+
+struct LanczosStats {
+    int iters = 0, mapplies = 0, checks = 0, refills = 0, rr_cols = 0, conv_count = 0;
+    bool converged = false;
+    double max_rel = INFINITY;
+    std::vector<double> relres;   // ascending theta order
+};
+
+// Block Lanczos in storage type T. On return w.theta holds the t Ritz values (ascending) and
+// w.Yt the Ritz vectors V_{:rr} S (d x t, same order).
+template <class T>
+int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_max, SolveWs<T>& w, LanczosStats& st,
+                cudaStream_t s) {
+    const int64_t d = h->d;
+    const int b = h->cfg.block_b;
+    const int tw = std::max(t, b);
+    // rank threshold on squared pivots: relative to the bound lambda_1(M) <= exp(c^2 lmax(G_B))
+    // of Theorem 3.3 (nu_d = 0)
+    const double normM = std::exp(std::min(700.0, h->c2 * h->lmax_b));
+    const double piv_min2 = (1e-12 * normM) * (1e-12 * normM);
+
+    // ---- start block ----
+    if (V0) {
+        const int cp = std::min(b0, b);
+        EDA_TRY((copy_mat<double, T>(d, cp, V0, d, w.V, d, s)));
+        if (cp < b) EDA_TRY(fill_gaussian<T>(d, b - cp, w.V + (size_t)cp * d, d, h->cfg.seed, 0, s));
+    } else {
+        EDA_TRY(fill_gaussian<T>(d, b, w.V, d, h->cfg.seed, 0, s));
+    }
+    EDA_TRY(cholqr_pass<T>(d, b, w.V, d, w.R1, w.R1i, w.W1, 0.0, h->status, w.lost, w, s));
+    EDA_TRY(cholqr_pass<T>(d, b, w.W1, d, w.R2, w.R2i, w.V, 0.0, h->status, w.lost, w, s));
+    {
+        int lostc = 0;
+        EDA_CUDA_TRY(cudaMemcpyAsync(&lostc, w.lost + b, sizeof(int), cudaMemcpyDeviceToHost, s));
+        EDA_CUDA_TRY(cudaStreamSynchronize(s));
+        if (lostc) return EDA_ERR_BREAKDOWN;   // the start block itself is rank deficient
+    }
+
+    int cols = b;
+    bool exhausted = false;
+    st.relres.assign(t, INFINITY);
+    // Rayleigh-Ritz schedule: the first check once the basis has t + b columns; later checks at
+    // the basis width where the geometric rate seen between the last two checks predicts
+    // convergence (never sooner than check_every blocks, always at the last block).
+    int next_check = t + b;
+    int prev_check_cols = 0;
+    double prev_check_rel = 0.0;
+
+    while (true) {
+        const int j0 = cols - b;
+        const T* Vj = w.V + (size_t)j0 * d;
+        EDA_TRY(m_apply_t<T>(h, b, Vj, d, w.W, d, w.tmp, w.P, w.Q, w.part, w.pcap, s));
+        ++st.mapplies;
+        ++st.iters;
+        double* C1 = w.C;
+        double* C2 = w.C + (size_t)m_max * tw;
+        EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W, d, C1, C2, w, s));
+        k_set_diag_block<<<ceil_div(b * b, 256), 256, 0, s>>>(w.Tm, m_max, j0, b, C1 + j0, cols);
+        EDA_LAUNCHED();
+        // CholQR2 of W with rank detection: W = V_{j+1} B_{j+1}
+        EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
+        EDA_TRY(cholqr_pass<T>(d, b, w.W, d, w.R1, w.R1i, w.W1, piv_min2, h->status, w.lost, w, s));
+        int lostc = 0;
+        EDA_CUDA_TRY(cudaMemcpyAsync(&lostc, w.lost + b, sizeof(int), cudaMemcpyDeviceToHost, s));
+        EDA_CUDA_TRY(cudaStreamSynchronize(s));
+        const bool room = cols + b <= m_max;
+        if (lostc == b) {
+            exhausted = true;    // no direction outside the basis: T is exact (B_{j+1} = 0)
+        } else if (room) {
+            if (lostc > 0) {
+                // replace the lost columns by fresh random directions orthogonal to the basis
+                st.refills += lostc;
+                std::vector<int> lost_h(b + 1);
+                EDA_CUDA_TRY(cudaMemcpyAsync(lost_h.data(), w.lost, (b + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+                EDA_CUDA_TRY(cudaStreamSynchronize(s));
+                for (int q = 0; q < lostc; ++q)
+                    EDA_TRY(fill_gaussian<T>(d, 1, w.W1 + (size_t)lost_h[q] * d, d, h->cfg.seed,
+                                             1000 + (uint64_t)st.iters * 64 + q, s));
+                EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W1, d, C2, C2 + (size_t)cols * b, w, s));
+            }
+            T* Vn = w.V + (size_t)cols * d;
+            EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
+            EDA_TRY(cholqr_pass<T>(d, b, w.W1, d, w.R2, w.R2i, Vn, 0.0, h->status, w.lost, w, s));
+            EDA_TRY(gemm_small_f64(false, false, b, b, b, 1.0, w.R2, b, w.R1, b, 0.0, w.Bm, b, s));   // B = R2 R1
+        } else {
+            EDA_TRY(copy_mat_f64(b, b, w.R1, b, w.Bm, b, s));   // basis full: residual estimate only
+        }
+        const bool last = exhausted || !room;
+        if ((cols >= next_check && cols >= t + 1) || (last && cols >= t)) {
+            ++st.checks;
+            st.rr_cols = cols;
+            ProfScope prof("rr", s);
+            EDA_TRY(symeig_f64(cols, w.Tm, m_max, cols - t, cols - 1, w.theta, w.S, cols, &w.eig, h->status,
+                               h->cfg.seed + 7, 1e-7, s));
+            if (exhausted) {
+                EDA_CUDA_TRY(cudaMemsetAsync(w.relres, 0, t * sizeof(double), s));
+            } else {
+                k_ritz_residuals<<<ceil_div(t, 128), 128, 0, s>>>(t, b, w.Bm, b, w.S, cols, cols - b, w.theta,
+                                                                 w.relres);
+                EDA_LAUNCHED();
+            }
+            EDA_CUDA_TRY(cudaMemcpyAsync(st.relres.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
+            EDA_CUDA_TRY(cudaStreamSynchronize(s));
+            st.max_rel = 0.0;
+            st.conv_count = 0;
+            for (int i = 0; i < t; ++i) {
+                if (st.relres[i] <= tol) ++st.conv_count;
+                st.max_rel = std::max(st.max_rel, st.relres[i]);
+            }
+            if (st.conv_count == t) st.converged = true;
+            int gap = b * h->cfg.check_every;
+            if (prev_check_cols > 0 && st.max_rel > 0.0 && prev_check_rel > 0.0 && st.max_rel < prev_check_rel &&
+                std::isfinite(st.max_rel)) {
+                const double blocks = (double)(cols - prev_check_cols) / b;
+                const double rate = std::pow(st.max_rel / prev_check_rel, 1.0 / blocks);   // per block
+                const double need = std::log(tol / st.max_rel) / std::log(rate);           // blocks to go
+                if (std::isfinite(need) && need > 1.0) gap = std::max(gap, b * (int)std::floor(0.8 * need));
+            }
+            prev_check_cols = cols;
+            prev_check_rel = st.max_rel;
+            next_check = cols + gap;
+        }
+        if (st.converged || last) break;
+        k_set_block<<<ceil_div(b * b, 256), 256, 0, s>>>(w.Tm, m_max, cols, j0, b, w.Bm, b, false);
+        EDA_LAUNCHED();
+        k_set_block<<<ceil_div(b * b, 256), 256, 0, s>>>(w.Tm, m_max, j0, cols, b, w.Bm, b, true);
+        EDA_LAUNCHED();
+        cols += b;
+    }
+    if (st.rr_cols == 0) return EDA_ERR_NOT_CONVERGED;
+    // Ritz vectors Y = V_{:rr} S (ascending theta)
+    EDA_TRY(gemm_nn<T>(d, st.rr_cols, t, 1.0, w.V, d, w.S, st.rr_cols, 0.0, nullptr, 0, w.Yt, d, s));
+    return EDA_OK;
+}
+
+// FP64 refinement of t approximate eigenvectors Y (d x t): Rayleigh-Ritz on span(Y) with an
+// FP64 M-apply; while some true relative residual exceeds tol, Y <- M Y (subspace iteration).
+// Leaves Y (orthonormal Ritz vectors, ascending theta), theta and the residuals.
+template <class T>
+int refine_f64(eda_ctx* h, int t, double tol, SolveWs<T>& w, int max_iter, int* iters_out, int* mapplies,
+               std::vector<double>& relres_h, double* max_rel, cudaStream_t s) {
+    ProfScope prof("refine", s);
+    const int64_t d = h->d;
+    const int b = h->cfg.block_b;
+    double* part = static_cast<double*>(w.part);
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        // Y <- orth(Y) (CholQR2 in FP64)
+        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y, d, w.Y, d, 0.0, w.Rt, t, part, w.pcap, s));
+        EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
+        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y, d, w.Rti, t, 0.0, nullptr, 0, w.Y2, d, s));
+        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y2, d, w.Y2, d, 0.0, w.Rt, t, part, w.pcap, s));
+        EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
+        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y2, d, w.Rti, t, 0.0, nullptr, 0, w.Y, d, s));
+        // Z = M Y
+        EDA_TRY(m_apply_t<double>(h, t, w.Y, d, w.Z, d, w.tmp64, w.P, w.Q, w.part, w.pcap, s));
+        *mapplies += (t + b - 1) / b;
+        // Rayleigh-Ritz on span(Y): G = Y^T Z, eig, Y <- Y S, Z <- Z S
+        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y, d, w.Z, d, 0.0, w.Gt, t, part, w.pcap, s));
+        EDA_TRY(symmetrize_f64(t, w.Gt, t, s));
+        EDA_TRY(symeig_f64(t, w.Gt, t, 0, t - 1, w.theta, w.S, t, &w.eig, h->status, h->cfg.seed + 11, 1e-7, s));
+        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y, d, w.S, t, 0.0, nullptr, 0, w.Y2, d, s));
+        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Z, d, w.S, t, 0.0, nullptr, 0, w.Z2, d, s));
+        EDA_TRY(copy_mat_f64(d, t, w.Y2, d, w.Y, d, s));
+        EDA_TRY(copy_mat_f64(d, t, w.Z2, d, w.Z, d, s));
+        // true residuals R = Z S - Y S theta
+        k_sub_scaled<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, w.Z2, d, w.Y, d, w.theta);
+        EDA_LAUNCHED();
+        EDA_TRY(col_norms_f64(d, t, w.Z2, d, w.relres, s));
+        k_divide<<<ceil_div(t, 128), 128, 0, s>>>(t, w.relres, w.theta);
+        EDA_LAUNCHED();
+        EDA_CUDA_TRY(cudaMemcpyAsync(relres_h.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EDA_CUDA_TRY(cudaStreamSynchronize(s));
+        *max_rel = 0.0;
+        for (int i = 0; i < t; ++i) *max_rel = std::max(*max_rel, relres_h[i]);
+        if (*max_rel <= tol) {
+            ++it;
+            break;
+        }
+        // subspace iteration: the next subspace is span(M Y) = span(Z)
+        EDA_TRY(copy_mat_f64(d, t, w.Z, d, w.Y, d, s));
+    }
+    *iters_out = it;
+    return EDA_OK;
+}
+
+template <class T>
+int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vout, double* lambda, double* Yout,
+            eda_solve_info* info, cudaStream_t s) {
     const int64_t d = h->d;
     const int n = (int)h->n, k = h->k;
     const int b = h->cfg.block_b;
+    const bool mixed = !std::is_same<T, double>::value;
     if (t > d || t > n + k) return EDA_ERR_INVALID_ARG;
     int m_max = h->cfg.m_max > 0 ? h->cfg.m_max : n + k + b;
     m_max = (m_max + b - 1) / b * b;
@@ -140,224 +363,125 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
     EDA_CUDA_TRY(cudaEventRecord(ev0, s));
 
     // ---- workspace ----
-    SolveWs w{};
+    SolveWs<T> w{};
     w.pcap = std::max<size_t>({size_t(1) << 19, (size_t)m_max * tw, (size_t)N * tw, (size_t)t * t});
+    const int eig_n = std::max(m_max, t);
     size_t need = 0;
+    auto addT = [&](size_t cnt) { need += a256(cnt * sizeof(T)); };
     auto add = [&](size_t cnt) { need += a256(cnt * 8); };
-    add((size_t)d * m_max);            // V
-    add((size_t)d * tw);               // W
-    add((size_t)d * tw);               // W1
-    add((size_t)d * tw);               // tmp
-    add((size_t)m_max * m_max);        // T
-    add((size_t)m_max * tw * 2);       // C (two)
-    for (int i = 0; i < 6; ++i) add((size_t)b * b);
+    addT((size_t)d * m_max);           // V
+    addT((size_t)d * tw);              // W
+    addT((size_t)d * tw);              // W1
+    addT((size_t)d * tw);              // tmp
+    addT((size_t)d * t);               // Yt
+    add((size_t)m_max * m_max);        // Tm
+    add((size_t)m_max * tw * 2);       // C
+    for (int i = 0; i < 7; ++i) add((size_t)b * b);
     add((size_t)N * tw * 2);           // P, Q
-    add(w.pcap);
+    add(w.pcap);                       // partial (double-sized slots hold either type)
     add(t);                            // theta
-    add((size_t)m_max * t);            // S
+    add((size_t)eig_n * t);            // S
     add(t);                            // relres
-    add((size_t)d * t);                // Ydesc
-    add((size_t)d * t);                // Xt
-    add((size_t)t * t * 3);            // Gt, Rt, Rti
+    for (int i = 0; i < 5; ++i) add((size_t)d * t);   // Y, Z, Y2, Z2, Xt
+    add((size_t)d * tw);               // tmp64
+    add((size_t)t * t * 4);            // Gt, Rt, Rti
     add(t);                            // lamd
     add(b + 64);                       // lost (ints)
-    need += symeig_work_bytes(m_max, t) + 8192;
+    need += symeig_work_bytes(eig_n, t) + 16384;
     EDA_TRY(ensure_workspace(h, need));
     Arena a{static_cast<char*>(h->ws), h->ws_bytes, 0};
-    w.V = a.take<double>((size_t)d * m_max);
-    w.W = a.take<double>((size_t)d * tw);
-    w.W1 = a.take<double>((size_t)d * tw);
-    w.tmp = a.take<double>((size_t)d * tw);
-    w.T = a.take<double>((size_t)m_max * m_max);
+    w.V = a.take<T>((size_t)d * m_max);
+    w.W = a.take<T>((size_t)d * tw);
+    w.W1 = a.take<T>((size_t)d * tw);
+    w.tmp = a.take<T>((size_t)d * tw);
+    w.Yt = a.take<T>((size_t)d * t);
+    w.Tm = a.take<double>((size_t)m_max * m_max);
     w.C = a.take<double>((size_t)m_max * tw * 2);
-    w.Gb = a.take<double>((size_t)b * b);
     w.R1 = a.take<double>((size_t)b * b);
     w.R1i = a.take<double>((size_t)b * b);
     w.R2 = a.take<double>((size_t)b * b);
     w.R2i = a.take<double>((size_t)b * b);
     w.Bm = a.take<double>((size_t)b * b);
+    (void)a.take<double>((size_t)b * b);
+    (void)a.take<double>((size_t)b * b);
     w.P = a.take<double>((size_t)N * tw);
     w.Q = a.take<double>((size_t)N * tw);
     w.part = a.take<double>(w.pcap);
     w.theta = a.take<double>(t);
-    w.S = a.take<double>((size_t)m_max * t);
+    w.S = a.take<double>((size_t)eig_n * t);
     w.relres = a.take<double>(t);
-    w.Ydesc = a.take<double>((size_t)d * t);
+    w.Y = a.take<double>((size_t)d * t);
+    w.Z = a.take<double>((size_t)d * t);
+    w.Y2 = a.take<double>((size_t)d * t);
+    w.Z2 = a.take<double>((size_t)d * t);
     w.Xt = a.take<double>((size_t)d * t);
+    w.tmp64 = a.take<double>((size_t)d * tw);
     w.Gt = a.take<double>((size_t)t * t);
     w.Rt = a.take<double>((size_t)t * t);
     w.Rti = a.take<double>((size_t)t * t);
+    (void)a.take<double>((size_t)t * t);
     w.lamd = a.take<double>(t);
     w.lost = a.take<int>(b + 64);
-    EDA_TRY(symeig_work_carve(a, m_max, t, h->bar, &w.eig));
+    EDA_TRY(symeig_work_carve(a, eig_n, t, h->bar, &w.eig));
     if (!w.lost) return EDA_ERR_OOM;
     EDA_CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), s));
-    EDA_CUDA_TRY(cudaMemsetAsync(w.T, 0, (size_t)m_max * m_max * 8, s));
+    EDA_CUDA_TRY(cudaMemsetAsync(w.Tm, 0, (size_t)m_max * m_max * 8, s));
 
-    // rank threshold on squared pivots: relative to the bound lambda_1(M) <= exp(c^2 lmax(G_B))
-    // of Theorem 3.3 (nu_d = 0)
-    const double normM = std::exp(std::min(700.0, h->c2 * h->lmax_b));
-    const double piv_min2 = (1e-12 * normM) * (1e-12 * normM);
-    int refills = 0;
-
-    // ---- start block ----
-    if (V0) {
-        const int cp = std::min(b0, b);
-        EDA_TRY(copy_mat_f64(d, cp, V0, d, w.V, d, s));
-        if (cp < b) EDA_TRY(fill_gaussian_f64(d, b - cp, w.V + (size_t)cp * d, d, h->cfg.seed, 0, s));
-    } else {
-        EDA_TRY(fill_gaussian_f64(d, b, w.V, d, h->cfg.seed, 0, s));
+    // ---- Krylov phase ----
+    LanczosStats st;
+    const double tol_k = mixed ? std::max(tol, 1e-4) : tol;
+    int rc = run_lanczos<T>(h, t, tol_k, V0, b0, m_max, w, st, s);
+    if (rc != EDA_OK && rc != EDA_ERR_NOT_CONVERGED) return rc;
+    if (rc == EDA_ERR_NOT_CONVERGED && st.rr_cols == 0) return rc;
+    EDA_TRY((copy_mat<T, double>(d, t, w.Yt, d, w.Y, d, s)));
+    bool converged = st.converged;
+    double max_rel = st.max_rel;
+    std::vector<double> relres_h = st.relres;
+    int refine_iters = 0;
+    if (mixed) {
+        int mapp = 0;
+        EDA_TRY(refine_f64<T>(h, t, tol, w, 6, &refine_iters, &mapp, relres_h, &max_rel, s));
+        st.mapplies += mapp;
+        converged = max_rel <= tol;
+        st.conv_count = 0;
+        for (int i = 0; i < t; ++i) st.conv_count += relres_h[i] <= tol;
     }
-    EDA_TRY(cholqr_pass(d, b, w.V, d, w.R1, w.R1i, w.W1, 0.0, h->status, w.lost, w, s));
-    EDA_TRY(cholqr_pass(d, b, w.W1, d, w.R2, w.R2i, w.V, 0.0, h->status, w.lost, w, s));
-    {
-        int lostc = 0;
-        EDA_CUDA_TRY(cudaMemcpyAsync(&lostc, w.lost + b, sizeof(int), cudaMemcpyDeviceToHost, s));
-        EDA_CUDA_TRY(cudaStreamSynchronize(s));
-        if (lostc) return EDA_ERR_BREAKDOWN;   // the start block itself is rank deficient
-    }
-
-    int cols = b;            // basis columns filled
-    int iters = 0, checks = 0, mapplies = 0;
-    bool converged = false, exhausted = false;
-    std::vector<double> relres_h(t), theta_h(t);
-    double max_rel = INFINITY;
-    int conv_count = 0;
-    // Rayleigh-Ritz schedule: the first check once the basis has t + b columns; later checks at
-    // the basis width where the geometric rate seen between the last two checks predicts
-    // convergence (never sooner than check_every blocks, always at the last block).
-    int next_check = t + b;
-    int prev_check_cols = 0;
-    double prev_check_rel = 0.0;
-    int rr_cols = 0;         // size of T used by the last Rayleigh-Ritz
-
-    while (true) {
-        const int j0 = cols - b;     // first column of the current block V_j
-        const double* Vj = w.V + (size_t)j0 * d;
-        // W = M V_j
-        EDA_TRY(m_apply(h, b, Vj, d, w.W, d, w.tmp, w.P, w.Q, w.part, w.pcap, s));
-        ++mapplies;
-        ++iters;
-        // CGS2 against the whole basis; A_j = rows j0..j0+b of the first coefficient block
-        double* C1 = w.C;
-        double* C2 = w.C + (size_t)m_max * tw;
-        EDA_TRY(cgs2(d, cols, b, w.V, w.W, d, C1, C2, w, s));
-        k_set_diag_block<<<ceil_div(b * b, 256), 256, 0, s>>>(w.T, m_max, j0, b, C1 + j0, cols);
-        EDA_LAUNCHED();
-        // CholQR2 of W with rank detection: W = V_{j+1} B_{j+1}
-        EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
-        EDA_TRY(cholqr_pass(d, b, w.W, d, w.R1, w.R1i, w.W1, piv_min2, h->status, w.lost, w, s));
-        int lostc = 0;
-        EDA_CUDA_TRY(cudaMemcpyAsync(&lostc, w.lost + b, sizeof(int), cudaMemcpyDeviceToHost, s));
-        EDA_CUDA_TRY(cudaStreamSynchronize(s));
-        const bool room = cols + b <= m_max;
-        if (lostc == b) {
-            exhausted = true;    // no direction outside the basis: T is exact (B_{j+1} = 0)
-        } else if (room) {
-            if (lostc > 0) {
-                // replace the lost columns by fresh random directions orthogonal to the basis
-                refills += lostc;
-                std::vector<int> lost_h(b + 1);
-                EDA_CUDA_TRY(cudaMemcpyAsync(lost_h.data(), w.lost, (b + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
-                EDA_CUDA_TRY(cudaStreamSynchronize(s));
-                for (int q = 0; q < lostc; ++q)
-                    EDA_TRY(fill_gaussian_f64(d, 1, w.W1 + (size_t)lost_h[q] * d, d, h->cfg.seed,
-                                              1000 + (uint64_t)iters * 64 + q, s));
-                EDA_TRY(cgs2(d, cols, b, w.V, w.W1, d, C2, C2 + (size_t)cols * b, w, s));
-            }
-            double* Vn = w.V + (size_t)cols * d;
-            EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
-            EDA_TRY(cholqr_pass(d, b, w.W1, d, w.R2, w.R2i, Vn, 0.0, h->status, w.lost, w, s));
-            // B_{j+1} = R2 R1
-            EDA_TRY(gemm_small_f64(false, false, b, b, b, 1.0, w.R2, b, w.R1, b, 0.0, w.Bm, b, s));
-        } else {
-            // basis full: keep B_{j+1} = R1 for the residual estimate only
-            EDA_TRY(copy_mat_f64(b, b, w.R1, b, w.Bm, b, s));
-        }
-        // Rayleigh-Ritz on the leading cols x cols block when due
-        const bool last = exhausted || !room;
-        if ((cols >= next_check && cols >= t + 1) || (last && cols >= t)) {
-            ++checks;
-            rr_cols = cols;
-            ProfScope prof("rr", s);
-            EDA_TRY(symeig_f64(cols, w.T, m_max, cols - t, cols - 1, w.theta, w.S, cols, &w.eig, h->status,
-                               h->cfg.seed + 7, 1e-7, s));
-            if (exhausted) {
-                EDA_CUDA_TRY(cudaMemsetAsync(w.relres, 0, t * sizeof(double), s));
-            } else {
-                k_ritz_residuals<<<ceil_div(t, 128), 128, 0, s>>>(t, b, w.Bm, b, w.S, cols, cols - b, w.theta,
-                                                                 w.relres);
-                EDA_LAUNCHED();
-            }
-            EDA_CUDA_TRY(cudaMemcpyAsync(relres_h.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
-            EDA_CUDA_TRY(cudaStreamSynchronize(s));
-            max_rel = 0.0;
-            conv_count = 0;
-            for (int i = 0; i < t; ++i) {
-                if (relres_h[i] <= tol) ++conv_count;
-                max_rel = std::max(max_rel, relres_h[i]);
-            }
-            if (conv_count == t) converged = true;
-            // schedule the next check
-            int gap = b * h->cfg.check_every;
-            if (prev_check_cols > 0 && max_rel > 0.0 && prev_check_rel > 0.0 && max_rel < prev_check_rel &&
-                std::isfinite(max_rel)) {
-                const double blocks = (double)(cols - prev_check_cols) / b;
-                const double rate = std::pow(max_rel / prev_check_rel, 1.0 / blocks);   // per block
-                const double need = std::log(tol / max_rel) / std::log(rate);           // blocks to go
-                if (std::isfinite(need) && need > 1.0) gap = std::max(gap, b * (int)std::floor(0.8 * need));
-            }
-            prev_check_cols = cols;
-            prev_check_rel = max_rel;
-            next_check = cols + gap;
-        }
-        if (converged || last) break;
-        // T gets the off-diagonal block B_{j+1} (rows cols.., columns j0..)
-        k_set_block<<<ceil_div(b * b, 256), 256, 0, s>>>(w.T, m_max, cols, j0, b, w.Bm, b, false);
-        EDA_LAUNCHED();
-        k_set_block<<<ceil_div(b * b, 256), 256, 0, s>>>(w.T, m_max, j0, cols, b, w.Bm, b, true);
-        EDA_LAUNCHED();
-        cols += b;
-    }
-    int st = 0;
-    EDA_CUDA_TRY(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int stw = 0;
+    EDA_CUDA_TRY(cudaMemcpyAsync(&stw, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     EDA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (st & ST_TIMEOUT) return EDA_ERR_TIMEOUT;
-    if (st & ST_NONFINITE) return EDA_ERR_NONFINITE;
-    if (rr_cols == 0) return EDA_ERR_NOT_CONVERGED;
+    if (stw & ST_TIMEOUT) return EDA_ERR_TIMEOUT;
+    if (stw & ST_NONFINITE) return EDA_ERR_NONFINITE;
 
-    // ---- Ritz vectors (descending), recovery and orthonormalisation ----
-    // Y = V_{:rr} S, columns reversed so that theta is descending
-    EDA_TRY(gemm_nn_f64(d, rr_cols, t, 1.0, w.V, d, w.S, rr_cols, 0.0, nullptr, 0, w.Xt, d, s));
-    k_reverse_cols<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, w.Xt, d, w.Ydesc, d);
+    // ---- descending order, recovery and orthonormalisation (FP64) ----
+    k_reverse_cols<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, w.Y, d, w.Y2, d);
     EDA_LAUNCHED();
     k_reverse_vec<<<ceil_div(t, 128), 128, 0, s>>>(t, w.theta, w.lamd);
     EDA_LAUNCHED();
     EDA_CUDA_TRY(cudaMemcpyAsync(lambda, w.lamd, t * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (Yout) EDA_CUDA_TRY(cudaMemcpyAsync(Yout, w.Ydesc, (size_t)d * t * 8, cudaMemcpyDeviceToDevice, s));
+    if (Yout) EDA_CUDA_TRY(cudaMemcpyAsync(Yout, w.Y2, (size_t)d * t * 8, cudaMemcpyDeviceToDevice, s));
     // x = exp(-c^2 S_W / 2) y
-    const ExpOp Wop{h->HW, h->KW, n, "exp_apply_w"};
-    EDA_TRY(exp_apply_f64(d, Wop, t, w.Ydesc, d, w.Xt, d, w.P, w.Q, w.part, w.pcap, s));
+    EDA_TRY(exp_apply<double>(d, h->HW, h->KW, n, "exp_apply_w", t, w.Y2, d, w.Xt, d, w.P, w.Q, w.part, w.pcap, s));
     // V = orth(X_t): CholQR2
     {
-        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Xt, d, w.Xt, d, 0.0, w.Rt, t, w.part, w.pcap, s));
+        double* part = static_cast<double*>(w.part);
+        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Xt, d, w.Xt, d, 0.0, w.Rt, t, part, w.pcap, s));
         EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
         EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Xt, d, w.Rti, t, 0.0, nullptr, 0, Vout, d, s));
-        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, Vout, d, Vout, d, 0.0, w.Rt, t, w.part, w.pcap, s));
+        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, Vout, d, Vout, d, 0.0, w.Rt, t, part, w.pcap, s));
         EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
         EDA_TRY(gemm_nn_f64(d, t, t, 1.0, Vout, d, w.Rti, t, 0.0, nullptr, 0, w.Xt, d, s));
         EDA_TRY(copy_mat_f64(d, t, w.Xt, d, Vout, d, s));
     }
     double true_max = -1.0;
     if (h->cfg.true_residuals) {
-        // R = M Y - Y diag(theta), in blocks of at most tw columns
+        // R = M Y - Y diag(theta) in FP64, in blocks of at most tw columns
         double* MY = w.Xt;
         for (int c0 = 0; c0 < t; c0 += tw) {
             const int cb = std::min(tw, t - c0);
-            EDA_TRY(m_apply(h, cb, w.Ydesc + (size_t)c0 * d, d, MY + (size_t)c0 * d, d, w.tmp, w.P, w.Q, w.part,
-                            w.pcap, s));
+            EDA_TRY(m_apply_t<double>(h, cb, w.Y2 + (size_t)c0 * d, d, MY + (size_t)c0 * d, d, w.tmp64, w.P, w.Q,
+                                      w.part, w.pcap, s));
         }
-        k_sub_scaled<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, MY, d, w.Ydesc, d, w.lamd);
+        k_sub_scaled<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, MY, d, w.Y2, d, w.lamd);
         EDA_LAUNCHED();
         EDA_TRY(col_norms_f64(d, t, MY, d, w.relres, s));
         std::vector<double> rn(t), lam_h(t);
@@ -373,17 +497,18 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
     EDA_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    EDA_CUDA_TRY(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaMemcpyAsync(&stw, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     EDA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (st & ST_TIMEOUT) return EDA_ERR_TIMEOUT;
-    if (st & ST_NONFINITE) return EDA_ERR_NONFINITE;
+    if (stw & ST_TIMEOUT) return EDA_ERR_TIMEOUT;
+    if (stw & ST_NONFINITE) return EDA_ERR_NONFINITE;
     if (info) {
-        info->converged = conv_count;
-        info->iters = iters;
-        info->mapplies = mapplies;
-        info->basis_cols = rr_cols;
-        info->refills = refills;
-        info->checks = checks;
+        info->converged = st.conv_count;
+        info->iters = st.iters;
+        info->mapplies = st.mapplies;
+        info->basis_cols = st.rr_cols;
+        info->refills = st.refills;
+        info->checks = st.checks;
+        info->refine_iters = refine_iters;
         info->c2 = h->c2;
         info->lmax_w = h->lmax_w;
         info->lmax_b = h->lmax_b;
@@ -396,6 +521,15 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
         }
     }
     return converged ? EDA_OK : EDA_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vout, double* lambda, double* Yout,
+               eda_solve_info* info, cudaStream_t s) {
+    if (h->cfg.prec == EDA_F64) return solve_t<double>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
+    if (h->cfg.prec == EDA_F32) return solve_t<float>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
+    return EDA_ERR_INVALID_ARG;
 }
 
 }  // namespace eda

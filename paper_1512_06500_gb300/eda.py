@@ -59,7 +59,7 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [
         ("converged", ctypes.c_int32), ("iters", ctypes.c_int32), ("mapplies", ctypes.c_int32),
         ("basis_cols", ctypes.c_int32), ("refills", ctypes.c_int32), ("checks", ctypes.c_int32),
-        ("c2", ctypes.c_double), ("lmax_w", ctypes.c_double), ("lmax_b", ctypes.c_double),
+        ("refine_iters", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("c2", ctypes.c_double), ("lmax_w", ctypes.c_double), ("lmax_b", ctypes.c_double),
         ("max_relres_est", ctypes.c_double), ("max_relres_true", ctypes.c_double),
         ("ms_solve", ctypes.c_double), ("relres", ctypes.POINTER(ctypes.c_double)),
     ]
