@@ -58,9 +58,10 @@ typedef enum {
 } eda_op;
 
 typedef struct {
-    int32_t prec;                /* eda_prec of the Krylov sweeps: EDA_F64 (plain FP64) or   */
-                                 /* EDA_F32 (single-precision H, basis and sweeps, then FP64 */
-                                 /* refinement of the Ritz vectors to tol)                   */
+    int32_t prec;                /* eda_prec of the Krylov sweeps: EDA_F64 (plain FP64),      */
+                                 /* EDA_F32 (single-precision H, basis and sweeps) or         */
+                                 /* EDA_BF16 (bf16 H on the tensor cores, single-precision    */
+                                 /* basis); the last two end with FP64 refinement to tol      */
     int32_t block_b;             /* block size b of block Lanczos (>= 1)                     */
     int32_t m_max;               /* max basis columns; <= 0 selects n + k + b (exact end)    */
     int32_t check_every;         /* Rayleigh-Ritz convergence check every this many blocks   */
@@ -117,7 +118,10 @@ int eda_build_from_factors(const double* HW, int64_t n, const double* HB, int64_
 
 /* Y = exp(alpha H H^T) X for op SW (H = H_W) or SB (H = H_B), or Y = M X for
  * op M (Theorem 3.1; Algorithm 2 steps 6L-12L for M). X, Y: d x b, leading
- * dimension ldx, io_dtype EDA_F64. X and Y must not overlap. */
+ * dimension ldx. io_dtype EDA_F64 uses the FP64 factors (any handle, any alpha);
+ * io_dtype EDA_F32 uses the handle's working precision (prec EDA_F32: single-
+ * precision sweeps; prec EDA_BF16: bf16 H on the tensor cores) and accepts only the
+ * stored alphas (-c^2/2 for SW, c^2 for SB). X and Y must not overlap. */
 int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y,
                   int64_t ldx, int32_t b, int32_t io_dtype, void* stream);
 

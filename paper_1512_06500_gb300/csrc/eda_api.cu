@@ -38,6 +38,8 @@ int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* 
                eda_solve_info* info, cudaStream_t s);
 int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t ldy, double* tmp, double* P,
             double* Q, double* partial, size_t partial_cap, cudaStream_t s);
+int m_apply_f32(eda_ctx* h, int b, const float* X, int64_t ldx, float* Y, int64_t ldy, float* tmp, double* P,
+                double* Q, double* partial, size_t partial_cap, cudaStream_t s);
 
 namespace {
 
@@ -169,6 +171,20 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         h->HB32 = reinterpret_cast<float*>(static_cast<char*>(p) + bw);
         EDA_TRY((copy_mat<double, float>(d, n, h->HW, d, h->HW32, d, s)));
         EDA_TRY((copy_mat<double, float>(d, k, h->HB, d, h->HB32, d, s)));
+    } else if (h->cfg.prec == EDA_BF16) {
+        // bf16 H_W and H_B in the column-major (sweep 1) and row-major (sweep 2) tensor-core layouts
+        const size_t sz[4] = {align256((size_t)tc_pad_rows(d) * n * 2), align256((size_t)d * tc_pad_cols(n) * 2),
+                              align256((size_t)tc_pad_rows(d) * k * 2), align256((size_t)d * tc_pad_cols(k) * 2)};
+        void* p = nullptr;
+        EDA_CUDA_TRY(cudaMalloc(&p, sz[0] + sz[1] + sz[2] + sz[3]));
+        h->block32 = p;
+        char* c = static_cast<char*>(p);
+        __nv_bfloat16* b0 = reinterpret_cast<__nv_bfloat16*>(c);
+        __nv_bfloat16* b1 = reinterpret_cast<__nv_bfloat16*>(c + sz[0]);
+        __nv_bfloat16* b2 = reinterpret_cast<__nv_bfloat16*>(c + sz[0] + sz[1]);
+        __nv_bfloat16* b3 = reinterpret_cast<__nv_bfloat16*>(c + sz[0] + sz[1] + sz[2]);
+        EDA_TRY(tc_factor_make(h->HW, d, n, b0, b1, &h->tcW, s));
+        EDA_TRY(tc_factor_make(h->HB, d, k, b2, b3, &h->tcB, s));
     }
     Arena scratch{static_cast<char*>(h->block), h->block_bytes, h->build_arena_off};
     const size_t N = std::max<int64_t>(n, k);
@@ -212,7 +228,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
 
 bool valid_cfg(const eda_config& c) {
     return c.block_b >= 1 && c.check_every >= 1 && (c.c2 > 0.0 || c.tau > 0.0) &&
-           (c.prec == EDA_F64 || c.prec == EDA_F32);
+           (c.prec == EDA_F64 || c.prec == EDA_F32 || c.prec == EDA_BF16);
 }
 
 }  // namespace
@@ -306,11 +322,14 @@ int eda_build_from_factors(const double* HW, int64_t n, const double* HB, int64_
 
 int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y, int64_t ldx, int32_t b,
                   int32_t io_dtype, void* stream) {
-    if (!h || !X || !Y || b < 1 || ldx < h->d || io_dtype != EDA_F64) return EDA_ERR_INVALID_ARG;
+    if (!h || !X || !Y || b < 1 || ldx < h->d) return EDA_ERR_INVALID_ARG;
+    if (io_dtype != EDA_F64 && !(io_dtype == EDA_F32 && (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16)))
+        return EDA_ERR_INVALID_ARG;
+    const size_t esz = io_dtype == EDA_F64 ? sizeof(double) : sizeof(float);
     if (op != EDA_OP_SW && op != EDA_OP_SB && op != EDA_OP_M) return EDA_ERR_INVALID_ARG;
     const char* xb = static_cast<const char*>(X);
     const char* yb = static_cast<const char*>(Y);
-    const size_t span = ((size_t)(b - 1) * ldx + h->d) * sizeof(double);
+    const size_t span = ((size_t)(b - 1) * ldx + h->d) * esz;
     if (xb < yb + span && yb < xb + span) return EDA_ERR_INVALID_ARG;   // X and Y overlap
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t d = h->d;
@@ -326,6 +345,20 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
     double* tmp = a.take<double>((size_t)d * b);
     const double* x = static_cast<const double*>(X);
     double* y = static_cast<double*>(Y);
+    if (io_dtype == EDA_F32) {
+        const float* xf = static_cast<const float*>(X);
+        float* yf = static_cast<float*>(Y);
+        if (op == EDA_OP_M) return m_apply_f32(h, b, xf, ldx, yf, ldx, reinterpret_cast<float*>(tmp), P, Q, part, pcap, s);
+        const bool isW = (op == EDA_OP_SW);
+        const int m = isW ? (int)h->n : h->k;
+        const double* K = isW ? h->KW : h->KB;
+        if (alpha != (isW ? -0.5 * h->c2 : h->c2)) return EDA_ERR_INVALID_ARG;   // stored operators only
+        if (h->cfg.prec == EDA_BF16)
+            return exp_apply_tc(isW ? h->tcW : h->tcB, K, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf, ldx, P,
+                                Q, part, pcap, h->status, s);
+        return exp_apply<float>(d, isW ? h->HW32 : h->HB32, K, m, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf,
+                                ldx, P, Q, part, pcap, s);
+    }
     if (op == EDA_OP_M) return m_apply(h, b, x, ldx, y, ldx, tmp, P, Q, part, pcap, s);
     // K(alpha) for the requested alpha: rebuild from the stored eigenpairs when alpha differs
     const bool isW = (op == EDA_OP_SW);

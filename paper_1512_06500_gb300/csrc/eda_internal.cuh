@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
 #include <vector>
@@ -186,6 +187,22 @@ int exp_apply_f64(int64_t d, const ExpOp& op, int b, const double* X, int64_t ld
                   int64_t ldy, double* P, double* Q, double* partial, size_t partial_cap,
                   cudaStream_t s);
 
+// ---------------------------------------------------------------- tensor-core exp-apply (bf16 H)
+struct TcFactor {
+    const __nv_bfloat16* Hcm = nullptr;   // column-major, leading dimension ldh (>= d, zero padded)
+    const __nv_bfloat16* Hrm = nullptr;   // row-major d x ldm (zero padded columns)
+    int64_t d = 0, ldh = 0;
+    int m = 0, ldm = 0;
+};
+inline int64_t tc_pad_rows(int64_t d) { return (d + 63) / 64 * 64; }
+inline int tc_pad_cols(int m) { return (m + 63) / 64 * 64; }
+// Convert an FP64 factor H (d x m, column-major, ld d) to the two bf16 layouts of the kernels.
+int tc_factor_make(const double* H, int64_t d, int m, __nv_bfloat16* Hcm, __nv_bfloat16* Hrm, TcFactor* f,
+                   cudaStream_t s);
+// Y = X + H K (H^T X) with bf16 H on the tensor cores; X, Y single precision; P, Q double.
+int exp_apply_tc(const TcFactor& f, const double* K, const char* tag, int b, const float* X, int64_t ldx, float* Y,
+                 int64_t ldy, double* P, double* Q, void* partial, size_t partial_cap, int* status, cudaStream_t s);
+
 }  // namespace eda
 
 // The handle.
@@ -204,9 +221,11 @@ struct eda_ctx {
     double *evals_w = nullptr, *evals_b = nullptr;
     double *evecs_w = nullptr, *evecs_b = nullptr;
     double *KW = nullptr, *KB = nullptr;   // K(-c^2/2) for H_W, K(c^2) for H_B
-    // single-precision copies of H_W, H_B for the mixed-precision solver (prec = EDA_F32)
+    // single-precision copies of H_W, H_B for the mixed-precision solver (prec = EDA_F32), and
+    // bf16 copies in the two tensor-core layouts (prec = EDA_BF16)
     void* block32 = nullptr;
     float *HW32 = nullptr, *HB32 = nullptr;
+    eda::TcFactor tcW, tcB;
     int* status = nullptr;                 // device status word
     eda::GridBarrier bar{};
     size_t build_arena_off = 0;            // start of the build scratch inside `block`

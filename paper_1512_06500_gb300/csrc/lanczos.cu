@@ -143,6 +143,17 @@ int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* 
     const T* HW = HStore<T>::W(h);
     const T* HB = HStore<T>::B(h);
     const int n = (int)h->n;
+    if (std::is_same<T, float>::value && h->cfg.prec == EDA_BF16) {
+        // bf16 H on the tensor cores (the basis stays single precision)
+        const float* Xf = reinterpret_cast<const float*>(X);
+        float* Yf = reinterpret_cast<float*>(Y);
+        float* tf = reinterpret_cast<float*>(tmp);
+        EDA_TRY(exp_apply_tc(h->tcW, h->KW, "exp_apply_w", b, Xf, ldx, tf, d, P, Q, partial, partial_cap, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcB, h->KB, "exp_apply_b", b, tf, d, Yf, ldy, P, Q, partial, partial_cap, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcW, h->KW, "exp_apply_w", b, Yf, ldy, tf, d, P, Q, partial, partial_cap, h->status, s));
+        EDA_TRY((copy_mat<float, float>(d, b, tf, d, Yf, ldy, s)));
+        return EDA_OK;
+    }
     EDA_TRY(exp_apply<T>(d, HW, h->KW, n, "exp_apply_w", b, X, ldx, tmp, d, P, Q, partial, partial_cap, s));
     EDA_TRY(exp_apply<T>(d, HB, h->KB, h->k, "exp_apply_b", b, tmp, d, Y, ldy, P, Q, partial, partial_cap, s));
     EDA_TRY(exp_apply<T>(d, HW, h->KW, n, "exp_apply_w", b, Y, ldy, tmp, d, P, Q, partial, partial_cap, s));
@@ -153,6 +164,11 @@ int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* 
 int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t ldy, double* tmp, double* P,
             double* Q, double* partial, size_t partial_cap, cudaStream_t s) {
     return m_apply_t<double>(h, b, X, ldx, Y, ldy, tmp, P, Q, partial, partial_cap, s);
+}
+
+int m_apply_f32(eda_ctx* h, int b, const float* X, int64_t ldx, float* Y, int64_t ldy, float* tmp, double* P,
+                double* Q, double* partial, size_t partial_cap, cudaStream_t s) {
+    return m_apply_t<float>(h, b, X, ldx, Y, ldy, tmp, P, Q, partial, partial_cap, s);
 }
 
 namespace {
@@ -528,7 +544,8 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
 int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vout, double* lambda, double* Yout,
                eda_solve_info* info, cudaStream_t s) {
     if (h->cfg.prec == EDA_F64) return solve_t<double>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
-    if (h->cfg.prec == EDA_F32) return solve_t<float>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
+    if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16)
+        return solve_t<float>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
     return EDA_ERR_INVALID_ARG;
 }
 

@@ -199,14 +199,18 @@ class Handle:
         self.close()
 
     def apply_exp(self, op, X, alpha=0.0, out=None, stream=None):
-        """Y = exp(alpha H H^T) X (op SW/SB) or Y = M X (op M); X: (b, d) float64 CUDA tensor."""
-        _need_cuda(X, "X", torch.float64)
+        """Y = exp(alpha H H^T) X (op SW/SB) or Y = M X (op M); X: (b, d) CUDA tensor.
+
+        float64 X uses the FP64 factors; float32 X uses the handle's working precision
+        (single-precision sweeps, or bf16 H on the tensor cores).
+        """
+        _need_cuda(X, "X")
         b, d = X.shape
         if d != self.d:
             raise ValueError("X has the wrong dimension")
         Y = out if out is not None else torch.empty_like(X)
-        _check(load().eda_apply_exp(self._h, op, float(alpha), _ptr(X), _ptr(Y), d, b, EDA_F64, _stream(stream)),
-               "eda_apply_exp")
+        _check(load().eda_apply_exp(self._h, op, float(alpha), _ptr(X), _ptr(Y), d, b, _dtype_code(X),
+                                    _stream(stream)), "eda_apply_exp")
         return Y
 
     def solve(self, t, tol, V0=None, want_y=False, relres=False, stream=None, check=True):

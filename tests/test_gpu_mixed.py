@@ -66,3 +66,52 @@ def test_mixed_matches_fp64_path_small(eda):
     _, lam32, V32, info, _, _ = _run(eda, p, 5, 2, 8.0, 1e-10, eda.EDA_F32)
     assert np.max(np.abs(lam32 - lam64) / lam64) <= 1e-10
     assert O.sin_angle(V64, V32) <= 1e-8
+
+
+# ----------------------------------------------------------------- bf16 tensor-core exp-apply
+
+def _bf16_round(a):
+    """float64 -> float32 -> bfloat16 (round to nearest even) -> float64, as the kernels convert H."""
+    t = torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16)
+    return t.to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("d,k,nj,b", [(4096, 40, 5, 8), (1000, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 16), (2048, 20, 7, 32),
+                                      (777, 5, 3, 40)])
+def test_tc_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
+    # The tensor-core product uses bf16(H) exactly and hi + lo bf16 pairs for X and Q, accumulating in
+    # FP32: against an FP64 evaluation of X + bf16(H) K (bf16(H)^T X) the error is the hi + lo rounding
+    # (2^-17 relative) plus FP32 accumulation, so 1e-4 relative is a sharp bound that any operand or
+    # layout mistake (a transposed core matrix, a wrong K step) violates by orders of magnitude.
+    p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=500 + d)
+    cfg = eda.config(prec=eda.EDA_BF16, block_b=min(b, 16), tau=10.0)
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        f = h.factors()
+        rng = np.random.default_rng(d + b)
+        Xb = rng.standard_normal((b, d)).astype(np.float32)
+        for op, H, K, alpha in ((eda.OP_SW, f["HW"], f["KW"], -0.5 * h.c2), (eda.OP_SB, f["HB"], f["KB"], h.c2)):
+            Y = h.apply_exp(op, _dev(Xb), alpha=alpha).cpu().numpy().astype(np.float64)
+            Hb = _bf16_round(H.cpu().numpy())          # (m, d) rows = columns of H
+            Kn = K.cpu().numpy()
+            X64 = Xb.astype(np.float64)
+            ref = X64 + ((Hb.T @ (Kn @ (Hb @ X64.T))).T)
+            err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+            assert err <= 1e-4, (op, err)
+            # and against the exact FP64 operator: the bf16 rounding of H (2^-9) sets the scale
+            exact = X64 + ((H.cpu().numpy().T @ (Kn @ (H.cpu().numpy() @ X64.T))).T)
+            assert np.linalg.norm(Y - exact) / np.linalg.norm(exact) <= 2e-2
+
+
+@pytest.mark.parametrize("name,tol,eig_tol", [("d4096_k40", 1e-8, 1e-6), ("d16384_k100", 1e-8, 1e-6)])
+def test_bf16_tensor_core_solver(eda, name, tol, eig_tol):
+    c = synth.CONFIGS[name]
+    p = synth.config_problem(name)
+    c2, lam, V, info, Ptr, Pte = _run(eda, p, c["t"], c["b"], c["tau"], tol, eda.EDA_BF16)
+    assert info["refine_iters"] >= 1
+    assert info["max_relres_true"] <= 10 * tol
+    ref = O.eda(p.X, p.labels, p.k, c["t"], c2=c2, tier="projected")
+    rel = np.abs(lam - ref["lam_t"]) / ref["lam_t"]
+    assert rel.max() <= eig_tol, rel.max()
+    lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
+    lab_o, _, _ = O.nn_classify(O.project(ref["V"], p.X), p.labels, O.project(ref["V"], p.Xtest))
+    assert np.array_equal(lab_g, lab_o)
