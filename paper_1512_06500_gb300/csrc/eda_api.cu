@@ -171,20 +171,6 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         h->HB32 = reinterpret_cast<float*>(static_cast<char*>(p) + bw);
         EDA_TRY((copy_mat<double, float>(d, n, h->HW, d, h->HW32, d, s)));
         EDA_TRY((copy_mat<double, float>(d, k, h->HB, d, h->HB32, d, s)));
-    } else if (h->cfg.prec == EDA_BF16) {
-        // bf16 H_W and H_B in the column-major (sweep 1) and row-major (sweep 2) tensor-core layouts
-        const size_t sz[4] = {align256((size_t)tc_pad_rows(d) * n * 2), align256((size_t)d * tc_pad_cols(n) * 2),
-                              align256((size_t)tc_pad_rows(d) * k * 2), align256((size_t)d * tc_pad_cols(k) * 2)};
-        void* p = nullptr;
-        EDA_CUDA_TRY(cudaMalloc(&p, sz[0] + sz[1] + sz[2] + sz[3]));
-        h->block32 = p;
-        char* c = static_cast<char*>(p);
-        __nv_bfloat16* b0 = reinterpret_cast<__nv_bfloat16*>(c);
-        __nv_bfloat16* b1 = reinterpret_cast<__nv_bfloat16*>(c + sz[0]);
-        __nv_bfloat16* b2 = reinterpret_cast<__nv_bfloat16*>(c + sz[0] + sz[1]);
-        __nv_bfloat16* b3 = reinterpret_cast<__nv_bfloat16*>(c + sz[0] + sz[1] + sz[2]);
-        EDA_TRY(tc_factor_make(h->HW, d, n, b0, b1, &h->tcW, s));
-        EDA_TRY(tc_factor_make(h->HB, d, k, b2, b3, &h->tcB, s));
     }
     Arena scratch{static_cast<char*>(h->block), h->block_bytes, h->build_arena_off};
     const size_t N = std::max<int64_t>(n, k);
@@ -221,6 +207,39 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     if (!tmp) return EDA_ERR_OOM;
     EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
     EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
+    if (h->cfg.prec == EDA_BF16) {
+        // bf16 H_W, H_B in the column-major (sweep 1) and row-major (sweep 2) tensor-core layouts,
+        // single-precision K, and the staging buffers of X and Q with their tensor maps
+        const int64_t ldh = tc_pad_rows(d);
+        const int ldq = std::max(tc_pad_cols(n), tc_pad_cols(k));
+        const size_t sz[10] = {align256((size_t)ldh * n * 2), align256((size_t)d * tc_pad_cols(n) * 2),
+                               align256((size_t)ldh * k * 2), align256((size_t)d * tc_pad_cols(k) * 2),
+                               align256((size_t)n * n * 4),  align256((size_t)k * k * 4),
+                               align256((size_t)ldh * 32 * 2) * 2, align256((size_t)ldq * 32 * 2) * 2,
+                               align256((size_t)std::max(n, k) * 32 * 4), 0};
+        size_t tot = 0;
+        for (size_t v : sz) tot += v;
+        void* p = nullptr;
+        EDA_CUDA_TRY(cudaMalloc(&p, tot));
+        h->block32 = p;
+        char* c = static_cast<char*>(p);
+        auto bf = [&](size_t off) { return reinterpret_cast<__nv_bfloat16*>(c + off); };
+        size_t off = 0;
+        __nv_bfloat16* HcW = bf(off); off += sz[0];
+        __nv_bfloat16* HrW = bf(off); off += sz[1];
+        __nv_bfloat16* HcB = bf(off); off += sz[2];
+        __nv_bfloat16* HrB = bf(off); off += sz[3];
+        float* KW32 = reinterpret_cast<float*>(c + off); off += sz[4];
+        float* KB32 = reinterpret_cast<float*>(c + off); off += sz[5];
+        __nv_bfloat16* Xhi = bf(off);
+        __nv_bfloat16* Xlo = bf(off + sz[6] / 2); off += sz[6];
+        __nv_bfloat16* Qhi = bf(off);
+        __nv_bfloat16* Qlo = bf(off + sz[7] / 2); off += sz[7];
+        float* P = reinterpret_cast<float*>(c + off);
+        EDA_TRY(tc_factor_make(h->HW, d, n, h->KW, HcW, HrW, KW32, &h->tcW, s));
+        EDA_TRY(tc_factor_make(h->HB, d, k, h->KB, HcB, HrB, KB32, &h->tcB, s));
+        EDA_TRY(tc_buffers_make(ldh, ldq, Xhi, Xlo, Qhi, Qlo, P, &h->tcbuf));
+    }
     int st = 0;
     EDA_TRY(read_status(h, s, &st));
     return status_to_code(st);
@@ -354,8 +373,8 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
         const double* K = isW ? h->KW : h->KB;
         if (alpha != (isW ? -0.5 * h->c2 : h->c2)) return EDA_ERR_INVALID_ARG;   // stored operators only
         if (h->cfg.prec == EDA_BF16)
-            return exp_apply_tc(isW ? h->tcW : h->tcB, K, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf, ldx, P,
-                                Q, part, pcap, h->status, s);
+            return exp_apply_tc(isW ? h->tcW : h->tcB, h->tcbuf, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf,
+                                ldx, part, pcap, h->status, s);
         return exp_apply<float>(d, isW ? h->HW32 : h->HB32, K, m, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf,
                                 ldx, P, Q, part, pcap, s);
     }

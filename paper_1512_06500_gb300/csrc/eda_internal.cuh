@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of the EDA library.
 #pragma once
 
+#include <cuda.h>            // CUtensorMap (types only; the encoder is looked up at run time)
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -188,20 +189,40 @@ int exp_apply_f64(int64_t d, const ExpOp& op, int b, const double* X, int64_t ld
                   cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core exp-apply (bf16 H)
+// One factor H (d x m) in the two bf16 layouts the tensor-core sweeps read, with its tensor maps.
 struct TcFactor {
+    CUtensorMap mapA1;                    // Hcm: inner K = ldh, outer m, box 8 x 128
+    CUtensorMap mapA2;                    // Hrm: inner K = ldm, outer d, box 8 x 128
+    CUtensorMap mapA1_3, mapA2_3;         // the same as 3-D views, one box per 64-element K stage
+    bool maps3d = false;
     const __nv_bfloat16* Hcm = nullptr;   // column-major, leading dimension ldh (>= d, zero padded)
     const __nv_bfloat16* Hrm = nullptr;   // row-major d x ldm (zero padded columns)
+    const float* K32 = nullptr;           // K in single precision (m x m)
     int64_t d = 0, ldh = 0;
     int m = 0, ldm = 0;
 };
+// Per-handle staging buffers of the sweeps (bf16 hi/lo pairs of X and Q) with their tensor maps,
+// for N = 16 ([0]) and N = 32 ([1]) column boxes.
+struct TcBuffers {
+    CUtensorMap mapXh[2], mapXl[2], mapQh[2], mapQl[2];
+    CUtensorMap mapXh3[2], mapXl3[2], mapQh3[2], mapQl3[2];
+    bool maps3d = false;
+    __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Qhi = nullptr, *Qlo = nullptr;
+    float* P = nullptr;                   // m x 32 single-precision H^T X
+    int64_t ldh = 0;
+    int ldq = 0;
+};
 inline int64_t tc_pad_rows(int64_t d) { return (d + 63) / 64 * 64; }
 inline int tc_pad_cols(int m) { return (m + 63) / 64 * 64; }
-// Convert an FP64 factor H (d x m, column-major, ld d) to the two bf16 layouts of the kernels.
-int tc_factor_make(const double* H, int64_t d, int m, __nv_bfloat16* Hcm, __nv_bfloat16* Hrm, TcFactor* f,
-                   cudaStream_t s);
-// Y = X + H K (H^T X) with bf16 H on the tensor cores; X, Y single precision; P, Q double.
-int exp_apply_tc(const TcFactor& f, const double* K, const char* tag, int b, const float* X, int64_t ldx, float* Y,
-                 int64_t ldy, double* P, double* Q, void* partial, size_t partial_cap, int* status, cudaStream_t s);
+// Convert an FP64 factor H (d x m, ld d) and its K (m x m) to the tensor-core layouts.
+int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bfloat16* Hcm, __nv_bfloat16* Hrm,
+                   float* K32, TcFactor* f, cudaStream_t s);
+int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, __nv_bfloat16* Qhi,
+                    __nv_bfloat16* Qlo, float* P, TcBuffers* b);
+// Y = X + H K (H^T X) with bf16 H on the tensor cores; X, Y single precision. partial holds
+// splits * m * min(b, 32) floats.
+int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
+                 float* Y, int64_t ldy, void* partial, size_t partial_cap, int* status, cudaStream_t s);
 
 }  // namespace eda
 
@@ -226,6 +247,7 @@ struct eda_ctx {
     void* block32 = nullptr;
     float *HW32 = nullptr, *HB32 = nullptr;
     eda::TcFactor tcW, tcB;
+    eda::TcBuffers tcbuf;
     int* status = nullptr;                 // device status word
     eda::GridBarrier bar{};
     size_t build_arena_off = 0;            // start of the build scratch inside `block`

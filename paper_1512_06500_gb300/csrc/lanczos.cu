@@ -148,9 +148,9 @@ int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* 
         const float* Xf = reinterpret_cast<const float*>(X);
         float* Yf = reinterpret_cast<float*>(Y);
         float* tf = reinterpret_cast<float*>(tmp);
-        EDA_TRY(exp_apply_tc(h->tcW, h->KW, "exp_apply_w", b, Xf, ldx, tf, d, P, Q, partial, partial_cap, h->status, s));
-        EDA_TRY(exp_apply_tc(h->tcB, h->KB, "exp_apply_b", b, tf, d, Yf, ldy, P, Q, partial, partial_cap, h->status, s));
-        EDA_TRY(exp_apply_tc(h->tcW, h->KW, "exp_apply_w", b, Yf, ldy, tf, d, P, Q, partial, partial_cap, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Xf, ldx, tf, d, partial, partial_cap, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcB, h->tcbuf, "exp_apply_b", b, tf, d, Yf, ldy, partial, partial_cap, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Yf, ldy, tf, d, partial, partial_cap, h->status, s));
         EDA_TRY((copy_mat<float, float>(d, b, tf, d, Yf, ldy, s)));
         return EDA_OK;
     }
