@@ -208,37 +208,33 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
     EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
     if (h->cfg.prec == EDA_BF16) {
-        // bf16 H_W, H_B in the column-major (sweep 1) and row-major (sweep 2) tensor-core layouts,
-        // single-precision K, and the staging buffers of X and Q with their tensor maps
+        // bf16 H_W, H_B column-major (sweep 1), bf16 H K row-major (sweep 2), and the staging
+        // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)
         const int64_t ldh = tc_pad_rows(d);
         const int ldq = std::max(tc_pad_cols(n), tc_pad_cols(k));
-        const size_t sz[10] = {align256((size_t)ldh * n * 2), align256((size_t)d * tc_pad_cols(n) * 2),
-                               align256((size_t)ldh * k * 2), align256((size_t)d * tc_pad_cols(k) * 2),
-                               align256((size_t)n * n * 4),  align256((size_t)k * k * 4),
-                               align256((size_t)ldh * 32 * 2) * 2, align256((size_t)ldq * 32 * 2) * 2,
-                               align256((size_t)std::max(n, k) * 32 * 4), 0};
+        const size_t sz[6] = {align256((size_t)ldh * n * 2), align256((size_t)d * tc_pad_cols(n) * 2),
+                              align256((size_t)ldh * k * 2), align256((size_t)d * tc_pad_cols(k) * 2),
+                              align256((size_t)ldh * 32 * 2) * 2, align256((size_t)ldq * 32 * 2) * 2};
         size_t tot = 0;
         for (size_t v : sz) tot += v;
         void* p = nullptr;
         EDA_CUDA_TRY(cudaMalloc(&p, tot));
         h->block32 = p;
+        EDA_CUDA_TRY(cudaMemsetAsync(p, 0, tot, s));
         char* c = static_cast<char*>(p);
         auto bf = [&](size_t off) { return reinterpret_cast<__nv_bfloat16*>(c + off); };
         size_t off = 0;
         __nv_bfloat16* HcW = bf(off); off += sz[0];
-        __nv_bfloat16* HrW = bf(off); off += sz[1];
+        __nv_bfloat16* HKW = bf(off); off += sz[1];
         __nv_bfloat16* HcB = bf(off); off += sz[2];
-        __nv_bfloat16* HrB = bf(off); off += sz[3];
-        float* KW32 = reinterpret_cast<float*>(c + off); off += sz[4];
-        float* KB32 = reinterpret_cast<float*>(c + off); off += sz[5];
+        __nv_bfloat16* HKB = bf(off); off += sz[3];
         __nv_bfloat16* Xhi = bf(off);
-        __nv_bfloat16* Xlo = bf(off + sz[6] / 2); off += sz[6];
+        __nv_bfloat16* Xlo = bf(off + sz[4] / 2); off += sz[4];
         __nv_bfloat16* Qhi = bf(off);
-        __nv_bfloat16* Qlo = bf(off + sz[7] / 2); off += sz[7];
-        float* P = reinterpret_cast<float*>(c + off);
-        EDA_TRY(tc_factor_make(h->HW, d, n, h->KW, HcW, HrW, KW32, &h->tcW, s));
-        EDA_TRY(tc_factor_make(h->HB, d, k, h->KB, HcB, HrB, KB32, &h->tcB, s));
-        EDA_TRY(tc_buffers_make(ldh, ldq, Xhi, Xlo, Qhi, Qlo, P, &h->tcbuf));
+        __nv_bfloat16* Qlo = bf(off + sz[5] / 2); off += sz[5];
+        EDA_TRY(tc_factor_make(h->HW, d, n, h->KW, HcW, HKW, &h->tcW, h->status, s));
+        EDA_TRY(tc_factor_make(h->HB, d, k, h->KB, HcB, HKB, &h->tcB, h->status, s));
+        EDA_TRY(tc_buffers_make(ldh, ldq, Xhi, Xlo, Qhi, Qlo, &h->tcbuf));
     }
     int st = 0;
     EDA_TRY(read_status(h, s, &st));
@@ -374,7 +370,7 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
         if (alpha != (isW ? -0.5 * h->c2 : h->c2)) return EDA_ERR_INVALID_ARG;   // stored operators only
         if (h->cfg.prec == EDA_BF16)
             return exp_apply_tc(isW ? h->tcW : h->tcB, h->tcbuf, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf,
-                                ldx, part, pcap, h->status, s);
+                                ldx, part, pcap, 0, h->status, s);
         return exp_apply<float>(d, isW ? h->HW32 : h->HB32, K, m, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf,
                                 ldx, P, Q, part, pcap, s);
     }

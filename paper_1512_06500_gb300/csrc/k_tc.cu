@@ -1,17 +1,22 @@
 // Tensor-core exp-vector product for H stored in bfloat16 (5th-generation tensor cores: tcgen05.mma
-// with the accumulator in tensor memory, operands brought in by the Tensor Memory Accelerator):
+// with the accumulator in tensor memory, operands brought in by the Tensor Memory Accelerator).
+// Theorem 3.1 gives exp(alpha H H^T) X = X + (H K) (H^T X) with K = alpha phi(alpha H^T H); the
+// d x m product H K is formed once per factor (it is itself a sweep-2 product, below), so one
+// exp-apply is
 //     split     X -> (Xhi, Xlo) bf16 pair          (hi = bf16(x), lo = bf16(x - hi))
 //     sweep 1   P = H^T X      M = m (columns of H), N = b, K = d, split over d across CTAs
-//     small     Q = K P        (FP32, written directly as a bf16 hi/lo pair)
-//     sweep 2   Y = X + H Q    M = d, N = b, K = m, from a row-major bf16 copy of H
+//     reduce    P = sum of the split partials in FP64, written as a bf16 (hi, lo) pair
+//     sweep 2   Y = X + (H K) P   M = d, N = b, K = m, from a row-major bf16 copy of H K
 // Every product is bf16 x (bf16 hi + bf16 lo) with FP32 accumulation, so the error is set by the
-// bf16 rounding of H; split sums are added in FP64.
+// bf16 rounding of H and of H K; split sums are added in FP64. Sweep 2 can also write the bf16 pair
+// of Y, which is the split step of the next exp-apply in a chain, and Y may alias X.
 //
-// Each CTA runs a 4-stage shared-memory ring: one thread issues cp.async.bulk.tensor loads (a box of
-// 8 elements x rows lands exactly in the no-swizzle K-major core-matrix layout: row r of 16-byte
-// chunk c at c * rows * 16 + r * 16), one thread issues tcgen05.mma (4 K-steps of 16, hi and lo per
-// step) and commits each stage to the stage's "empty" mbarrier; the four warps read the 128 x N FP32
-// accumulator out of tensor memory at the end. Every wait is bounded (ST_TIMEOUT on give-up).
+// Each CTA runs a 4-stage shared-memory ring: one thread issues cp.async.bulk.tensor loads of
+// 64-element (128-byte) K slices in the 128-byte-swizzled layout (row r of a tile at r * 128 bytes,
+// its 16-byte chunk c at chunk c ^ (r mod 8)); one thread issues tcgen05.mma (4 K-steps of 16,
+// hi and lo per step, each K-step a 32-byte advance of the descriptor start inside the swizzle
+// atom) and commits each stage to the stage's "empty" mbarrier; the four warps read the 128 x N
+// FP32 accumulator out of tensor memory at the end. Every wait is bounded (ST_TIMEOUT on give-up).
 #include "eda_internal.cuh"
 
 #include <cuda.h>
@@ -85,13 +90,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "l"(map), "r"(x), "r"(y), "r"(smem_u32(mbar))
         : "memory");
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
-        : "memory");
-}
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -104,14 +102,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension byte offset (between
-// core matrices along K), stride-dimension byte offset (between 8-row groups along M/N), version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte-swizzled layout: start
+// address, leading-dimension offset (unused inside one swizzle atom, encoded 1), stride-dimension
+// offset 1024 bytes (between 8-row groups), version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 // Instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, shape M x N.
@@ -119,26 +119,38 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The ring; every tile starts on a 1024-byte boundary (the swizzle pattern repeats every 8 rows of
+// 128 bytes), which holds because the struct is placed on such a boundary and every member size is a
+// multiple of 1024.
 template <int N>
 struct TcRing {
-    __nv_bfloat16 A[TC_STAGES][TC_M * TC_KS];   // 16 KB per stage
-    __nv_bfloat16 Bh[TC_STAGES][N * TC_KS];
+    __nv_bfloat16 A[TC_STAGES][TC_M * TC_KS];   // 16 KB per stage: 128 rows x 128 bytes
+    __nv_bfloat16 Bh[TC_STAGES][N * TC_KS];     // N rows x 128 bytes
     __nv_bfloat16 Bl[TC_STAGES][N * TC_KS];
     uint64_t full[TC_STAGES];
     uint64_t empty[TC_STAGES];
     uint64_t done;
     uint32_t tbase;
 };
+template <int N>
+constexpr size_t tc_smem_bytes() {
+    return sizeof(TcRing<N>) + 1024;
+}
+template <int N>
+__device__ __forceinline__ TcRing<N>& tc_ring(unsigned char* raw) {
+    const uint32_t mis = smem_u32(raw) & 1023u;
+    return *reinterpret_cast<TcRing<N>*>(raw + ((1024u - mis) & 1023u));
+}
 
 // Main loop shared by both sweeps: K stages [0, nst) starting at element k_begin; A rows from
 // a_row0 (tensor map tmA), B rows 0..N-1 (tmBh, tmBl, same K coordinates). Returns false on timeout.
 template <int N>
 __device__ bool tc_mainloop(TcRing<N>& sm, const CUtensorMap* tmA, const CUtensorMap* tmBh, const CUtensorMap* tmBl,
-                            int a_row0, int k_begin, int nst, uint32_t tmem, int* status, bool maps3d) {
+                            int a_row0, int k_begin, int nst, uint32_t tmem, int* status) {
     const int tid = threadIdx.x;
     bool ok = true;
     if (tid == 0) {
-        // producer: one thread issues all bulk tensor loads
+        // producer: one thread issues all bulk tensor loads (three boxes per stage)
         constexpr uint32_t bytes = TC_M * TC_KS * 2 + 2 * N * TC_KS * 2;
         for (int s = 0; s < nst && ok; ++s) {
             const int slot = s % TC_STAGES;
@@ -146,26 +158,12 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const CUtensorMap* tmA, const CUtenso
             if (!ok) break;
             mbar_expect_tx(&sm.full[slot], bytes);
             const int k0 = k_begin + s * TC_KS;
-            char* A = reinterpret_cast<char*>(sm.A[slot]);
-            char* Bh = reinterpret_cast<char*>(sm.Bh[slot]);
-            char* Bl = reinterpret_cast<char*>(sm.Bl[slot]);
-            if (maps3d) {
-                // (element-in-chunk, row, chunk) boxes land directly in the core-matrix layout
-                tma_load_3d(A, tmA, 0, a_row0, k0 / 8, &sm.full[slot]);
-                tma_load_3d(Bh, tmBh, 0, 0, k0 / 8, &sm.full[slot]);
-                tma_load_3d(Bl, tmBl, 0, 0, k0 / 8, &sm.full[slot]);
-            } else {
-#pragma unroll
-                for (int c = 0; c < TC_KS / 8; ++c) {
-                    tma_load_2d(A + c * TC_M * 16, tmA, k0 + 8 * c, a_row0, &sm.full[slot]);
-                    tma_load_2d(Bh + c * N * 16, tmBh, k0 + 8 * c, 0, &sm.full[slot]);
-                    tma_load_2d(Bl + c * N * 16, tmBl, k0 + 8 * c, 0, &sm.full[slot]);
-                }
-            }
+            tma_load_2d(sm.A[slot], tmA, k0, a_row0, &sm.full[slot]);
+            tma_load_2d(sm.Bh[slot], tmBh, k0, 0, &sm.full[slot]);
+            tma_load_2d(sm.Bl[slot], tmBl, k0, 0, &sm.full[slot]);
         }
     } else if (tid == 32) {
         // MMA issuer
-        constexpr uint32_t LA = TC_M * 16, LB = N * 16;   // byte stride between 16-byte K chunks
         constexpr uint32_t id = idesc_bf16(TC_M, N);
         for (int s = 0; s < nst; ++s) {
             const int slot = s % TC_STAGES;
@@ -177,9 +175,9 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const CUtensorMap* tmA, const CUtenso
             const uint32_t a0 = smem_u32(sm.A[slot]), bh = smem_u32(sm.Bh[slot]), bl = smem_u32(sm.Bl[slot]);
 #pragma unroll
             for (int ks = 0; ks < TC_KS / 16; ++ks) {
-                const uint64_t ad = smem_desc(a0 + ks * 2 * LA, LA, 128);
-                mma_bf16(tmem, ad, smem_desc(bh + ks * 2 * LB, LB, 128), id, (s == 0 && ks == 0) ? 0u : 1u);
-                mma_bf16(tmem, ad, smem_desc(bl + ks * 2 * LB, LB, 128), id, 1u);
+                const uint64_t ad = smem_desc_sw128(a0 + ks * 32);
+                mma_bf16(tmem, ad, smem_desc_sw128(bh + ks * 32), id, (s == 0 && ks == 0) ? 0u : 1u);
+                mma_bf16(tmem, ad, smem_desc_sw128(bl + ks * 32), id, 1u);
             }
             mma_commit(&sm.empty[slot]);
         }
@@ -228,16 +226,16 @@ __global__ void __launch_bounds__(128) k_tc_sweep1(const __grid_constant__ CUten
                                                     const __grid_constant__ CUtensorMap tmBh,
                                                     const __grid_constant__ CUtensorMap tmBl, int m, int b,
                                                     int rows_per_split, int ldh, float* __restrict__ partial,
-                                                    int* status, int maps3d) {
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    TcRing<N>& sm = *reinterpret_cast<TcRing<N>*>(smraw);
+                                                    int* status) {
+    extern __shared__ unsigned char smraw[];
+    TcRing<N>& sm = tc_ring<N>(smraw);
     tc_setup<N>(sm);
     const uint32_t tmem = sm.tbase;
     const int i0 = blockIdx.x * TC_M;
     const int split = blockIdx.y;
     const int k_begin = split * rows_per_split;
     const int nst = (min(ldh, k_begin + rows_per_split) - k_begin) / TC_KS;
-    const bool ok = tc_mainloop<N>(sm, &tmA, &tmBh, &tmBl, i0, k_begin, nst, tmem, status, maps3d != 0);
+    const bool ok = tc_mainloop<N>(sm, &tmA, &tmBh, &tmBl, i0, k_begin, nst, tmem, status);
     const int warp = threadIdx.x >> 5;
     const int i = i0 + 32 * warp + (threadIdx.x & 31);
     float* out = partial + (int64_t)split * m * b;
@@ -255,20 +253,25 @@ __global__ void __launch_bounds__(128) k_tc_sweep1(const __grid_constant__ CUten
     tc_teardown<N>(sm, tmem);
 }
 
-// ---- sweep 2: Y[r, j] = X[r, j] + sum_l H[r, l] Q[l, j] -------------------------------------------------------
-template <int N>
+// ---- sweep 2 -------------------------------------------------------------------------------------------------
+// acc[r, j] = sum_l A[r, l] B[l, j] over the full K range (ldm), A row-major bf16, B a bf16 (hi, lo) pair.
+//   MODE 0: Y[r, j] = X[r, j] + acc (Y may alias X); when Yhi is not null also the bf16 pair of Y
+//           (column-major, leading dimension ldh), for the next exp-apply's sweep 1.
+//   MODE 1: O[r * ldo + j] = bf16(acc) (row-major bf16 store of a 32-column slice of H K).
+template <int N, int MODE>
 __global__ void __launch_bounds__(128) k_tc_sweep2(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmBh,
                                                     const __grid_constant__ CUtensorMap tmBl, int64_t d, int ldm, int b,
-                                                    const float* __restrict__ X, int64_t ldx, float* __restrict__ Y,
-                                                    int64_t ldy, int* status, int maps3d) {
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    TcRing<N>& sm = *reinterpret_cast<TcRing<N>*>(smraw);
+                                                    const float* X, int64_t ldx, float* Y, int64_t ldy,
+                                                    __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldh,
+                                                    __nv_bfloat16* O, int64_t ldo, int* status) {
+    extern __shared__ unsigned char smraw[];
+    TcRing<N>& sm = tc_ring<N>(smraw);
     tc_setup<N>(sm);
     const uint32_t tmem = sm.tbase;
     const int r0 = blockIdx.x * TC_M;
     const int nst = ldm / TC_KS;
-    const bool ok = tc_mainloop<N>(sm, &tmA, &tmBh, &tmBl, r0, 0, nst, tmem, status, maps3d != 0);
+    const bool ok = tc_mainloop<N>(sm, &tmA, &tmBh, &tmBl, r0, 0, nst, tmem, status);
     const int warp = threadIdx.x >> 5;
     const int64_t row = r0 + 32 * warp + (threadIdx.x & 31);
 #pragma unroll
@@ -276,12 +279,28 @@ __global__ void __launch_bounds__(128) k_tc_sweep2(const __grid_constant__ CUten
         uint32_t r[16];
         tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, r);
         tmem_wait_ld();
+        if (MODE == 0) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const int j = c0 + c;
-            if (row < d && j < b) {
-                const float acc = (ok && nst > 0) ? __uint_as_float(r[c]) : 0.f;
-                Y[(int64_t)j * ldy + row] = X[(int64_t)j * ldx + row] + acc;
+            for (int c = 0; c < 16; ++c) {
+                const int j = c0 + c;
+                if (row < d && j < b) {
+                    const float acc = (ok && nst > 0) ? __uint_as_float(r[c]) : 0.f;
+                    const float y = X[(int64_t)j * ldx + row] + acc;
+                    Y[(int64_t)j * ldy + row] = y;
+                    if (Yhi) {
+                        const __nv_bfloat16 hv = __float2bfloat16_rn(y);
+                        Yhi[(int64_t)j * ldh + row] = hv;
+                        Ylo[(int64_t)j * ldh + row] = __float2bfloat16_rn(y - __bfloat162float(hv));
+                    }
+                }
+            }
+        } else if (row < d) {
+            __nv_bfloat16* o = O + row * ldo + c0;
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                const float a0 = (ok && nst > 0) ? __uint_as_float(r[c]) : 0.f;
+                const float a1 = (ok && nst > 0) ? __uint_as_float(r[c + 1]) : 0.f;
+                *reinterpret_cast<__nv_bfloat162*>(o + c) = __floats2bfloat162_rn(a0, a1);
             }
         }
     }
@@ -301,57 +320,48 @@ __global__ void k_split_x(int64_t d, int b, const float* __restrict__ X, int64_t
     Xlo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// P[i, j] = sum_s partial[s][j][i] in FP64 (fixed order), stored as float
-__global__ void k_reduce_f32(int m, int b, int splits, const float* __restrict__ partial, float* __restrict__ P) {
+// P[i, j] = sum_s partial[s][j][i] in FP64 (fixed order), written as the bf16 pair (Phi, Plo),
+// column-major with leading dimension ldq; rows m..ldq-1 are zero.
+__global__ void k_reduce_split(int m, int b, int splits, const float* __restrict__ partial, int ldq,
+                               __nv_bfloat16* Phi, __nv_bfloat16* Plo) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)m * b) return;
-    double acc = 0.0;
-    for (int s = 0; s < splits; ++s) acc += (double)partial[(int64_t)s * m * b + e];
-    P[e] = (float)acc;
+    if (e >= (int64_t)ldq * b) return;
+    const int i = (int)(e % ldq);
+    const int j = (int)(e / ldq);
+    float p = 0.f;
+    if (i < m) {
+        const float* src = partial + (int64_t)j * m + i;
+        const int64_t stride = (int64_t)m * b;
+        double acc = 0.0;
+        int s = 0;
+        for (; s + 4 <= splits; s += 4) {
+            const float v0 = src[(s + 0) * stride], v1 = src[(s + 1) * stride];
+            const float v2 = src[(s + 2) * stride], v3 = src[(s + 3) * stride];
+            acc += (double)v0;
+            acc += (double)v1;
+            acc += (double)v2;
+            acc += (double)v3;
+        }
+        for (; s < splits; ++s) acc += (double)src[s * stride];
+        p = (float)acc;
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(p);
+    Phi[e] = h;
+    Plo[e] = __float2bfloat16_rn(p - __bfloat162float(h));
 }
 
-// Q = K P (m x m times m x b, FP32) written as bf16 hi/lo, column-major ld ldq (rows m..ldq-1 zero).
-// CTA = 4 warps for one 32-row block and NB columns; warp w sums a quarter of the inner dimension
-// (K is read once per NB columns); quarters are added in a fixed order through shared memory.
-template <int NB>
-__global__ void __launch_bounds__(128) k_kp_split(int m, int b, const float* __restrict__ K, const float* __restrict__ P,
-                                                  int ldq, __nv_bfloat16* Qhi, __nv_bfloat16* Qlo) {
-    __shared__ float part[3][32][NB + 1];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + lane;
-    const int j0 = blockIdx.y * NB;
-    P += (int64_t)j0 * m;
-    Qhi += (int64_t)j0 * ldq;
-    Qlo += (int64_t)j0 * ldq;
-    b = min(NB, b - j0);
-    const int q = (m + 3) / 4;
-    const int lb = w * q, le = min(m, lb + q);
-    float acc[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) acc[j] = 0.f;
-    if (i < m) {
-        for (int l = lb; l < le; ++l) {
-            const float kv = K[(int64_t)l * m + i];
-#pragma unroll
-            for (int j = 0; j < NB; ++j)
-                if (j < b) acc[j] = fmaf(kv, __ldg(P + (int64_t)j * m + l), acc[j]);
-        }
-    }
-    if (w > 0) {
-#pragma unroll
-        for (int j = 0; j < NB; ++j) part[w - 1][lane][j] = acc[j];
-    }
-    __syncthreads();
-    if (w == 0 && i < ldq) {
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            if (j >= b) break;
-            const float qv = (i < m) ? (acc[j] + part[0][lane][j]) + (part[1][lane][j] + part[2][lane][j]) : 0.f;
-            const __nv_bfloat16 h = __float2bfloat16_rn(qv);
-            Qhi[(int64_t)j * ldq + i] = h;
-            Qlo[(int64_t)j * ldq + i] = __float2bfloat16_rn(qv - __bfloat162float(h));
-        }
-    }
+// Columns c0 .. c0+31 of the symmetric FP64 K (m x m, ld m) as 32 rows of a bf16 pair with
+// leading dimension ldq (entry (l, j) = K[l, c0 + j]); entries outside K are zero.
+__global__ void k_kslice_split(int m, int c0, const double* __restrict__ K, int ldq, __nv_bfloat16* Khi,
+                               __nv_bfloat16* Klo) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)ldq * 32) return;
+    const int l = (int)(e % ldq);
+    const int c = c0 + (int)(e / ldq);
+    const float v = (l < m && c < m) ? (float)K[(int64_t)c * m + l] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Khi[e] = h;
+    Klo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
 // column-major FP64 d x m -> column-major bf16 with leading dimension ldh (zero rows beyond d)
@@ -370,10 +380,6 @@ __global__ void k_to_bf16_rm(int64_t d, int m, const double* __restrict__ H, int
     const int64_t r = e / ldm;
     const int c = (int)(e % ldm);
     out[e] = __float2bfloat16_rn(c < m ? (float)H[(int64_t)c * ld + r] : 0.f);
-}
-__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ o) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) o[e] = (float)a[e];
 }
 
 // ---- tensor maps ------------------------------------------------------------------------------------------------
@@ -396,53 +402,48 @@ EncodeTiledFn encoder() {
     return fn;
 }
 
-// 3-D view of the same bf16 matrix: (element within a 16-byte chunk, row, chunk) with strides
-// (2 B, ld * 2 B, 16 B) and a box of 8 x box_rows x 8, i.e. one whole 64-element K stage whose
-// chunks land box_rows * 16 bytes apart: the no-swizzle core-matrix layout. Returns false when
-// the encoder does not accept this view (the caller then uses 2-D boxes).
-bool make_map3(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_rows) {
-    EncodeTiledFn enc = encoder();
-    if (!enc || inner % 8) return false;
-    const cuuint64_t dims[3] = {8, outer, inner / 8};
-    const cuuint64_t strides[2] = {ld * 2, 16};
-    const cuuint32_t box[3] = {8, box_rows, 8};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-// 2-D bf16 tensor: inner extent `inner` (contiguous), `outer` rows of stride `ld` elements; box of
-// 8 inner elements x `box_rows` rows (16 bytes x rows); reads outside the extents return zeros.
+// 2-D bf16 tensor: inner extent `inner` (contiguous, a multiple of 64), `outer` rows of stride `ld`
+// elements; box of 64 inner elements (128 bytes) x `box_rows` rows, 128-byte swizzle; reads outside
+// the extents return zeros.
 int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_rows) {
     EncodeTiledFn enc = encoder();
     if (!enc) return EDA_ERR_CUDA;
+    if (inner % TC_KS || ld % TC_KS || (reinterpret_cast<uintptr_t>(base) & 15)) return EDA_ERR_INVALID_ARG;
     const cuuint64_t dims[2] = {inner, outer};
     const cuuint64_t strides[1] = {ld * 2};
-    const cuuint32_t box[2] = {8, box_rows};
+    const cuuint32_t box[2] = {TC_KS, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? EDA_OK : EDA_ERR_CUDA;
 }
 
+template <int N, int MODE>
+int set_smem_attr() {
+    static bool done = false;
+    if (!done) {
+        EDA_CUDA_TRY(cudaFuncSetAttribute(k_tc_sweep2<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc_smem_bytes<N>()));
+        if (MODE == 0)
+            EDA_CUDA_TRY(cudaFuncSetAttribute(k_tc_sweep1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)tc_smem_bytes<N>()));
+        done = true;
+    }
+    return EDA_OK;
+}
+
 template <int N>
 int launch_tc(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, int64_t ldx, float* Y, int64_t ldy,
-              float* partial, size_t partial_cap, int* status, cudaStream_t s) {
-    const size_t smem = sizeof(TcRing<N>) + 1024;
-    static bool attr = false;
-    if (!attr) {
-        EDA_CUDA_TRY(cudaFuncSetAttribute(k_tc_sweep1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        EDA_CUDA_TRY(cudaFuncSetAttribute(k_tc_sweep2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+              float* partial, size_t partial_cap, bool x_split_ready, bool emit_split, int* status, cudaStream_t s) {
+    EDA_TRY((set_smem_attr<N, 0>()));
+    constexpr size_t smem = tc_smem_bytes<N>();
     const int m = f.m;
     const int nb = N == 16 ? 0 : 1;
-    // split X into its bf16 pair
-    k_split_x<<<ceil_div(f.ldh * b, 256), 256, 0, s>>>(f.d, b, X, ldx, f.ldh, bufs.Xhi, bufs.Xlo);
-    EDA_LAUNCHED();
+    if (!x_split_ready) {
+        k_split_x<<<ceil_div(f.ldh * b, 256), 256, 0, s>>>(f.d, b, X, ldx, f.ldh, bufs.Xhi, bufs.Xlo);
+        EDA_LAUNCHED();
+    }
     // sweep 1 over split ranges of whole stages
     const int tiles = ceil_div(m, TC_M);
     const int kst = (int)(f.ldh / TC_KS);
@@ -453,23 +454,18 @@ int launch_tc(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, i
     splits = ceil_div(f.ldh, rows);
     {
         ProfScope prof("tc_sweep1", s);
-        const int m3 = (f.maps3d && bufs.maps3d) ? 1 : 0;
-        k_tc_sweep1<N><<<dim3(tiles, splits), 128, smem, s>>>(m3 ? f.mapA1_3 : f.mapA1, m3 ? bufs.mapXh3[nb] : bufs.mapXh[nb],
-                                                            m3 ? bufs.mapXl3[nb] : bufs.mapXl[nb], m, b, rows,
-                                                            (int)f.ldh, partial, status, m3);
+        k_tc_sweep1<N><<<dim3(tiles, splits), 128, smem, s>>>(f.mapA1, bufs.mapXh[nb], bufs.mapXl[nb], m, b, rows,
+                                                            (int)f.ldh, partial, status);
         EDA_LAUNCHED();
     }
-    k_reduce_f32<<<ceil_div((int64_t)m * b, 256), 256, 0, s>>>(m, b, splits, partial, bufs.P);
-    EDA_LAUNCHED();
-    k_kp_split<8><<<dim3(ceil_div(f.ldm, 32), ceil_div(b, 8)), 128, 0, s>>>(m, b, f.K32, bufs.P, bufs.ldq, bufs.Qhi,
-                                                                            bufs.Qlo);
+    k_reduce_split<<<ceil_div((int64_t)bufs.ldq * b, 256), 256, 0, s>>>(m, b, splits, partial, bufs.ldq, bufs.Qhi,
+                                                                        bufs.Qlo);
     EDA_LAUNCHED();
     {
         ProfScope prof("tc_sweep2", s);
-        const int m3 = (f.maps3d && bufs.maps3d) ? 1 : 0;
-        k_tc_sweep2<N><<<ceil_div(f.d, TC_M), 128, smem, s>>>(m3 ? f.mapA2_3 : f.mapA2, m3 ? bufs.mapQh3[nb] : bufs.mapQh[nb],
-                                                            m3 ? bufs.mapQl3[nb] : bufs.mapQl[nb], f.d, f.ldm, b, X, ldx,
-                                                            Y, ldy, status, m3);
+        k_tc_sweep2<N, 0><<<ceil_div(f.d, TC_M), 128, smem, s>>>(
+            f.mapA2, bufs.mapQh[nb], bufs.mapQl[nb], f.d, f.ldm, b, X, ldx, Y, ldy, emit_split ? bufs.Xhi : nullptr,
+            emit_split ? bufs.Xlo : nullptr, f.ldh, nullptr, 0, status);
         EDA_LAUNCHED();
     }
     return EDA_OK;
@@ -477,36 +473,64 @@ int launch_tc(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, i
 
 }  // namespace
 
-int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bfloat16* Hcm, __nv_bfloat16* Hrm,
-                   float* K32, TcFactor* f, cudaStream_t s) {
+int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bfloat16* Hcm, __nv_bfloat16* HKrm,
+                   TcFactor* f, int* status, cudaStream_t s) {
     f->d = d;
     f->m = m;
     f->ldh = tc_pad_rows(d);
     f->ldm = tc_pad_cols(m);
     f->Hcm = Hcm;
-    f->Hrm = Hrm;
-    f->K32 = K32;
+    f->HKrm = HKrm;
     k_to_bf16_cm<<<ceil_div(f->ldh * m, 256), 256, 0, s>>>(d, m, H, d, Hcm, f->ldh);
     EDA_LAUNCHED();
-    k_to_bf16_rm<<<ceil_div(d * f->ldm, 256), 256, 0, s>>>(d, m, H, d, Hrm, f->ldm);
-    EDA_LAUNCHED();
-    k_to_f32<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>((int64_t)m * m, K, K32);
-    EDA_LAUNCHED();
-    // sweep 1 reads columns of H (K = d contiguous), sweep 2 reads rows (K = m contiguous)
+    // sweep 1 reads columns of H (K = d contiguous)
     EDA_TRY(make_map(&f->mapA1, Hcm, (uint64_t)f->ldh, (uint64_t)m, (uint64_t)f->ldh, TC_M));
-    EDA_TRY(make_map(&f->mapA2, Hrm, (uint64_t)f->ldm, (uint64_t)d, (uint64_t)f->ldm, TC_M));
-    f->maps3d = make_map3(&f->mapA1_3, Hcm, (uint64_t)f->ldh, (uint64_t)m, (uint64_t)f->ldh, TC_M) &&
-                make_map3(&f->mapA2_3, Hrm, (uint64_t)f->ldm, (uint64_t)d, (uint64_t)f->ldm, TC_M);
-    return EDA_OK;
+    // H K (d x m, row-major bf16) as sweep-2 products: A = bf16(H) row-major, B = 32-column slices of K
+    // as bf16 pairs. Temporaries are freed before returning (the stream is synchronised first).
+    const int ldm = f->ldm;
+    __nv_bfloat16* Hrm = nullptr;
+    __nv_bfloat16* Ks = nullptr;
+    const size_t hbytes = ((size_t)d * ldm * 2 + 255) / 256 * 256;
+    const size_t kbytes = (size_t)ldm * 32 * 2;
+    if (cudaMalloc(&Hrm, hbytes + 2 * kbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return EDA_ERR_OOM;
+    }
+    Ks = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(Hrm) + hbytes);
+    __nv_bfloat16* Khi = Ks;
+    __nv_bfloat16* Klo = Ks + (size_t)ldm * 32;
+    int rc = EDA_OK;
+    do {
+        k_to_bf16_rm<<<ceil_div(d * ldm, 256), 256, 0, s>>>(d, m, H, d, Hrm, ldm);
+        launch_counter()++;
+        if (cudaPeekAtLastError() != cudaSuccess) { rc = EDA_ERR_CUDA; break; }
+        CUtensorMap mA, mKh, mKl;
+        if ((rc = make_map(&mA, Hrm, (uint64_t)ldm, (uint64_t)d, (uint64_t)ldm, TC_M)) != EDA_OK) break;
+        if ((rc = make_map(&mKh, Khi, (uint64_t)ldm, 32, (uint64_t)ldm, 32)) != EDA_OK) break;
+        if ((rc = make_map(&mKl, Klo, (uint64_t)ldm, 32, (uint64_t)ldm, 32)) != EDA_OK) break;
+        if ((rc = set_smem_attr<32, 1>()) != EDA_OK) break;
+        for (int c0 = 0; c0 < ldm && rc == EDA_OK; c0 += 32) {
+            k_kslice_split<<<ceil_div((int64_t)ldm * 32, 256), 256, 0, s>>>(m, c0, K, ldm, Khi, Klo);
+            k_tc_sweep2<32, 1><<<ceil_div(d, TC_M), 128, tc_smem_bytes<32>(), s>>>(
+                mA, mKh, mKl, d, ldm, 32, nullptr, 0, nullptr, 0, nullptr, nullptr, 0, HKrm + c0, ldm, status);
+            launch_counter() += 2;
+            if (cudaPeekAtLastError() != cudaSuccess) rc = EDA_ERR_CUDA;
+        }
+        if (rc == EDA_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = EDA_ERR_CUDA;
+    } while (false);
+    if (rc != EDA_OK) cudaStreamSynchronize(s);
+    cudaFree(Hrm);
+    if (rc != EDA_OK) return rc;
+    // sweep 2 reads rows of H K (K = m contiguous)
+    return make_map(&f->mapA2, HKrm, (uint64_t)ldm, (uint64_t)d, (uint64_t)ldm, TC_M);
 }
 
 int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, __nv_bfloat16* Qhi,
-                    __nv_bfloat16* Qlo, float* P, TcBuffers* b) {
+                    __nv_bfloat16* Qlo, TcBuffers* b) {
     b->Xhi = Xhi;
     b->Xlo = Xlo;
     b->Qhi = Qhi;
     b->Qlo = Qlo;
-    b->P = P;
     b->ldh = ldh;
     b->ldq = ldq;
     for (int i = 0; i < 2; ++i) {
@@ -516,26 +540,22 @@ int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo
         EDA_TRY(make_map(&b->mapQh[i], Qhi, (uint64_t)ldq, 32, (uint64_t)ldq, rows));
         EDA_TRY(make_map(&b->mapQl[i], Qlo, (uint64_t)ldq, 32, (uint64_t)ldq, rows));
     }
-    b->maps3d = true;
-    for (int i = 0; i < 2; ++i) {
-        const uint32_t rows = i == 0 ? 16 : 32;
-        b->maps3d = b->maps3d && make_map3(&b->mapXh3[i], Xhi, (uint64_t)ldh, 32, (uint64_t)ldh, rows) &&
-                    make_map3(&b->mapXl3[i], Xlo, (uint64_t)ldh, 32, (uint64_t)ldh, rows) &&
-                    make_map3(&b->mapQh3[i], Qhi, (uint64_t)ldq, 32, (uint64_t)ldq, rows) &&
-                    make_map3(&b->mapQl3[i], Qlo, (uint64_t)ldq, 32, (uint64_t)ldq, rows);
-    }
     return EDA_OK;
 }
 
 int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
-                 float* Y, int64_t ldy, void* partial, size_t partial_cap, int* status, cudaStream_t s) {
+                 float* Y, int64_t ldy, void* partial, size_t partial_cap, int flags, int* status, cudaStream_t s) {
     ProfScope prof(tag, s);
     float* part = static_cast<float*>(partial);
-    if (b <= 16) return launch_tc<16>(f, bufs, b, X, ldx, Y, ldy, part, partial_cap, status, s);
+    // the split pair lives in one 32-column staging buffer: chaining needs a single slice
+    const bool chain = b <= 32;
+    const bool ready = chain && (flags & TC_X_SPLIT_READY);
+    const bool emit = chain && (flags & TC_EMIT_SPLIT);
+    if (b <= 16) return launch_tc<16>(f, bufs, b, X, ldx, Y, ldy, part, partial_cap, ready, emit, status, s);
     for (int c0 = 0; c0 < b; c0 += 32) {
         const int cb = std::min(32, b - c0);
         EDA_TRY(launch_tc<32>(f, bufs, cb, X + (int64_t)c0 * ldx, ldx, Y + (int64_t)c0 * ldy, ldy, part, partial_cap,
-                              status, s));
+                              ready, emit, status, s));
     }
     return EDA_OK;
 }

@@ -144,14 +144,17 @@ int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* 
     const T* HB = HStore<T>::B(h);
     const int n = (int)h->n;
     if (std::is_same<T, float>::value && h->cfg.prec == EDA_BF16) {
-        // bf16 H on the tensor cores (the basis stays single precision)
+        // bf16 H on the tensor cores (the basis stays single precision); the three products chain
+        // through the bf16 staging pair and run in place on Y
         const float* Xf = reinterpret_cast<const float*>(X);
         float* Yf = reinterpret_cast<float*>(Y);
-        float* tf = reinterpret_cast<float*>(tmp);
-        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Xf, ldx, tf, d, partial, partial_cap, h->status, s));
-        EDA_TRY(exp_apply_tc(h->tcB, h->tcbuf, "exp_apply_b", b, tf, d, Yf, ldy, partial, partial_cap, h->status, s));
-        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Yf, ldy, tf, d, partial, partial_cap, h->status, s));
-        EDA_TRY((copy_mat<float, float>(d, b, tf, d, Yf, ldy, s)));
+        (void)tmp;
+        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Xf, ldx, Yf, ldy, partial, partial_cap,
+                             TC_EMIT_SPLIT, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcB, h->tcbuf, "exp_apply_b", b, Yf, ldy, Yf, ldy, partial, partial_cap,
+                             TC_X_SPLIT_READY | TC_EMIT_SPLIT, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Yf, ldy, Yf, ldy, partial, partial_cap,
+                             TC_X_SPLIT_READY, h->status, s));
         return EDA_OK;
     }
     EDA_TRY(exp_apply<T>(d, HW, h->KW, n, "exp_apply_w", b, X, ldx, tmp, d, P, Q, partial, partial_cap, s));

@@ -79,10 +79,12 @@ def _bf16_round(a):
 @pytest.mark.parametrize("d,k,nj,b", [(4096, 40, 5, 8), (1000, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 16), (2048, 20, 7, 32),
                                       (777, 5, 3, 40)])
 def test_tc_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
-    # The tensor-core product uses bf16(H) exactly and hi + lo bf16 pairs for X and Q, accumulating in
-    # FP32: against an FP64 evaluation of X + bf16(H) K (bf16(H)^T X) the error is the hi + lo rounding
-    # (2^-17 relative) plus FP32 accumulation, so 1e-4 relative is a sharp bound that any operand or
-    # layout mistake (a transposed core matrix, a wrong K step) violates by orders of magnitude.
+    # The tensor-core product is X + bf16(H K) (bf16(H)^T X): H and the precomputed d x m product H K
+    # are stored in bf16, X and P = H^T X enter as hi + lo bf16 pairs, accumulation is FP32. Against an
+    # FP64 evaluation of that expression the error is the hi + lo rounding (2^-17 relative), FP32
+    # accumulation, and the rare entries of H K whose FP32 and FP64 values round to different bf16
+    # neighbours, so 1e-4 relative is a sharp bound that any operand or layout mistake (a transposed
+    # core matrix, a wrong swizzle, a wrong K step) violates by orders of magnitude.
     p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=500 + d)
     cfg = eda.config(prec=eda.EDA_BF16, block_b=min(b, 16), tau=10.0)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
@@ -91,14 +93,16 @@ def test_tc_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
         Xb = rng.standard_normal((b, d)).astype(np.float32)
         for op, H, K, alpha in ((eda.OP_SW, f["HW"], f["KW"], -0.5 * h.c2), (eda.OP_SB, f["HB"], f["KB"], h.c2)):
             Y = h.apply_exp(op, _dev(Xb), alpha=alpha).cpu().numpy().astype(np.float64)
-            Hb = _bf16_round(H.cpu().numpy())          # (m, d) rows = columns of H
+            Hn = H.cpu().numpy()                       # (m, d): rows are the columns of H
+            Hb = _bf16_round(Hn)
             Kn = K.cpu().numpy()
+            HKb = _bf16_round(Hb.T @ Kn)               # (d, m)
             X64 = Xb.astype(np.float64)
-            ref = X64 + ((Hb.T @ (Kn @ (Hb @ X64.T))).T)
+            ref = X64 + (HKb @ (Hb @ X64.T)).T
             err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
             assert err <= 1e-4, (op, err)
-            # and against the exact FP64 operator: the bf16 rounding of H (2^-9) sets the scale
-            exact = X64 + ((H.cpu().numpy().T @ (Kn @ (H.cpu().numpy() @ X64.T))).T)
+            # and against the exact FP64 operator: the bf16 rounding of H and H K (2^-9) sets the scale
+            exact = X64 + ((Hn.T @ (Kn @ (Hn @ X64.T))).T)
             assert np.linalg.norm(Y - exact) / np.linalg.norm(exact) <= 2e-2
 
 
