@@ -208,13 +208,14 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
     EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
     if (h->cfg.prec == EDA_BF16) {
-        // bf16 H_W, H_B column-major (sweep 1), bf16 H K row-major (sweep 2), and the staging
+        // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
         // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)
         const int64_t ldh = tc_pad_rows(d);
         const int ldq = std::max(tc_pad_cols(n), tc_pad_cols(k));
-        const size_t sz[6] = {align256((size_t)ldh * n * 2), align256((size_t)d * tc_pad_cols(n) * 2),
-                              align256((size_t)ldh * k * 2), align256((size_t)d * tc_pad_cols(k) * 2),
-                              align256((size_t)ldh * 32 * 2) * 2, align256((size_t)ldq * 32 * 2) * 2};
+        const size_t sz[7] = {align256((size_t)tc_tiles_sweep1(d, n) * 2), align256((size_t)tc_tiles_sweep2(d, n) * 2),
+                              align256((size_t)tc_tiles_sweep1(d, k) * 2), align256((size_t)tc_tiles_sweep2(d, k) * 2),
+                              align256((size_t)ldh * 32 * 2) * 2, align256((size_t)ldq * 32 * 2) * 2,
+                              align256(tc_partial_floats(std::max(n, k)) * 4)};
         size_t tot = 0;
         for (size_t v : sz) tot += v;
         void* p = nullptr;
@@ -232,9 +233,10 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         __nv_bfloat16* Xlo = bf(off + sz[4] / 2); off += sz[4];
         __nv_bfloat16* Qhi = bf(off);
         __nv_bfloat16* Qlo = bf(off + sz[5] / 2); off += sz[5];
+        float* partial = reinterpret_cast<float*>(c + off); off += sz[6];
         EDA_TRY(tc_factor_make(h->HW, d, n, h->KW, HcW, HKW, &h->tcW, h->status, s));
         EDA_TRY(tc_factor_make(h->HB, d, k, h->KB, HcB, HKB, &h->tcB, h->status, s));
-        EDA_TRY(tc_buffers_make(ldh, ldq, Xhi, Xlo, Qhi, Qlo, &h->tcbuf));
+        EDA_TRY(tc_buffers_make(ldh, ldq, Xhi, Xlo, Qhi, Qlo, partial, tc_partial_floats(std::max(n, k)), &h->tcbuf));
     }
     int st = 0;
     EDA_TRY(read_status(h, s, &st));
@@ -370,7 +372,7 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
         if (alpha != (isW ? -0.5 * h->c2 : h->c2)) return EDA_ERR_INVALID_ARG;   // stored operators only
         if (h->cfg.prec == EDA_BF16)
             return exp_apply_tc(isW ? h->tcW : h->tcB, h->tcbuf, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf,
-                                ldx, part, pcap, 0, h->status, s);
+                                ldx, 0, h->status, s);
         return exp_apply<float>(d, isW ? h->HW32 : h->HB32, K, m, isW ? "exp_apply_w" : "exp_apply_b", b, xf, ldx, yf,
                                 ldx, P, Q, part, pcap, s);
     }

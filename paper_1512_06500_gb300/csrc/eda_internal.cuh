@@ -189,39 +189,43 @@ int exp_apply_f64(int64_t d, const ExpOp& op, int b, const double* X, int64_t ld
                   cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core exp-apply (bf16 H)
-// One factor H (d x m) in the two bf16 layouts the tensor-core sweeps read, with its tensor maps
-// (64-element x 128-row boxes, 128-byte swizzle).
+// One factor H (d x m) in the two pre-tiled bf16 layouts the tensor-core sweeps read: 128-row x
+// 64-element tiles, each a contiguous 16 KB block in the 128-byte-swizzled shared-memory image.
 struct TcFactor {
-    CUtensorMap mapA1;                    // Hcm: inner K = ldh, outer m
-    CUtensorMap mapA2;                    // HKrm: inner K = ldm, outer d
-    const __nv_bfloat16* Hcm = nullptr;   // bf16(H), column-major, leading dimension ldh (>= d, zero padded)
-    const __nv_bfloat16* HKrm = nullptr;  // bf16(H K(alpha)), row-major d x ldm (zero padded columns)
-    int64_t d = 0, ldh = 0;
-    int m = 0, ldm = 0;
+    const __nv_bfloat16* A1 = nullptr;    // bf16(H): tile rows = columns of H, K along d (sweep 1)
+    const __nv_bfloat16* A2 = nullptr;    // bf16(H K(alpha)): tile rows = rows of H, K along m (sweep 2)
+    int64_t d = 0, ldh = 0;               // ldh = d rounded up to 64
+    int m = 0, ldm = 0;                   // ldm = m rounded up to 64
 };
 // Per-handle staging buffers of the sweeps (bf16 hi/lo pairs of X and of P = H^T X, 32 columns
 // each) with their tensor maps for N = 16 ([0]) and N = 32 ([1]) column boxes.
 struct TcBuffers {
     CUtensorMap mapXh[2], mapXl[2], mapQh[2], mapQl[2];
+    float* partial = nullptr;             // split-K partials of sweep 1
+    size_t partial_cap = 0;               // in floats
     __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Qhi = nullptr, *Qlo = nullptr;
     int64_t ldh = 0;
     int ldq = 0;
 };
 inline int64_t tc_pad_rows(int64_t d) { return (d + 63) / 64 * 64; }
 inline int tc_pad_cols(int m) { return (m + 63) / 64 * 64; }
-// Convert an FP64 factor H (d x m, ld d) to bf16 (column-major, ld ldh) and form bf16(H K) row-major
-// (d x ldm) from K (m x m, FP64) on the tensor cores. Synchronises the stream (temporaries).
-int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bfloat16* Hcm, __nv_bfloat16* HKrm,
+// Element counts of the two tiled layouts of a d x m factor.
+int64_t tc_tiles_sweep1(int64_t d, int m);
+int64_t tc_tiles_sweep2(int64_t d, int m);
+// Tile an FP64 factor H (d x m, ld d) as bf16 for sweep 1 and form the tiled bf16(H K) for sweep 2 from
+// K (m x m, FP64) on the tensor cores. Synchronises the stream (temporaries).
+int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bfloat16* A1, __nv_bfloat16* A2,
                    TcFactor* f, int* status, cudaStream_t s);
+// Floats of split-K partials needed for factors with at most m_max columns (two CTAs per SM).
+size_t tc_partial_floats(int m_max);
 int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, __nv_bfloat16* Qhi,
-                    __nv_bfloat16* Qlo, TcBuffers* b);
+                    __nv_bfloat16* Qlo, float* partial, size_t partial_cap, TcBuffers* b);
 // exp_apply_tc flags: the staging pair already holds the split of X (skip the split step); write the
 // split of Y into the staging pair (for the next exp-apply). Both apply only when b <= 32.
 enum : int { TC_X_SPLIT_READY = 1, TC_EMIT_SPLIT = 2 };
 // Y = X + H K (H^T X) with bf16 H on the tensor cores; X, Y single precision, Y may alias X.
-// partial holds splits * m * min(b, 32) floats.
 int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
-                 float* Y, int64_t ldy, void* partial, size_t partial_cap, int flags, int* status, cudaStream_t s);
+                 float* Y, int64_t ldy, int flags, int* status, cudaStream_t s);
 
 }  // namespace eda
 

@@ -90,6 +90,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "l"(map), "r"(x), "r"(y), "r"(smem_u32(mbar))
         : "memory");
 }
+// Contiguous global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+// Programmatic dependent launch: wait for the preceding grid (and, transitively, all earlier work
+// in the stream) to complete; allow the next grid to start its independent prologue.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -119,6 +130,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Pre-tiled operand layout in HBM: the operand is cut into 128-row x 64-element tiles, each stored as
+// one contiguous 16 KB block that is byte-for-byte the 128-byte-swizzled shared-memory image (row rr
+// at rr * 128 bytes, 16-byte chunk c at chunk c ^ (rr mod 8)); tiles of one 128-row band follow each
+// other along K (kbs tiles per band). A stage of the main loop is then one contiguous bulk copy.
+__host__ __device__ __forceinline__ int64_t tile_off(int64_t r, int64_t kk, int kbs) {
+    const int64_t rt = r >> 7, rr = r & 127, kb = kk >> 6, kc = kk & 63;
+    const int64_t c = kc >> 3, e = kc & 7;
+    return ((rt * kbs + kb) << 13) + rr * 64 + ((c ^ (rr & 7)) << 3) + e;
+}
+
 // The ring; every tile starts on a 1024-byte boundary (the swizzle pattern repeats every 8 rows of
 // 128 bytes), which holds because the struct is placed on such a boundary and every member size is a
 // multiple of 1024.
@@ -142,25 +163,38 @@ __device__ __forceinline__ TcRing<N>& tc_ring(unsigned char* raw) {
     return *reinterpret_cast<TcRing<N>*>(raw + ((1024u - mis) & 1023u));
 }
 
-// Main loop shared by both sweeps: K stages [0, nst) starting at element k_begin; A rows from
-// a_row0 (tensor map tmA), B rows 0..N-1 (tmBh, tmBl, same K coordinates). Returns false on timeout.
+// Main loop shared by both sweeps: K stages [0, nst); A stage s is the contiguous 16 KB tile image at
+// Atiles + s * 8192 (already in the swizzled layout), B rows 0..N-1 come from tmBh, tmBl at K
+// coordinate k_begin + 64 s. Returns false on timeout.
 template <int N>
-__device__ bool tc_mainloop(TcRing<N>& sm, const CUtensorMap* tmA, const CUtensorMap* tmBh, const CUtensorMap* tmBl,
-                            int a_row0, int k_begin, int nst, uint32_t tmem, int* status) {
+__device__ bool tc_mainloop(TcRing<N>& sm, const __nv_bfloat16* Atiles, const CUtensorMap* tmBh,
+                            const CUtensorMap* tmBl, int k_begin, int nst, uint32_t tmem, int* status) {
     const int tid = threadIdx.x;
     bool ok = true;
     if (tid == 0) {
-        // producer: one thread issues all bulk tensor loads (three boxes per stage)
-        constexpr uint32_t bytes = TC_M * TC_KS * 2 + 2 * N * TC_KS * 2;
-        for (int s = 0; s < nst && ok; ++s) {
+        // producer: one thread issues all loads (one bulk copy and two tensor boxes per stage). The A
+        // tiles (H or H K) do not depend on earlier kernels: the first ring's worth is requested before
+        // waiting on the preceding grid, whose outputs (the B pair) are loaded after the wait.
+        constexpr uint32_t abytes = TC_M * TC_KS * 2;
+        constexpr uint32_t bytes = abytes + 2 * N * TC_KS * 2;
+        const int pre = min(nst, TC_STAGES);
+        for (int s = 0; s < pre; ++s) {
+            mbar_expect_tx(&sm.full[s], bytes);
+            bulk_load(sm.A[s], Atiles + (int64_t)s * (TC_M * TC_KS), abytes, &sm.full[s]);
+        }
+        pdl_wait();
+        for (int s = 0; s < pre; ++s) {
+            tma_load_2d(sm.Bh[s], tmBh, k_begin + s * TC_KS, 0, &sm.full[s]);
+            tma_load_2d(sm.Bl[s], tmBl, k_begin + s * TC_KS, 0, &sm.full[s]);
+        }
+        for (int s = pre; s < nst && ok; ++s) {
             const int slot = s % TC_STAGES;
-            if (s >= TC_STAGES) ok = mbar_wait(&sm.empty[slot], ((s / TC_STAGES) - 1) & 1, status);
+            ok = mbar_wait(&sm.empty[slot], ((s / TC_STAGES) - 1) & 1, status);
             if (!ok) break;
             mbar_expect_tx(&sm.full[slot], bytes);
-            const int k0 = k_begin + s * TC_KS;
-            tma_load_2d(sm.A[slot], tmA, k0, a_row0, &sm.full[slot]);
-            tma_load_2d(sm.Bh[slot], tmBh, k0, 0, &sm.full[slot]);
-            tma_load_2d(sm.Bl[slot], tmBl, k0, 0, &sm.full[slot]);
+            bulk_load(sm.A[slot], Atiles + (int64_t)s * (TC_M * TC_KS), abytes, &sm.full[slot]);
+            tma_load_2d(sm.Bh[slot], tmBh, k_begin + s * TC_KS, 0, &sm.full[slot]);
+            tma_load_2d(sm.Bl[slot], tmBl, k_begin + s * TC_KS, 0, &sm.full[slot]);
         }
     } else if (tid == 32) {
         // MMA issuer
@@ -173,11 +207,15 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const CUtensorMap* tmA, const CUtenso
             }
             tc_fence_after();
             const uint32_t a0 = smem_u32(sm.A[slot]), bh = smem_u32(sm.Bh[slot]), bl = smem_u32(sm.Bl[slot]);
+            // four independent accumulators (hi/lo x even/odd K-step) so consecutive MMAs do not wait
+            // on one another's accumulation; they are added in the epilogue
 #pragma unroll
             for (int ks = 0; ks < TC_KS / 16; ++ks) {
                 const uint64_t ad = smem_desc_sw128(a0 + ks * 32);
-                mma_bf16(tmem, ad, smem_desc_sw128(bh + ks * 32), id, (s == 0 && ks == 0) ? 0u : 1u);
-                mma_bf16(tmem, ad, smem_desc_sw128(bl + ks * 32), id, 1u);
+                const uint32_t acc = (s == 0 && ks < 2) ? 0u : 1u;
+                const uint32_t col = (uint32_t)((ks & 1) * N);
+                mma_bf16(tmem + col, ad, smem_desc_sw128(bh + ks * 32), id, acc);
+                mma_bf16(tmem + 2 * N + col, ad, smem_desc_sw128(bl + ks * 32), id, acc);
             }
             mma_commit(&sm.empty[slot]);
         }
@@ -190,6 +228,7 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const CUtensorMap* tmA, const CUtenso
     __syncthreads();
     const bool fin = s_ok != 0;
     tc_fence_after();
+    pdl_wait();   // returns at once by now (the producer has waited); orders this thread's epilogue
     return fin;
 }
 
@@ -197,7 +236,7 @@ template <int N>
 __device__ void tc_setup(TcRing<N>& sm) {
     const int tid = threadIdx.x;
     if ((tid >> 5) == 0) {
-        tmem_alloc(&sm.tbase, 32);
+        tmem_alloc(&sm.tbase, 4 * N);
         tmem_relinquish();
     }
     if (tid == 0) {
@@ -213,16 +252,31 @@ __device__ void tc_setup(TcRing<N>& sm) {
     tc_fence_after();
 }
 
+// Columns c0 .. c0+15 of the accumulator of this thread's lane (TMEM lane = row within the tile):
+// the sum of the four partial accumulators.
+template <int N>
+__device__ __forceinline__ void tc_read16(uint32_t tmem, int warp, int c0, float (&v)[16]) {
+    uint32_t r[4][16];
+    const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + c0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) tmem_ld16(base + a * N, r[a]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        v[c] = (__uint_as_float(r[0][c]) + __uint_as_float(r[1][c])) +
+               (__uint_as_float(r[2][c]) + __uint_as_float(r[3][c]));
+}
+
 template <int N>
 __device__ void tc_teardown(TcRing<N>& sm, uint32_t tmem) {
     tc_fence_before();
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 32);
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 4 * N);
 }
 
 // ---- sweep 1: partial[split][j][i] = sum_{k in split} H[k, i] X[k, j] ---------------------------------------
 template <int N>
-__global__ void __launch_bounds__(128) k_tc_sweep1(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(128) k_tc_sweep1(const __nv_bfloat16* __restrict__ A1, int kbs,
                                                     const __grid_constant__ CUtensorMap tmBh,
                                                     const __grid_constant__ CUtensorMap tmBl, int m, int b,
                                                     int rows_per_split, int ldh, float* __restrict__ partial,
@@ -230,24 +284,25 @@ __global__ void __launch_bounds__(128) k_tc_sweep1(const __grid_constant__ CUten
     extern __shared__ unsigned char smraw[];
     TcRing<N>& sm = tc_ring<N>(smraw);
     tc_setup<N>(sm);
+    pdl_trigger();
     const uint32_t tmem = sm.tbase;
     const int i0 = blockIdx.x * TC_M;
     const int split = blockIdx.y;
     const int k_begin = split * rows_per_split;
     const int nst = (min(ldh, k_begin + rows_per_split) - k_begin) / TC_KS;
-    const bool ok = tc_mainloop<N>(sm, &tmA, &tmBh, &tmBl, i0, k_begin, nst, tmem, status);
+    const __nv_bfloat16* At = A1 + ((int64_t)blockIdx.x * kbs + k_begin / TC_KS) * (TC_M * TC_KS);
+    const bool ok = tc_mainloop<N>(sm, At, &tmBh, &tmBl, k_begin, nst, tmem, status);
     const int warp = threadIdx.x >> 5;
     const int i = i0 + 32 * warp + (threadIdx.x & 31);
     float* out = partial + (int64_t)split * m * b;
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, r);
-        tmem_wait_ld();
+        float v[16];
+        tc_read16<N>(tmem, warp, c0, v);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const int j = c0 + c;
-            if (i < m && j < b) out[(int64_t)j * m + i] = (ok && nst > 0) ? __uint_as_float(r[c]) : 0.f;
+            if (i < m && j < b) out[(int64_t)j * m + i] = (ok && nst > 0) ? v[c] : 0.f;
         }
     }
     tc_teardown<N>(sm, tmem);
@@ -259,33 +314,43 @@ __global__ void __launch_bounds__(128) k_tc_sweep1(const __grid_constant__ CUten
 //           (column-major, leading dimension ldh), for the next exp-apply's sweep 1.
 //   MODE 1: O[r * ldo + j] = bf16(acc) (row-major bf16 store of a 32-column slice of H K).
 template <int N, int MODE>
-__global__ void __launch_bounds__(128) k_tc_sweep2(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(128) k_tc_sweep2(const __nv_bfloat16* __restrict__ A2,
                                                     const __grid_constant__ CUtensorMap tmBh,
                                                     const __grid_constant__ CUtensorMap tmBl, int64_t d, int ldm, int b,
                                                     const float* X, int64_t ldx, float* Y, int64_t ldy,
                                                     __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldh,
-                                                    __nv_bfloat16* O, int64_t ldo, int* status) {
+                                                    __nv_bfloat16* O, int ldo_kbs, int o_col0, int* status) {
     extern __shared__ unsigned char smraw[];
     TcRing<N>& sm = tc_ring<N>(smraw);
     tc_setup<N>(sm);
+    pdl_trigger();
     const uint32_t tmem = sm.tbase;
     const int r0 = blockIdx.x * TC_M;
     const int nst = ldm / TC_KS;
-    const bool ok = tc_mainloop<N>(sm, &tmA, &tmBh, &tmBl, r0, 0, nst, tmem, status);
+    const __nv_bfloat16* At = A2 + (int64_t)blockIdx.x * nst * (TC_M * TC_KS);
+    const bool ok = tc_mainloop<N>(sm, At, &tmBh, &tmBl, 0, nst, tmem, status);
     const int warp = threadIdx.x >> 5;
     const int64_t row = r0 + 32 * warp + (threadIdx.x & 31);
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, r);
-        tmem_wait_ld();
+        float r[16];
+        tc_read16<N>(tmem, warp, c0, r);
         if (MODE == 0) {
+            // all loads of this thread's X row segment before any store: Y may alias X, but only
+            // element for element within this thread, so the reordering is safe and lets the 16
+            // loads overlap instead of paying one round trip each
+            float xv[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int j = c0 + c;
+                xv[c] = (row < d && j < b) ? X[(int64_t)j * ldx + row] : 0.f;
+            }
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const int j = c0 + c;
                 if (row < d && j < b) {
-                    const float acc = (ok && nst > 0) ? __uint_as_float(r[c]) : 0.f;
-                    const float y = X[(int64_t)j * ldx + row] + acc;
+                    const float acc = (ok && nst > 0) ? r[c] : 0.f;
+                    const float y = xv[c] + acc;
                     Y[(int64_t)j * ldy + row] = y;
                     if (Yhi) {
                         const __nv_bfloat16 hv = __float2bfloat16_rn(y);
@@ -295,12 +360,19 @@ __global__ void __launch_bounds__(128) k_tc_sweep2(const __grid_constant__ CUten
                 }
             }
         } else if (row < d) {
-            __nv_bfloat16* o = O + row * ldo + c0;
+            // 16 consecutive K columns o_col0 + c0 .. +15 of row `row` in the tiled layout: two
+            // 8-element chunks, each one 16-byte store
 #pragma unroll
-            for (int c = 0; c < 16; c += 2) {
-                const float a0 = (ok && nst > 0) ? __uint_as_float(r[c]) : 0.f;
-                const float a1 = (ok && nst > 0) ? __uint_as_float(r[c + 1]) : 0.f;
-                *reinterpret_cast<__nv_bfloat162*>(o + c) = __floats2bfloat162_rn(a0, a1);
+            for (int h = 0; h < 2; ++h) {
+                const int col = o_col0 + c0 + 8 * h;
+                __align__(16) __nv_bfloat162 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float a0 = (ok && nst > 0) ? r[8 * h + 2 * q] : 0.f;
+                    const float a1 = (ok && nst > 0) ? r[8 * h + 2 * q + 1] : 0.f;
+                    v[q] = __floats2bfloat162_rn(a0, a1);
+                }
+                *reinterpret_cast<uint4*>(O + tile_off(row, col, ldo_kbs)) = *reinterpret_cast<const uint4*>(v);
             }
         }
     }
@@ -310,6 +382,7 @@ __global__ void __launch_bounds__(128) k_tc_sweep2(const __grid_constant__ CUten
 // X (d x b, ld ldx) -> Xhi, Xlo (bf16, column-major ld ldh, rows >= d zero)
 __global__ void k_split_x(int64_t d, int b, const float* __restrict__ X, int64_t ldx, int64_t ldh,
                           __nv_bfloat16* Xhi, __nv_bfloat16* Xlo) {
+    pdl_trigger();   // the next sweep may start its H prefetch; it waits for this grid before reading X
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ldh * b) return;
     const int64_t r = e % ldh;
@@ -320,34 +393,42 @@ __global__ void k_split_x(int64_t d, int b, const float* __restrict__ X, int64_t
     Xlo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// P[i, j] = sum_s partial[s][j][i] in FP64 (fixed order), written as the bf16 pair (Phi, Plo),
-// column-major with leading dimension ldq; rows m..ldq-1 are zero.
-__global__ void k_reduce_split(int m, int b, int splits, const float* __restrict__ partial, int ldq,
-                               __nv_bfloat16* Phi, __nv_bfloat16* Plo) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)ldq * b) return;
-    const int i = (int)(e % ldq);
-    const int j = (int)(e / ldq);
-    float p = 0.f;
+// P[i, j] = sum_s partial[s][j][i] in FP64, written as the bf16 pair (Phi, Plo), column-major with
+// leading dimension ldq; rows m..ldq-1 are zero. CTA = 32 rows (lanes) of one column j (blockIdx.y);
+// warp w sums the split range [w q, (w + 1) q) in order, then warp 0 adds the eight warp sums in
+// order: a fixed summation order independent of timing.
+__global__ void __launch_bounds__(256) k_reduce_split(int m, int b, int splits, const float* __restrict__ partial,
+                                                      int ldq, __nv_bfloat16* Phi, __nv_bfloat16* Plo) {
+    __shared__ double part[8][33];
+    pdl_trigger();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const int j = blockIdx.y;
+    const int q = (splits + 7) / 8;
+    const int s0 = w * q, s1 = min(splits, s0 + q);
+    double acc = 0.0;
     if (i < m) {
-        const float* src = partial + (int64_t)j * m + i;
         const int64_t stride = (int64_t)m * b;
-        double acc = 0.0;
-        int s = 0;
-        for (; s + 4 <= splits; s += 4) {
-            const float v0 = src[(s + 0) * stride], v1 = src[(s + 1) * stride];
-            const float v2 = src[(s + 2) * stride], v3 = src[(s + 3) * stride];
-            acc += (double)v0;
-            acc += (double)v1;
-            acc += (double)v2;
-            acc += (double)v3;
-        }
-        for (; s < splits; ++s) acc += (double)src[s * stride];
-        p = (float)acc;
+        const float* src = partial + (int64_t)j * m + i;
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (s0 + u < s1) ? src[(s0 + u) * stride] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += (double)v[u];
+        for (int s = s0 + 8; s < s1; ++s) acc += (double)src[s * stride];
     }
-    const __nv_bfloat16 h = __float2bfloat16_rn(p);
-    Phi[e] = h;
-    Plo[e] = __float2bfloat16_rn(p - __bfloat162float(h));
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && i < ldq) {
+        double t = 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t += part[u][lane];
+        const float p = (i < m) ? (float)t : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(p);
+        Phi[(int64_t)j * ldq + i] = h;
+        Plo[(int64_t)j * ldq + i] = __float2bfloat16_rn(p - __bfloat162float(h));
+    }
 }
 
 // Columns c0 .. c0+31 of the symmetric FP64 K (m x m, ld m) as 32 rows of a bf16 pair with
@@ -364,22 +445,26 @@ __global__ void k_kslice_split(int m, int c0, const double* __restrict__ K, int 
     Klo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// column-major FP64 d x m -> column-major bf16 with leading dimension ldh (zero rows beyond d)
-__global__ void k_to_bf16_cm(int64_t d, int m, const double* __restrict__ H, int64_t ld, __nv_bfloat16* out,
-                             int64_t ldh) {
+// bf16 tiled image of an FP64 factor H (d x m, column-major, ld d). by_column = 1: tile rows are the
+// columns of H and K runs along d (sweep 1 operand); by_column = 0: tile rows are the rows of H and
+// K runs along m (sweep 2 operand, and the build-time H of H K). Entries outside H are zero.
+__global__ void k_tile_bf16(int64_t d, int m, const double* __restrict__ H, int by_column, int kbs, int64_t total,
+                            __nv_bfloat16* out) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ldh * m) return;
-    const int64_t r = e % ldh;
-    const int64_t c = e / ldh;
-    out[e] = __float2bfloat16_rn(r < d ? (float)H[c * ld + r] : 0.f);
-}
-// column-major FP64 d x m -> row-major bf16 d x ldm (zero columns beyond m)
-__global__ void k_to_bf16_rm(int64_t d, int m, const double* __restrict__ H, int64_t ld, __nv_bfloat16* out, int ldm) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= d * ldm) return;
-    const int64_t r = e / ldm;
-    const int c = (int)(e % ldm);
-    out[e] = __float2bfloat16_rn(c < m ? (float)H[(int64_t)c * ld + r] : 0.f);
+    if (e >= total) return;
+    const int64_t tile = e >> 13;
+    const int within = (int)(e & 8191);
+    const int rr = within >> 6, pc = (within >> 3) & 7, el = within & 7;
+    const int c = pc ^ (rr & 7);
+    const int64_t r = (tile / kbs) * TC_M + rr;
+    const int64_t kk = (tile % kbs) * TC_KS + c * 8 + el;
+    double v = 0.0;
+    if (by_column) {
+        if (r < m && kk < d) v = H[r * d + kk];
+    } else {
+        if (r < d && kk < m) v = H[kk * d + r];
+    }
+    out[e] = __float2bfloat16_rn((float)v);
 }
 
 // ---- tensor maps ------------------------------------------------------------------------------------------------
@@ -419,6 +504,25 @@ int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
     return r == CUDA_SUCCESS ? EDA_OK : EDA_ERR_CUDA;
 }
 
+// Launch with programmatic stream serialisation: the kernel may start while the preceding kernel of
+// the stream drains; it orders its dependent reads with griddepcontrol.wait.
+template <class... KArgs, class... Args>
+int launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    EDA_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+    launch_counter()++;
+    return EDA_OK;
+}
+
 template <int N, int MODE>
 int set_smem_attr() {
     static bool done = false;
@@ -435,7 +539,9 @@ int set_smem_attr() {
 
 template <int N>
 int launch_tc(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, int64_t ldx, float* Y, int64_t ldy,
-              float* partial, size_t partial_cap, bool x_split_ready, bool emit_split, int* status, cudaStream_t s) {
+              bool x_split_ready, bool emit_split, int* status, cudaStream_t s) {
+    float* partial = bufs.partial;
+    const size_t partial_cap = bufs.partial_cap;
     EDA_TRY((set_smem_attr<N, 0>()));
     constexpr size_t smem = tc_smem_bytes<N>();
     const int m = f.m;
@@ -452,81 +558,77 @@ int launch_tc(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, i
     if ((size_t)splits * m * b > partial_cap) return EDA_ERR_INVALID_ARG;
     const int rows = ceil_div(kst, splits) * TC_KS;
     splits = ceil_div(f.ldh, rows);
-    {
-        ProfScope prof("tc_sweep1", s);
-        k_tc_sweep1<N><<<dim3(tiles, splits), 128, smem, s>>>(f.mapA1, bufs.mapXh[nb], bufs.mapXl[nb], m, b, rows,
-                                                            (int)f.ldh, partial, status);
-        EDA_LAUNCHED();
-    }
-    k_reduce_split<<<ceil_div((int64_t)bufs.ldq * b, 256), 256, 0, s>>>(m, b, splits, partial, bufs.ldq, bufs.Qhi,
-                                                                        bufs.Qlo);
-    EDA_LAUNCHED();
-    {
-        ProfScope prof("tc_sweep2", s);
-        k_tc_sweep2<N, 0><<<ceil_div(f.d, TC_M), 128, smem, s>>>(
-            f.mapA2, bufs.mapQh[nb], bufs.mapQl[nb], f.d, f.ldm, b, X, ldx, Y, ldy, emit_split ? bufs.Xhi : nullptr,
-            emit_split ? bufs.Xlo : nullptr, f.ldh, nullptr, 0, status);
-        EDA_LAUNCHED();
-    }
+    EDA_TRY(launch_pdl(k_tc_sweep1<N>, dim3(tiles, splits), dim3(128), smem, s, f.A1, (int)(f.ldh / TC_KS),
+                       bufs.mapXh[nb], bufs.mapXl[nb], m, b, rows, (int)f.ldh, partial, status));
+    EDA_TRY(launch_pdl(k_reduce_split, dim3(ceil_div(bufs.ldq, 32), b), dim3(256), 0, s, m, b, splits,
+                       (const float*)partial, bufs.ldq, bufs.Qhi, bufs.Qlo));
+    EDA_TRY(launch_pdl(k_tc_sweep2<N, 0>, dim3(ceil_div(f.d, TC_M)), dim3(128), smem, s, f.A2, bufs.mapQh[nb],
+                       bufs.mapQl[nb], f.d, f.ldm, b, X, ldx, Y, ldy, emit_split ? bufs.Xhi : nullptr,
+                       emit_split ? bufs.Xlo : nullptr, f.ldh, (__nv_bfloat16*)nullptr, 0, 0, status));
     return EDA_OK;
 }
 
 }  // namespace
 
-int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bfloat16* Hcm, __nv_bfloat16* HKrm,
+int64_t tc_tiles_sweep1(int64_t d, int m) { return (int64_t)ceil_div(m, TC_M) * TC_M * tc_pad_rows(d); }
+int64_t tc_tiles_sweep2(int64_t d, int m) { return (int64_t)ceil_div(d, TC_M) * TC_M * tc_pad_cols(m); }
+
+int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bfloat16* A1, __nv_bfloat16* A2,
                    TcFactor* f, int* status, cudaStream_t s) {
     f->d = d;
     f->m = m;
     f->ldh = tc_pad_rows(d);
     f->ldm = tc_pad_cols(m);
-    f->Hcm = Hcm;
-    f->HKrm = HKrm;
-    k_to_bf16_cm<<<ceil_div(f->ldh * m, 256), 256, 0, s>>>(d, m, H, d, Hcm, f->ldh);
-    EDA_LAUNCHED();
-    // sweep 1 reads columns of H (K = d contiguous)
-    EDA_TRY(make_map(&f->mapA1, Hcm, (uint64_t)f->ldh, (uint64_t)m, (uint64_t)f->ldh, TC_M));
-    // H K (d x m, row-major bf16) as sweep-2 products: A = bf16(H) row-major, B = 32-column slices of K
-    // as bf16 pairs. Temporaries are freed before returning (the stream is synchronised first).
+    f->A1 = A1;
+    f->A2 = A2;
     const int ldm = f->ldm;
-    __nv_bfloat16* Hrm = nullptr;
-    __nv_bfloat16* Ks = nullptr;
-    const size_t hbytes = ((size_t)d * ldm * 2 + 255) / 256 * 256;
+    const int kbs1 = (int)(f->ldh / TC_KS), kbs2 = ldm / TC_KS;
+    {
+        const int64_t tot = tc_tiles_sweep1(d, m);
+        k_tile_bf16<<<ceil_div(tot, 256), 256, 0, s>>>(d, m, H, 1, kbs1, tot, A1);
+        EDA_LAUNCHED();
+    }
+    // H K (tiled like the sweep-2 operand) as sweep-2 products: A = tiled bf16(H) by rows, B = 32-column
+    // slices of K as bf16 pairs. Temporaries are freed before returning (the stream is synchronised).
+    const int64_t tot2 = tc_tiles_sweep2(d, m);
+    __nv_bfloat16* Hr = nullptr;
+    const size_t hbytes = ((size_t)tot2 * 2 + 255) / 256 * 256;
     const size_t kbytes = (size_t)ldm * 32 * 2;
-    if (cudaMalloc(&Hrm, hbytes + 2 * kbytes) != cudaSuccess) {
+    if (cudaMalloc(&Hr, hbytes + 2 * kbytes) != cudaSuccess) {
         cudaGetLastError();
         return EDA_ERR_OOM;
     }
-    Ks = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(Hrm) + hbytes);
-    __nv_bfloat16* Khi = Ks;
-    __nv_bfloat16* Klo = Ks + (size_t)ldm * 32;
+    __nv_bfloat16* Khi = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(Hr) + hbytes);
+    __nv_bfloat16* Klo = Khi + (size_t)ldm * 32;
     int rc = EDA_OK;
     do {
-        k_to_bf16_rm<<<ceil_div(d * ldm, 256), 256, 0, s>>>(d, m, H, d, Hrm, ldm);
+        k_tile_bf16<<<ceil_div(tot2, 256), 256, 0, s>>>(d, m, H, 0, kbs2, tot2, Hr);
         launch_counter()++;
         if (cudaPeekAtLastError() != cudaSuccess) { rc = EDA_ERR_CUDA; break; }
-        CUtensorMap mA, mKh, mKl;
-        if ((rc = make_map(&mA, Hrm, (uint64_t)ldm, (uint64_t)d, (uint64_t)ldm, TC_M)) != EDA_OK) break;
+        CUtensorMap mKh, mKl;
         if ((rc = make_map(&mKh, Khi, (uint64_t)ldm, 32, (uint64_t)ldm, 32)) != EDA_OK) break;
         if ((rc = make_map(&mKl, Klo, (uint64_t)ldm, 32, (uint64_t)ldm, 32)) != EDA_OK) break;
         if ((rc = set_smem_attr<32, 1>()) != EDA_OK) break;
         for (int c0 = 0; c0 < ldm && rc == EDA_OK; c0 += 32) {
             k_kslice_split<<<ceil_div((int64_t)ldm * 32, 256), 256, 0, s>>>(m, c0, K, ldm, Khi, Klo);
             k_tc_sweep2<32, 1><<<ceil_div(d, TC_M), 128, tc_smem_bytes<32>(), s>>>(
-                mA, mKh, mKl, d, ldm, 32, nullptr, 0, nullptr, 0, nullptr, nullptr, 0, HKrm + c0, ldm, status);
+                Hr, mKh, mKl, d, ldm, 32, nullptr, 0, nullptr, 0, nullptr, nullptr, 0, A2, kbs2, c0, status);
             launch_counter() += 2;
             if (cudaPeekAtLastError() != cudaSuccess) rc = EDA_ERR_CUDA;
         }
         if (rc == EDA_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = EDA_ERR_CUDA;
     } while (false);
     if (rc != EDA_OK) cudaStreamSynchronize(s);
-    cudaFree(Hrm);
-    if (rc != EDA_OK) return rc;
-    // sweep 2 reads rows of H K (K = m contiguous)
-    return make_map(&f->mapA2, HKrm, (uint64_t)ldm, (uint64_t)d, (uint64_t)ldm, TC_M);
+    cudaFree(Hr);
+    return rc;
 }
 
+size_t tc_partial_floats(int m_max) { return (size_t)(2 * 152 + ceil_div(m_max, TC_M)) * TC_M * 32; }
+
 int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, __nv_bfloat16* Qhi,
-                    __nv_bfloat16* Qlo, TcBuffers* b) {
+                    __nv_bfloat16* Qlo, float* partial, size_t partial_cap, TcBuffers* b) {
+    b->partial = partial;
+    b->partial_cap = partial_cap;
     b->Xhi = Xhi;
     b->Xlo = Xlo;
     b->Qhi = Qhi;
@@ -544,18 +646,17 @@ int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo
 }
 
 int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
-                 float* Y, int64_t ldy, void* partial, size_t partial_cap, int flags, int* status, cudaStream_t s) {
+                 float* Y, int64_t ldy, int flags, int* status, cudaStream_t s) {
     ProfScope prof(tag, s);
-    float* part = static_cast<float*>(partial);
     // the split pair lives in one 32-column staging buffer: chaining needs a single slice
     const bool chain = b <= 32;
     const bool ready = chain && (flags & TC_X_SPLIT_READY);
     const bool emit = chain && (flags & TC_EMIT_SPLIT);
-    if (b <= 16) return launch_tc<16>(f, bufs, b, X, ldx, Y, ldy, part, partial_cap, ready, emit, status, s);
+    if (b <= 16) return launch_tc<16>(f, bufs, b, X, ldx, Y, ldy, ready, emit, status, s);
     for (int c0 = 0; c0 < b; c0 += 32) {
         const int cb = std::min(32, b - c0);
-        EDA_TRY(launch_tc<32>(f, bufs, cb, X + (int64_t)c0 * ldx, ldx, Y + (int64_t)c0 * ldy, ldy, part, partial_cap,
-                              ready, emit, status, s));
+        EDA_TRY(launch_tc<32>(f, bufs, cb, X + (int64_t)c0 * ldx, ldx, Y + (int64_t)c0 * ldy, ldy, ready, emit,
+                              status, s));
     }
     return EDA_OK;
 }

@@ -149,12 +149,10 @@ int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* 
         const float* Xf = reinterpret_cast<const float*>(X);
         float* Yf = reinterpret_cast<float*>(Y);
         (void)tmp;
-        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Xf, ldx, Yf, ldy, partial, partial_cap,
-                             TC_EMIT_SPLIT, h->status, s));
-        EDA_TRY(exp_apply_tc(h->tcB, h->tcbuf, "exp_apply_b", b, Yf, ldy, Yf, ldy, partial, partial_cap,
-                             TC_X_SPLIT_READY | TC_EMIT_SPLIT, h->status, s));
-        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Yf, ldy, Yf, ldy, partial, partial_cap,
-                             TC_X_SPLIT_READY, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Xf, ldx, Yf, ldy, TC_EMIT_SPLIT, h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcB, h->tcbuf, "exp_apply_b", b, Yf, ldy, Yf, ldy, TC_X_SPLIT_READY | TC_EMIT_SPLIT,
+                             h->status, s));
+        EDA_TRY(exp_apply_tc(h->tcW, h->tcbuf, "exp_apply_w", b, Yf, ldy, Yf, ldy, TC_X_SPLIT_READY, h->status, s));
         return EDA_OK;
     }
     EDA_TRY(exp_apply<T>(d, HW, h->KW, n, "exp_apply_w", b, X, ldx, tmp, d, P, Q, partial, partial_cap, s));
