@@ -379,27 +379,45 @@ __global__ void __launch_bounds__(128) k_tc_sweep2(const __nv_bfloat16* __restri
     tc_teardown<N>(sm, tmem);
 }
 
-// X (d x b, ld ldx) -> Xhi, Xlo (bf16, column-major ld ldh, rows >= d zero)
+// X (d x b, ld ldx) -> Xhi, Xlo (bf16, column-major ld ldh, rows >= d zero). One thread per 8 rows of
+// one column: two 16-byte stores; 16-byte loads when X allows them (vec), else eight scalar loads.
 __global__ void k_split_x(int64_t d, int b, const float* __restrict__ X, int64_t ldx, int64_t ldh,
-                          __nv_bfloat16* Xhi, __nv_bfloat16* Xlo) {
+                          __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int vec) {
     pdl_trigger();   // the next sweep may start its H prefetch; it waits for this grid before reading X
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ldh * b) return;
-    const int64_t r = e % ldh;
-    const int64_t j = e / ldh;
-    const float x = r < d ? X[j * ldx + r] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    Xhi[e] = h;
-    Xlo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t groups = ldh / 8;
+    if (g >= groups * b) return;
+    const int64_t r = (g % groups) * 8;
+    const int64_t j = g / groups;
+    const float* src = X + j * ldx + r;
+    float x[8];
+    if (vec && r + 8 <= d) {
+        const float4 a = *reinterpret_cast<const float4*>(src);
+        const float4 c = *reinterpret_cast<const float4*>(src + 4);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = c.x; x[5] = c.y; x[6] = c.z; x[7] = c.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = (r + u < d) ? src[u] : 0.f;
+    }
+    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        hi[u] = __float2bfloat16_rn(x[u]);
+        lo[u] = __float2bfloat16_rn(x[u] - __bfloat162float(hi[u]));
+    }
+    *reinterpret_cast<uint4*>(Xhi + j * ldh + r) = *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(Xlo + j * ldh + r) = *reinterpret_cast<const uint4*>(lo);
 }
 
-// P[i, j] = sum_s partial[s][j][i] in FP64, written as the bf16 pair (Phi, Plo), column-major with
-// leading dimension ldq; rows m..ldq-1 are zero. CTA = 32 rows (lanes) of one column j (blockIdx.y);
-// warp w sums the split range [w q, (w + 1) q) in order, then warp 0 adds the eight warp sums in
-// order: a fixed summation order independent of timing.
+// P[i, j] = sum_s partial[s][j][i], written as the bf16 pair (Phi, Plo), column-major with leading
+// dimension ldq; rows m..ldq-1 are zero. CTA = 32 rows (lanes) of one column j (blockIdx.y); warp w
+// sums the split range [w q, (w + 1) q) in order, then warp 0 adds the eight warp sums in order: a
+// fixed summation order independent of timing. Single precision: the partials are FP32 tensor-core
+// accumulators and the product is bf16-accurate, while FP64 adds cost ~30x more issue slots here.
 __global__ void __launch_bounds__(256) k_reduce_split(int m, int b, int splits, const float* __restrict__ partial,
                                                       int ldq, __nv_bfloat16* Phi, __nv_bfloat16* Plo) {
-    __shared__ double part[8][33];
+    __shared__ float part[8][33];
     pdl_trigger();
     pdl_wait();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -407,7 +425,7 @@ __global__ void __launch_bounds__(256) k_reduce_split(int m, int b, int splits, 
     const int j = blockIdx.y;
     const int q = (splits + 7) / 8;
     const int s0 = w * q, s1 = min(splits, s0 + q);
-    double acc = 0.0;
+    float acc = 0.f;
     if (i < m) {
         const int64_t stride = (int64_t)m * b;
         const float* src = partial + (int64_t)j * m + i;
@@ -415,16 +433,16 @@ __global__ void __launch_bounds__(256) k_reduce_split(int m, int b, int splits, 
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = (s0 + u < s1) ? src[(s0 + u) * stride] : 0.f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc += (double)v[u];
-        for (int s = s0 + 8; s < s1; ++s) acc += (double)src[s * stride];
+        for (int u = 0; u < 8; ++u) acc += v[u];
+        for (int s = s0 + 8; s < s1; ++s) acc += src[s * stride];
     }
     part[w][lane] = acc;
     __syncthreads();
     if (w == 0 && i < ldq) {
-        double t = 0.0;
+        float t = 0.f;
 #pragma unroll
         for (int u = 0; u < 8; ++u) t += part[u][lane];
-        const float p = (i < m) ? (float)t : 0.f;
+        const float p = (i < m) ? t : 0.f;
         const __nv_bfloat16 h = __float2bfloat16_rn(p);
         Phi[(int64_t)j * ldq + i] = h;
         Plo[(int64_t)j * ldq + i] = __float2bfloat16_rn(p - __bfloat162float(h));
@@ -547,7 +565,8 @@ int launch_tc(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, i
     const int m = f.m;
     const int nb = N == 16 ? 0 : 1;
     if (!x_split_ready) {
-        k_split_x<<<ceil_div(f.ldh * b, 256), 256, 0, s>>>(f.d, b, X, ldx, f.ldh, bufs.Xhi, bufs.Xlo);
+        const int vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0 && ldx % 4 == 0) ? 1 : 0;
+        k_split_x<<<ceil_div(f.ldh / 8 * b, 256), 256, 0, s>>>(f.d, b, X, ldx, f.ldh, bufs.Xhi, bufs.Xlo, vec);
         EDA_LAUNCHED();
     }
     // sweep 1 over split ranges of whole stages
