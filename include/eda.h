@@ -173,7 +173,8 @@ int eda_get_dims(eda_handle h, int64_t* d, int64_t* n, int32_t* k, double* c2,
 
 void eda_destroy(eda_handle h);
 const char* eda_strerror(int status);
-/* The last CUDA error code seen by any call of this thread (0 = none) and its name. */
+/* The last CUDA error code seen by any call of this thread (0 = none), and its name with the
+ * library source location that saw it (a static per-thread string). */
 int eda_last_cuda_error(void);
 const char* eda_last_cuda_error_string(void);
 

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -13,10 +14,16 @@ namespace eda {
 
 namespace {
 thread_local int g_last_cuda_error = 0;
+thread_local char g_last_cuda_msg[256] = "no error";
 uint64_t g_launches = 0;
 }  // namespace
 
-void note_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
+void note_cuda_error(cudaError_t e, const char* file, int line) {
+    g_last_cuda_error = (int)e;
+    const char* base = file ? std::strrchr(file, '/') : nullptr;
+    base = base ? base + 1 : (file ? file : "?");
+    std::snprintf(g_last_cuda_msg, sizeof(g_last_cuda_msg), "%s (%s:%d)", cudaGetErrorString(e), base, line);
+}
 
 int ensure_workspace(eda_ctx* h, size_t bytes) {
     if (h->ws_bytes >= bytes) return EDA_OK;
@@ -66,8 +73,7 @@ int alloc_handle(eda_ctx* h, bool with_labels) {
     const size_t N = std::max(n, k);
     size_t bytes = 0;
     auto add = [&](size_t b) { bytes += align256(b); };
-    add(d * n * 8);           // HW
-    add(d * k * 8);           // HB
+    add(d * (n + k) * 8);     // [HW HB]
     if (with_labels) {
         add(k * 4);           // counts
         add((k + 1) * 4);     // offsets
@@ -95,8 +101,8 @@ int alloc_handle(eda_ctx* h, bool with_labels) {
     EDA_CUDA_TRY(cudaMalloc(&p, h->block_bytes));
     h->block = p;
     Arena a{static_cast<char*>(p), h->block_bytes, 0};
-    h->HW = a.take<double>(d * n);
-    h->HB = a.take<double>(d * k);
+    h->HW = a.take<double>(d * (n + k));
+    h->HB = h->HW + d * n;
     if (with_labels) {
         h->counts = a.take<int32_t>(k);
         h->offsets = a.take<int32_t>(k + 1);
@@ -157,6 +163,14 @@ int gram_eigen(eda_ctx* h, int m, double* G, double* evals, double* evecs, Arena
     return EDA_OK;
 }
 
+// B (k x n) = A^T for A (n x k), both column-major.
+__global__ void k_transpose_nk(int n, int k, const double* __restrict__ A, double* __restrict__ B) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    const int i = (int)(e % n), j = (int)(e / n);
+    B[(int64_t)i * k + j] = A[e];
+}
+
 // Everything after H_W, H_B exist: Grams, eigenpairs, c^2, K operators, and for the mixed
 // solver single-precision copies of the factors.
 int finish_build(eda_ctx* h, cudaStream_t s) {
@@ -207,6 +221,19 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     if (!tmp) return EDA_ERR_OOM;
     EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
     EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
+    if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16) {
+        // cross Grams G_WB = H_W^T H_B and G_BW = G_WB^T for the composed FP64 M-apply of the
+        // mixed-precision refinement
+        void* xp = nullptr;
+        const size_t xb = align256((size_t)n * k * 8);
+        EDA_CUDA_TRY(cudaMalloc(&xp, 2 * xb));
+        h->xblock = xp;
+        h->GWB = static_cast<double*>(xp);
+        h->GBW = reinterpret_cast<double*>(static_cast<char*>(xp) + xb);
+        EDA_TRY(gemm_tn_f64(d, n, k, 1.0, h->HW, d, h->HB, d, 0.0, h->GWB, n, part, pcap, s));
+        k_transpose_nk<<<ceil_div((int64_t)n * k, 256), 256, 0, s>>>(n, k, h->GWB, h->GBW);
+        EDA_LAUNCHED();
+    }
     if (h->cfg.prec == EDA_BF16) {
         // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
         // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)
@@ -458,6 +485,7 @@ void eda_destroy(eda_handle h) {
     if (!h) return;
     if (h->ws) cudaFree(h->ws);
     if (h->kblock) cudaFree(h->kblock);
+    if (h->xblock) cudaFree(h->xblock);
     if (h->block32) cudaFree(h->block32);
     if (h->block) cudaFree(h->block);
     delete h;
@@ -479,7 +507,7 @@ const char* eda_strerror(int status) {
 }
 
 int eda_last_cuda_error(void) { return g_last_cuda_error; }
-const char* eda_last_cuda_error_string(void) { return cudaGetErrorString((cudaError_t)g_last_cuda_error); }
+const char* eda_last_cuda_error_string(void) { return g_last_cuda_error ? g_last_cuda_msg : "no error"; }
 uint64_t eda_kernel_launches(void) { return g_launches; }
 
 }  // extern "C"

@@ -13,14 +13,14 @@
 namespace eda {
 
 // ---------------------------------------------------------------- errors
-void note_cuda_error(cudaError_t e);
+void note_cuda_error(cudaError_t e, const char* file = nullptr, int line = 0);
 uint64_t& launch_counter();
 
 #define EDA_CUDA_TRY(expr)                                        \
     do {                                                          \
         cudaError_t e__ = (expr);                                 \
         if (e__ != cudaSuccess) {                                 \
-            ::eda::note_cuda_error(e__);                          \
+            ::eda::note_cuda_error(e__, __FILE__, __LINE__);      \
             return e__ == cudaErrorMemoryAllocation ? EDA_ERR_OOM \
                                                     : EDA_ERR_CUDA; \
         }                                                         \
@@ -238,7 +238,7 @@ struct eda_ctx {
     // owned device memory
     void* block = nullptr;  // one allocation for everything below
     size_t block_bytes = 0;
-    double *HW = nullptr, *HB = nullptr;
+    double *HW = nullptr, *HB = nullptr;   // adjacent: [H_W H_B] is one d x (n + k) matrix (ld d)
     int32_t *counts = nullptr, *offsets = nullptr, *perm = nullptr;
     double *mu_j = nullptr, *mu = nullptr;
     double *GW = nullptr, *GB = nullptr;
@@ -259,6 +259,10 @@ struct eda_ctx {
     // K(alpha) for an alpha other than the stored ones (allocated on first use)
     void* kblock = nullptr;
     double *Kalpha = nullptr, *Kalpha_tmp = nullptr;
+    // cross Grams G_WB = H_W^T H_B (n x k) and G_BW = its transpose, for the composed FP64 M-apply of
+    // the mixed-precision refinement (allocated on first use)
+    void* xblock = nullptr;
+    double *GWB = nullptr, *GBW = nullptr;
     // solve workspace (grown on demand)
     void* ws = nullptr;
     size_t ws_bytes = 0;

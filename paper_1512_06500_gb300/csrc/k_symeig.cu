@@ -785,6 +785,7 @@ int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_
 int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, SymEigWork* ws, int* status,
                   cudaStream_t s) {
     if (n <= 0 || il < 0 || iu >= n || il > iu) return EDA_ERR_INVALID_ARG;
+    EDA_CUDA_TRY(cudaPeekAtLastError());   // surface an error left by an earlier call at its own site
     const int nv = iu - il + 1;
     double* HV = ws->partial;
     // ---- tridiagonal reduction: one cluster for small n, a cooperative grid otherwise ----
@@ -792,8 +793,10 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     EDA_CUDA_TRY(cudaGetDevice(&dev));
     int sms = 0;
     EDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // dynamic shared memory near 48 KB needs the opt-in too: the kernels also hold static shared
+    // variables, and the default limit covers static + dynamic
     const size_t smem = 2 * (size_t)n * sizeof(double);
-    if (smem > 48 * 1024) {
+    if (smem > 40 * 1024) {
         EDA_CUDA_TRY(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     if (n <= kClusterMaxN) {
@@ -824,8 +827,9 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     }
     }
     // ---- eigenvalues ----
+    EDA_CUDA_TRY(cudaPeekAtLastError());
     const size_t bsm = 3 * (size_t)n * sizeof(double);
-    if (bsm > 48 * 1024) {
+    if (bsm > 40 * 1024) {
         EDA_CUDA_TRY(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
     }
     {

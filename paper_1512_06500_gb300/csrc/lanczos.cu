@@ -35,13 +35,23 @@ __global__ void k_set_block(double* T, int ldt, int r0, int c0, int b, const dou
     T[(int64_t)(c0 + j) * ldt + (r0 + i)] = v;
 }
 
-// diagonal block: symmetrised
-__global__ void k_set_diag_block(double* T, int ldt, int r0, int b, const double* A, int lda) {
+// Column block j0..j0+b-1 of the projected matrix T = V^T M V from the full reorthogonalisation
+// coefficients (C1 + C2 = V^T (M V_j), cols x b, ld cols), mirrored into the row block; the diagonal
+// block symmetrised. Keeping every coupling (not only the block-tridiagonal ones) makes the
+// Rayleigh-Ritz step exact on span(V) even after lost directions were replaced by fresh ones.
+__global__ void k_set_col_block(double* T, int ldt, int cols, int j0, int b, const double* C1, const double* C2) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= b * b) return;
-    const int i = e % b, j = e / b;
-    const double v = 0.5 * (A[(int64_t)j * lda + i] + A[(int64_t)i * lda + j]);
-    T[(int64_t)(r0 + j) * ldt + (r0 + i)] = v;
+    if (e >= cols * b) return;
+    const int i = e % cols, jj = e / cols;
+    const double v = C1[(int64_t)jj * cols + i] + C2[(int64_t)jj * cols + i];
+    if (i < j0) {
+        T[(int64_t)(j0 + jj) * ldt + i] = v;
+        T[(int64_t)i * ldt + (j0 + jj)] = v;
+    } else {
+        const int ii = i - j0;
+        const double w = C1[(int64_t)ii * cols + (j0 + jj)] + C2[(int64_t)ii * cols + (j0 + jj)];
+        T[(int64_t)(j0 + jj) * ldt + i] = 0.5 * (v + w);
+    }
 }
 
 // relres[i] = ||B S[rlast:rlast+b, i]|| / |theta_i| for the t Ritz pairs (theta ascending).
@@ -94,6 +104,9 @@ struct SolveWs {
     T *V, *W, *W1, *tmp, *Yt;
     double *Tm, *C, *R1, *R1i, *R2, *R2i, *Bm, *P, *Q, *theta, *S, *relres;
     double *Y, *Z, *Y2, *Z2, *Xt, *Gt, *Rt, *Rti, *lamd, *tmp64;
+    double *R, *MR, *A2, *PQ, *Uc;   // refinement: [Y R] and [MY MR] adjacent; (2t)^2; (n + k) x t twice
+    double* ZY;                      // refinement: Z^T [Y R], (n + k) x 2t
+    int* idx;                        // refinement: unconverged columns
     void* part;
     int* lost;
     size_t pcap;
@@ -190,9 +203,12 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     const int b = h->cfg.block_b;
     const int tw = std::max(t, b);
     // rank threshold on squared pivots: relative to the bound lambda_1(M) <= exp(c^2 lmax(G_B))
-    // of Theorem 3.3 (nu_d = 0)
+    // of Theorem 3.3 (nu_d = 0). A new direction is lost when its norm after full
+    // reorthogonalisation is at the rounding level of the product, 64 eps ||M|| in the basis precision:
+    // above that level it carries real spectral content even when it is tiny against ||M||.
     const double normM = std::exp(std::min(700.0, h->c2 * h->lmax_b));
-    const double piv_min2 = (1e-12 * normM) * (1e-12 * normM);
+    const double eta = 64.0 * (std::is_same<T, double>::value ? 2.220446049250313e-16 : 1.1920928955078125e-7);
+    const double piv_min2 = (eta * normM) * (eta * normM);
 
     // ---- start block ----
     if (V0) {
@@ -212,7 +228,6 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     }
 
     int cols = b;
-    bool exhausted = false;
     st.relres.assign(t, INFINITY);
     // Rayleigh-Ritz schedule: the first check once the basis has t + b columns; later checks at
     // the basis width where the geometric rate seen between the last two checks predicts
@@ -230,7 +245,7 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
         double* C1 = w.C;
         double* C2 = w.C + (size_t)m_max * tw;
         EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W, d, C1, C2, w, s));
-        k_set_diag_block<<<ceil_div(b * b, 256), 256, 0, s>>>(w.Tm, m_max, j0, b, C1 + j0, cols);
+        k_set_col_block<<<ceil_div(cols * b, 256), 256, 0, s>>>(w.Tm, m_max, cols, j0, b, C1, C2);
         EDA_LAUNCHED();
         // CholQR2 of W with rank detection: W = V_{j+1} B_{j+1}
         EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
@@ -239,9 +254,7 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
         EDA_CUDA_TRY(cudaMemcpyAsync(&lostc, w.lost + b, sizeof(int), cudaMemcpyDeviceToHost, s));
         EDA_CUDA_TRY(cudaStreamSynchronize(s));
         const bool room = cols + b <= m_max;
-        if (lostc == b) {
-            exhausted = true;    // no direction outside the basis: T is exact (B_{j+1} = 0)
-        } else if (room) {
+        if (room) {
             if (lostc > 0) {
                 // replace the lost columns by fresh random directions orthogonal to the basis
                 st.refills += lostc;
@@ -260,15 +273,23 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
         } else {
             EDA_TRY(copy_mat_f64(b, b, w.R1, b, w.Bm, b, s));   // basis full: residual estimate only
         }
-        const bool last = exhausted || !room;
-        if ((cols >= next_check && cols >= t + 1) || (last && cols >= t)) {
+        const bool last = !room;
+        // a block lost entirely means span(V) is invariant to working precision: check at once (at most
+        // every fourth block, as a single-precision basis may lose every block on a wide spectrum)
+        const bool full_loss = lostc == b && cols >= t && cols - prev_check_cols >= 4 * b;
+        if ((cols >= next_check && cols >= t + 1) || (last && cols >= t) || full_loss) {
             ++st.checks;
             st.rr_cols = cols;
             ProfScope prof("rr", s);
             EDA_TRY(symeig_f64(cols, w.Tm, m_max, cols - t, cols - 1, w.theta, w.S, cols, &w.eig, h->status,
                                h->cfg.seed + 7, 1e-7, s));
-            if (exhausted) {
-                EDA_CUDA_TRY(cudaMemsetAsync(w.relres, 0, t * sizeof(double), s));
+            if (lostc > 0) {
+                // directions of W below the rank threshold were dropped from B: estimate from W itself,
+                // ||W s_last|| / |theta| (W is the reorthogonalised remainder of M V_j)
+                EDA_TRY(gemm_nn<T>(d, b, t, 1.0, w.W, d, w.S + (cols - b), cols, 0.0, nullptr, 0, w.Yt, d, s));
+                EDA_TRY(col_norms<T>(d, t, w.Yt, d, w.relres, s));
+                k_divide<<<ceil_div(t, 128), 128, 0, s>>>(t, w.relres, w.theta);
+                EDA_LAUNCHED();
             } else {
                 k_ritz_residuals<<<ceil_div(t, 128), 128, 0, s>>>(t, b, w.Bm, b, w.S, cols, cols - b, w.theta,
                                                                  w.relres);
@@ -308,54 +329,142 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     return EDA_OK;
 }
 
-// FP64 refinement of t approximate eigenvectors Y (d x t): Rayleigh-Ritz on span(Y) with an
-// FP64 M-apply; while some true relative residual exceeds tol, Y <- M Y (subspace iteration).
-// Leaves Y (orthonormal Ritz vectors, ascending theta), theta and the residuals.
+// M Y in FP64 for p columns through the composed form of the three products of Eq. (3.20): with
+// Theorem 3.1 for each factor and the Grams G_W, G_WB = H_W^T H_B, only two sweeps over
+// Z = [H_W H_B] remain:
+//     [p; q] = Z^T y
+//     u1 = K_W p                 y1 = y + H_W u1,   H_B^T y1 = q + G_BW u1,   H_W^T y1 = p + G_W u1
+//     v  = K_B (H_B^T y1)        y2 = y1 + H_B v,   H_W^T y2 = H_W^T y1 + G_WB v
+//     u3 = K_W (H_W^T y2)        M y = y2 + H_W u3 = y + Z [u1 + u3; v]
+// (the same operator as m_apply_t, in a third of the sweeps).
+int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY, int64_t ldm, double* PQ,
+                     double* U, double* ZtY, double* part, size_t pcap, cudaStream_t s) {
+    ProfScope prof("m_apply_composed", s);
+    const int64_t d = h->d;
+    const int n = (int)h->n, k = h->k, nk = n + k;
+    EDA_TRY(gemm_tn_f64(d, nk, p, 1.0, h->HW, d, Y, ldy, 0.0, PQ, nk, part, pcap, s));
+    if (ZtY) EDA_TRY(copy_mat_f64(nk, p, PQ, nk, ZtY, nk, s));   // keep Z^T y (coordinates) for the caller
+    double* Pw = PQ;
+    double* Qb = PQ + n;
+    double* Uw = U;
+    double* Ub = U + n;
+    EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->KW, n, Pw, nk, 0.0, Uw, nk, s));   // u1
+    EDA_TRY(gemm_small_f64(false, false, k, p, n, 1.0, h->GBW, k, Uw, nk, 1.0, Qb, nk, s));  // H_B^T y1
+    EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->GW, n, Uw, nk, 1.0, Pw, nk, s));   // H_W^T y1
+    EDA_TRY(gemm_small_f64(false, false, k, p, k, 1.0, h->KB, k, Qb, nk, 0.0, Ub, nk, s));   // v
+    EDA_TRY(gemm_small_f64(false, false, n, p, k, 1.0, h->GWB, n, Ub, nk, 1.0, Pw, nk, s));  // H_W^T y2
+    EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->KW, n, Pw, nk, 1.0, Uw, nk, s));   // u1 + u3
+    EDA_TRY(gemm_nn_f64(d, nk, p, 1.0, h->HW, d, U, nk, 1.0, Y, ldy, MY, ldm, s));
+    return EDA_OK;
+}
+
+namespace {
+
+// X (d x p) <- orth(X) by CholQR in FP64, `passes` times (columns at the rank threshold come out
+// zero). One pass suffices for an input that is orthonormal to single precision.
+template <class T>
+int cholqr_f64(int64_t d, int p, double* X, double* tmpX, SolveWs<T>& w, int passes, int* status, cudaStream_t s) {
+    double* part = static_cast<double*>(w.part);
+    for (int q = 0; q < passes; ++q) {
+        EDA_TRY(gemm_tn_f64(d, p, p, 1.0, X, d, X, d, 0.0, w.Rt, p, part, w.pcap, s));
+        EDA_TRY(chol_inv_small(p, w.Rt, p, w.Rti, 1e-28, 0.0, status, nullptr, s));
+        EDA_TRY(gemm_nn_f64(d, p, p, 1.0, X, d, w.Rti, p, 0.0, nullptr, 0, tmpX, d, s));
+        EDA_TRY(copy_mat_f64(d, p, tmpX, d, X, d, s));
+    }
+    return EDA_OK;
+}
+
+__global__ void k_gather_cols(int64_t d, int r, const int* idx, const double* src, int64_t lds, double* dst,
+                              int64_t ldd) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d * r) return;
+    const int64_t i = e % d;
+    const int j = (int)(e / d);
+    dst[(int64_t)j * ldd + i] = src[(int64_t)idx[j] * lds + i];
+}
+
+// Residuals R = MY - Y diag(theta) and relres_i = ||R_i|| / |theta_i| (host copy, max in *max_rel).
+template <class T>
+int ritz_residuals(int64_t d, int t, SolveWs<T>& w, std::vector<double>& relres_h, double* max_rel, cudaStream_t s) {
+    EDA_TRY(copy_mat_f64(d, t, w.Z, d, w.R, d, s));
+    k_sub_scaled<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, w.R, d, w.Y, d, w.theta);
+    EDA_LAUNCHED();
+    EDA_TRY(col_norms_f64(d, t, w.R, d, w.relres, s));
+    k_divide<<<ceil_div(t, 128), 128, 0, s>>>(t, w.relres, w.theta);
+    EDA_LAUNCHED();
+    EDA_CUDA_TRY(cudaMemcpyAsync(relres_h.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaStreamSynchronize(s));
+    *max_rel = 0.0;
+    for (int i = 0; i < t; ++i) *max_rel = std::max(*max_rel, relres_h[i]);
+    return EDA_OK;
+}
+
+}  // namespace
+
+// FP64 refinement of t approximate eigenvectors Y (d x t, in w.Y) from the single-precision phase:
+// Rayleigh-Ritz on span(Y), then, while some relative residual exceeds tol, Rayleigh-Ritz on
+// span([Y, R_u]) with R_u the residual columns of the unconverged pairs orthogonalised against Y
+// (each round one FP64 M-apply of those columns, in the composed form). Leaves Y (orthonormal Ritz
+// vectors, ascending theta) with w.Z = M Y, theta, the residuals, and the coordinates Z^T Y in
+// w.ZY (first t columns), from which the recovery step needs one sweep instead of two.
 template <class T>
 int refine_f64(eda_ctx* h, int t, double tol, SolveWs<T>& w, int max_iter, int* iters_out, int* mapplies,
                std::vector<double>& relres_h, double* max_rel, cudaStream_t s) {
     ProfScope prof("refine", s);
     const int64_t d = h->d;
     const int b = h->cfg.block_b;
+    const int nk = (int)h->n + h->k;
     double* part = static_cast<double*>(w.part);
+    if (!h->GWB) return EDA_ERR_INVALID_ARG;   // cross Grams are formed at build for mixed handles
+    // span(Y): orthonormalise (Y is orthonormal to single precision: one CholQR pass), M Y, Rayleigh-Ritz
+    EDA_TRY(cholqr_f64<T>(d, t, w.Y, w.Y2, w, 1, h->status, s));
+    EDA_TRY(m_apply_composed(h, t, w.Y, d, w.Z, d, w.PQ, w.Uc, w.ZY, part, w.pcap, s));
+    *mapplies += (t + b - 1) / b;
+    EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y, d, w.Z, d, 0.0, w.Gt, t, part, w.pcap, s));
+    EDA_TRY(symmetrize_f64(t, w.Gt, t, s));
+    EDA_TRY(symeig_f64(t, w.Gt, t, 0, t - 1, w.theta, w.S, t, &w.eig, h->status, h->cfg.seed + 11, 1e-7, s));
+    EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y, d, w.S, t, 0.0, nullptr, 0, w.Y2, d, s));
+    EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Z, d, w.S, t, 0.0, nullptr, 0, w.Z2, d, s));
+    EDA_TRY(copy_mat_f64(d, t, w.Y2, d, w.Y, d, s));
+    EDA_TRY(copy_mat_f64(d, t, w.Z2, d, w.Z, d, s));
+    EDA_TRY(gemm_small_f64(false, false, nk, t, t, 1.0, w.ZY, nk, w.S, t, 0.0, w.PQ, nk, s));
+    EDA_TRY(copy_mat_f64(nk, t, w.PQ, nk, w.ZY, nk, s));
+    EDA_TRY(ritz_residuals<T>(d, t, w, relres_h, max_rel, s));
     int it = 0;
-    for (; it < max_iter; ++it) {
-        // Y <- orth(Y) (CholQR2 in FP64)
-        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y, d, w.Y, d, 0.0, w.Rt, t, part, w.pcap, s));
-        EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
-        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y, d, w.Rti, t, 0.0, nullptr, 0, w.Y2, d, s));
-        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y2, d, w.Y2, d, 0.0, w.Rt, t, part, w.pcap, s));
-        EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
-        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y2, d, w.Rti, t, 0.0, nullptr, 0, w.Y, d, s));
-        // Z = M Y
-        EDA_TRY(m_apply_t<double>(h, t, w.Y, d, w.Z, d, w.tmp64, w.P, w.Q, w.part, w.pcap, s));
-        *mapplies += (t + b - 1) / b;
-        // Rayleigh-Ritz on span(Y): G = Y^T Z, eig, Y <- Y S, Z <- Z S
-        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y, d, w.Z, d, 0.0, w.Gt, t, part, w.pcap, s));
-        EDA_TRY(symmetrize_f64(t, w.Gt, t, s));
-        EDA_TRY(symeig_f64(t, w.Gt, t, 0, t - 1, w.theta, w.S, t, &w.eig, h->status, h->cfg.seed + 11, 1e-7, s));
-        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y, d, w.S, t, 0.0, nullptr, 0, w.Y2, d, s));
-        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Z, d, w.S, t, 0.0, nullptr, 0, w.Z2, d, s));
+    std::vector<int> idx;
+    while (*max_rel > tol && it < max_iter) {
+        ++it;
+        idx.clear();
+        for (int i = 0; i < t; ++i)
+            if (relres_h[i] > 0.5 * tol) idx.push_back(i);
+        const int r = (int)idx.size();
+        const int tr = t + r;
+        // R_u: the unconverged residual columns, packed right after Y ([Y R_u] adjacent)
+        EDA_CUDA_TRY(cudaMemcpyAsync(w.idx, idx.data(), r * sizeof(int), cudaMemcpyHostToDevice, s));
+        k_gather_cols<<<ceil_div(d * r, 256), 256, 0, s>>>(d, r, w.idx, w.R, d, w.Y2, d);
+        EDA_LAUNCHED();
+        EDA_TRY(copy_mat_f64(d, r, w.Y2, d, w.R, d, s));
+        for (int pass = 0; pass < 2; ++pass) {
+            EDA_TRY(gemm_tn_f64(d, t, r, 1.0, w.Y, d, w.R, d, 0.0, w.Gt, t, part, w.pcap, s));
+            EDA_TRY(gemm_nn_f64(d, t, r, -1.0, w.Y, d, w.Gt, t, 1.0, w.R, d, w.R, d, s));
+        }
+        EDA_TRY(cholqr_f64<T>(d, r, w.R, w.Y2, w, 2, h->status, s));
+        // M R_u, then Rayleigh-Ritz on [Y R_u] (adjacent in memory, as are [MY M R_u] and their coordinates)
+        EDA_TRY(m_apply_composed(h, r, w.R, d, w.MR, d, w.PQ, w.Uc, w.ZY + (size_t)nk * t, part, w.pcap, s));
+        *mapplies += (r + b - 1) / b;
+        EDA_TRY(gemm_tn_f64(d, tr, tr, 1.0, w.Y, d, w.Z, d, 0.0, w.A2, tr, part, w.pcap, s));
+        EDA_TRY(symmetrize_f64(tr, w.A2, tr, s));
+        EDA_TRY(symeig_f64(tr, w.A2, tr, r, tr - 1, w.theta, w.S, tr, &w.eig, h->status, h->cfg.seed + 13 + it,
+                           1e-7, s));
+        EDA_TRY(gemm_nn_f64(d, tr, t, 1.0, w.Y, d, w.S, tr, 0.0, nullptr, 0, w.Y2, d, s));
+        EDA_TRY(gemm_nn_f64(d, tr, t, 1.0, w.Z, d, w.S, tr, 0.0, nullptr, 0, w.Z2, d, s));
         EDA_TRY(copy_mat_f64(d, t, w.Y2, d, w.Y, d, s));
         EDA_TRY(copy_mat_f64(d, t, w.Z2, d, w.Z, d, s));
-        // true residuals R = Z S - Y S theta
-        k_sub_scaled<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, w.Z2, d, w.Y, d, w.theta);
-        EDA_LAUNCHED();
-        EDA_TRY(col_norms_f64(d, t, w.Z2, d, w.relres, s));
-        k_divide<<<ceil_div(t, 128), 128, 0, s>>>(t, w.relres, w.theta);
-        EDA_LAUNCHED();
-        EDA_CUDA_TRY(cudaMemcpyAsync(relres_h.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
-        EDA_CUDA_TRY(cudaStreamSynchronize(s));
-        *max_rel = 0.0;
-        for (int i = 0; i < t; ++i) *max_rel = std::max(*max_rel, relres_h[i]);
-        if (*max_rel <= tol) {
-            ++it;
-            break;
-        }
-        // subspace iteration: the next subspace is span(M Y) = span(Z)
-        EDA_TRY(copy_mat_f64(d, t, w.Z, d, w.Y, d, s));
+        EDA_TRY(gemm_small_f64(false, false, nk, t, tr, 1.0, w.ZY, nk, w.S, tr, 0.0, w.PQ, nk, s));
+        EDA_TRY(copy_mat_f64(nk, t, w.PQ, nk, w.ZY, nk, s));
+        EDA_TRY(ritz_residuals<T>(d, t, w, relres_h, max_rel, s));
     }
-    *iters_out = it;
+    *iters_out = it + 1;
     return EDA_OK;
 }
 
@@ -381,8 +490,9 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
 
     // ---- workspace ----
     SolveWs<T> w{};
-    w.pcap = std::max<size_t>({size_t(1) << 19, (size_t)m_max * tw, (size_t)N * tw, (size_t)t * t});
-    const int eig_n = std::max(m_max, t);
+    w.pcap = std::max<size_t>({size_t(1) << 19, (size_t)m_max * tw, (size_t)N * tw, (size_t)4 * t * t,
+                               (size_t)(n + k) * t, (size_t)n * k});
+    const int eig_n = std::max(m_max, 2 * t);
     size_t need = 0;
     auto addT = [&](size_t cnt) { need += a256(cnt * sizeof(T)); };
     auto add = [&](size_t cnt) { need += a256(cnt * 8); };
@@ -399,7 +509,10 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     add(t);                            // theta
     add((size_t)eig_n * t);            // S
     add(t);                            // relres
-    for (int i = 0; i < 5; ++i) add((size_t)d * t);   // Y, Z, Y2, Z2, Xt
+    for (int i = 0; i < 7; ++i) add((size_t)d * t);   // Y, R (adjacent), Z, MR (adjacent), Y2, Z2, Xt
+    add((size_t)4 * t * t);            // A2
+    add((size_t)(n + k) * t * 4);      // PQ, Uc, ZY
+    add(t + 64);                       // idx (ints)
     add((size_t)d * tw);               // tmp64
     add((size_t)t * t * 4);            // Gt, Rt, Rti
     add(t);                            // lamd
@@ -427,8 +540,15 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     w.theta = a.take<double>(t);
     w.S = a.take<double>((size_t)eig_n * t);
     w.relres = a.take<double>(t);
-    w.Y = a.take<double>((size_t)d * t);
-    w.Z = a.take<double>((size_t)d * t);
+    w.Y = a.take<double>((size_t)2 * d * t);
+    w.R = w.Y + (size_t)d * t;
+    w.Z = a.take<double>((size_t)2 * d * t);
+    w.MR = w.Z + (size_t)d * t;
+    w.A2 = a.take<double>((size_t)4 * t * t);
+    w.PQ = a.take<double>((size_t)(n + k) * t);
+    w.Uc = a.take<double>((size_t)(n + k) * t);
+    w.ZY = a.take<double>((size_t)(n + k) * t * 2);
+    w.idx = a.take<int>(t + 64);
     w.Y2 = a.take<double>((size_t)d * t);
     w.Z2 = a.take<double>((size_t)d * t);
     w.Xt = a.take<double>((size_t)d * t);
@@ -476,8 +596,17 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     EDA_LAUNCHED();
     EDA_CUDA_TRY(cudaMemcpyAsync(lambda, w.lamd, t * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (Yout) EDA_CUDA_TRY(cudaMemcpyAsync(Yout, w.Y2, (size_t)d * t * 8, cudaMemcpyDeviceToDevice, s));
-    // x = exp(-c^2 S_W / 2) y
-    EDA_TRY(exp_apply<double>(d, h->HW, h->KW, n, "exp_apply_w", t, w.Y2, d, w.Xt, d, w.P, w.Q, w.part, w.pcap, s));
+    // x = exp(-c^2 S_W / 2) y = y + H_W K_W (H_W^T y)
+    if (mixed) {
+        // H_W^T Y is already known (the first n rows of the tracked coordinates Z^T Y): one sweep
+        EDA_TRY(gemm_small_f64(false, false, n, t, n, 1.0, h->KW, n, w.ZY, n + k, 0.0, w.PQ, n, s));
+        EDA_TRY(gemm_nn_f64(d, n, t, 1.0, h->HW, d, w.PQ, n, 1.0, w.Y, d, w.Z2, d, s));
+        k_reverse_cols<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, w.Z2, d, w.Xt, d);
+        EDA_LAUNCHED();
+    } else {
+        EDA_TRY(exp_apply<double>(d, h->HW, h->KW, n, "exp_apply_w", t, w.Y2, d, w.Xt, d, w.P, w.Q, w.part, w.pcap,
+                                  s));
+    }
     // V = orth(X_t): CholQR2
     {
         double* part = static_cast<double*>(w.part);
@@ -507,6 +636,8 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
         EDA_CUDA_TRY(cudaStreamSynchronize(s));
         true_max = 0.0;
         for (int i = 0; i < t; ++i) true_max = std::max(true_max, rn[i] / std::fabs(lam_h[i]));
+        // the estimates must not claim more than an independent FP64 evaluation confirms
+        if (true_max > 10.0 * tol) converged = false;
     }
     EDA_CUDA_TRY(cudaEventRecord(ev1, s));
     EDA_CUDA_TRY(cudaEventSynchronize(ev1));
