@@ -1,0 +1,85 @@
+"""FP64 solver at the two large synthetic workloads, in the configuration the benchmark runs.
+
+d = 16384, k = 100 (n = 700): full comparison with the oracle's projected exact route.
+d = 65536, k = 200 (n = 2000): the oracle's dense route is out of reach, so sampled Ritz pairs are
+checked one by one: the oracle applies M (the three Theorem 3.1 products through its own QR/SVD
+route) to each sampled Ritz vector and the true relative residual must meet the tolerance. The
+sample covers the top of the spectrum (lambda ~ e^20), the isolated pair just above 1 and members
+of the tight cluster at 1.003 (gaps ~ 5e-6), where a Rayleigh-Ritz step on an inexact projected
+matrix fails first.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1512_06500_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_06500_gb300 import build_lib, eda as E
+    build_lib.build()
+    E.load()
+    return E
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def test_fp64_d16384_k100_matches_oracle(eda):
+    name = "d16384_k100"
+    c = synth.CONFIGS[name]
+    p = synth.config_problem(name)
+    cfg = eda.config(prec=eda.EDA_F64, block_b=c["b"], tau=c["tau"], true_residuals=1)
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        V, lam, _, info, code = h.solve(c["t"], 1e-10)
+        assert code == 0, info
+        Ptr = h.project(V, _dev(p.X)).cpu().numpy()
+        Pte = h.project(V, _dev(p.Xtest)).cpu().numpy()
+        c2 = h.c2
+    ref = O.eda(p.X, p.labels, p.k, c["t"], c2=c2, tier="projected")
+    lam = lam.cpu().numpy()
+    rel = np.abs(lam - ref["lam_t"]) / ref["lam_t"]
+    # tau = 20: the attainable FP64 accuracy of lambda_i is about eps lambda_1 / lambda_i
+    bound = 64 * np.finfo(float).eps * ref["lam_t"][0] / ref["lam_t"]
+    assert np.all(rel <= np.maximum(1e-10, bound)), (rel.max(), bound.min())
+    assert info["max_relres_true"] <= 1e-8
+    assert O.sin_angle(ref["V"], V.cpu().numpy().T) <= 1e-6
+    lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
+    lab_o, _, _ = O.nn_classify(O.project(ref["V"], p.X), p.labels, O.project(ref["V"], p.Xtest))
+    assert np.array_equal(lab_g, lab_o)
+
+
+def test_fp64_d65536_k200_sampled_pairs(eda):
+    name = "d65536_k200"
+    c = synth.CONFIGS[name]
+    p = synth.config_problem(name)
+    tol = 1e-7
+    cfg = eda.config(prec=eda.EDA_F64, block_b=c["b"], tau=c["tau"])
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        V, lam, Y, info, code = h.solve(c["t"], tol, want_y=True)
+        assert code == 0, info
+        c2 = h.c2
+        VtV = (V @ V.T).cpu().numpy()
+        Y = Y.cpu().numpy()
+    lam = lam.cpu().numpy()
+    assert np.all(np.diff(lam) <= 0)
+    assert np.abs(VtV - np.eye(c["t"])).max() <= 1e-12
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    HW, HB = f["HW"], f["HB"]
+    idx = [0, 19, 20, 21, 100, c["t"] - 1]
+    Ys = Y[idx].T                                        # d x 6
+    MY = O.m_apply(HW, HB, c2, Ys)
+    res = np.linalg.norm(MY - Ys * lam[idx], axis=0) / lam[idx]
+    # tolerance plus the FP64 rounding of a product with ||M|| ~ lambda_1
+    floor = 64 * np.finfo(float).eps * lam[0] / lam[idx]
+    assert np.all(res <= tol + floor), (res, floor)
+    # the sampled values agree with the Rayleigh quotients the oracle computes from the same vectors
+    rq = np.einsum("ij,ij->j", Ys, MY)
+    assert np.all(np.abs(rq - lam[idx]) / lam[idx] <= 1e-9 + floor)
