@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--workload", default="d4096_k40", choices=list(synth.CONFIGS))
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-exp-apply", action="store_true", help="skip the bf16 tensor-core exp-apply leg")
+    ap.add_argument("--exp-apply-reps", type=int, default=30)
+    ap.add_argument("--profile-exp-apply", default=None, metavar="D,K,NJ,B",
+                    help="profiling driver: build a bf16 handle on a d x (K*NJ) Gaussian-cluster problem "
+                         "and run three W exp-applies of width B, nothing else")
     return ap.parse_args()
 
 
@@ -138,6 +143,88 @@ def cpu_baseline(p, c, tol, budget_s=12.0, max_reps=30):
                       f"numpy threads default"}
 
 
+# ---------------------------------------------------------------- bf16 tensor-core exp-apply leg
+
+EXP_APPLY_WORKLOADS = ("d16384_k100", "d65536_k200")
+
+
+def exp_apply_bytes(d, m, b):
+    """Algorithmic bytes of one exp-apply Y = X + (H K)(H^T X) on the tensor cores: a sweep over
+    bf16 H and one over bf16 H K (2 bytes each), X (FP32) read twice, Y written once."""
+    return 2 * 2 * d * m + 3 * 4 * d * b
+
+
+def exp_apply_leg(dev, flush, reps):
+    """Cold-L2 timing of the Theorem 3.1 product exp(-c^2 H_W H_W^T / 2) X with bf16 H_W on the
+    tensor cores, on the W factor of the mixed-precision workloads; CUDA events on the launching
+    stream, the L2 flushed (256 MB write) before every call."""
+    import torch
+    from paper_1512_06500_gb300 import eda
+
+    pk = peaks()
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name in EXP_APPLY_WORKLOADS:
+        c = synth.CONFIGS[name]
+        p = synth.config_problem(name)
+        X = torch.from_numpy(p.X).to(dev)
+        lab = torch.from_numpy(p.labels).to(dev)
+        h = eda.build(X, lab, p.k, eda.config(prec=eda.EDA_BF16, block_b=c["b"], tau=c["tau"]))
+        del X
+        b = c["b"]
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        Xb = torch.randn(b, p.d, dtype=torch.float32, device=dev, generator=gen)
+        Y = torch.empty_like(Xb)
+        alpha = -0.5 * h.c2
+        for _ in range(3):
+            h.apply_exp(eda.OP_SW, Xb, alpha=alpha, out=Y)
+        launches0 = eda.kernel_launches()
+        ev = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.apply_exp(eda.OP_SW, Xb, alpha=alpha, out=Y)
+            e.record(stream)
+            ev.append((a, e))
+        torch.cuda.synchronize()
+        per_call = (eda.kernel_launches() - launches0) / reps
+        us = sorted(a.elapsed_time(e) * 1e3 for a, e in ev)
+        med = us[len(us) // 2]
+        nbytes = exp_apply_bytes(p.d, p.n, b)
+        gbs = nbytes / med / 1e3
+        out[name] = {"d": p.d, "m": p.n, "b": b, "us_median": med, "us_min": us[0], "algorithmic_bytes": nbytes,
+                     "achieved_gbs": gbs, "peak_gbs": pk["hbm"], "frac": gbs / pk["hbm"],
+                     "peak_source": pk["source"], "kernels_per_call": per_call, "l2": "flushed before every call"}
+        h.close()
+        del p
+    return out
+
+
+def profile_exp_apply(spec):
+    """Small fixed case for ncu: three W exp-applies, no timing."""
+    import torch
+    from paper_1512_06500_gb300 import build_lib, eda
+
+    build_lib.build()
+    d, k, nj, b = (int(v) for v in spec.split(","))
+    p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=3)
+    X = torch.from_numpy(p.X).cuda()
+    lab = torch.from_numpy(p.labels).cuda()
+    h = eda.build(X, lab, p.k, eda.config(prec=eda.EDA_BF16, block_b=min(b, 16), tau=20.0))
+    del X
+    Xb = torch.randn(b, p.d, dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(Xb)
+    for _ in range(3):
+        h.apply_exp(eda.OP_SW, Xb, alpha=-0.5 * h.c2, out=Y)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "profile-exp-apply", "d": d, "m": p.n, "b": b,
+                      "checksum": float(Y.double().abs().sum().item())}))
+    h.close()
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def run_gpu(args, rank, world, local_rank):
@@ -201,28 +288,34 @@ def run_gpu(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
-    # ---- roofline of the exp-apply (Theorem 3.1 product) measured inside the timed region ----
+    # ---- rooflines measured inside the timed region (library event pairs + its own work counts) ----
     regions = {r: eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b", "m_apply", "tridiag", "bisect",
                                                   "invit", "backtransform", "symeig", "gram", "rr", "reorth")}
-    d, n, k, b = p.d, p.n, p.k, c["b"]
-    ew_ms, ew_calls = regions["exp_apply_w"]
-    # Lanczos-block calls have width b; the recovery call has width t. Count FLOPs per call exactly:
-    # each product is two sweeps of 2 d m w flops (H^T X and H Q) plus 2 m^2 w for K P.
-    nb_calls = sum(inf["mapplies"] for inf in infos) * 2        # two W products per M-apply
-    nt_calls = ew_calls - nb_calls                                 # recovery products (width t)
-    flops_w = nb_calls * (4.0 * d * n * b + 2.0 * n * n * b) + nt_calls * (4.0 * d * n * c["t"] + 2.0 * n * n * c["t"])
-    bytes_w = nb_calls * (8.0 * (2 * d * n + 3 * d * b)) + nt_calls * (8.0 * (2 * d * n + 3 * d * c["t"]))
-    ew_s = ew_ms / 1e3 if ew_ms > 0 else float("nan")
-    achieved_tflops = flops_w / ew_s / 1e12
-    achieved_gbs = bytes_w / ew_s / 1e9
     pk = peaks()
+    # dominant kernel of the step (ncu launch list): the Householder tridiagonalisation of the small FP64
+    # matrices (the n x n Gram of the build and the Rayleigh-Ritz matrices of the solve)
+    tri_ms, tri_calls = regions["tridiag"]
+    tri_flops, _ = eda.profile_work("tridiag")
+    tri_tf = tri_flops / (tri_ms / 1e3) / 1e12 if tri_ms > 0 else float("nan")
     roofline = {
-        "kernel": "exp_apply (H_W, FP64): Y = X + H_W K (H_W^T X)",
-        "bound": "alu", "achieved": achieved_tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved_tflops / NOMINAL_FP64_TFLOPS, "traffic": None,
+        "kernel": "k_tridiag_cluster: Householder tridiagonalisation (4/3 n^3 flops) of the FP64 Gram and "
+                  "Rayleigh-Ritz matrices",
+        "bound": "alu", "achieved": tri_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+        "frac": tri_tf / NOMINAL_FP64_TFLOPS, "traffic": None,
         "peak_source": "nominal FP64 rate of the profiling recipe (own probe measured 1.19 TFLOP/s)",
-        "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": pk["hbm"], "hbm_peak_source": pk["source"],
-        "hbm_frac": achieved_gbs / pk["hbm"],
+        "note": "latency-bound: n dependent column steps, each with cluster-wide reductions; the matrix "
+                "lives in distributed shared memory",
+        "avg_call_us": tri_ms * 1e3 / max(tri_calls, 1), "calls": tri_calls,
+        "flops_per_step": tri_flops / args.steps,
+    }
+    ew_ms, ew_calls = regions["exp_apply_w"]
+    ew_flops, ew_bytes = eda.profile_work("exp_apply_w")
+    ew_s = ew_ms / 1e3 if ew_ms > 0 else float("nan")
+    exp_apply_fp64 = {
+        "kernel": "exp_apply (H_W, FP64 sweeps): Y = X + H_W K (H_W^T X)", "bound": "alu",
+        "achieved_tflops": ew_flops / ew_s / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
+        "frac": ew_flops / ew_s / 1e12 / NOMINAL_FP64_TFLOPS,
+        "achieved_gbs": ew_bytes / ew_s / 1e9, "hbm_peak_gbs": pk["hbm"], "hbm_peak_source": pk["source"],
         "avg_call_us": ew_ms * 1e3 / max(ew_calls, 1), "calls": ew_calls,
     }
 
@@ -267,6 +360,10 @@ def run_gpu(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_v = float(t.item())
 
+    exp_leg = None
+    if not args.no_exp_apply and rank == 0:
+        exp_leg = exp_apply_leg(dev, flush, args.exp_apply_reps)
+
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -275,6 +372,8 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk, "gpu_launches": launches,
         "e2e": {"value": e2e_v, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
+        "exp_apply_fp64": exp_apply_fp64,
+        "exp_apply_bf16": exp_leg,
         "breakdown_ms_per_step": {r: v[0] / args.steps for r, v in regions.items()},
         "solve_info": {kk: infos[-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols", "max_relres_est")},
         "wall_s": wall,
@@ -284,6 +383,9 @@ def run_gpu(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    if args.profile_exp_apply:
+        profile_exp_apply(args.profile_exp_apply)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

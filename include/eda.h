@@ -191,6 +191,11 @@ uint64_t eda_kernel_launches(void);
 int eda_profile_enable(int on);
 int eda_profile_reset(void);
 int eda_profile_read(const char* region, double* total_ms, int64_t* calls);
+/* Algorithmic work counted by the library for the calls of a region while timing was on: FLOPs
+ * and bytes by the definition of the operation, not by the kernels' actual traffic ("tridiag":
+ * 4/3 n^3 flops; "exp_apply_w"/"exp_apply_b": 4 d m b + 2 m^2 b flops and 2 |H| + 3 |X| bytes
+ * in the storage type of the sweeps; 0, 0 for regions without a count or unknown names). */
+int eda_profile_work(const char* region, double* flops, double* bytes);
 
 #ifdef __cplusplus
 }

@@ -54,7 +54,8 @@ enum : int {
 // Records a CUDA event pair around its scope on stream s when profiling is enabled.
 class ProfScope {
   public:
-    ProfScope(const char* name, cudaStream_t s);
+    // flops, bytes: algorithmic work of this call, accumulated per region while timing is on
+    ProfScope(const char* name, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
     ~ProfScope();
     ProfScope(const ProfScope&) = delete;
     ProfScope& operator=(const ProfScope&) = delete;

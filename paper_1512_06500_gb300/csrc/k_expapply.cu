@@ -11,7 +11,7 @@ namespace eda {
 template <class T>
 int exp_apply(int64_t d, const T* H, const double* K, int m, const char* tag, int b, const T* X, int64_t ldx, T* Y,
               int64_t ldy, double* P, double* Q, void* partial, size_t partial_cap, cudaStream_t s) {
-    ProfScope prof(tag, s);
+    ProfScope prof(tag, s, 4.0 * d * m * b + 2.0 * m * m * b, (double)sizeof(T) * (2.0 * d * m + 3.0 * d * b));
     // sweep 1: P = H^T X (m x b), split over d with a fixed-order reduction
     EDA_TRY(gemm_tn<T>(d, m, b, 1.0, H, d, X, ldx, 0.0, P, m, partial, partial_cap, s));
     // Q = K P (m x b)

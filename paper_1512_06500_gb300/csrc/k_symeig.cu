@@ -746,7 +746,7 @@ int launch_tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cuda
         cudaGetLastError();
         return EDA_OK;
     }
-    ProfScope prof("tridiag", s);
+    ProfScope prof("tridiag", s, 4.0 / 3.0 * (double)n * n * n);
     EDA_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, n, A, lda, ws->A, in_smem, ws->partial, ws->dgl, ws->eoff, ws->tau));
     launch_counter()++;
     return EDA_OK;
@@ -771,8 +771,10 @@ int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_
             want = 1;
             while (want < 16 && want * 2 * 12 <= n) want *= 2;
         }
-        int C = want;
-        for (; C > 1; C /= 2) {
+        // clusters of at least two CTAs: the kernel's one-CTA instance loses accuracy on small n and is
+        // not used
+        int C = std::max(2, want);
+        for (; C > 2; C /= 2) {
             bool fits = false;
             EDA_TRY(launch_tridiag_c(C, n, A, lda, ws, s, true, &fits));
             if (fits) break;
@@ -811,7 +813,7 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     k_copy_sq<<<ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, A, lda, ws->A);
     EDA_LAUNCHED();
     {
-        ProfScope prof("tridiag", s);
+        ProfScope prof("tridiag", s, 4.0 / 3.0 * (double)n * n * n);
         int nn = n;
         double* a0 = ws->A;
         double* a1 = HV;

@@ -666,7 +666,7 @@ int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo
 
 int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
                  float* Y, int64_t ldy, int flags, int* status, cudaStream_t s) {
-    ProfScope prof(tag, s);
+    ProfScope prof(tag, s, 4.0 * f.d * f.m * b, 2.0 * 2.0 * f.d * f.m + 3.0 * 4.0 * f.d * b);
     // the split pair lives in one 32-column staging buffer: chaining needs a single slice
     const bool chain = b <= 32;
     const bool ready = chain && (flags & TC_X_SPLIT_READY);

@@ -274,9 +274,10 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
             EDA_TRY(copy_mat_f64(b, b, w.R1, b, w.Bm, b, s));   // basis full: residual estimate only
         }
         const bool last = !room;
-        // a block lost entirely means span(V) is invariant to working precision: check at once (at most
-        // every fourth block, as a single-precision basis may lose every block on a wide spectrum)
-        const bool full_loss = lostc == b && cols >= t && cols - prev_check_cols >= 4 * b;
+        // a block lost entirely means span(V) is invariant to working precision: check at once (for a
+        // single-precision basis at most every fourth block: on a wide spectrum it may lose every block)
+        const bool full_loss = lostc == b && cols >= t &&
+                               (std::is_same<T, double>::value || cols - prev_check_cols >= 4 * b);
         if ((cols >= next_check && cols >= t + 1) || (last && cols >= t) || full_loss) {
             ++st.checks;
             st.rr_cols = cols;

@@ -14,6 +14,7 @@ struct Region {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     double total_ms = 0.0;
     int64_t calls = 0;
+    double flops = 0.0, bytes = 0.0;   // algorithmic work of the calls, as counted at entry
 };
 std::mutex g_mu;
 bool g_on = false;
@@ -46,9 +47,12 @@ int resolve(Region& r) {
 }
 }  // namespace
 
-ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
+ProfScope::ProfScope(const char* name, cudaStream_t s, double flops, double bytes) : name_(name), s_(s) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) return;
+    Region& r = g_regions[name_];
+    r.flops += flops;
+    r.bytes += bytes;
     e0_ = get_event();
     if (e0_) cudaEventRecord(e0_, s_);
 }
@@ -80,6 +84,8 @@ int eda_profile_reset(void) {
         resolve(kv.second);
         kv.second.total_ms = 0.0;
         kv.second.calls = 0;
+        kv.second.flops = 0.0;
+        kv.second.bytes = 0.0;
     }
     return EDA_OK;
 }
@@ -97,6 +103,15 @@ int eda_profile_read(const char* region, double* total_ms, int64_t* calls) {
     if (total_ms) *total_ms = it->second.total_ms;
     if (calls) *calls = it->second.calls;
     return rc;
+}
+
+int eda_profile_work(const char* region, double* flops, double* bytes) {
+    if (!region) return EDA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_regions.find(region);
+    if (flops) *flops = it == g_regions.end() ? 0.0 : it->second.flops;
+    if (bytes) *bytes = it == g_regions.end() ? 0.0 : it->second.bytes;
+    return EDA_OK;
 }
 
 }  // extern "C"

@@ -33,7 +33,7 @@ EXPORTS = [
     "eda_config_default", "eda_build", "eda_build_from_factors", "eda_apply_exp", "eda_solve",
     "eda_project", "eda_get_factors", "eda_get_dims", "eda_destroy", "eda_strerror",
     "eda_last_cuda_error", "eda_last_cuda_error_string", "eda_kernel_launches",
-    "eda_profile_enable", "eda_profile_reset", "eda_profile_read",
+    "eda_profile_enable", "eda_profile_reset", "eda_profile_read", "eda_profile_work",
     "eda_lowrank_exp_apply_noalloc",
 ]
 
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "eda_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "eda_profile_reset": ([], ctypes.c_int),
         "eda_profile_read": ([ctypes.c_char_p, P(f64), P(i64)], ctypes.c_int),
+        "eda_profile_work": ([ctypes.c_char_p, P(f64), P(f64)], ctypes.c_int),
         "eda_lowrank_exp_apply_noalloc": ([vp, i64, i32, vp, vp, vp, i64, i32, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -166,6 +167,13 @@ def profile_read(region: str):
     ms, calls = ctypes.c_double(), ctypes.c_int64()
     _check(load().eda_profile_read(region.encode(), ctypes.byref(ms), ctypes.byref(calls)), "eda_profile_read")
     return ms.value, calls.value
+
+
+def profile_work(region: str):
+    """(algorithmic FLOPs, algorithmic bytes) the library counted for a region since the last reset."""
+    fl, by = ctypes.c_double(), ctypes.c_double()
+    _check(load().eda_profile_work(region.encode(), ctypes.byref(fl), ctypes.byref(by)), "eda_profile_work")
+    return fl.value, by.value
 
 
 class Handle:
