@@ -160,6 +160,39 @@ int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_
 int eda_lowrank_exp_apply_noalloc(const double* H, int64_t d, int32_t m, const double* K,
                                   const double* X, double* Y, int64_t ld, int32_t b, void* stream);
 
+/* One problem of a batched solve (all pointers device pointers except info.relres).
+ * Inputs as for eda_build / eda_solve; block_b = 0 uses the batch configuration's block size,
+ * or the tuned one when that is 0 as well. Outputs: V (d x t, orthonormal basis of the
+ * generalized eigenvectors), lambda (t, descending), status (eda_status of this problem) and info
+ * (info.relres is not filled). */
+typedef struct {
+    const void* X;               /* d x n samples, x_dtype EDA_F64 or EDA_F32, leading dim ldx  */
+    int32_t x_dtype;
+    int32_t k;                   /* classes                                                   */
+    int64_t d, n, ldx;
+    const int32_t* labels;       /* n class ids in [0, k)                                     */
+    int32_t t;                   /* wanted eigenpairs                                         */
+    int32_t block_b;             /* 0: batch default / tuned                                  */
+    double tol;                  /* relative residual of every wanted pair                    */
+    double* V;                   /* out: d x t                                                */
+    double* lambda;              /* out: t                                                    */
+    int32_t status;              /* out                                                       */
+    int32_t reserved;
+    eda_solve_info info;         /* out                                                       */
+} eda_problem;
+
+/* Solve nprob independent problems of uneven d, n, k (random training splits, class subsets): the
+ * single-problem path of eda_build and eda_solve for each, run side by side by `workers` host
+ * threads (<= 0: 16), each with its own CUDA stream, largest problems first. When cfg->block_b is
+ * 0, each problem shape gets the block size that minimises the measured time of one M-apply of
+ * width b times the ceil(t / b) + 2 blocks of a solve (b in {4, 8, 16, 32}). The batch starts after
+ * the work already queued on `stream` and `stream` waits for all of it; the call returns when every
+ * problem is done. Returns EDA_OK when every problem converged, else the first hard error of a
+ * problem, else EDA_ERR_NOT_CONVERGED; per-problem results are in probs[i].status. The paper has
+ * no batched counterpart: its experiments solve one split at a time. */
+int eda_solve_batched(eda_problem* probs, int32_t nprob, const eda_config* cfg, int32_t workers,
+                      void* stream);
+
 /* Copy out build results into caller device buffers (any pointer may be NULL):
  * HW d x n, HB d x k, counts k, perm n, GW n x n, GB k x k, KW n x n
  * (alpha = -c^2/2), KB k x k (alpha = c^2), evals_w n, evals_b k (ascending). */

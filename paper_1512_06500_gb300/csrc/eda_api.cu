@@ -15,7 +15,7 @@ namespace eda {
 namespace {
 thread_local int g_last_cuda_error = 0;
 thread_local char g_last_cuda_msg[256] = "no error";
-uint64_t g_launches = 0;
+std::atomic<uint64_t> g_launches{0};
 }  // namespace
 
 void note_cuda_error(cudaError_t e, const char* file, int line) {
@@ -38,7 +38,7 @@ int ensure_workspace(eda_ctx* h, size_t bytes) {
     h->ws_bytes = bytes;
     return EDA_OK;
 }
-uint64_t& launch_counter() { return g_launches; }
+std::atomic<uint64_t>& launch_counter() { return g_launches; }
 
 // Solve-side entry points implemented in lanczos.cu.
 int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* V, double* lambda, double* Y,
@@ -508,6 +508,6 @@ const char* eda_strerror(int status) {
 
 int eda_last_cuda_error(void) { return g_last_cuda_error; }
 const char* eda_last_cuda_error_string(void) { return g_last_cuda_error ? g_last_cuda_msg : "no error"; }
-uint64_t eda_kernel_launches(void) { return g_launches; }
+uint64_t eda_kernel_launches(void) { return g_launches.load(); }
 
 }  // extern "C"

@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <cstddef>
 #include <vector>
+#include <atomic>
+#include <mutex>
 
 #include "../../include/eda.h"
 
@@ -14,7 +16,7 @@ namespace eda {
 
 // ---------------------------------------------------------------- errors
 void note_cuda_error(cudaError_t e, const char* file = nullptr, int line = 0);
-uint64_t& launch_counter();
+std::atomic<uint64_t>& launch_counter();   // kernels launched by this process (all threads)
 
 #define EDA_CUDA_TRY(expr)                                        \
     do {                                                          \

@@ -711,22 +711,26 @@ template <int C>
 int launch_tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_t s, bool probe_only,
                            bool* fits) {
     auto kern = k_tridiag_cluster<C>;
+    static std::mutex mu;                 // the function attributes below are shared by all threads
     static size_t smem_set = 0;
     static bool attrs = false;
-    if (!attrs) {
-        attrs = true;
-        if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaGetLastError();
-    }
     const int ncl = (n + C - 1) / C;
     const size_t vec_bytes = (4 * (size_t)n + 2) * sizeof(double);
     const size_t a_bytes = (size_t)ncl * n * sizeof(double);
     const int in_smem = (vec_bytes + a_bytes <= 200 * 1024) ? 1 : 0;
     const size_t smem = vec_bytes + (in_smem ? a_bytes : 0);
-    if (smem > smem_set) {
-        EDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)std::max<size_t>(smem, 48 * 1024)));
-        smem_set = std::max<size_t>(smem, 48 * 1024);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attrs) {
+            attrs = true;
+            if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaGetLastError();
+        }
+        if (smem > smem_set) {
+            EDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)std::max<size_t>(smem, 48 * 1024)));
+            smem_set = std::max<size_t>(smem, 48 * 1024);
+        }
     }
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -765,6 +769,8 @@ int launch_tridiag_c(int C, int n, const double* A, int lda, SymEigWork* ws, cud
 
 int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_t s) {
     static int chosen_C[kClusterMaxN + 1] = {};   // cluster size that passed the occupancy check, per n
+    static std::mutex mu;
+    std::unique_lock<std::mutex> lk(mu);
     if (!chosen_C[n]) {
         int want = 2;
         if (n > 64) {
@@ -781,7 +787,9 @@ int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_
         }
         chosen_C[n] = C;
     }
-    return launch_tridiag_c(chosen_C[n], n, A, lda, ws, s, false, nullptr);
+    const int C = chosen_C[n];
+    lk.unlock();
+    return launch_tridiag_c(C, n, A, lda, ws, s, false, nullptr);
 }
 
 int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, SymEigWork* ws, int* status,
@@ -799,7 +807,14 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     // variables, and the default limit covers static + dynamic
     const size_t smem = 2 * (size_t)n * sizeof(double);
     if (smem > 40 * 1024) {
-        EDA_CUDA_TRY(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // raise-only, under a lock: concurrent solves of different sizes share the attribute
+        static std::mutex mu;
+        static size_t set = 0;
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > set) {
+            EDA_CUDA_TRY(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            set = smem;
+        }
     }
     if (n <= kClusterMaxN) {
         EDA_TRY(tridiag_cluster(n, A, lda, ws, s));
@@ -832,7 +847,13 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     EDA_CUDA_TRY(cudaPeekAtLastError());
     const size_t bsm = 3 * (size_t)n * sizeof(double);
     if (bsm > 40 * 1024) {
-        EDA_CUDA_TRY(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+        static std::mutex mu;
+        static size_t set = 0;
+        std::lock_guard<std::mutex> lk(mu);
+        if (bsm > set) {
+            EDA_CUDA_TRY(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+            set = bsm;
+        }
     }
     {
         ProfScope prof("bisect", s);

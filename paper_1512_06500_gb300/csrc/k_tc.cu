@@ -543,7 +543,9 @@ int launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaS
 
 template <int N, int MODE>
 int set_smem_attr() {
+    static std::mutex mu;
     static bool done = false;
+    std::lock_guard<std::mutex> lk(mu);
     if (!done) {
         EDA_CUDA_TRY(cudaFuncSetAttribute(k_tc_sweep2<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)tc_smem_bytes<N>()));

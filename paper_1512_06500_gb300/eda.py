@@ -34,7 +34,7 @@ EXPORTS = [
     "eda_project", "eda_get_factors", "eda_get_dims", "eda_destroy", "eda_strerror",
     "eda_last_cuda_error", "eda_last_cuda_error_string", "eda_kernel_launches",
     "eda_profile_enable", "eda_profile_reset", "eda_profile_read", "eda_profile_work",
-    "eda_lowrank_exp_apply_noalloc",
+    "eda_lowrank_exp_apply_noalloc", "eda_solve_batched",
 ]
 
 
@@ -66,6 +66,16 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "relres"}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("X", ctypes.c_void_p), ("x_dtype", ctypes.c_int32), ("k", ctypes.c_int32),
+        ("d", ctypes.c_int64), ("n", ctypes.c_int64), ("ldx", ctypes.c_int64),
+        ("labels", ctypes.c_void_p), ("t", ctypes.c_int32), ("block_b", ctypes.c_int32),
+        ("tol", ctypes.c_double), ("V", ctypes.c_void_p), ("lam", ctypes.c_void_p),
+        ("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("info", SolveInfo),
+    ]
 
 
 _lib = None
@@ -101,6 +111,7 @@ def load(path: str | None = None):
         "eda_profile_read": ([ctypes.c_char_p, P(f64), P(i64)], ctypes.c_int),
         "eda_profile_work": ([ctypes.c_char_p, P(f64), P(f64)], ctypes.c_int),
         "eda_lowrank_exp_apply_noalloc": ([vp, i64, i32, vp, vp, vp, i64, i32, vp], ctypes.c_int),
+        "eda_solve_batched": ([P(Problem), i32, P(Config), i32, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -167,6 +178,37 @@ def profile_read(region: str):
     ms, calls = ctypes.c_double(), ctypes.c_int64()
     _check(load().eda_profile_read(region.encode(), ctypes.byref(ms), ctypes.byref(calls)), "eda_profile_read")
     return ms.value, calls.value
+
+
+def solve_batched(problems, cfg=None, workers=0, stream=None):
+    """Solve independent problems side by side (eda_solve_batched).
+
+    problems: sequence of dicts with X ((n, d) CUDA tensor, float64 or float32), labels ((n,) int32
+    CUDA tensor), k, t, tol and optionally block_b. Returns (results, code): one dict per problem
+    with V ((t, d) float64), lam ((t,) float64), status and info, and the batch status.
+    """
+    arr = (Problem * len(problems))()
+    keep = []
+    for i, pr in enumerate(problems):
+        X, lab = pr["X"], pr["labels"]
+        _need_cuda(X, "X")
+        _need_cuda(lab, "labels", torch.int32)
+        n, d = X.shape
+        t = int(pr["t"])
+        V = torch.empty((t, d), dtype=torch.float64, device=X.device)
+        lam = torch.empty(t, dtype=torch.float64, device=X.device)
+        keep.append((V, lam))
+        arr[i] = Problem(X=X.data_ptr(), x_dtype=_dtype_code(X), k=int(pr["k"]), d=d, n=n, ldx=d,
+                         labels=lab.data_ptr(), t=t, block_b=int(pr.get("block_b", 0)), tol=float(pr["tol"]),
+                         V=V.data_ptr(), lam=lam.data_ptr(), status=0)
+    c = cfg if cfg is not None else config(block_b=0)
+    code = load().eda_solve_batched(arr, len(problems), ctypes.byref(c), int(workers), _stream(stream))
+    if code not in (0, -8):
+        raise EdaError(code, "eda_solve_batched")
+    out = []
+    for i, (V, lam) in enumerate(keep):
+        out.append(dict(V=V, lam=lam, status=arr[i].status, info=arr[i].info.as_dict()))
+    return out, code
 
 
 def profile_work(region: str):

@@ -128,6 +128,11 @@ def config_problem(name, split=0):
     return gaussian_clusters(c["d"], c["k"], c["n_j"], seed=seed, n_test_per_class=c["test"], name=name)
 
 
+# The batched workload: 64 independent problems, d in {1024, 4096, 16384}, k ~ U[10, 100],
+# n_j ~ U[3, 10] per class, t = k - 1, scale target tau = 10.
+BATCHED = dict(count=64, seed=5000, tau=10.0)
+
+
 def batched_problems(count=64, seed=5000, d_choices=(1024, 4096, 16384), k_range=(10, 100), nj_range=(3, 10)):
     """Independent problems of uneven size: d from d_choices, k ~ U[k_range], n_j ~ U[nj_range] per class."""
     rng = np.random.default_rng(seed)

@@ -79,3 +79,42 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_batched_invalid_arguments_rejected_before_device_work(lib):
+    from paper_1512_06500_gb300 import eda
+    L, _ = lib
+    c = eda.config()
+    assert L.eda_solve_batched(None, -1, ctypes.byref(c), 0, None) == -1
+    assert L.eda_solve_batched(None, 2, ctypes.byref(c), 0, None) == -1
+    assert L.eda_solve_batched(None, 0, ctypes.byref(c), 0, None) == 0
+    arr = (eda.Problem * 1)()
+    # k > n, and (separately) a missing output pointer: rejected by validation alone
+    arr[0] = eda.Problem(X=1, x_dtype=0, k=5, d=10, n=3, ldx=10, labels=1, t=2, block_b=0, tol=1e-6, V=1, lam=1)
+    assert L.eda_solve_batched(arr, 1, ctypes.byref(c), 0, None) == -1
+    arr[0] = eda.Problem(X=1, x_dtype=0, k=2, d=10, n=3, ldx=10, labels=1, t=2, block_b=0, tol=1e-6, V=0, lam=1)
+    assert L.eda_solve_batched(arr, 1, ctypes.byref(c), 0, None) == -1
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc not available")
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the C structs have the header's sizes and field offsets."""
+    from paper_1512_06500_gb300 import eda
+    checks = [("eda_config", eda.Config), ("eda_solve_info", eda.SolveInfo), ("eda_problem", eda.Problem)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for cname, py in checks:
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            cf = "lambda" if fname == "lam" else fname
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {cf}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-o", str(exe), str(src)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              check=True).stdout.splitlines())
+    for cname, py in checks:
+        assert int(out[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
