@@ -177,6 +177,29 @@ def cpu_baseline(p, c, tol, budget_s=12.0, max_reps=30):
                       f"numpy threads default"}
 
 
+# ---------------------------------------------------------------- multi-rank helpers (no collective on the data path)
+
+def rank_problem(workload, rank):
+    """The independent problem a rank solves: its own random split (weak scaling)."""
+    return synth.config_problem(workload, split=rank)
+
+
+def rank_batch_seed(rank):
+    """Seed of the 64-problem batch a rank solves (every rank its own batch)."""
+    return synth.BATCHED["seed"] + 1000 * rank
+
+
+def max_over_ranks(value, device):
+    """The maximum of a per-rank time over all ranks (the value itself on one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- bf16 tensor-core exp-apply leg
 
 EXP_APPLY_WORKLOADS = ("d16384_k100", "d65536_k200")
@@ -269,7 +292,7 @@ def run_gpu_batched(args, rank, world, local_rank):
     build_lib.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    ps = synth.batched_problems(synth.BATCHED["count"], seed=synth.BATCHED["seed"] + 1000 * rank)
+    ps = synth.batched_problems(synth.BATCHED["count"], seed=rank_batch_seed(rank))
     Xs = [torch.from_numpy(p.X).to(dev) for p in ps]
     labs = [torch.from_numpy(p.labels).to(dev) for p in ps]
     probs = [dict(X=X, labels=lab, k=p.k, t=p.k - 1, tol=args.tol) for X, lab, p in zip(Xs, labs, ps)]
@@ -309,10 +332,7 @@ def run_gpu_batched(args, rank, world, local_rank):
     eda.profile_enable(False)
     launches = eda.kernel_launches() - launches0
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     tri_ms, tri_calls = eda.profile_read("tridiag")
     tri_flops, _ = eda.profile_work("tridiag")
     ew = [eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b")]
@@ -359,10 +379,7 @@ def run_gpu_batched(args, rank, world, local_rank):
     h2d = sum(x.numel() * 8 + l.numel() * 4 for x, l in zip(Xh, labh))
     d2h = sum((p.k - 1) * (p.d + 1) * 8 for p in ps)
     e2e_v = sum(e2e_ms) / len(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_v], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_v = float(t.item())
+    e2e_v = max_over_ranks(e2e_v, dev)
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -386,7 +403,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     c = synth.CONFIGS[args.workload]
-    p = synth.config_problem(args.workload, split=rank)
+    p = rank_problem(args.workload, rank)
     X = torch.from_numpy(p.X).to(dev)
     lab = torch.from_numpy(p.labels).to(dev)
     Xt = torch.from_numpy(p.Xtest).to(dev)
@@ -434,10 +451,7 @@ def run_gpu(args, rank, world, local_rank):
     launches = eda.kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
 
     # ---- rooflines measured inside the timed region (library event pairs + its own work counts) ----
     regions = {r: eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b", "m_apply", "tridiag", "bisect",
@@ -506,10 +520,7 @@ def run_gpu(args, rank, world, local_rank):
     h2d = Xh.numel() * 8 + labh.numel() * 4 + Xth.numel() * 8
     d2h = Vh.numel() * 8 + lamh.numel() * 8 + Ph.numel() * 8
     e2e_v = sum(e2e_ms) / len(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_v], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_v = float(t.item())
+    e2e_v = max_over_ranks(e2e_v, dev)
 
     exp_leg = None
     if not args.no_exp_apply and rank == 0:
