@@ -335,6 +335,9 @@ def run_gpu_batched(args, rank, world, local_rank):
     ms = max_over_ranks(ms, dev)
     tri_ms, tri_calls = eda.profile_read("tridiag")
     tri_flops, _ = eda.profile_work("tridiag")
+    breakdown = {r: eda.profile_read(r)[0] / args.steps
+                 for r in ("gram", "symeig", "tridiag", "bisect", "invit", "backtransform", "m_apply", "exp_apply_w",
+                           "exp_apply_b", "rr", "reorth")}
     ew = [eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b")]
     ewk = [eda.profile_work(r) for r in ("exp_apply_w", "exp_apply_b")]
     exp_ms = sum(v[0] for v in ew)
@@ -389,6 +392,7 @@ def run_gpu_batched(args, rank, world, local_rank):
         "clocks": clk, "gpu_launches": launches,
         "e2e": {"value": e2e_v, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline, "exp_apply_fp64": exp_apply_fp64,
+        "breakdown_ms_per_step_summed_over_streams": breakdown,
         "solve_info": {"mapplies_total": sum(r["info"]["mapplies"] for r in res),
                        "max_relres_est": max(r["info"]["max_relres_est"] for r in res)},
     }
