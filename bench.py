@@ -489,6 +489,7 @@ def run_gpu(args, rank, world, local_rank):
     }
 
     # ---- end to end through the public API with host buffers ----
+    d = p.d
     Xh = torch.from_numpy(p.X).pin_memory()
     labh = torch.from_numpy(p.labels).pin_memory()
     Xth = torch.from_numpy(p.Xtest).pin_memory()
