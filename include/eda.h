@@ -69,7 +69,11 @@ typedef struct {
     double c2;                   /* explicit c^2 when > 0 (tau is then ignored)              */
     uint64_t seed;               /* seed of the counter-based start block / refill vectors  */
     int32_t true_residuals;      /* 1: eda_solve also reports true FP64 residuals            */
-    int32_t reserved[7];
+    int32_t m_form;              /* FP64 M-apply: 0 = the three products of the symmetric     */
+                                 /* form one after another (Eq. 3.20); 1 = their composed     */
+                                 /* form M = I + Z C Z^T, Z = [H_W H_B] (Theorem 3.1 for each  */
+                                 /* factor; two sweeps over Z instead of six over H_W, H_B)   */
+    int32_t reserved[6];
 } eda_config;
 
 typedef struct {
@@ -91,7 +95,7 @@ typedef struct {
 typedef struct eda_ctx* eda_handle;
 
 /* Fill *cfg with defaults: F64, b = 8, m_max = 0 (n + k + b), check_every = 1,
- * tau = 10, c2 = 0, seed = 1, true_residuals = 0. */
+ * tau = 10, c2 = 0, seed = 1, true_residuals = 0, m_form = 0. */
 int eda_config_default(eda_config* cfg);
 
 /* Build a handle from labelled samples (Section 1; Algorithm 2 step 1 with the

@@ -221,9 +221,9 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     if (!tmp) return EDA_ERR_OOM;
     EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
     EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
-    if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16) {
-        // cross Grams G_WB = H_W^T H_B and G_BW = G_WB^T for the composed FP64 M-apply of the
-        // mixed-precision refinement
+    if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16 || h->cfg.m_form == 1) {
+        // cross Grams G_WB = H_W^T H_B and G_BW = G_WB^T for the composed FP64 M-apply (the
+        // mixed-precision refinement, and the FP64 Krylov phase with m_form = 1)
         void* xp = nullptr;
         const size_t xb = align256((size_t)n * k * 8);
         EDA_CUDA_TRY(cudaMalloc(&xp, 2 * xb));
@@ -272,7 +272,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
 
 bool valid_cfg(const eda_config& c) {
     return c.block_b >= 1 && c.check_every >= 1 && (c.c2 > 0.0 || c.tau > 0.0) &&
-           (c.prec == EDA_F64 || c.prec == EDA_F32 || c.prec == EDA_BF16);
+           (c.prec == EDA_F64 || c.prec == EDA_F32 || c.prec == EDA_BF16) && (c.m_form == 0 || c.m_form == 1);
 }
 
 }  // namespace
@@ -377,8 +377,9 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
     if (xb < yb + span && yb < xb + span) return EDA_ERR_INVALID_ARG;   // X and Y overlap
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t d = h->d;
-    const int N = (int)std::max<int64_t>(h->n, h->k);
-    // temporaries: P, Q (N x b), split-K partials, and one d x b block for op M
+    // temporaries: P, Q ((n + k) x b: also the coordinates of the composed M-apply), split-K
+    // partials, and one d x b block for op M
+    const int N = (int)(h->n + h->k);
     const size_t pcap = std::max<size_t>(1u << 19, (size_t)N * b);
     const size_t need = align256((size_t)N * b * 8) * 2 + align256(pcap * 8) + align256((size_t)d * b * 8) + 4096;
     EDA_TRY(eda::ensure_workspace(h, need));

@@ -147,11 +147,18 @@ template <> struct HStore<float> {
 
 }  // namespace
 
-// Y = M X = E_W^{-1/2} E_B E_W^{-1/2} X, the three products (iii)-(v) of Eq. (320).
+int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY, int64_t ldm, double* PQ,
+                     double* U, double* ZtY, double* part, size_t pcap, cudaStream_t s);
+
+// Y = M X = E_W^{-1/2} E_B E_W^{-1/2} X, the three products (iii)-(v) of Eq. (320); in FP64 with
+// m_form = 1 (and allow_composed) their composed form instead. P and Q hold (n + k) x b doubles.
 template <class T>
 int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* tmp, double* P, double* Q,
-              void* partial, size_t partial_cap, cudaStream_t s) {
+              void* partial, size_t partial_cap, cudaStream_t s, bool allow_composed = true) {
     ProfScope prof("m_apply", s);
+    if (std::is_same<T, double>::value && allow_composed && h->cfg.m_form == 1 && h->GWB)
+        return m_apply_composed(h, b, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<double*>(Y), ldy, P,
+                                Q, nullptr, static_cast<double*>(partial), partial_cap, s);
     const int64_t d = h->d;
     const T* HW = HStore<T>::W(h);
     const T* HB = HStore<T>::B(h);
@@ -330,6 +337,8 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     return EDA_OK;
 }
 
+}  // namespace
+
 // M Y in FP64 for p columns through the composed form of the three products of Eq. (3.20): with
 // Theorem 3.1 for each factor and the Grams G_W, G_WB = H_W^T H_B, only two sweeps over
 // Z = [H_W H_B] remain:
@@ -340,9 +349,10 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
 // (the same operator as m_apply_t, in a third of the sweeps).
 int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY, int64_t ldm, double* PQ,
                      double* U, double* ZtY, double* part, size_t pcap, cudaStream_t s) {
-    ProfScope prof("m_apply_composed", s);
     const int64_t d = h->d;
     const int n = (int)h->n, k = h->k, nk = n + k;
+    ProfScope prof("m_apply_composed", s, 4.0 * d * nk * p + 2.0 * p * (3.0 * n * n + 2.0 * n * k + k * k),
+                   8.0 * (2.0 * d * nk + 3.0 * d * p));
     EDA_TRY(gemm_tn_f64(d, nk, p, 1.0, h->HW, d, Y, ldy, 0.0, PQ, nk, part, pcap, s));
     if (ZtY) EDA_TRY(copy_mat_f64(nk, p, PQ, nk, ZtY, nk, s));   // keep Z^T y (coordinates) for the caller
     double* Pw = PQ;
@@ -399,8 +409,6 @@ int ritz_residuals(int64_t d, int t, SolveWs<T>& w, std::vector<double>& relres_
     for (int i = 0; i < t; ++i) *max_rel = std::max(*max_rel, relres_h[i]);
     return EDA_OK;
 }
-
-}  // namespace
 
 // FP64 refinement of t approximate eigenvectors Y (d x t, in w.Y) from the single-precision phase:
 // Rayleigh-Ritz on span(Y), then, while some relative residual exceeds tol, Rayleigh-Ritz on
@@ -505,7 +513,7 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     add((size_t)m_max * m_max);        // Tm
     add((size_t)m_max * tw * 2);       // C
     for (int i = 0; i < 7; ++i) add((size_t)b * b);
-    add((size_t)N * tw * 2);           // P, Q
+    add((size_t)(n + k) * tw * 2);     // P, Q (also the (n + k) x b coordinates of the composed M-apply)
     add(w.pcap);                       // partial (double-sized slots hold either type)
     add(t);                            // theta
     add((size_t)eig_n * t);            // S
@@ -535,8 +543,8 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     w.Bm = a.take<double>((size_t)b * b);
     (void)a.take<double>((size_t)b * b);
     (void)a.take<double>((size_t)b * b);
-    w.P = a.take<double>((size_t)N * tw);
-    w.Q = a.take<double>((size_t)N * tw);
+    w.P = a.take<double>((size_t)(n + k) * tw);
+    w.Q = a.take<double>((size_t)(n + k) * tw);
     w.part = a.take<double>(w.pcap);
     w.theta = a.take<double>(t);
     w.S = a.take<double>((size_t)eig_n * t);
@@ -626,7 +634,7 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
         for (int c0 = 0; c0 < t; c0 += tw) {
             const int cb = std::min(tw, t - c0);
             EDA_TRY(m_apply_t<double>(h, cb, w.Y2 + (size_t)c0 * d, d, MY + (size_t)c0 * d, d, w.tmp64, w.P, w.Q,
-                                      w.part, w.pcap, s));
+                                      w.part, w.pcap, s, /*allow_composed=*/false));
         }
         k_sub_scaled<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, MY, d, w.Y2, d, w.lamd);
         EDA_LAUNCHED();

@@ -118,3 +118,11 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(out[cname]) == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_library_has_no_undefined_internal_symbols(lib):
+    """Every function of the library's own namespace that is referenced is defined in it."""
+    _, path = lib
+    out = subprocess.run(["nm", "-D", "--undefined-only", path], capture_output=True, text=True, check=True).stdout
+    undefined = [line.split()[-1] for line in out.splitlines() if "_ZN3eda" in line or " eda_" in line]
+    assert not undefined, undefined

@@ -117,8 +117,8 @@ def test_apply_exp_zero_factor_is_identity(eda):
 
 # ----------------------------------------------------------------- full solve
 
-def _solve_and_compare(eda, p, t, b, tau, tol=1e-12, tier="auto", check_every=1):
-    cfg = eda.config(block_b=b, tau=tau, check_every=check_every, true_residuals=1)
+def _solve_and_compare(eda, p, t, b, tau, tol=1e-12, tier="auto", check_every=1, m_form=0):
+    cfg = eda.config(block_b=b, tau=tau, check_every=check_every, true_residuals=1, m_form=m_form)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         V, lam, Y, info, code = h.solve(t, tol, want_y=True, relres=True)
         assert code == 0, info
@@ -163,6 +163,26 @@ def test_solve_ragged_blocks(eda, b, check_every):
     # block size that does not divide t, uneven classes, d not a multiple of any tile
     p = _problem(333, 7, [2, 3, 5, 1, 4, 3, 2], seed=55, test=2)
     _solve_and_compare(eda, p, p.k - 1, b, 8.0, check_every=check_every)
+
+
+@pytest.mark.parametrize("name", ["d256_k8", "d4096_k40"])
+def test_solve_composed_m_form(eda, name):
+    # the same operator M in its composed form I + Z C Z^T (two sweeps over [H_W H_B]); the
+    # independent true-residual check still uses the three products
+    c = synth.CONFIGS[name]
+    p = synth.config_problem(name)
+    _solve_and_compare(eda, p, c["t"], c["b"], c["tau"], m_form=1)
+
+
+def test_apply_m_composed_matches_three_products(eda):
+    p = _problem(777, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], seed=31)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((6, 777))
+    out = []
+    for form in (0, 1):
+        with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(tau=8.0, m_form=form)) as h:
+            out.append(h.apply_exp(eda.OP_M, _dev(X)).cpu().numpy())
+    assert np.linalg.norm(out[1] - out[0]) <= 1e-13 * np.linalg.norm(out[0])
 
 
 def test_solve_commuting_diagonal_closed_form(eda):
