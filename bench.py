@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="d4096_k40", choices=list(synth.CONFIGS) + ["batched64"])
     ap.add_argument("--workers", type=int, default=16, help="host workers of the batched solve")
+    ap.add_argument("--m-form", type=int, default=1, choices=[0, 1],
+                    help="FP64 M-apply: 0 = the three products one after another, 1 = their composed form")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exp-apply", action="store_true", help="skip the bf16 tensor-core exp-apply leg")
@@ -118,12 +120,14 @@ def workload_config(args):
                             f"n_j ~ U[3, 10] per class, t = k - 1, tau = {synth.BATCHED['tau']}, tol={args.tol}",
                 "l2": "flushed (256 MB write) before every step",
                 "precision": "plain FP64 sweeps and small steps; block size tuned per problem shape",
+                "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form],
                 "workers": args.workers}
     c = synth.CONFIGS[args.workload]
     return {"workload": f"{args.workload}: d={c['d']}, k={c['k']}, n_j={c['n_j']} (n={c['k'] * c['n_j']}), "
                         f"t={c['t']}, b={c['b']}, tau={c['tau']}, tol={args.tol}",
             "l2": "flushed (256 MB write) before every step",
-            "precision": "plain FP64 sweeps and small steps"}
+            "precision": "plain FP64 sweeps and small steps",
+            "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form]}
 
 
 # ---------------------------------------------------------------- CPU oracle leg
@@ -296,7 +300,7 @@ def run_gpu_batched(args, rank, world, local_rank):
     Xs = [torch.from_numpy(p.X).to(dev) for p in ps]
     labs = [torch.from_numpy(p.labels).to(dev) for p in ps]
     probs = [dict(X=X, labels=lab, k=p.k, t=p.k - 1, tol=args.tol) for X, lab, p in zip(Xs, labs, ps)]
-    cfg = eda.config(block_b=0, tau=synth.BATCHED["tau"])
+    cfg = eda.config(block_b=0, tau=synth.BATCHED["tau"], m_form=args.m_form)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -411,7 +415,7 @@ def run_gpu(args, rank, world, local_rank):
     X = torch.from_numpy(p.X).to(dev)
     lab = torch.from_numpy(p.labels).to(dev)
     Xt = torch.from_numpy(p.Xtest).to(dev)
-    cfg = eda.config(block_b=c["b"], tau=c["tau"], check_every=1)
+    cfg = eda.config(block_b=c["b"], tau=c["tau"], check_every=1, m_form=args.m_form)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
 

@@ -32,11 +32,12 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
 
 
-def test_fp64_d16384_k100_matches_oracle(eda):
+@pytest.mark.parametrize("m_form", [0, 1])
+def test_fp64_d16384_k100_matches_oracle(eda, m_form):
     name = "d16384_k100"
     c = synth.CONFIGS[name]
     p = synth.config_problem(name)
-    cfg = eda.config(prec=eda.EDA_F64, block_b=c["b"], tau=c["tau"], true_residuals=1)
+    cfg = eda.config(prec=eda.EDA_F64, block_b=c["b"], tau=c["tau"], true_residuals=1, m_form=m_form)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         V, lam, _, info, code = h.solve(c["t"], 1e-10)
         assert code == 0, info
@@ -56,12 +57,13 @@ def test_fp64_d16384_k100_matches_oracle(eda):
     assert np.array_equal(lab_g, lab_o)
 
 
-def test_fp64_d65536_k200_sampled_pairs(eda):
+@pytest.mark.parametrize("m_form", [0, 1])
+def test_fp64_d65536_k200_sampled_pairs(eda, m_form):
     name = "d65536_k200"
     c = synth.CONFIGS[name]
     p = synth.config_problem(name)
     tol = 1e-7
-    cfg = eda.config(prec=eda.EDA_F64, block_b=c["b"], tau=c["tau"])
+    cfg = eda.config(prec=eda.EDA_F64, block_b=c["b"], tau=c["tau"], m_form=m_form)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         V, lam, Y, info, code = h.solve(c["t"], tol, want_y=True)
         assert code == 0, info
