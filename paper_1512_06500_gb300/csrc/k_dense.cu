@@ -246,6 +246,75 @@ __global__ void k_gemm_small(bool ta, bool tb, int m, int p, int kk, double alph
 }
 
 // Single-CTA right-looking upper Cholesky G = R^T R with rank detection, then R^{-1}.
+// The same factorisation for b <= 32 by one warp with the matrix in shared memory: lane c owns
+// column c; one reciprocal per pivot; warp-level synchronisation only. Rank decisions (threshold,
+// lost list in pivot order, status bits) are those of k_chol_inv.
+__global__ void __launch_bounds__(32) k_chol_inv_warp(int b, double* G, int ldg, double* Rinv, double rank_tol,
+                                                      double piv_min2, int* status, int* lost) {
+    __shared__ double sg[32][33];   // sg[c][r] = G[r, c]
+    __shared__ double sx[32][33];   // sx[c][i] = Rinv[i, c]
+    __shared__ double inv[32];
+    const int lane = threadIdx.x;
+    const bool live = lane < b;
+    if (live)
+        for (int r = 0; r <= lane; ++r) sg[lane][r] = G[(int64_t)lane * ldg + r];
+    double dg = live ? G[(int64_t)lane * ldg + lane] : 0.0;
+    const bool bad = live && !isfinite(dg);
+    double mx = fabs(dg);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
+    const double thr = fmax(rank_tol * mx, piv_min2);
+    int nlost = 0;
+    __syncwarp();
+    for (int j = 0; j < b; ++j) {
+        const double g = sg[j][j];
+        const bool lost_j = !(g > thr) || mx == 0.0;
+        const double piv = lost_j ? 0.0 : sqrt(g);
+        const double ip = lost_j ? 0.0 : 1.0 / piv;
+        __syncwarp();   // every lane has read the pivot before lane 0 overwrites it
+        if (lane == 0) {
+            if (lost_j) {
+                if (lost) lost[nlost] = j;
+                atomicOr(status, ST_RANKLOSS);
+            }
+            sg[j][j] = piv;
+            inv[j] = ip;
+        }
+        nlost += lost_j ? 1 : 0;
+        // row j of R (entries (j, c) for c > j), then the trailing update of column c
+        if (live && lane > j) sg[lane][j] *= ip;
+        __syncwarp();
+        if (live && lane > j) {
+            const double rjc = sg[lane][j];
+            for (int c1 = j + 1; c1 <= lane; ++c1) sg[lane][c1] -= sg[c1][j] * rjc;
+        }
+        __syncwarp();
+    }
+    // Rinv = R^{-1} (upper triangular): lane c solves R x = e_c from the bottom up
+    if (live) {
+        const int c = lane;
+        for (int i = b - 1; i > c; --i) sx[c][i] = 0.0;
+        for (int i = c; i >= 0; --i) {
+            double a0 = (i == c) ? 1.0 : 0.0, a1 = 0.0;
+            int l = i + 1;
+            for (; l + 1 <= c; l += 2) {
+                a0 -= sg[l][i] * sx[c][l];
+                a1 -= sg[l + 1][i] * sx[c][l + 1];
+            }
+            if (l <= c) a0 -= sg[l][i] * sx[c][l];
+            sx[c][i] = (a0 + a1) * inv[i];
+        }
+    }
+    __syncwarp();
+    if (live) {
+        for (int r = 0; r < b; ++r) {
+            G[(int64_t)lane * ldg + r] = (r <= lane) ? sg[lane][r] : 0.0;
+            Rinv[(int64_t)lane * b + r] = sx[lane][r];
+        }
+    }
+    if (lane == 0 && lost) lost[b] = nlost;
+}
+
 __global__ void k_chol_inv(int b, double* G, int ldg, double* Rinv, double rank_tol, double piv_min2, int* status,
                            int* lost) {
     __shared__ double maxdiag;
@@ -496,7 +565,10 @@ int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const d
 
 int chol_inv_small(int b, double* G, int ldg, double* Rinv, double rank_tol, double piv_min2, int* status, int* lost,
                    cudaStream_t s) {
-    k_chol_inv<<<1, 256, 0, s>>>(b, G, ldg, Rinv, rank_tol, piv_min2, status, lost);
+    if (b <= 32)
+        k_chol_inv_warp<<<1, 32, 0, s>>>(b, G, ldg, Rinv, rank_tol, piv_min2, status, lost);
+    else
+        k_chol_inv<<<1, 256, 0, s>>>(b, G, ldg, Rinv, rank_tol, piv_min2, status, lost);
     EDA_LAUNCHED();
     return EDA_OK;
 }
