@@ -1,0 +1,71 @@
+"""Inexact solves: Krylov tolerance against nearest-neighbour agreement (Section 4, Table 4.4;
+Theorem 3.8 and Remark 3.4).
+
+The paper reports that loose tolerances (down to 1e-2) leave recognition unchanged, and Theorem 3.8
+explains why: projected distances move by at most sin(angle) ||x - y|| when the subspace moves by
+that angle. For each tolerance of the sweep the FP64 solver must (1) meet the tolerance, checked by an
+independent FP64 residual, and (2) give the oracle's 1-NN label for every held-out sample whose oracle
+margin exceeds the Theorem 3.8 allowance 4 sin(angle) max ||x - y||; from tol = 1e-6 on, the labels are
+identical. Run with -s to see the table of angles, eigenvalue errors and flips.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1512_06500_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOLS = [1e-2, 1e-4, 1e-6, 1e-8, 1e-10]
+
+
+@pytest.fixture(scope="module")
+def eda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_06500_gb300 import build_lib, eda as E
+    build_lib.build()
+    E.load()
+    return E
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+@pytest.mark.parametrize("name", ["d4096_k40", "d16384_k100"])
+def test_tolerance_sweep_against_nearest_neighbour(eda, name):
+    c = synth.CONFIGS[name]
+    p = synth.config_problem(name)
+    X, lab, Xt = _dev(p.X), _dev(p.labels), _dev(p.Xtest)
+    ref = None
+    rows = []
+    for tol in TOLS:
+        cfg = eda.config(block_b=c["b"], tau=c["tau"], true_residuals=1)
+        with eda.build(X, lab, p.k, cfg) as h:
+            V, lam, _, info, code = h.solve(c["t"], tol)
+            assert code == 0, (tol, info)
+            if ref is None:
+                ref = O.eda(p.X, p.labels, p.k, c["t"], c2=h.c2, tier="projected")
+                Ptr_o = O.project(ref["V"], p.X)
+                Pte_o = O.project(ref["V"], p.Xtest)
+                lab_o, _, margin = O.nn_classify(Ptr_o, p.labels, Pte_o)
+                zmax = max(np.linalg.norm(p.X[i] - p.Xtest[j]) for i in range(p.X.shape[0])
+                           for j in range(p.Xtest.shape[0]))
+            Ptr = h.project(V, X).cpu().numpy()
+            Pte = h.project(V, Xt).cpu().numpy()
+        assert info["max_relres_true"] <= 10 * tol, (tol, info["max_relres_true"])
+        Vg = V.cpu().numpy().T
+        s = O.sin_angle(ref["V"], Vg)
+        rel = np.abs(lam.cpu().numpy() - ref["lam_t"]) / ref["lam_t"]
+        lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
+        flips = np.flatnonzero(lab_g != lab_o)
+        allowance = 4 * s * zmax
+        assert np.all(margin[flips] <= allowance), (tol, margin[flips], allowance)
+        if tol <= 1e-6:
+            assert flips.size == 0, (tol, flips)
+        rows.append((tol, info["iters"], info["max_relres_true"], rel.max(), s, flips.size, lab_g.size))
+    print(f"\n{name}: tol, blocks, true rel-res, max eig rel err, sin(angle), 1-NN flips / held-out")
+    for r in rows:
+        print("  %.0e  %3d  %.2e  %.2e  %.2e  %d/%d" % r)
