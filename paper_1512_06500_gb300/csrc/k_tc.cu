@@ -152,6 +152,7 @@ struct TcRing {
     uint64_t empty[TC_STAGES];
     uint64_t done;
     uint32_t tbase;
+    int fail;                                    // a role thread gave up on a wait
 };
 template <int N>
 constexpr size_t tc_smem_bytes() {
@@ -171,6 +172,7 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const __nv_bfloat16* Atiles, const CU
                             const CUtensorMap* tmBl, int k_begin, int nst, uint32_t tmem, int* status) {
     const int tid = threadIdx.x;
     bool ok = true;
+    int issued = 0;   // producer: stages whose copies have been requested
     if (tid == 0) {
         // producer: one thread issues all loads (one bulk copy and two tensor boxes per stage). The A
         // tiles (H or H K) do not depend on earlier kernels: the first ring's worth is requested before
@@ -187,6 +189,7 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const __nv_bfloat16* Atiles, const CU
             tma_load_2d(sm.Bh[s], tmBh, k_begin + s * TC_KS, 0, &sm.full[s]);
             tma_load_2d(sm.Bl[s], tmBl, k_begin + s * TC_KS, 0, &sm.full[s]);
         }
+        issued = pre;
         for (int s = pre; s < nst && ok; ++s) {
             const int slot = s % TC_STAGES;
             ok = mbar_wait(&sm.empty[slot], ((s / TC_STAGES) - 1) & 1, status);
@@ -195,6 +198,7 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const __nv_bfloat16* Atiles, const CU
             bulk_load(sm.A[slot], Atiles + (int64_t)s * (TC_M * TC_KS), abytes, &sm.full[slot]);
             tma_load_2d(sm.Bh[slot], tmBh, k_begin + s * TC_KS, 0, &sm.full[slot]);
             tma_load_2d(sm.Bl[slot], tmBl, k_begin + s * TC_KS, 0, &sm.full[slot]);
+            issued = s + 1;
         }
     } else if (tid == 32) {
         // MMA issuer
@@ -223,10 +227,17 @@ __device__ bool tc_mainloop(TcRing<N>& sm, const __nv_bfloat16* Atiles, const CU
     }
     // one thread waits for the accumulator; the others rest on the CTA barrier instead of spinning
     __shared__ int s_ok;
+    if ((tid == 0 || tid == 32) && !ok) sm.fail = 1;
     if (tid == 0) s_ok = (mbar_wait(&sm.done, 0, status) && ok) ? 1 : 0;
     if (tid == 32 && !ok) atomicOr(status, ST_TIMEOUT);
     __syncthreads();
-    const bool fin = s_ok != 0;
+    const bool fin = s_ok != 0 && sm.fail == 0;
+    if (tid == 0 && !fin) {
+        // after a give-up, wait (bounded again) for this CTA's copies of the last ring that may still
+        // be in flight, so that none lands after the CTA's shared memory is released
+        for (int st = max(0, issued - TC_STAGES); st < issued; ++st)
+            mbar_wait(&sm.full[st % TC_STAGES], (st / TC_STAGES) & 1, status);
+    }
     tc_fence_after();
     pdl_wait();   // returns at once by now (the producer has waited); orders this thread's epilogue
     return fin;
@@ -246,6 +257,7 @@ __device__ void tc_setup(TcRing<N>& sm) {
         }
         mbar_init(&sm.done, 1);
         fence_mbar_init();
+        sm.fail = 0;
     }
     tc_fence_before();
     __syncthreads();

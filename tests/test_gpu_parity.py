@@ -115,6 +115,22 @@ def test_apply_exp_zero_factor_is_identity(eda):
         assert np.array_equal(Y, Xb)
 
 
+def test_single_class_has_no_between_class_scatter(eda):
+    # k = 1: H_B = sqrt(n)(mu_1 - mu) = 0, so exp(alpha S_B) X = X exactly, and c^2 comes from G_W alone
+    d, n = 300, 9
+    rng = np.random.default_rng(12)
+    X = rng.random((n, d))
+    labels = np.zeros(n, dtype=np.int32)
+    with eda.build(_dev(X), _dev(labels), 1, eda.config(tau=10.0)) as h:
+        Xb = rng.standard_normal((3, d))
+        Y = h.apply_exp(eda.OP_SB, _dev(Xb), alpha=h.c2).cpu().numpy()
+        assert np.array_equal(Y, Xb)
+        # the eigensolver resolves the 1 x 1 zero Gram to an absolute ~1e-19, negligible in c^2 (A1)
+        assert h.lmax_b <= 1e-15 * h.lmax_w
+        lw = float(np.linalg.eigvalsh(O.gram(O.scatter_factors(X, labels, 1)["HW"]))[-1])
+        assert abs(h.c2 - 10.0 / lw) <= 1e-12 * (10.0 / lw)
+
+
 # ----------------------------------------------------------------- full solve
 
 def _solve_and_compare(eda, p, t, b, tau, tol=1e-12, tier="auto", check_every=1, m_form=0):
@@ -158,8 +174,10 @@ def test_solve_d4096_k40_b8(eda):
     assert info["basis_cols"] <= p.n + p.k + c["b"]
 
 
-@pytest.mark.parametrize("b,check_every", [(1, 3), (3, 2), (5, 1)])
+@pytest.mark.parametrize("b,check_every", [(1, 3), (3, 2), (5, 1), (40, 1)])
 def test_solve_ragged_blocks(eda, b, check_every):
+    # b = 40 is wider than the sample count (n = 20): most of every block lies inside the basis and is
+    # refilled with fresh directions
     # block size that does not divide t, uneven classes, d not a multiple of any tile
     p = _problem(333, 7, [2, 3, 5, 1, 4, 3, 2], seed=55, test=2)
     _solve_and_compare(eda, p, p.k - 1, b, 8.0, check_every=check_every)
