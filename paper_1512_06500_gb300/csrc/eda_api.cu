@@ -50,6 +50,7 @@ int m_apply_f32(eda_ctx* h, int b, const float* X, int64_t ldx, float* Y, int64_
 
 namespace {
 
+constexpr int kEigClusterMaxN = 512;   // the eigensolver's cluster path (no grid barrier) up to this size
 constexpr double kSigRel = 32.0;   // eigenvalues <= kSigRel * n * eps * lambda_max are the Gram's null space
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -96,6 +97,11 @@ int alloc_handle(eda_ctx* h, bool with_labels) {
     add(symeig_work_bytes((int)N, (int)N));
     add(pcap * 8);
     add(3 * N * N * 8 + 256);
+    // the second, concurrent Gram eigensolve: its workspace, partials and temporaries
+    add(symeig_work_bytes((int)std::min(n, k), (int)std::min(n, k)));
+    add(std::max<size_t>(1u << 16, std::min(n, k) * std::min(n, k)) * 8);
+    add(3 * std::min(n, k) * std::min(n, k) * 8 + 256);
+    add(4096);
     h->block_bytes = bytes + 4096;
     void* p = nullptr;
     EDA_CUDA_TRY(cudaMalloc(&p, h->block_bytes));
@@ -130,6 +136,27 @@ int alloc_handle(eda_ctx* h, bool with_labels) {
 
 // Eigenpairs of one Gram G (m x m): all eigenvalues, vectors for the significant ones, and
 // K(alpha). Returns lambda_max and the number of significant eigenpairs.
+// The part of a Gram eigensolve after its eigenvalues are on the host (w, ascending): lambda_max, the
+// significant eigenpairs (above kSigRel * m * eps * lambda_max) and their vectors, refined by one
+// Newton-Schulz step. tmp: 3 m^2 + 64 doubles; part/pcap: split-K partials.
+int gram_eigen_finish(eda_ctx* h, int m, const std::vector<double>& w, double* evals, double* evecs,
+                      SymEigWork* ws, double* tmp, double* part, size_t pcap, double* lmax, int* nsig, int* first_out,
+                      cudaStream_t s) {
+    for (double v : w)
+        if (!std::isfinite(v)) return EDA_ERR_NONFINITE;
+    *lmax = std::max(w[m - 1], 0.0);
+    const double thr = kSigRel * m * DBL_EPSILON * *lmax;
+    int first = 0;
+    while (first < m && !(w[first] > thr)) ++first;
+    *nsig = m - first;
+    *first_out = first;
+    if (*nsig > 0) {
+        EDA_TRY(symeig_vectors(m, *nsig, evals + first, evecs, m, ws, h->cfg.seed, 1e-7, s));
+        EDA_TRY(newton_schulz_f64(m, *nsig, evecs, m, 1, tmp, part, pcap, s));
+    }
+    return EDA_OK;
+}
+
 int gram_eigen(eda_ctx* h, int m, double* G, double* evals, double* evecs, Arena& scratch, double* part, size_t pcap,
                double* lmax, int* nsig, cudaStream_t s) {
     if (m <= 0) {
@@ -146,21 +173,67 @@ int gram_eigen(eda_ctx* h, int m, double* G, double* evals, double* evecs, Arena
     int st = 0;
     EDA_TRY(read_status(h, s, &st));
     if (int c = status_to_code(st)) return c;
-    for (double v : w)
-        if (!std::isfinite(v)) return EDA_ERR_NONFINITE;
-    *lmax = std::max(w[m - 1], 0.0);
-    const double thr = kSigRel * m * DBL_EPSILON * *lmax;
+    double* tmp = scratch.take<double>(3 * (size_t)m * m + 64);
+    if (!tmp) return EDA_ERR_OOM;
     int first = 0;
-    while (first < m && !(w[first] > thr)) ++first;
-    *nsig = m - first;
-    if (*nsig > 0) {
-        EDA_TRY(symeig_vectors(m, *nsig, evals + first, evecs, m, &ws, h->cfg.seed, 1e-7, s));
-        double* tmp = scratch.take<double>(3 * (size_t)m * m + 64);
-        if (!tmp) return EDA_ERR_OOM;
-        EDA_TRY(newton_schulz_f64(m, *nsig, evecs, m, 1, tmp, part, pcap, s));
-    }
+    EDA_TRY(gram_eigen_finish(h, m, w, evals, evecs, &ws, tmp, part, pcap, lmax, nsig, &first, s));
     h->nsig_first = first;   // only meaningful for the last call; the callers store their own copy
     return EDA_OK;
+}
+
+// Both Gram eigensolves side by side on two streams (each runs in one thread-block cluster, so
+// together they still leave most SMs idle): eigenvalues of G_W on s and of G_B on a second stream,
+// one host wait for both, then the eigenvectors of each on its stream. Separate workspaces,
+// temporaries and split-K partials per solve; the second stream joins s before returning.
+int gram_eigen_pair(eda_ctx* h, Arena& scratch, double* partW, size_t pcapW, int* nsw, int* nsb, int* first_w,
+                    int* first_b, cudaStream_t s) {
+    const int n = (int)h->n, k = h->k;
+    SymEigWork wsW{}, wsB{};
+    EDA_TRY(symeig_work_carve(scratch, n, n, h->bar, &wsW));
+    EDA_TRY(symeig_work_carve(scratch, k, k, h->bar, &wsB));
+    const size_t pcapB = std::max<size_t>(1u << 16, (size_t)k * k);
+    double* partB = scratch.take<double>(pcapB);
+    double* tmpW = scratch.take<double>(3 * (size_t)n * n + 64);
+    double* tmpB = scratch.take<double>(3 * (size_t)k * k + 64);
+    if (!partB || !tmpW || !tmpB) return EDA_ERR_OOM;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int rc = EDA_OK;
+    std::vector<double> ww(n), wb(k);
+    do {
+        if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(s2, fork, 0) != cudaSuccess) {
+            rc = EDA_ERR_CUDA;
+            break;
+        }
+        if ((rc = symeig_values(n, h->GW, n, 0, n - 1, h->evals_w, &wsW, h->status, s)) != EDA_OK) break;
+        if ((rc = symeig_values(k, h->GB, k, 0, k - 1, h->evals_b, &wsB, h->status, s2)) != EDA_OK) break;
+        if (cudaMemcpyAsync(ww.data(), h->evals_w, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(wb.data(), h->evals_b, k * sizeof(double), cudaMemcpyDeviceToHost, s2) != cudaSuccess ||
+            cudaStreamSynchronize(s2) != cudaSuccess) {
+            rc = EDA_ERR_CUDA;
+            break;
+        }
+        int st = 0;
+        if ((rc = read_status(h, s, &st)) != EDA_OK) break;
+        if ((rc = status_to_code(st)) != EDA_OK) break;
+        if ((rc = gram_eigen_finish(h, n, ww, h->evals_w, h->evecs_w, &wsW, tmpW, partW, pcapW, &h->lmax_w, nsw,
+                                    first_w, s)) != EDA_OK)
+            break;
+        if ((rc = gram_eigen_finish(h, k, wb, h->evals_b, h->evecs_b, &wsB, tmpB, partB, pcapB, &h->lmax_b, nsb,
+                                    first_b, s2)) != EDA_OK)
+            break;
+    } while (false);
+    if (s2) {
+        if (join && cudaEventRecord(join, s2) == cudaSuccess) cudaStreamWaitEvent(s, join, 0);
+        else cudaStreamSynchronize(s2);
+        cudaStreamDestroy(s2);   // released once its queued work has finished
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    return rc;
 }
 
 // B (k x n) = A^T for A (n x k), both column-major.
@@ -201,12 +274,17 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
     EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));
     const size_t mark = scratch.used;
-    int nsw = 0, nsb = 0;
-    EDA_TRY(gram_eigen(h, n, h->GW, h->evals_w, h->evecs_w, scratch, part, pcap, &h->lmax_w, &nsw, s));
-    const int first_w = h->nsig_first;
-    scratch.used = mark;
-    EDA_TRY(gram_eigen(h, k, h->GB, h->evals_b, h->evecs_b, scratch, part, pcap, &h->lmax_b, &nsb, s));
-    const int first_b = h->nsig_first;
+    int nsw = 0, nsb = 0, first_w = 0, first_b = 0;
+    if (n <= kEigClusterMaxN && k <= kEigClusterMaxN) {
+        // both on the cluster path (no grid barrier): solve side by side
+        EDA_TRY(gram_eigen_pair(h, scratch, part, pcap, &nsw, &nsb, &first_w, &first_b, s));
+    } else {
+        EDA_TRY(gram_eigen(h, n, h->GW, h->evals_w, h->evecs_w, scratch, part, pcap, &h->lmax_w, &nsw, s));
+        first_w = h->nsig_first;
+        scratch.used = mark;
+        EDA_TRY(gram_eigen(h, k, h->GB, h->evals_b, h->evecs_b, scratch, part, pcap, &h->lmax_b, &nsb, s));
+        first_b = h->nsig_first;
+    }
     scratch.used = mark;
     h->nsig_w = nsw;
     h->nsig_b = nsb;
