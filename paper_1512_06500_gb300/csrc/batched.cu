@@ -144,6 +144,7 @@ extern "C" int eda_solve_batched(eda_problem* probs, int32_t nprob, const eda_co
     std::vector<int> worker_rc(W, EDA_OK);
 
     auto work = [&](int w) {
+        symeig_set_shared_gpu(true);   // no grid-wide barriers while other problems run beside this one
         if (cudaSetDevice(dev) != cudaSuccess ||
             cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming) != cudaSuccess ||

@@ -703,7 +703,15 @@ int symeig_work_carve(Arena& a, int n, int nv, GridBarrier bar, SymEigWork* w) {
     return EDA_OK;
 }
 
-constexpr int kClusterMaxN = 512;
+constexpr int kClusterMaxN = 512;        // the cluster path up to here; a cooperative grid beyond
+constexpr int kClusterMaxNShared = 1024; // limit of the cluster path when the GPU is shared (see below)
+
+// Host threads that run many problems side by side (the batched solver) set this: a cooperative
+// grid with a software grid barrier needs all its CTAs resident at once, which concurrent kernels
+// of other problems can delay beyond the barrier's limit, while a thread-block cluster is scheduled
+// as one unit by the hardware. Such threads take the cluster path (matrix in a global slab) up to
+// kClusterMaxNShared.
+thread_local bool tl_shared_gpu = false;
 
 // Launch k_tridiag_cluster<C> on one cluster of C CTAs (a power of two, 16 only when the device
 // accepts that non-portable cluster size with the needed shared memory).
@@ -768,7 +776,7 @@ int launch_tridiag_c(int C, int n, const double* A, int lda, SymEigWork* ws, cud
 }
 
 int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_t s) {
-    static int chosen_C[kClusterMaxN + 1] = {};   // cluster size that passed the occupancy check, per n
+    static int chosen_C[kClusterMaxNShared + 1] = {};   // cluster size that passed the occupancy check, per n
     static std::mutex mu;
     std::unique_lock<std::mutex> lk(mu);
     if (!chosen_C[n]) {
@@ -816,7 +824,7 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
             set = smem;
         }
     }
-    if (n <= kClusterMaxN) {
+    if (n <= (tl_shared_gpu ? kClusterMaxNShared : kClusterMaxN)) {
         EDA_TRY(tridiag_cluster(n, A, lda, ws, s));
     } else {
     int per_sm = 0;
@@ -958,5 +966,7 @@ int newton_schulz_f64(int n, int nv, double* Z, int ldz, int steps, double* tmp,
     }
     return EDA_OK;
 }
+
+void symeig_set_shared_gpu(bool on) { tl_shared_gpu = on; }
 
 }  // namespace eda
