@@ -236,10 +236,11 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
 
     int cols = b;
     st.relres.assign(t, INFINITY);
-    // Rayleigh-Ritz schedule: the first check once the basis has t + b columns; later checks at
-    // the basis width where the geometric rate seen between the last two checks predicts
-    // convergence (never sooner than check_every blocks, always at the last block).
-    int next_check = t + b;
+    // Rayleigh-Ritz schedule: the first check once the basis has t + 2b columns (block Lanczos needs
+    // about two blocks beyond the t wanted directions; an earlier check costs a small eigensolve and
+    // rarely succeeds); later checks at the basis width where the geometric rate seen between the last
+    // two checks predicts convergence (never sooner than check_every blocks, always at the last block).
+    int next_check = t + 2 * b;
     int prev_check_cols = 0;
     double prev_check_rel = 0.0;
 
