@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="d4096_k40", choices=list(synth.CONFIGS) + ["batched64"])
-    ap.add_argument("--workers", type=int, default=16, help="host workers of the batched solve")
+    ap.add_argument("--workers", type=int, default=32, help="host workers of the batched solve")
     ap.add_argument("--m-form", type=int, default=1, choices=[0, 1],
                     help="FP64 M-apply: 0 = the three products one after another, 1 = their composed form")
     ap.add_argument("--tol", type=float, default=1e-6)
