@@ -197,6 +197,34 @@ def test_m_apply_matches_dense_symmetric_form():
     assert np.linalg.norm(O.m_apply(f["HW"], f["HB"], c2, X) - ref) < 1e-12 * np.linalg.norm(ref)
 
 
+def test_composed_form_of_the_three_products():
+    """M - I = Z C Z^T with Z = [H_W H_B] (Theorem 3.1 applied to each factor of the symmetric form):
+    the small-space recurrence the library's composed M-apply follows, written out here in numpy from
+    G_W, G_WB = H_W^T H_B, K_W = K(-c^2/2) and K_B = K(c^2), equals the three products; and so does
+    folding K into the factor, X + (H K)(H^T X)."""
+    rng = np.random.default_rng(33)
+    p = synth.gaussian_clusters(d=60, k=4, n_per_class=[3, 5, 2, 4], seed=33)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    HW, HB = f["HW"], f["HB"]
+    c2 = 0.7
+    KW = O.phi_operator(O.gram(HW), -0.5 * c2)
+    KB = O.phi_operator(O.gram(HB), c2)
+    GW, GWB = HW.T @ HW, HW.T @ HB
+    Y = rng.standard_normal((60, 3))
+    pw, qb = HW.T @ Y, HB.T @ Y
+    u1 = KW @ pw                       # y1 = y + H_W u1
+    q1 = qb + GWB.T @ u1               # H_B^T y1
+    p1 = pw + GW @ u1                  # H_W^T y1
+    v = KB @ q1                        # y2 = y1 + H_B v
+    p2 = p1 + GWB @ v                  # H_W^T y2
+    u3 = KW @ p2                       # M y = y2 + H_W u3
+    composed = Y + HW @ (u1 + u3) + HB @ v
+    ref = O.m_apply(HW, HB, c2, Y)
+    assert np.linalg.norm(composed - ref) <= 1e-13 * np.linalg.norm(ref)
+    folded = Y + (HW @ KW) @ (HW.T @ Y)
+    assert np.linalg.norm(folded - O.lowrank_exp_apply(HW, -0.5 * c2, Y)) <= 1e-13 * np.linalg.norm(folded)
+
+
 # ---------------------------------------------------------------- Section 3.2/3.3
 
 def test_commuting_diagonal_closed_form():
