@@ -385,6 +385,83 @@ __global__ void k_chol_inv(int b, double* G, int ldg, double* Rinv, double rank_
     if (threadIdx.x == 0 && lost) lost[b] = nlost;
 }
 
+// k_chol_inv with G and R^{-1} held in shared memory (b <= kCholSmemMax): every entry is formed by
+// the same operations in the same order as there, so the results are identical; only the memory
+// latency of the pivot loop and of the back substitution goes.
+constexpr int kCholSmemMax = 90;
+
+__global__ void __launch_bounds__(256) k_chol_inv_smem(int b, double* G, int ldg, double* Rinv, double rank_tol,
+                                                       double piv_min2, int* status, int* lost) {
+    extern __shared__ double smc[];
+    double* sg = smc;              // sg[c * b + r] = G[r, c]
+    double* sx = smc + b * b;      // sx[c * b + i] = Rinv[i, c]
+    __shared__ double maxdiag;
+    __shared__ int nlost;
+    __shared__ double piv;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) sg[e] = G[(int64_t)(e / b) * ldg + e % b];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        bool bad = false;
+        for (int j = 0; j < b; ++j) {
+            const double g = sg[j * b + j];
+            if (!isfinite(g)) bad = true;
+            mx = fmax(mx, fabs(g));
+        }
+        maxdiag = mx;
+        nlost = 0;
+        if (bad) atomicOr(status, ST_NONFINITE);
+    }
+    __syncthreads();
+    const double thr = fmax(rank_tol * maxdiag, piv_min2);
+    for (int j = 0; j < b; ++j) {
+        if (threadIdx.x == 0) {
+            const double g = sg[j * b + j];
+            if (!(g > thr) || maxdiag == 0.0) {
+                piv = 0.0;
+                if (lost) lost[nlost] = j;
+                nlost++;
+                atomicOr(status, ST_RANKLOSS);
+            } else {
+                piv = sqrt(g);
+            }
+            sg[j * b + j] = piv;
+        }
+        __syncthreads();
+        const double rjj = piv;
+        for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) {
+            const double v = (rjj > 0.0) ? sg[c * b + j] / rjj : 0.0;
+            sg[c * b + j] = v;
+        }
+        __syncthreads();
+        const int rem = b - j - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int c1 = j + 1 + e % rem, c2 = j + 1 + e / rem;
+            if (c1 <= c2) sg[c2 * b + c1] -= sg[c1 * b + j] * sg[c2 * b + j];
+        }
+        __syncthreads();
+    }
+    for (int c = threadIdx.x; c < b; c += blockDim.x) {
+        for (int i = b - 1; i >= 0; --i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            if (i > c) v = 0.0;
+            else {
+                for (int l = i + 1; l <= c; ++l) v -= sg[l * b + i] * sx[c * b + l];
+                const double rii = sg[i * b + i];
+                v = (rii > 0.0) ? v / rii : 0.0;
+            }
+            sx[c * b + i] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int r = e % b, c = e / b;
+        G[(int64_t)c * ldg + r] = (r > c) ? 0.0 : sg[e];
+        Rinv[e] = sx[e];
+    }
+    if (threadIdx.x == 0 && lost) lost[b] = nlost;
+}
+
 template <class Ti, class To>
 __global__ void k_copy(int64_t rows, int cols, const Ti* __restrict__ A, int64_t lda, To* __restrict__ B,
                        int64_t ldb) {
@@ -565,10 +642,20 @@ int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const d
 
 int chol_inv_small(int b, double* G, int ldg, double* Rinv, double rank_tol, double piv_min2, int* status, int* lost,
                    cudaStream_t s) {
-    if (b <= 32)
+    if (b <= 32) {
         k_chol_inv_warp<<<1, 32, 0, s>>>(b, G, ldg, Rinv, rank_tol, piv_min2, status, lost);
-    else
+    } else if (b <= kCholSmemMax) {
+        static std::once_flag once;
+        static cudaError_t attr_rc = cudaSuccess;
+        std::call_once(once, [] {
+            attr_rc = cudaFuncSetAttribute(k_chol_inv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(2 * sizeof(double) * kCholSmemMax * kCholSmemMax));
+        });
+        EDA_CUDA_TRY(attr_rc);
+        k_chol_inv_smem<<<1, 256, 2 * sizeof(double) * b * b, s>>>(b, G, ldg, Rinv, rank_tol, piv_min2, status, lost);
+    } else {
         k_chol_inv<<<1, 256, 0, s>>>(b, G, ldg, Rinv, rank_tol, piv_min2, status, lost);
+    }
     EDA_LAUNCHED();
     return EDA_OK;
 }

@@ -513,8 +513,13 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 // Inverse iteration, one thread per eigenvector; factor arrays laid out [array][i][q] so that
 // the threads of a warp touch consecutive addresses. Gaussian elimination with partial pivoting
 // of T - lambda I takes one reciprocal per row (of the pivot); the two triangular solves carry
-// the running entries in registers, so the sequential chains never wait on memory.
+// the running entries in registers. Every pass over the stored arrays reads IV_U rows at a time
+// into registers before it uses them, so one memory latency is paid per IV_U rows instead of per
+// row (the loads of a pass never depend on its stores: row i + 1 is read before row i is written,
+// and the values read are the ones the previous pass left).
 // Output: Zt[i][q] (n x nv, row stride nv).
+constexpr int IV_U = 16;
+
 __global__ void k_invit(int n, int nv, const double* __restrict__ dgl, const double* __restrict__ eoff,
                         const double* __restrict__ lam, double* lu, double* Zt, uint64_t seed) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -556,40 +561,90 @@ __global__ void k_invit(int n, int nv, const double* __restrict__ dgl, const dou
         const uint64_t h = mix64(seed ^ mix64(((uint64_t)q << 32) + (uint64_t)i + 0x5851F42D4C957F2Dull));
         x[i * S + q] = 2.0 * ((h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
     }
+    double sc = 1.0;   // scale of the previous pass, applied to x as it is read
     for (int it = 0; it < 2; ++it) {
         // forward: L^{-1} P b, the running entry carried in a register
         double carry = x[q];
-        for (int i = 0; i + 1 < n; ++i) {
-            const double f = DL[i * S + q];
-            const double nxt = x[(i + 1) * S + q];
-            if (PIV[i * S + q] != 0.0) {
-                x[i * S + q] = nxt;
-                carry = carry - f * nxt;
-            } else {
-                x[i * S + q] = carry;
-                carry = nxt - f * carry;
+        if (it > 0) carry *= sc;
+        for (int i0 = 0; i0 + 1 < n; i0 += IV_U) {
+            double f[IV_U], nx[IV_U], pv[IV_U];
+#pragma unroll
+            for (int u = 0; u < IV_U; ++u) {
+                const int i = i0 + u;
+                if (i + 1 < n) {
+                    f[u] = DL[i * S + q];
+                    pv[u] = PIV[i * S + q];
+                    nx[u] = x[(i + 1) * S + q];
+                    if (it > 0) nx[u] *= sc;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < IV_U; ++u) {
+                const int i = i0 + u;
+                if (i + 1 < n) {
+                    if (pv[u] != 0.0) {
+                        x[i * S + q] = nx[u];
+                        carry = carry - f[u] * nx[u];
+                    } else {
+                        x[i * S + q] = carry;
+                        carry = nx[u] - f[u] * carry;
+                    }
+                }
             }
         }
         x[(int64_t)(n - 1) * S + q] = carry;
         // back: U^{-1}, carrying the two previous solution entries
         double v1 = 0.0, v2 = 0.0, mx = 0.0;
-        for (int i = n - 1; i >= 0; --i) {
-            double v = x[i * S + q];
-            if (i + 1 < n) v -= DU[i * S + q] * v1;
-            if (i + 2 < n) v -= DU2[i * S + q] * v2;
-            v *= RD[i * S + q];
-            x[i * S + q] = v;
-            mx = fmax(mx, fabs(v));
-            v2 = v1;
-            v1 = v;
+        for (int i0 = n - 1; i0 >= 0; i0 -= IV_U) {
+            double xv[IV_U], du[IV_U], du2[IV_U], rd[IV_U];
+#pragma unroll
+            for (int u = 0; u < IV_U; ++u) {
+                const int i = i0 - u;
+                if (i >= 0) {
+                    xv[u] = x[i * S + q];
+                    du[u] = (i + 1 < n) ? DU[i * S + q] : 0.0;
+                    du2[u] = (i + 2 < n) ? DU2[i * S + q] : 0.0;
+                    rd[u] = RD[i * S + q];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < IV_U; ++u) {
+                const int i = i0 - u;
+                if (i >= 0) {
+                    double v = xv[u];
+                    if (i + 1 < n) v -= du[u] * v1;
+                    if (i + 2 < n) v -= du2[u] * v2;
+                    v *= rd[u];
+                    x[i * S + q] = v;
+                    mx = fmax(mx, fabs(v));
+                    v2 = v1;
+                    v1 = v;
+                }
+            }
         }
-        const double sc = (mx > 0.0 && isfinite(mx)) ? 1.0 / mx : 0.0;
-        for (int i = 0; i < n; ++i) x[i * S + q] *= sc;
+        sc = (mx > 0.0 && isfinite(mx)) ? 1.0 / mx : 0.0;
     }
+    // the last pass's scale, then the norm and the normalisation
     double nrm = 0.0;
-    for (int i = 0; i < n; ++i) nrm = fma(x[i * S + q], x[i * S + q], nrm);
-    const double sc = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
-    for (int i = 0; i < n; ++i) x[i * S + q] *= sc;
+    for (int i0 = 0; i0 < n; i0 += IV_U) {
+        double xv[IV_U];
+#pragma unroll
+        for (int u = 0; u < IV_U; ++u)
+            if (i0 + u < n) xv[u] = x[(i0 + u) * S + q] * sc;
+#pragma unroll
+        for (int u = 0; u < IV_U; ++u)
+            if (i0 + u < n) nrm = fma(xv[u], xv[u], nrm);
+    }
+    const double sn = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
+    for (int i0 = 0; i0 < n; i0 += IV_U) {
+        double xv[IV_U];
+#pragma unroll
+        for (int u = 0; u < IV_U; ++u)
+            if (i0 + u < n) xv[u] = x[(i0 + u) * S + q];
+#pragma unroll
+        for (int u = 0; u < IV_U; ++u)
+            if (i0 + u < n) x[(i0 + u) * S + q] = (xv[u] * sc) * sn;
+    }
 }
 
 // Zt (row-major n x nv) -> Z (column-major, ldz)
@@ -621,7 +676,8 @@ __global__ void k_backtransform(int n, int nv, const double* __restrict__ HV, co
 }
 
 // The same with the column held in registers (NPL entries per lane, n <= 32 * NPL), so that the
-// chain of reflectors never waits on memory.
+// chain of reflectors never waits on memory: reflector j - 1 and its scalar are read while
+// reflector j is applied.
 template <int NPL>
 __global__ void __launch_bounds__(32) k_backtransform_reg(int n, int nv, const double* __restrict__ HV,
                                                           const double* __restrict__ tau, double* Z, int ldz) {
@@ -635,16 +691,35 @@ __global__ void __launch_bounds__(32) k_backtransform_reg(int n, int nv, const d
         const int i = lane + 32 * k;
         z[k] = (i < n) ? zc[i] : 0.0;
     }
-    for (int j = n - 3; j >= 0; --j) {
-        const double tj = __ldg(tau + j);
-        if (tj == 0.0) continue;
-        const double* u = HV + (int64_t)j * n;     // zero for i <= j
-        double uu[NPL];
-        double d0 = 0.0, d1 = 0.0;
+    double un[NPL];   // the next reflector (zero for i <= j)
+    double tn = 0.0;
+    if (n >= 3) {
+        const double* u = HV + (int64_t)(n - 3) * n;
+        tn = __ldg(tau + n - 3);
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
             const int i = lane + 32 * k;
-            uu[k] = (i < n) ? __ldg(u + i) : 0.0;
+            un[k] = (i < n) ? __ldg(u + i) : 0.0;
+        }
+    }
+    for (int j = n - 3; j >= 0; --j) {
+        double uu[NPL];
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) uu[k] = un[k];
+        const double tj = tn;
+        if (j > 0) {
+            const double* u = HV + (int64_t)(j - 1) * n;
+            tn = __ldg(tau + j - 1);
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int i = lane + 32 * k;
+                un[k] = (i < n) ? __ldg(u + i) : 0.0;
+            }
+        }
+        if (tj == 0.0) continue;
+        double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
             if (k & 1) d1 = fma(uu[k], z[k], d1);
             else d0 = fma(uu[k], z[k], d0);
         }
