@@ -49,9 +49,39 @@ int m_apply_f32(eda_ctx* h, int b, const float* X, int64_t ldx, float* Y, int64_
                 double* Q, double* partial, size_t partial_cap, cudaStream_t s);
 
 namespace {
+// B (k x n) = A^T for A (n x k), both column-major.
+__global__ void k_transpose_nk(int n, int k, const double* __restrict__ A, double* __restrict__ B) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    const int i = (int)(e % n), j = (int)(e / n);
+    B[(int64_t)i * k + j] = A[e];
+}
+}  // namespace
+
+// Cross Grams G_WB = H_W^T H_B and G_BW = G_WB^T for the composed FP64 M-apply (the mixed-precision
+// refinement, the FP64 Krylov phase with m_form = 1, and the FP64 verification after refills);
+// formed once per handle. part: split-K partials of at least n k doubles.
+int ensure_cross_gram(eda_ctx* h, double* part, size_t pcap, cudaStream_t s) {
+    if (h->GWB) return EDA_OK;
+    const int n = (int)h->n, k = h->k;
+    const size_t xb = ((size_t)n * k * 8 + 255) & ~size_t(255);
+    void* xp = nullptr;
+    EDA_CUDA_TRY(cudaMalloc(&xp, 2 * xb));
+    h->xblock = xp;
+    h->GWB = static_cast<double*>(xp);
+    h->GBW = reinterpret_cast<double*>(static_cast<char*>(xp) + xb);
+    EDA_TRY(gemm_tn_f64(h->d, n, k, 1.0, h->HW, h->d, h->HB, h->d, 0.0, h->GWB, n, part, pcap, s));
+    k_transpose_nk<<<ceil_div((int64_t)n * k, 256), 256, 0, s>>>(n, k, h->GWB, h->GBW);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+namespace {
 
 constexpr int kEigClusterMaxN = 512;   // the eigensolver's cluster path (no grid barrier) up to this size
 constexpr double kSigRel = 32.0;   // eigenvalues <= kSigRel * n * eps * lambda_max are the Gram's null space
+constexpr int kLanczosSteps = 64;  // steps of the largest-eigenvalue Lanczos run on a Gram
+constexpr double kLmaxCert = 8.0;  // accept its theta_1 when the error bound is <= kLmaxCert * eps * theta_1
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -236,12 +266,115 @@ int gram_eigen_pair(eda_ctx* h, Arena& scratch, double* partW, size_t pcapW, int
     return rc;
 }
 
-// B (k x n) = A^T for A (n x k), both column-major.
-__global__ void k_transpose_nk(int n, int k, const double* __restrict__ A, double* __restrict__ B) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n * k) return;
-    const int i = (int)(e % n), j = (int)(e / n);
-    B[(int64_t)i * k + j] = A[e];
+
+// A second stream for the independent halves of the build (the two Grams), joined back into the
+// caller's stream when it goes out of scope.
+struct AuxStream {
+    cudaStream_t main = nullptr, aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int open(cudaStream_t s) {
+        main = s;
+        if (cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess)
+            return EDA_ERR_CUDA;
+        return EDA_OK;
+    }
+    int fork() {
+        EDA_CUDA_TRY(cudaEventRecord(ev_fork, main));
+        EDA_CUDA_TRY(cudaStreamWaitEvent(aux, ev_fork, 0));
+        return EDA_OK;
+    }
+    int join() {
+        EDA_CUDA_TRY(cudaEventRecord(ev_join, aux));
+        EDA_CUDA_TRY(cudaStreamWaitEvent(main, ev_join, 0));
+        return EDA_OK;
+    }
+    ~AuxStream() {
+        if (aux) {
+            if (!ev_join || cudaEventRecord(ev_join, aux) != cudaSuccess ||
+                cudaStreamWaitEvent(main, ev_join, 0) != cudaSuccess)
+                cudaStreamSynchronize(aux);
+            cudaStreamDestroy(aux);   // released once its queued work has finished
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+    }
+};
+
+// lambda_max of a Gram from its Lanczos run (theta_1, theta_2, |z_m|, beta_m), or -1 when the
+// bounds do not place theta_1 within kLmaxCert * eps * theta_1 of an eigenvalue. Residual bound
+// r = beta_m |z_m|; with the Ritz gap g = theta_1 - theta_2 > 2 r the quadratic bound r^2 / (g - r)
+// applies.
+double lmax_certified(const double* o) {
+    const double t1 = o[0], t2 = o[1], r = o[2] * o[3];
+    if (!std::isfinite(t1) || !std::isfinite(r)) return -1.0;
+    double bound = r;
+    const double gap = t1 - t2;
+    if (gap > 2.0 * r) bound = std::min(bound, r * r / (gap - r));
+    if (!(bound <= kLmaxCert * DBL_EPSILON * std::max(t1, 0.0))) return -1.0;
+    return std::max(t1, 0.0);
+}
+
+// lambda_max of G_W and G_B without their eigenvectors: one Lanczos run per Gram, side by side on two
+// streams, one host wait for both; a Gram whose bound does not certify its estimate falls back to
+// the full eigensolver's largest eigenvalue.
+int gram_lmax_pair(eda_ctx* h, Arena& scratch, AuxStream& aux, cudaStream_t s) {
+    const int n = (int)h->n, k = h->k;
+    SymEigWork wsW{}, wsB{};
+    EDA_TRY(symeig_work_carve(scratch, n, 1, h->bar, &wsW));
+    EDA_TRY(symeig_work_carve(scratch, k, 1, h->bar, &wsB));
+    double* out = scratch.take<double>(8);
+    if (!out) return EDA_ERR_OOM;
+    EDA_TRY(aux.fork());
+    EDA_TRY(lanczos_top(n, h->GW, n, std::min(n, kLanczosSteps), h->cfg.seed, &wsW, out, s));
+    EDA_TRY(lanczos_top(k, h->GB, k, std::min(k, kLanczosSteps), h->cfg.seed, &wsB, out + 4, aux.aux));
+    EDA_TRY(aux.join());
+    double o[8];
+    EDA_CUDA_TRY(cudaMemcpyAsync(o, out, sizeof(o), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaStreamSynchronize(s));
+    double lw = lmax_certified(o), lb = lmax_certified(o + 4);
+    for (int g = 0; g < 2; ++g) {
+        double& l = g == 0 ? lw : lb;
+        if (l >= 0.0) continue;
+        const int m = g == 0 ? n : k;
+        double* w = g == 0 ? h->evals_w : h->evals_b;
+        EDA_TRY(symeig_values(m, g == 0 ? h->GW : h->GB, m, m - 1, m - 1, w, g == 0 ? &wsW : &wsB, h->status, s));
+        double top = 0.0;
+        EDA_CUDA_TRY(cudaMemcpyAsync(&top, w, sizeof(double), cudaMemcpyDeviceToHost, s));
+        EDA_CUDA_TRY(cudaStreamSynchronize(s));
+        int st = 0;
+        EDA_TRY(read_status(h, s, &st));
+        if (int c = status_to_code(st)) return c;
+        if (!std::isfinite(top)) return EDA_ERR_NONFINITE;
+        l = std::max(top, 0.0);
+    }
+    h->lmax_w = lw;
+    h->lmax_b = lb;
+    return EDA_OK;
+}
+
+// The Grams' eigenpairs (eigenvalues, significant eigenvectors) for a handle whose K came from
+// scaling and squaring: computed on first request (exported eigenvalues, K(alpha) for another alpha).
+// lambda_max and c^2 keep the values the build used.
+int ensure_eigen(eda_ctx* h, cudaStream_t s) {
+    if (h->eig_ready) return EDA_OK;
+    const int n = (int)h->n, k = h->k;
+    const size_t N = std::max<int64_t>(n, k);
+    Arena scratch{static_cast<char*>(h->block), h->block_bytes, h->build_arena_off};
+    const size_t pcap = std::max<size_t>(1u << 19, N * N);
+    double* part = scratch.take<double>(pcap);
+    if (!part) return EDA_ERR_OOM;
+    const size_t mark = scratch.used;
+    double lm = 0.0;
+    int ns = 0;
+    EDA_TRY(gram_eigen(h, n, h->GW, h->evals_w, h->evecs_w, scratch, part, pcap, &lm, &ns, s));
+    h->nsig_w = ns;
+    scratch.used = mark;
+    EDA_TRY(gram_eigen(h, k, h->GB, h->evals_b, h->evecs_b, scratch, part, pcap, &lm, &ns, s));
+    h->nsig_b = ns;
+    h->eig_ready = true;
+    return EDA_OK;
 }
 
 // Everything after H_W, H_B exist: Grams, eigenpairs, c^2, K operators, and for the mixed
@@ -275,7 +408,14 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));
     const size_t mark = scratch.used;
     int nsw = 0, nsb = 0, first_w = 0, first_b = 0;
-    if (n <= kEigClusterMaxN && k <= kEigClusterMaxN) {
+    // Small Grams: lambda_max by Lanczos and K by scaling and squaring (dense products that fill the
+    // GPU) instead of the eigensolver's sequential column steps; the eigenpairs follow on request.
+    const bool by_squaring = n <= kLanczosMaxN && k <= kLanczosMaxN;
+    AuxStream aux;
+    if (by_squaring) {
+        EDA_TRY(aux.open(s));
+        EDA_TRY(gram_lmax_pair(h, scratch, aux, s));
+    } else if (n <= kEigClusterMaxN && k <= kEigClusterMaxN) {
         // both on the cluster path (no grid barrier): solve side by side
         EDA_TRY(gram_eigen_pair(h, scratch, part, pcap, &nsw, &nsb, &first_w, &first_b, s));
     } else {
@@ -288,6 +428,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     scratch.used = mark;
     h->nsig_w = nsw;
     h->nsig_b = nsb;
+    h->eig_ready = !by_squaring;
     if (h->cfg.c2 > 0.0) {
         h->c2 = h->cfg.c2;
     } else {
@@ -295,23 +436,26 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         if (!(m > 0.0)) return EDA_ERR_INVALID_ARG;   // both scatter matrices vanish
         h->c2 = h->cfg.tau / m;
     }
-    double* tmp = scratch.take<double>(N * N + 64);
-    if (!tmp) return EDA_ERR_OOM;
-    EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
-    EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
-    if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16 || h->cfg.m_form == 1) {
-        // cross Grams G_WB = H_W^T H_B and G_BW = G_WB^T for the composed FP64 M-apply (the
-        // mixed-precision refinement, and the FP64 Krylov phase with m_form = 1)
-        void* xp = nullptr;
-        const size_t xb = align256((size_t)n * k * 8);
-        EDA_CUDA_TRY(cudaMalloc(&xp, 2 * xb));
-        h->xblock = xp;
-        h->GWB = static_cast<double*>(xp);
-        h->GBW = reinterpret_cast<double*>(static_cast<char*>(xp) + xb);
-        EDA_TRY(gemm_tn_f64(d, n, k, 1.0, h->HW, d, h->HB, d, 0.0, h->GWB, n, part, pcap, s));
-        k_transpose_nk<<<ceil_div((int64_t)n * k, 256), 256, 0, s>>>(n, k, h->GWB, h->GBW);
-        EDA_LAUNCHED();
+    if (by_squaring) {
+        double* workW = scratch.take<double>(6 * (size_t)n * n);
+        double* workB = scratch.take<double>(6 * (size_t)k * k);
+        if (!workW || !workB) return EDA_ERR_OOM;
+        {
+            ProfScope prof("phi_squaring", s);
+            EDA_TRY(aux.fork());
+            EDA_TRY(phi_by_squaring(n, h->GW, -0.5 * h->c2, h->lmax_w, h->KW, workW, s));
+            EDA_TRY(phi_by_squaring(k, h->GB, h->c2, h->lmax_b, h->KB, workB, aux.aux));
+            EDA_TRY(aux.join());
+        }
+        scratch.used = mark;
+    } else {
+        double* tmp = scratch.take<double>(N * N + 64);
+        if (!tmp) return EDA_ERR_OOM;
+        EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
+        EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
     }
+    if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16 || h->cfg.m_form == 1)
+        EDA_TRY(ensure_cross_gram(h, part, pcap, s));
     if (h->cfg.prec == EDA_BF16) {
         // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
         // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)
@@ -489,6 +633,7 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
     const double stored = isW ? -0.5 * h->c2 : h->c2;
     const double* K = isW ? h->KW : h->KB;
     if (alpha != stored) {
+        EDA_TRY(ensure_eigen(h, s));
         if (!h->kblock) {
             void* kb = nullptr;
             EDA_CUDA_TRY(cudaMalloc(&kb, 2 * align256((size_t)N * N * 8)));
@@ -544,6 +689,7 @@ int eda_get_factors(eda_handle h, double* HW, double* HB, int32_t* counts, int32
     EDA_TRY(cp(GB, h->GB, k * k * 8));
     EDA_TRY(cp(KW, h->KW, n * n * 8));
     EDA_TRY(cp(KB, h->KB, k * k * 8));
+    if (evals_w || evals_b) EDA_TRY(eda::ensure_eigen(h, s));
     EDA_TRY(cp(evals_w, h->evals_w, n * 8));
     EDA_TRY(cp(evals_b, h->evals_b, k * 8));
     return EDA_OK;

@@ -158,6 +158,15 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
                   int* status, cudaStream_t s);
 int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, uint64_t seed,
                    double cluster_rel, cudaStream_t s);
+// Lanczos estimate of the largest eigenvalue of a symmetric positive semidefinite n x n matrix A
+// (n <= kLanczosMaxN): m steps of the three-term recurrence in one thread-block cluster, then the
+// two largest eigenvalues of the m x m tridiagonal and the last entry of the unit eigenvector of the
+// largest. out (device, 4 doubles): theta_1, theta_2 (-DBL_MAX when m = 1), |z_m|, beta_m; the
+// distance from theta_1 to an eigenvalue of A is at most beta_m |z_m|, and at most
+// (beta_m z_m)^2 / (theta_1 - theta_2 - beta_m |z_m|) when that gap is positive. ws: carved for n.
+constexpr int kLanczosMaxN = 256;
+int lanczos_top(int n, const double* A, int lda, int m, uint64_t seed, SymEigWork* ws, double* out,
+                cudaStream_t s);
 // Orthonormalise the columns of Z (n x nv) against each other by Newton-Schulz steps
 // Z <- Z (3 I - Z^T Z) / 2; tmp holds 2 * nv * nv + n * nv doubles.
 int newton_schulz_f64(int n, int nv, double* Z, int ldz, int steps, double* tmp, double* partial,
@@ -176,6 +185,10 @@ int check_finite_f64(int64_t rows, int cols, const double* A, int64_t lda, int* 
 // and phi(0) = 1. tmp: n * ns doubles.
 int phi_operator(int n, int ns, const double* lam, const double* W, int ldw, double alpha,
                  double* K, double* tmp, cudaStream_t s);
+// The same K(alpha) = alpha phi(alpha G) from G itself by scaling and squaring (dense products
+// only), given lmax >= the largest eigenvalue of G. work: 6 m^2 doubles.
+int phi_by_squaring(int m, const double* G, double alpha, double lmax, double* K, double* work,
+                    cudaStream_t s);
 
 // ---------------------------------------------------------------- exp-apply
 struct ExpOp {
@@ -261,6 +274,8 @@ struct eda_ctx {
     size_t build_arena_off = 0;            // start of the build scratch inside `block`
     int nsig_first = 0;                    // scratch result of the last Gram eigensolve
     int nsig_w = 0, nsig_b = 0;            // significant eigenpairs kept for K_W, K_B
+    bool eig_ready = false;                // evals / evecs hold the Grams' eigenpairs (computed on
+                                           // demand when K came from scaling and squaring)
     // K(alpha) for an alpha other than the stored ones (allocated on first use)
     void* kblock = nullptr;
     double *Kalpha = nullptr, *Kalpha_tmp = nullptr;
@@ -276,4 +291,6 @@ struct eda_ctx {
 namespace eda {
 // Grow the handle's solve workspace to at least `bytes` (contents are not preserved).
 int ensure_workspace(eda_ctx* h, size_t bytes);
+// Form the cross Grams G_WB, G_BW of the handle if they are not there yet.
+int ensure_cross_gram(eda_ctx* h, double* part, size_t pcap, cudaStream_t s);
 }  // namespace eda

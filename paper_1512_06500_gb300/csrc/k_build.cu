@@ -2,7 +2,9 @@
 // finite checks, and the small operator K(alpha) = alpha phi(alpha G) of Theorem 3.1.
 #include "eda_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
+#include <utility>
 
 namespace eda {
 
@@ -132,6 +134,25 @@ __global__ void k_add_diag(int n, double alpha, double* K) {
     if (i < n) K[(int64_t)i * n + i] += alpha;
 }
 
+// D = c0 I + c1 P1 + c2 P2 + c3 P3 (m x m, ld m); a null P contributes nothing.
+__global__ void k_lincomb4(int m, double c0, double c1, const double* P1, double c2, const double* P2, double c3,
+                           const double* P3, double* D) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int i = (int)(e % m), j = (int)(e / m);
+    double v = (i == j) ? c0 : 0.0;
+    if (P1) v = fma(c1, P1[e], v);
+    if (P2) v = fma(c2, P2[e], v);
+    if (P3) v = fma(c3, P3[e], v);
+    D[e] = v;
+}
+
+// D = a S (m x m)
+__global__ void k_scale_sq(int m, double a, const double* S, double* D) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (int64_t)m * m) D[e] = a * S[e];
+}
+
 }  // namespace
 
 int segment_labels(const int32_t* labels, int n, int k, int32_t* counts, int32_t* offsets, int32_t* perm,
@@ -195,6 +216,74 @@ int phi_operator(int n, int ns, const double* lam, const double* W, int ldw, dou
     k_add_diag<<<ceil_div(n, 256), 256, 0, s>>>(n, alpha, K);
     EDA_LAUNCHED();
     return EDA_OK;
+}
+
+
+// K(alpha) = alpha phi(alpha G) of a symmetric positive semidefinite Gram G (m x m) without its
+// eigenvectors, for matrices small enough that a few dense products cost less than the eigensolver's
+// sequential steps. With B = alpha G / 2^s, s the least integer with |alpha| lambda_max / 2^s <= 1:
+// phi(B) = sum_{k=0}^{17} B^k / (k+1)! (the first omitted term is below 1/19! < 2^-56 for ||B|| <= 1),
+// evaluated in Paterson-Stockmeyer form in the powers B, B^2, B^3 and B^4; e^B = I + B phi(B); then s
+// doublings phi(2B) = phi(B) (I + e^B) / 2 and e^(2B) = (e^B)^2. Every factor is a polynomial in G, so
+// all products commute in exact arithmetic; the result is symmetrised. 7 + 2 s dense m x m x m
+// products. work: 6 m^2 doubles.
+int phi_by_squaring(int m, const double* G, double alpha, double lmax, double* K, double* work, cudaStream_t s) {
+    if (m <= 0) return EDA_OK;
+    const size_t mm = (size_t)m * m;
+    const int eb = ceil_div((int64_t)mm, 256);
+    const double rho = fabs(alpha) * std::max(lmax, 0.0);
+    int sq = 0;
+    while (sq < 60 && std::ldexp(rho, -sq) > 1.0) ++sq;
+    double c[20];
+    {
+        double f = 1.0;
+        for (int k = 0; k < 20; ++k) {
+            f *= (double)(k + 1);
+            c[k] = 1.0 / f;                          // 1 / (k+1)!
+        }
+    }
+    double* P1 = work;
+    double* P2 = work + mm;
+    double* P3 = work + 2 * mm;
+    double* P4 = work + 3 * mm;
+    double* F = work + 4 * mm;
+    double* T = work + 5 * mm;
+    auto mul = [&](const double* A, const double* B, double beta, double* C) {
+        return gemm_small_f64(false, false, m, m, m, 1.0, A, m, B, m, beta, C, m, s);
+    };
+    k_scale_sq<<<eb, 256, 0, s>>>(m, std::ldexp(alpha, -sq), G, P1);
+    EDA_LAUNCHED();
+    EDA_TRY(mul(P1, P1, 0.0, P2));
+    EDA_TRY(mul(P2, P1, 0.0, P3));
+    EDA_TRY(mul(P3, P1, 0.0, P4));
+    // Horner in B^4 over the blocks c_{4i} .. c_{4i+3}, i = 4 (c_16, c_17) down to 0
+    k_lincomb4<<<eb, 256, 0, s>>>(m, c[16], c[17], P1, 0.0, nullptr, 0.0, nullptr, F);
+    EDA_LAUNCHED();
+    for (int i = 3; i >= 0; --i) {
+        k_lincomb4<<<eb, 256, 0, s>>>(m, c[4 * i], c[4 * i + 1], P1, c[4 * i + 2], P2, c[4 * i + 3], P3, T);
+        EDA_LAUNCHED();
+        EDA_TRY(mul(F, P4, 1.0, T));               // T = F B^4 + Q_i
+        std::swap(F, T);
+    }
+    // E = I + B phi(B) (in P2; B^2 and B^3 are no longer needed)
+    double* E = P2;
+    double* E2 = P3;
+    k_lincomb4<<<eb, 256, 0, s>>>(m, 1.0, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, E);
+    EDA_LAUNCHED();
+    EDA_TRY(mul(P1, F, 1.0, E));
+    for (int q = 0; q < sq; ++q) {
+        k_scale_sq<<<eb, 256, 0, s>>>(m, 0.5, F, T);
+        EDA_LAUNCHED();
+        EDA_TRY(gemm_small_f64(false, false, m, m, m, 0.5, F, m, E, m, 1.0, T, m, s));   // phi(2B)
+        std::swap(F, T);
+        if (q + 1 < sq) {
+            EDA_TRY(mul(E, E, 0.0, E2));                                                   // e^(2B)
+            std::swap(E, E2);
+        }
+    }
+    k_scale_sq<<<eb, 256, 0, s>>>(m, alpha, F, K);
+    EDA_LAUNCHED();
+    return symmetrize_f64(m, K, m, s);
 }
 
 }  // namespace eda

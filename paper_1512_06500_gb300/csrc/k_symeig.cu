@@ -736,6 +736,137 @@ __global__ void __launch_bounds__(32) k_backtransform_reg(int n, int nv, const d
     }
 }
 
+// Largest eigenvalue of a symmetric positive semidefinite n x n matrix A (n <= 16 C) by the plain
+// symmetric Lanczos recurrence u = A v_j - beta_{j-1} v_{j-1}, alpha_j = v_j^T u,
+// u <- u - alpha_j v_j, beta_j = ||u||, v_{j+1} = u / beta_j, run for m steps in one thread-block
+// cluster of C CTAs. The extreme Ritz values of the tridiagonal T_m converge to the extreme
+// eigenvalues of A without reorthogonalisation (loss of orthogonality only adds copies of converged
+// Ritz values), so the recurrence alone is kept. CTA r owns rows [r nb, r nb + nb) of A (nb <= 16)
+// in its shared memory and every CTA keeps the whole current vector v; the two inner products of a
+// step are summed over the CTAs in a fixed order, so every CTA holds bitwise the same alpha_j and
+// beta_j. Output: T_m as dgl[0..m-1] (alpha) and eoff[0..m-1] (beta, eoff[m-1] = beta_m, the norm of
+// the residual after the last step). On breakdown (beta_j at rounding level) the recurrence stops
+// and the rest of T_m is zero: a diagonal block of zeros, which leaves the largest eigenvalue of the
+// nonnegative spectrum unchanged. Start vector: uniform in [-1, 1] from a counter-based hash of
+// (seed, index).
+constexpr int LZ_THREADS = 128;
+constexpr int LZ_ROWS = 16;
+constexpr int LZ_GROUPS = LZ_THREADS / LZ_ROWS;
+
+__global__ void __launch_bounds__(LZ_THREADS) k_lanczos(int n, const double* __restrict__ A, int lda, int m,
+                                                        uint64_t seed, double* dgl, double* eoff) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int nb = (n + C - 1) / C;
+    const int r0 = rank * nb;
+    const int nr = max(0, min(n, r0 + nb) - r0);
+    extern __shared__ double smz[];
+    double* Aloc = smz;                    // Aloc[c * LZ_ROWS + i] = A[r0 + i, c]
+    double* v = smz + (size_t)LZ_ROWS * n; // the current Lanczos vector, all n entries
+    __shared__ double part[LZ_GROUPS][LZ_ROWS];
+    __shared__ double vnew[LZ_ROWS];       // this CTA's rows of v_{j+1} (read by the other CTAs)
+    __shared__ double red[2];              // this CTA's partial sums of the step (read by the other CTAs)
+    __shared__ double s_ab[2];
+    __shared__ double s_red[32];
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int row = tid % LZ_ROWS, grp = tid / LZ_ROWS;
+    for (int e = tid; e < LZ_ROWS * n; e += LZ_THREADS) {
+        const int c = e / LZ_ROWS, i = e % LZ_ROWS;
+        Aloc[e] = (i < nr) ? A[(int64_t)c * lda + r0 + i] : 0.0;
+    }
+    // start vector: every CTA forms all n entries and their norm in the same order
+    double ss = 0.0;
+    for (int c = tid; c < n; c += LZ_THREADS) {
+        const uint64_t h = mix64(seed ^ mix64((uint64_t)c + 0x2545F4914F6CDD1Dull));
+        const double x = 2.0 * ((h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+        v[c] = x;
+        ss = fma(x, x, ss);
+    }
+    ss = block_sum(ss, s_red);
+    const double inv0 = (ss > 0.0) ? 1.0 / sqrt(ss) : 0.0;
+    __syncthreads();
+    for (int c = tid; c < n; c += LZ_THREADS) v[c] *= inv0;
+    double vp = 0.0;                       // v_{j-1} at this thread's row (warp 0, lanes < nr)
+    double beta = 0.0, anorm = 0.0;
+    if (tid == 0) s_stop = 0;
+    __syncthreads();
+    int j = 0;
+    for (; j < m; ++j) {
+        // u = A v over this CTA's rows: thread (row, grp) sums the columns c = grp mod LZ_GROUPS
+        double acc = 0.0;
+        for (int c = grp; c < n; c += LZ_GROUPS) acc = fma(Aloc[c * LZ_ROWS + row], v[c], acc);
+        part[grp][row] = acc;
+        __syncthreads();
+        double u = 0.0, vi = 0.0;
+        if (tid < 32) {
+            if (lane < nr) {
+                double t = part[0][lane];
+#pragma unroll
+                for (int g = 1; g < LZ_GROUPS; ++g) t += part[g][lane];
+                vi = v[r0 + lane];
+                u = fma(-beta, vp, t);
+            }
+            double a = vi * u;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) red[0] = a;
+        }
+        cluster.sync();                                    // partial alpha of every CTA published
+        if (tid < 32) {
+            double a = (lane < C) ? *cluster.map_shared_rank(&red[0], lane) : 0.0;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            u = (lane < nr) ? fma(-a, vi, u) : 0.0;
+            double b2 = u * u;
+            for (int o = 16; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+            if (lane == 0) {
+                s_ab[0] = a;
+                red[1] = b2;
+            }
+        }
+        cluster.sync();                                    // partial ||u||^2 of every CTA published
+        if (tid < 32) {
+            double b2 = (lane < C) ? *cluster.map_shared_rank(&red[1], lane) : 0.0;
+            for (int o = 16; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+            const double a = s_ab[0];
+            const double b = sqrt(b2);
+            anorm = fmax(anorm, fabs(a) + b + beta);
+            const bool stop = !(b > 16.0 * DBL_EPSILON * anorm);
+            if (rank == 0 && lane == 0) {
+                dgl[j] = a;
+                eoff[j] = stop ? 0.0 : b;
+            }
+            if (lane < nr) {
+                vp = vi;
+                vnew[lane] = stop ? 0.0 : u * (1.0 / b);
+            }
+            beta = b;
+            if (lane == 0) s_stop = stop ? 1 : 0;
+        }
+        cluster.sync();                                    // v_{j+1} published
+        if (s_stop) break;                                 // the same decision in every CTA
+        for (int c = tid; c < n; c += LZ_THREADS) v[c] = cluster.map_shared_rank(vnew, c / nb)[c % nb];
+        __syncthreads();
+    }
+    if (rank == 0)
+        for (int jj = j + 1 + tid; jj < m; jj += LZ_THREADS) {
+            dgl[jj] = 0.0;
+            eoff[jj] = 0.0;
+        }
+    cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// (theta_1, theta_2, |z_m|, beta_m) of the Lanczos tridiagonal: its two largest eigenvalues, the last
+// entry of the unit eigenvector of theta_1, and the residual norm after the last step.
+__global__ void k_lanczos_pack(int m, const double* w, const double* z, const double* eoff, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    out[0] = w[m >= 2 ? 1 : 0];
+    out[1] = (m >= 2) ? w[0] : -DBL_MAX;
+    out[2] = fabs(z[m - 1]);
+    out[3] = eoff[m - 1];
+}
+
 __global__ void k_copy_sq(int n, const double* A, int lda, double* B) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)n * n) return;
@@ -1039,6 +1170,48 @@ int newton_schulz_f64(int n, int nv, double* Z, int ldz, int steps, double* tmp,
         EDA_TRY(gemm_nn_f64(n, nv, nv, -0.5, Z, ldz, G, nv, 1.5, Z, ldz, Zn, n, s));
         EDA_TRY(copy_mat_f64(n, nv, Zn, n, Z, ldz, s));
     }
+    return EDA_OK;
+}
+
+int lanczos_top(int n, const double* A, int lda, int m, uint64_t seed, SymEigWork* ws, double* out,
+                cudaStream_t s) {
+    if (n < 1 || n > kLanczosMaxN || m < 1 || m > n) return EDA_ERR_INVALID_ARG;
+    const int C = (n + LZ_ROWS - 1) / LZ_ROWS;
+    {
+        static std::once_flag once;
+        std::call_once(once, [] {
+            cudaFuncSetAttribute(k_lanczos, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaGetLastError();
+        });
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(LZ_THREADS);
+    cfg.dynamicSmemBytes = (size_t)(LZ_ROWS + 1) * n * sizeof(double);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    {
+        ProfScope prof("lanczos", s);
+        EDA_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_lanczos, n, A, lda, m, seed, ws->dgl, ws->eoff));
+        launch_counter()++;
+    }
+    // the two largest eigenvalues of T_m and the eigenvector of the largest
+    const int nv = m >= 2 ? 2 : 1;
+    double* w = ws->vbuf;                       // nv values
+    double* lu = ws->lu;
+    double* zt = ws->lu + 5 * (size_t)m;        // m entries
+    k_bisect<<<nv, 32, 3 * (size_t)m * sizeof(double), s>>>(m, ws->dgl, ws->eoff, m - nv, nv, w);
+    EDA_LAUNCHED();
+    k_invit<<<1, 32, 0, s>>>(m, 1, ws->dgl, ws->eoff, w + nv - 1, lu, zt, seed);
+    EDA_LAUNCHED();
+    k_lanczos_pack<<<1, 32, 0, s>>>(m, w, zt, ws->eoff, out);
+    EDA_LAUNCHED();
     return EDA_OK;
 }
 

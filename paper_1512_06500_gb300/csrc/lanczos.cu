@@ -585,7 +585,13 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     double max_rel = st.max_rel;
     std::vector<double> relres_h = st.relres;
     int refine_iters = 0;
-    if (mixed) {
+    // FP64 phase: always for the mixed-precision solver; for the FP64 solver when directions were
+    // dropped and replaced by fresh ones during the Krylov phase. The Ritz residual estimate only sees
+    // the last block, while a direction dropped earlier (its size lost in the rounding of the block's
+    // Gram) leaves a residual no later block measures; so the pairs are verified, and refined if
+    // needed, with true FP64 residuals.
+    if (mixed || st.refills > 0) {
+        if (!mixed) EDA_TRY(ensure_cross_gram(h, static_cast<double*>(w.part), w.pcap, s));
         int mapp = 0;
         EDA_TRY(refine_f64<T>(h, t, tol, w, 6, &refine_iters, &mapp, relres_h, &max_rel, s));
         st.mapplies += mapp;
