@@ -29,6 +29,9 @@ from paper_1512_06500_gb300 import synth  # noqa: E402
 
 METRIC = "EDA solve time to t Ritz pairs @rel-res 1e-6; exp-apply GB/s vs HBM peak"
 NOMINAL_FP64_TFLOPS = 1.25          # GB300 FP64 (non-tensor), profiling recipe
+# DRAM bytes (read + write) of the two Gram launches of one d4096_k40 build (G_W: 6561536, G_B: 1322752)
+# from one ncu capture (profiles/gram_gemm_d4096_k40.md): H_W and H_B are read once, the products stay in L2
+GRAM_TRAFFIC_BYTES = 7884288
 FALLBACK_HBM_GBS = 6800.0           # profiling recipe fallback when no measured peaks exist
 FALLBACK_BF16_TFLOPS = 1900.0
 
@@ -464,23 +467,31 @@ def run_gpu(args, rank, world, local_rank):
     # ---- rooflines measured inside the timed region (library event pairs + its own work counts) ----
     regions = {r: eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
                                                   "tridiag", "bisect", "invit", "backtransform", "symeig", "gram",
-                                                  "rr", "reorth")}
+                                                  "lanczos", "phi_squaring", "rr", "reorth", "refine")}
     pk = peaks()
-    # dominant kernel of the step (ncu launch list): the Householder tridiagonalisation of the small FP64
-    # matrices (the n x n Gram of the build and the Rayleigh-Ritz matrices of the solve)
+    # dominant kernel of the step (ncu launch list): k_gemm_tn_partial<32, double>, whose largest launches
+    # are the FP64 Grams G_W = H_W^T H_W and G_B = H_B^T H_B of the build (2 d (n^2 + k^2) flops per step,
+    # timed as the library's "gram" region); FP64-ALU bound with H_W resident in L2
+    g_ms, g_calls = regions["gram"]
+    g_flops, _ = eda.profile_work("gram")
+    g_tf = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else float("nan")
+    roofline = {
+        "kernel": "k_gemm_tn_partial<32, double>: FP64 Grams G_W = H_W^T H_W, G_B = H_B^T H_B (2 d (n^2 + k^2) "
+                  "flops per build)",
+        "bound": "alu", "achieved": g_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+        "frac": g_tf / NOMINAL_FP64_TFLOPS, "traffic": GRAM_TRAFFIC_BYTES,
+        "peak_source": "nominal FP64 rate of the profiling recipe (own probe measured 1.19 TFLOP/s)",
+        "avg_call_us": g_ms * 1e3 / max(g_calls, 1), "calls": g_calls,
+        "flops_per_step": g_flops / args.steps,
+    }
     tri_ms, tri_calls = regions["tridiag"]
     tri_flops, _ = eda.profile_work("tridiag")
-    tri_tf = tri_flops / (tri_ms / 1e3) / 1e12 if tri_ms > 0 else float("nan")
-    roofline = {
-        "kernel": "k_tridiag_cluster: Householder tridiagonalisation (4/3 n^3 flops) of the FP64 Gram and "
-                  "Rayleigh-Ritz matrices",
-        "bound": "alu", "achieved": tri_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-        "frac": tri_tf / NOMINAL_FP64_TFLOPS, "traffic": None,
-        "peak_source": "nominal FP64 rate of the profiling recipe (own probe measured 1.19 TFLOP/s)",
-        "note": "latency-bound: n dependent column steps, each with cluster-wide reductions; the matrix "
-                "lives in distributed shared memory",
+    latency_bound = {
+        "kernel": "k_tridiag_cluster: Householder tridiagonalisation (4/3 n^3 flops) of the Rayleigh-Ritz matrices",
+        "achieved_tflops": tri_flops / (tri_ms / 1e3) / 1e12 if tri_ms > 0 else None,
         "avg_call_us": tri_ms * 1e3 / max(tri_calls, 1), "calls": tri_calls,
-        "flops_per_step": tri_flops / args.steps,
+        "note": "latency-bound: n dependent column steps, each a chain of FP64 instructions (64 cycles per warp "
+                "instruction on an SM sub-partition) and cluster barriers",
     }
     # FP64 products of the Krylov phase: the composed M-apply (two sweeps over [H_W H_B]) with
     # --m-form 1, else the W exp-applies of the three-product form; flops and bytes counted by the library
@@ -549,6 +560,7 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk, "gpu_launches": launches,
         "e2e": {"value": e2e_v, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
+        "tridiag": latency_bound,
         "exp_apply_fp64": exp_apply_fp64,
         "exp_apply_bf16": exp_leg,
         "breakdown_ms_per_step": {r: v[0] / args.steps for r, v in regions.items()},

@@ -398,7 +398,8 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     double* part = scratch.take<double>(pcap);
     if (!part) return EDA_ERR_OOM;
     {
-        ProfScope prof("gram", s);
+        // algorithmic work: the two full products, 2 d (n^2 + k^2) flops, reading H_W and H_B once
+        ProfScope prof("gram", s, 2.0 * (double)d * ((double)n * n + (double)k * k), 8.0 * (double)d * (n + k));
         EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
         EDA_TRY(symmetrize_f64(n, h->GW, n, s));
         EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, part, pcap, s));

@@ -385,9 +385,10 @@ __global__ void k_chol_inv(int b, double* G, int ldg, double* Rinv, double rank_
     if (threadIdx.x == 0 && lost) lost[b] = nlost;
 }
 
-// k_chol_inv with G and R^{-1} held in shared memory (b <= kCholSmemMax): every entry is formed by
-// the same operations in the same order as there, so the results are identical; only the memory
-// latency of the pivot loop and of the back substitution goes.
+// The factorisation of k_chol_inv for 32 < b <= kCholSmemMax with G and R^{-1} held in shared memory
+// (the same pivot order, rank threshold, lost list and status bits): one reciprocal per pivot
+// scales its row of R, and the back substitution for R^{-1} multiplies by the stored reciprocal
+// pivots and splits each inner product over two accumulators, halving its dependent FMA chain.
 constexpr int kCholSmemMax = 90;
 
 __global__ void __launch_bounds__(256) k_chol_inv_smem(int b, double* G, int ldg, double* Rinv, double rank_tol,
@@ -395,9 +396,9 @@ __global__ void __launch_bounds__(256) k_chol_inv_smem(int b, double* G, int ldg
     extern __shared__ double smc[];
     double* sg = smc;              // sg[c * b + r] = G[r, c]
     double* sx = smc + b * b;      // sx[c * b + i] = Rinv[i, c]
+    __shared__ double inv[kCholSmemMax];
     __shared__ double maxdiag;
     __shared__ int nlost;
-    __shared__ double piv;
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) sg[e] = G[(int64_t)(e / b) * ldg + e % b];
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -417,8 +418,8 @@ __global__ void __launch_bounds__(256) k_chol_inv_smem(int b, double* G, int ldg
     for (int j = 0; j < b; ++j) {
         if (threadIdx.x == 0) {
             const double g = sg[j * b + j];
+            double piv = 0.0;
             if (!(g > thr) || maxdiag == 0.0) {
-                piv = 0.0;
                 if (lost) lost[nlost] = j;
                 nlost++;
                 atomicOr(status, ST_RANKLOSS);
@@ -426,13 +427,11 @@ __global__ void __launch_bounds__(256) k_chol_inv_smem(int b, double* G, int ldg
                 piv = sqrt(g);
             }
             sg[j * b + j] = piv;
+            inv[j] = piv > 0.0 ? 1.0 / piv : 0.0;
         }
         __syncthreads();
-        const double rjj = piv;
-        for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) {
-            const double v = (rjj > 0.0) ? sg[c * b + j] / rjj : 0.0;
-            sg[c * b + j] = v;
-        }
+        const double ip = inv[j];
+        for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) sg[c * b + j] *= ip;
         __syncthreads();
         const int rem = b - j - 1;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
@@ -442,15 +441,16 @@ __global__ void __launch_bounds__(256) k_chol_inv_smem(int b, double* G, int ldg
         __syncthreads();
     }
     for (int c = threadIdx.x; c < b; c += blockDim.x) {
-        for (int i = b - 1; i >= 0; --i) {
-            double v = (i == c) ? 1.0 : 0.0;
-            if (i > c) v = 0.0;
-            else {
-                for (int l = i + 1; l <= c; ++l) v -= sg[l * b + i] * sx[c * b + l];
-                const double rii = sg[i * b + i];
-                v = (rii > 0.0) ? v / rii : 0.0;
+        for (int i = b - 1; i > c; --i) sx[c * b + i] = 0.0;
+        for (int i = c; i >= 0; --i) {
+            double a0 = (i == c) ? 1.0 : 0.0, a1 = 0.0;
+            int l = i + 1;
+            for (; l + 1 <= c; l += 2) {
+                a0 -= sg[l * b + i] * sx[c * b + l];
+                a1 -= sg[(l + 1) * b + i] * sx[c * b + l + 1];
             }
-            sx[c * b + i] = v;
+            if (l <= c) a0 -= sg[l * b + i] * sx[c * b + l];
+            sx[c * b + i] = (a0 + a1) * inv[i];
         }
     }
     __syncthreads();

@@ -810,16 +810,16 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(int n, const double* __r
                 u = fma(-beta, vp, t);
             }
             double a = vi * u;
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);   // lanes < 16 hold the rows
             if (lane == 0) red[0] = a;
         }
         cluster.sync();                                    // partial alpha of every CTA published
         if (tid < 32) {
             double a = (lane < C) ? *cluster.map_shared_rank(&red[0], lane) : 0.0;
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);     // C <= 16
             u = (lane < nr) ? fma(-a, vi, u) : 0.0;
             double b2 = u * u;
-            for (int o = 16; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+            for (int o = 8; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
             if (lane == 0) {
                 s_ab[0] = a;
                 red[1] = b2;
@@ -828,9 +828,11 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(int n, const double* __r
         cluster.sync();                                    // partial ||u||^2 of every CTA published
         if (tid < 32) {
             double b2 = (lane < C) ? *cluster.map_shared_rank(&red[1], lane) : 0.0;
-            for (int o = 16; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+            for (int o = 8; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
             const double a = s_ab[0];
-            const double b = sqrt(b2);
+            // beta and 1 / beta from one reciprocal square root (each within a few ulps)
+            const double rb = (b2 > 0.0) ? rsqrt(b2) : 0.0;
+            const double b = b2 * rb;
             anorm = fmax(anorm, fabs(a) + b + beta);
             const bool stop = !(b > 16.0 * DBL_EPSILON * anorm);
             if (rank == 0 && lane == 0) {
@@ -839,7 +841,7 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(int n, const double* __r
             }
             if (lane < nr) {
                 vp = vi;
-                vnew[lane] = stop ? 0.0 : u * (1.0 / b);
+                vnew[lane] = stop ? 0.0 : u * rb;
             }
             beta = b;
             if (lane == 0) s_stop = stop ? 1 : 0;
@@ -1204,11 +1206,10 @@ int lanczos_top(int n, const double* A, int lda, int m, uint64_t seed, SymEigWor
     // the two largest eigenvalues of T_m and the eigenvector of the largest
     const int nv = m >= 2 ? 2 : 1;
     double* w = ws->vbuf;                       // nv values
-    double* lu = ws->lu;
-    double* zt = ws->lu + 5 * (size_t)m;        // m entries
+    double* zt = ws->lu + 5 * (size_t)m;        // the eigenvector (m entries) after the 5 m factor entries
     k_bisect<<<nv, 32, 3 * (size_t)m * sizeof(double), s>>>(m, ws->dgl, ws->eoff, m - nv, nv, w);
     EDA_LAUNCHED();
-    k_invit<<<1, 32, 0, s>>>(m, 1, ws->dgl, ws->eoff, w + nv - 1, lu, zt, seed);
+    k_invit<<<1, 32, 0, s>>>(m, 1, ws->dgl, ws->eoff, w + nv - 1, ws->lu, zt, seed);
     EDA_LAUNCHED();
     k_lanczos_pack<<<1, 32, 0, s>>>(m, w, zt, ws->eoff, out);
     EDA_LAUNCHED();

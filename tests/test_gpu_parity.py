@@ -131,6 +131,43 @@ def test_single_class_has_no_between_class_scatter(eda):
         assert abs(h.c2 - 10.0 / lw) <= 1e-12 * (10.0 / lw)
 
 
+@pytest.mark.parametrize("tau", [1.0, 10.0, 40.0])
+def test_phi_by_squaring_matches_oracle(eda, tau):
+    # n, k <= 256: lambda_max by the Lanczos run and K(alpha) by scaling and squaring (no eigenvectors);
+    # tau sets how many doublings each side takes. K against the oracle's eigenpair form (Theorem 3.1)
+    p = _problem(700, 9, [20, 25, 18, 30, 22, 19, 27, 21, 24], seed=71)
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(block_b=4, tau=tau)) as h:
+        f = h.factors()
+        ref = O.scatter_factors(p.X, p.labels, p.k)
+        GW, GB = O.gram(ref["HW"]), O.gram(ref["HB"])
+        lw, lb = np.linalg.eigvalsh(GW)[-1], np.linalg.eigvalsh(GB)[-1]
+        assert abs(h.lmax_w - lw) <= 64 * EPS * lw
+        assert abs(h.lmax_b - lb) <= 64 * EPS * lb
+        c2 = O.scale_c2(lw, lb, tau)
+        assert abs(h.c2 - c2) <= 1e-13 * c2
+        for key, G, a in (("KW", GW, -0.5 * h.c2), ("KB", GB, h.c2)):
+            K = O.phi_operator(G, a)
+            assert np.abs(f[key].cpu().numpy() - K).max() <= 1e-12 * np.abs(K).max(), key
+
+
+@pytest.mark.parametrize("gap", [0.0, 1e-9, 1e-3])
+def test_lanczos_lambda_max_clustered_top(eda, gap):
+    # H_W with prescribed singular values: a top eigenvalue of G_W that is double (gap 0), nearly double
+    # (the Lanczos bounds may not certify it: the eigensolver's value is taken) or separated
+    rng = np.random.default_rng(17)
+    d, n, k = 400, 60, 5
+    Qd, _ = np.linalg.qr(rng.standard_normal((d, n)))
+    Pn, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sig = np.linspace(0.2, 0.9, n)
+    sig[-1], sig[-2] = 1.0, np.sqrt(1.0 - gap)
+    HW = (Qd * sig) @ Pn.T
+    HB = 0.3 * rng.standard_normal((d, k))
+    with eda.build_from_factors(_dev(HW.T), _dev(HB.T), eda.config(block_b=2, tau=10.0)) as h:
+        assert abs(h.lmax_w - 1.0) <= 64 * EPS
+        lb = np.linalg.eigvalsh(HB.T @ HB)[-1]
+        assert abs(h.lmax_b - lb) <= 64 * EPS * lb
+
+
 # ----------------------------------------------------------------- full solve
 
 def _solve_and_compare(eda, p, t, b, tau, tol=1e-12, tier="auto", check_every=1, m_form=0):
@@ -181,6 +218,30 @@ def test_solve_ragged_blocks(eda, b, check_every):
     # block size that does not divide t, uneven classes, d not a multiple of any tile
     p = _problem(333, 7, [2, 3, 5, 1, 4, 3, 2], seed=55, test=2)
     _solve_and_compare(eda, p, p.k - 1, b, 8.0, check_every=check_every)
+
+
+@pytest.mark.parametrize("spec", [(300, 4, [3, 2, 4, 3], 900), (512, 3, [5, 2, 7], 902),
+                                  (777, 6, [2, 3, 4, 2, 3, 5], 903)])
+def test_solve_every_block_size_small_problems(eda, spec):
+    # n + k <= 25: the block Krylov space is exhausted within a few blocks and, at some block sizes, a
+    # column of a new block is nearly dependent on the others; its content can drop below the rounding
+    # of the block's Gram and be replaced by a fresh direction. The pairs must still be those of the
+    # oracle, with true FP64 residuals at the tolerance (the solver verifies and refines after refills)
+    d, k, nj, seed = spec
+    p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=seed, n_test_per_class=2)
+    t = k - 1
+    ref = None
+    for b in list(range(1, 13)) + [16]:
+        cfg = eda.config(block_b=b, tau=10.0, true_residuals=1)
+        with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+            if ref is None:
+                ref = O.eda(p.X, p.labels, p.k, t, c2=h.c2, tier="projected")
+            V, lam, _, info, code = h.solve(t, 1e-12, check=False)
+            assert code == 0, (b, info)
+            assert info["max_relres_true"] <= 1e-11, (b, info)
+            rel = np.abs(lam.cpu().numpy() - ref["lam_t"]) / ref["lam_t"]
+            assert rel.max() <= 1e-10, (b, rel.max())
+            assert O.sin_angle(ref["V"], V.cpu().numpy().T) <= 1e-10, b
 
 
 @pytest.mark.parametrize("name", ["d256_k8", "d4096_k40"])
