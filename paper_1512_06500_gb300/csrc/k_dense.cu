@@ -530,8 +530,27 @@ int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, cons
     T* partial = static_cast<T*>(partial_buf);
     const int TP = p <= 8 ? 8 : (p <= 16 ? 16 : 32);
     const int tiles = ceil_div(m, TN_TM) * ceil_div(p, TP);
-    int splits = std::max(1, ceil_div(2 * 152, tiles));
-    splits = std::min<int64_t>(splits, std::max<int64_t>(1, (d + 63) / 64));
+    // Split count: the kernel is FP64- or bandwidth-bound per SM, so an SM holding one CTA more than
+    // the others sets the time. Among counts giving 1.8 to 4 CTAs per SM (after rounding the split
+    // rows to TN_KB), take the one that fills the 152 SMs most evenly, tiles * splits over
+    // 152 * ceil(tiles * splits / 152), preferring fewer splits unless another fills 2 % better.
+    int splits = 1;
+    {
+        const int smax = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(4 * 152, tiles), (d + 63) / 64));
+        const int smin = std::min(smax, std::max(1, (int)std::ceil(1.8 * 152 / tiles)));
+        double best = -1.0;
+        for (int s0 = smin; s0 <= smax; ++s0) {
+            int64_t rw = (d + s0 - 1) / s0;
+            rw = (rw + TN_KB - 1) / TN_KB * TN_KB;
+            const int sc = (int)std::max<int64_t>(1, (d + rw - 1) / rw);
+            const int64_t ctas = (int64_t)tiles * sc;
+            const double fill = (double)ctas / (152.0 * (double)((ctas + 151) / 152));
+            if (fill > best + 0.02) {
+                best = fill;
+                splits = sc;
+            }
+        }
+    }
     while (splits > 1 && (size_t)splits * m * p > partial_cap) --splits;
     if ((size_t)splits * m * p > partial_cap) return EDA_ERR_INVALID_ARG;
     int64_t rows = (d + splits - 1) / splits;

@@ -988,8 +988,10 @@ int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_
     static std::mutex mu;
     std::unique_lock<std::mutex> lk(mu);
     if (!chosen_C[n]) {
+        // about 12 or more columns per CTA: fewer FP64 instructions per warp and column step (each
+        // holds a sub-partition's FP64 pipe for ~64 cycles) outweigh the wider cluster barrier
         int want = 2;
-        if (n > 64) {
+        if (n > 32) {
             want = 1;
             while (want < 16 && want * 2 * 12 <= n) want *= 2;
         }
