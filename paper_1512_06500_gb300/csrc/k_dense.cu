@@ -36,21 +36,44 @@ __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m
 #pragma unroll
         for (int b = 0; b < TPT; ++b) acc[a][b] = T(0);
 
-    for (int64_t r0 = r_begin; r0 < r_end; r0 += TN_KB) {
-        // stage A rows r0..r0+KB of columns i0..i0+TM (coalesced along rows)
-        for (int e = threadIdx.x; e < TN_KB * TN_TM; e += TN_THREADS) {
+    // the next chunk of rows is read into registers while the current one is multiplied, so the
+    // global-memory latency overlaps the FP64 work (the products and their order are unchanged)
+    constexpr int PA = TN_KB * TN_TM / TN_THREADS;                  // A elements per thread and chunk
+    constexpr int PB = (TN_KB * TP + TN_THREADS - 1) / TN_THREADS;  // B elements per thread and chunk
+    T ra[PA], rb[PB];
+    auto fetch = [&](int64_t r0) {
+#pragma unroll
+        for (int q = 0; q < PA; ++q) {
+            const int e = threadIdx.x + q * TN_THREADS;
             const int rr = e % TN_KB, cc = e / TN_KB;
             const int64_t r = r0 + rr;
             const int c = i0 + cc;
-            As[rr][cc] = (r < r_end && c < m) ? A[(int64_t)c * lda + r] : T(0);
+            ra[q] = (r < r_end && c < m) ? A[(int64_t)c * lda + r] : T(0);
         }
-        for (int e = threadIdx.x; e < TN_KB * TP; e += TN_THREADS) {
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int e = threadIdx.x + q * TN_THREADS;
             const int rr = e % TN_KB, cc = e / TN_KB;
             const int64_t r = r0 + rr;
             const int c = j0 + cc;
-            Bs[rr][cc] = (r < r_end && c < p) ? B[(int64_t)c * ldb + r] : T(0);
+            rb[q] = (e < TN_KB * TP && r < r_end && c < p) ? B[(int64_t)c * ldb + r] : T(0);
+        }
+    };
+    if (r_begin < r_end) fetch(r_begin);
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += TN_KB) {
+        // stage A rows r0..r0+KB of columns i0..i0+TM and the matching rows of B
+#pragma unroll
+        for (int q = 0; q < PA; ++q) {
+            const int e = threadIdx.x + q * TN_THREADS;
+            As[e % TN_KB][e / TN_KB] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int e = threadIdx.x + q * TN_THREADS;
+            if (e < TN_KB * TP) Bs[e % TN_KB][e / TN_KB] = rb[q];
         }
         __syncthreads();
+        if (r0 + TN_KB < r_end) fetch(r0 + TN_KB);
 #pragma unroll 8
         for (int rr = 0; rr < TN_KB; ++rr) {
             T av[TMT], bv[TPT];
@@ -148,14 +171,27 @@ __global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double
         const int q = (lc + 3) / 4;
         const int lb = w * q, le = min(lc, lb + q);
         int l = lb;
-        for (; l + 3 < le; l += 4) {
-            T a[4];
+        // groups of four rows of A, the next group read while the current one is multiplied
+        T a[4];
+        if (l + 3 < le) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) a[u] = live ? Ar[(int64_t)(l0 + l + u) * lda] : T(0);
+        }
+        for (; l + 3 < le; l += 4) {
+            T an[4];
+            const bool more = l + 7 < le;
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) an[u] = live ? Ar[(int64_t)(l0 + l + 4 + u) * lda] : T(0);
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) acc[c] = fma(a[u], Bs[l + u][c], acc[c]);
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = an[u];
+            }
         }
         for (; l < le; ++l) {
             const T a0 = live ? Ar[(int64_t)(l0 + l) * lda] : T(0);
