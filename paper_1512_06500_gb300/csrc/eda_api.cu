@@ -131,6 +131,14 @@ int alloc_handle(eda_ctx* h, bool with_labels) {
     add(symeig_work_bytes((int)std::min(n, k), (int)std::min(n, k)));
     add(std::max<size_t>(1u << 16, std::min(n, k) * std::min(n, k)) * 8);
     add(3 * std::min(n, k) * std::min(n, k) * 8 + 256);
+    // the Lanczos / scaling-and-squaring build of small Grams: partials of the second stream, the two
+    // Lanczos workspaces and results, the squaring work of both Grams
+    add(std::max<size_t>(1u << 17, 64 * k * k) * 8);
+    add(symeig_work_bytes((int)n, 1));
+    add(symeig_work_bytes((int)k, 1));
+    add(8 * 8);
+    add(6 * n * n * 8);
+    add(6 * k * k * 8);
     add(4096);
     h->block_bytes = bytes + 4096;
     void* p = nullptr;
@@ -317,8 +325,8 @@ double lmax_certified(const double* o) {
 }
 
 // lambda_max of G_W and G_B without their eigenvectors: one Lanczos run per Gram, side by side on two
-// streams, one host wait for both; a Gram whose bound does not certify its estimate falls back to
-// the full eigensolver's largest eigenvalue.
+// streams (aux is already forked from s and holds the G_B product), one host wait for both; a Gram
+// whose bound does not certify its estimate falls back to the full eigensolver's largest eigenvalue.
 int gram_lmax_pair(eda_ctx* h, Arena& scratch, AuxStream& aux, cudaStream_t s) {
     const int n = (int)h->n, k = h->k;
     SymEigWork wsW{}, wsB{};
@@ -326,7 +334,6 @@ int gram_lmax_pair(eda_ctx* h, Arena& scratch, AuxStream& aux, cudaStream_t s) {
     EDA_TRY(symeig_work_carve(scratch, k, 1, h->bar, &wsB));
     double* out = scratch.take<double>(8);
     if (!out) return EDA_ERR_OOM;
-    EDA_TRY(aux.fork());
     EDA_TRY(lanczos_top(n, h->GW, n, std::min(n, kLanczosSteps), h->cfg.seed, &wsW, out, s));
     EDA_TRY(lanczos_top(k, h->GB, k, std::min(k, kLanczosSteps), h->cfg.seed, &wsB, out + 4, aux.aux));
     EDA_TRY(aux.join());
@@ -397,24 +404,44 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     const size_t pcap = std::max<size_t>(1u << 19, N * N);
     double* part = scratch.take<double>(pcap);
     if (!part) return EDA_ERR_OOM;
-    {
-        // algorithmic work: the two full products, 2 d (n^2 + k^2) flops, reading H_W and H_B once
-        ProfScope prof("gram", s, 2.0 * (double)d * ((double)n * n + (double)k * k), 8.0 * (double)d * (n + k));
-        EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
-        EDA_TRY(symmetrize_f64(n, h->GW, n, s));
-        EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, part, pcap, s));
-        EDA_TRY(symmetrize_f64(k, h->GB, k, s));
-    }
-    EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
-    EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));
-    const size_t mark = scratch.used;
-    int nsw = 0, nsb = 0, first_w = 0, first_b = 0;
     // Small Grams: lambda_max by Lanczos and K by scaling and squaring (dense products that fill the
     // GPU) instead of the eigensolver's sequential column steps; the eigenpairs follow on request.
+    // The B half (G_B, its Lanczos run, its K, the cross Gram) runs on a second stream beside the W half.
     const bool by_squaring = n <= kLanczosMaxN && k <= kLanczosMaxN;
+    const bool cross = h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16 || h->cfg.m_form == 1;
     AuxStream aux;
+    double* partB = nullptr;
+    size_t pcapB = 0;
     if (by_squaring) {
         EDA_TRY(aux.open(s));
+        pcapB = std::max<size_t>(1u << 17, 64 * (size_t)k * k);
+        partB = scratch.take<double>(pcapB);
+        if (!partB) return EDA_ERR_OOM;
+        EDA_TRY(aux.fork());
+        {
+            // algorithmic work of G_W: 2 d n^2 flops, reading H_W once
+            ProfScope prof("gram", s, 2.0 * (double)d * n * n, 8.0 * (double)d * n);
+            EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
+            EDA_TRY(symmetrize_f64(n, h->GW, n, s));
+        }
+        EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, partB, pcapB, aux.aux));
+        EDA_TRY(symmetrize_f64(k, h->GB, k, aux.aux));
+        EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
+        EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, aux.aux));
+    } else {
+        {
+            ProfScope prof("gram", s, 2.0 * (double)d * ((double)n * n + (double)k * k), 8.0 * (double)d * (n + k));
+            EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
+            EDA_TRY(symmetrize_f64(n, h->GW, n, s));
+            EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, part, pcap, s));
+            EDA_TRY(symmetrize_f64(k, h->GB, k, s));
+        }
+        EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
+        EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));
+    }
+    const size_t mark = scratch.used;
+    int nsw = 0, nsb = 0, first_w = 0, first_b = 0;
+    if (by_squaring) {
         EDA_TRY(gram_lmax_pair(h, scratch, aux, s));
     } else if (n <= kEigClusterMaxN && k <= kEigClusterMaxN) {
         // both on the cluster path (no grid barrier): solve side by side
@@ -446,6 +473,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
             EDA_TRY(aux.fork());
             EDA_TRY(phi_by_squaring(n, h->GW, -0.5 * h->c2, h->lmax_w, h->KW, workW, s));
             EDA_TRY(phi_by_squaring(k, h->GB, h->c2, h->lmax_b, h->KB, workB, aux.aux));
+            if (cross) EDA_TRY(ensure_cross_gram(h, partB, pcapB, aux.aux));
             EDA_TRY(aux.join());
         }
         scratch.used = mark;
@@ -455,8 +483,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
         EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
     }
-    if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16 || h->cfg.m_form == 1)
-        EDA_TRY(ensure_cross_gram(h, part, pcap, s));
+    if (cross && !by_squaring) EDA_TRY(ensure_cross_gram(h, part, pcap, s));
     if (h->cfg.prec == EDA_BF16) {
         // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
         // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)

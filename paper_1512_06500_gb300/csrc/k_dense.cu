@@ -140,17 +140,17 @@ __global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const T* __restr
 }
 
 // C[r, c] = beta * C0[r, c] + alpha * sum_l A[r, l] B[l, c] for tall A (d x m) and small B
-// (m x p). A CTA owns 32 rows and NC columns; its four warps (one per SM sub-partition, each of
-// which has its own narrow FP64 unit) split the inner dimension into quarters, each thread
-// keeps NC independent accumulators, the slice of B sits in shared memory, and the partial sums
-// of the quarters are added in a fixed order at the end.
+// (m x p). A CTA owns 32 rows and NC columns; its eight warps (two per SM sub-partition, so that
+// one issues FP64 work while the other waits on a load) split the inner dimension into eighths,
+// each thread keeps NC independent accumulators, the slice of B sits in shared memory, and the
+// partial sums of the eighths are added in a fixed pairwise order at the end.
 template <int NC, class T>
-__global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double alpha, const T* __restrict__ A,
+__global__ void __launch_bounds__(256) k_gemm_nn(int64_t d, int m, int p, double alpha, const T* __restrict__ A,
                                                  int64_t lda, const double* __restrict__ B, int ldb, double beta,
                                                  const T* C0, int64_t ldc0, T* C, int64_t ldc) {
     constexpr int LCH = 256;                 // rows of B staged per pass
     __shared__ T Bs[LCH][NC];
-    __shared__ T red[3][32][NC];
+    __shared__ T red[7][32][NC];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t r = (int64_t)blockIdx.x * 32 + lane;
     const int c0 = blockIdx.y * NC;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double
             Bs[l][c] = (c < nc) ? (T)B[(int64_t)(c0 + c) * ldb + l0 + l] : T(0);
         }
         __syncthreads();
-        const int q = (lc + 3) / 4;
+        const int q = (lc + 7) / 8;
         const int lb = w * q, le = min(lc, lb + q);
         int l = lb;
         // groups of four rows of A, the next group read while the current one is multiplied
@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(128) k_gemm_nn(int64_t d, int m, int p, double
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         if (c >= nc) break;
-        const T sum = (acc[c] + red[0][lane][c]) + (red[1][lane][c] + red[2][lane][c]);
+        const T sum = ((acc[c] + red[0][lane][c]) + (red[1][lane][c] + red[2][lane][c])) +
+                      ((red[3][lane][c] + red[4][lane][c]) + (red[5][lane][c] + red[6][lane][c]));
         T v = (T)alpha * sum;
         if (beta != 0.0) v = fma((T)beta, C0[(int64_t)(c0 + c) * ldc0 + r], v);
         C[(int64_t)(c0 + c) * ldc + r] = v;
@@ -617,13 +618,13 @@ int gemm_nn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, cons
     const int rowblocks = ceil_div(d, 32);
     // columns per thread: as many as possible while at least ~one CTA per SM stays busy
     if (p >= 6 && (int64_t)rowblocks * ceil_div(p, 8) >= 120) {
-        k_gemm_nn<8, T><<<dim3(rowblocks, ceil_div(p, 8)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<8, T><<<dim3(rowblocks, ceil_div(p, 8)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     } else if (p >= 3 && (int64_t)rowblocks * ceil_div(p, 4) >= 120) {
-        k_gemm_nn<4, T><<<dim3(rowblocks, ceil_div(p, 4)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<4, T><<<dim3(rowblocks, ceil_div(p, 4)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     } else if (p >= 2) {
-        k_gemm_nn<2, T><<<dim3(rowblocks, ceil_div(p, 2)), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<2, T><<<dim3(rowblocks, ceil_div(p, 2)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     } else {
-        k_gemm_nn<1, T><<<dim3(rowblocks, p), 128, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<1, T><<<dim3(rowblocks, p), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
     }
     EDA_LAUNCHED();
     return EDA_OK;
