@@ -99,14 +99,18 @@ typedef struct eda_ctx* eda_handle;
 int eda_config_default(eda_config* cfg);
 
 /* Build a handle from labelled samples (Section 1; Algorithm 2 step 1 with the
- * Gram/eigen form of steps 2-4).
+ * Gram form of steps 2-4).
  *   X       : d x n samples, x_dtype EDA_F64 or EDA_F32, leading dimension ldx >= d.
  *   labels  : n int32 class ids in [0, k).
  * Steps on the device: stable class segmentation; centroids mu_j, mu in a
  * fixed order (bit-exact FP64); H_W (d x n, class-major columns, input order
  * within a class) and H_B (d x k, columns sqrt(n_j)(mu_j - mu)); Gram
- * matrices G_W = H_W^T H_W, G_B = H_B^T H_B in FP64; their symmetric
- * eigendecompositions; c^2; and K(alpha) for alpha = -c^2/2 (W) and +c^2 (B).
+ * matrices G_W = H_W^T H_W, G_B = H_B^T H_B in FP64; their largest eigenvalues
+ * and c^2 (the scale of the samples' spread, A1: c^2 = tau / max lambda_max); and
+ * K(alpha) = alpha phi(alpha G) for alpha = -c^2/2 (W) and +c^2 (B) (Theorem 3.1). When n and
+ * k are at most 256, lambda_max comes from a Lanczos run whose error bound is checked (the
+ * symmetric eigensolver when the bound fails) and K from G by scaling and squaring; beyond,
+ * both come from the Grams' symmetric eigendecompositions.
  * Errors: INVALID_ARG (d < 1, n < 2, k < 1, k > n, ldx < d), BAD_LABELS,
  * NONFINITE (X has NaN/Inf), OOM, CUDA. *out is set only on EDA_OK.
  * X and labels are read only during the call (stream-ordered). */
@@ -125,7 +129,9 @@ int eda_build_from_factors(const double* HW, int64_t n, const double* HB, int64_
  * dimension ldx. io_dtype EDA_F64 uses the FP64 factors (any handle, any alpha);
  * io_dtype EDA_F32 uses the handle's working precision (prec EDA_F32: single-
  * precision sweeps; prec EDA_BF16: bf16 H on the tensor cores) and accepts only the
- * stored alphas (-c^2/2 for SW, c^2 for SB). X and Y must not overlap. */
+ * stored alphas (-c^2/2 for SW, c^2 for SB). X and Y must not overlap. An FP64 alpha other
+ * than the stored one needs the Gram's eigenpairs: the first such call computes them
+ * (symmetric eigensolver, with host synchronisation) if the build did not. */
 int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y,
                   int64_t ldx, int32_t b, int32_t io_dtype, void* stream);
 
@@ -199,7 +205,9 @@ int eda_solve_batched(eda_problem* probs, int32_t nprob, const eda_config* cfg, 
 
 /* Copy out build results into caller device buffers (any pointer may be NULL):
  * HW d x n, HB d x k, counts k, perm n, GW n x n, GB k x k, KW n x n
- * (alpha = -c^2/2), KB k x k (alpha = c^2), evals_w n, evals_b k (ascending). */
+ * (alpha = -c^2/2), KB k x k (alpha = c^2), evals_w n, evals_b k (ascending). The
+ * eigenvalues are computed by the first call that asks for them when the build did not
+ * need them (symmetric eigensolver on the stream, with host synchronisation). */
 int eda_get_factors(eda_handle h, double* HW, double* HB, int32_t* counts, int32_t* perm,
                     double* GW, double* GB, double* KW, double* KB, double* evals_w,
                     double* evals_b, void* stream);
