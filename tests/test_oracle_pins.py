@@ -156,6 +156,22 @@ def test_phi_and_phi_operator_series():
         assert np.abs(O.phi_operator(G, alpha) - ser).max() < 1e-14 * max(1.0, np.abs(ser).max())
 
 
+def test_phi_operator_doubling_identity():
+    """K(alpha) = alpha phi(alpha G) (Theorem 3.1) obeys K(2 alpha) = K(alpha) (2 I + G K(alpha)): from
+    phi(2 z) = phi(z) (1 + e^z) / 2 and e^(alpha G) = I + G K(alpha). A slip in phi (a dropped 1/z,
+    e^z for expm1), in the clamping of tiny eigenvalues or in the scaling by alpha breaks it."""
+    rng = np.random.default_rng(23)
+    for m, r in ((7, 7), (12, 5)):                       # full rank and rank deficient (null space)
+        H = rng.standard_normal((30, r)) @ rng.standard_normal((r, m))
+        G = H.T @ H
+        G /= np.linalg.eigvalsh(G)[-1]
+        for alpha in (0.3, -0.5, 2.0, -4.0):
+            K1 = O.phi_operator(G, alpha)
+            K2 = O.phi_operator(G, 2 * alpha)
+            rhs = K1 @ (2 * np.eye(m) + G @ K1)
+            assert np.abs(K2 - rhs).max() <= 1e-13 * np.abs(K2).max(), (m, alpha)
+
+
 # ---------------------------------------------------------------- Section 3.1
 
 @pytest.mark.parametrize("alpha", [1.0, -0.5, -1.0])
