@@ -403,11 +403,30 @@ __device__ __forceinline__ void sturm_count2_f64(int n, const double* d, const d
     }
 }
 
-// One warp per wanted eigenvalue (ascending index il + warp id). The tridiagonal is scaled by
-// 1 / ||T||; 33-way multisection first on single-precision counts (fast) until the interval is
-// 1e-5 wide, then, after widening it by that margin (far above the single-precision backward
-// error of the count, about 1e-6), on double-precision counts down to ~eps.
-__global__ void __launch_bounds__(32) k_bisect(int n, const double* __restrict__ dgl, const double* __restrict__ eoff,
+// One chain of sturm_count2_f64: the same operations in the same order, so the same count.
+__device__ __forceinline__ int sturm_count1_f64(int n, const double* d, const double* e2, double x0) {
+    double pm0 = 1.0;
+    double pc0 = fix_zero(d[0] - x0, 1.0);
+    int c0 = (int)((unsigned)__double2hiint(pc0) >> 31);
+    for (int i = 1; i < n; ++i) {
+        const double di = d[i], ei = e2[i - 1];
+        const double pn0 = fix_zero(fma(di - x0, pc0, -ei * pm0), pc0);
+        c0 += (int)(((unsigned)__double2hiint(pn0) ^ (unsigned)__double2hiint(pc0)) >> 31);
+        pm0 = pc0;
+        pc0 = pn0;
+        if ((i & 3) == 0) rescale_pair(pc0, pm0);
+    }
+    return c0;
+}
+
+// One CTA of two warps per wanted eigenvalue (ascending index il + blockIdx.x). The tridiagonal is
+// scaled by 1 / ||T||; 33-way multisection first on single-precision counts (fast; both warps run it
+// alike) until the interval is 1e-5 wide, then, after widening it by that margin (far above the
+// single-precision backward error of the count, about 1e-6), 65-way multisection on double-precision
+// counts down to ~eps: lane l of warp 0 counts at the shift 2 l + 1 of the 65-way split and lane l of
+// warp 1 at 2 l + 2, so each warp's FP64 chain carries one shift (the FP64 pipe of a sub-partition
+// holds a warp instruction for ~64 cycles, so two warps on two sub-partitions halve the time).
+__global__ void __launch_bounds__(64) k_bisect(int n, const double* __restrict__ dgl, const double* __restrict__ eoff,
                                                 int il, int nw, double* w) {
     extern __shared__ double smb[];
     double* d64 = smb;                                     // n
@@ -415,8 +434,10 @@ __global__ void __launch_bounds__(32) k_bisect(int n, const double* __restrict__
     float* d32 = reinterpret_cast<float*>(smb + 2 * n);    // n
     float* e232 = d32 + n;                                 // n
     __shared__ double s_tnorm;
-    const int lane = threadIdx.x & 31;
-    // ||T||_inf by the CTA
+    __shared__ unsigned s_ball[2];
+    __shared__ int s_cnt[2];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    // ||T||_inf by warp 0
     if (threadIdx.x < 32) {
         double m = 0.0;
         for (int i = lane; i < n; i += 32) {
@@ -437,8 +458,8 @@ __global__ void __launch_bounds__(32) k_bisect(int n, const double* __restrict__
         e232[i] = (float)(ei * ei);
     }
     __syncthreads();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= nw) return;
+    const int gw = blockIdx.x;
+    if (gw >= nw) return;                                   // uniform over the CTA
     const int idx = il + gw;
     // scaled Gershgorin interval is inside [-1, 1]
     float lo = -1.0f - 1e-6f, hi = 1.0f + 1e-6f;
@@ -459,33 +480,38 @@ __global__ void __launch_bounds__(32) k_bisect(int n, const double* __restrict__
         }
     }
     double dlo = (double)lo - 1e-5, dhi = (double)hi + 1e-5;
-    // confirm the bracket in double precision; fall back to the full interval if it fails
+    // confirm the bracket in double precision (warp 0 at dlo, warp 1 at dhi); fall back to the full
+    // interval if it fails
     {
-        int clo = 0, chi = 0;
-        if (lane == 0) sturm_count2_f64(n, d64, e264, dlo, dhi, clo, chi);
-        clo = __shfl_sync(0xffffffffu, clo, 0);
-        chi = __shfl_sync(0xffffffffu, chi, 0);
+        if (lane == 0) s_cnt[wp] = sturm_count1_f64(n, d64, e264, wp == 0 ? dlo : dhi);
+        __syncthreads();
+        const int clo = s_cnt[0], chi = s_cnt[1];
         if (!(clo <= idx && chi > idx)) {
             dlo = -1.0 - 1e-12;
             dhi = 1.0 + 1e-12;
         }
+        __syncthreads();
     }
     for (int round = 0; round < 24; ++round) {
         const double width = dhi - dlo;
         if (width <= 2.0 * DBL_EPSILON * fmax(fabs(dlo), fabs(dhi)) || width <= 0.5 * DBL_EPSILON) break;
         const double step = width / 65.0;
-        const double x0 = dlo + (2 * lane + 1) * step, x1 = dlo + (2 * lane + 2) * step;
-        int c0, c1;
-        sturm_count2_f64(n, d64, e264, x0, x1, c0, c1);
-        const unsigned above = __ballot_sync(0xffffffffu, c0 > idx || c1 > idx);
+        const double x = dlo + (2 * lane + 1 + wp) * step;   // warp 0: shifts 2 l + 1, warp 1: 2 l + 2
+        const int c = sturm_count1_f64(n, d64, e264, x);
+        const unsigned b = __ballot_sync(0xffffffffu, c > idx);
+        if (lane == 0) s_ball[wp] = b;
+        __syncthreads();
+        const unsigned b0 = s_ball[0], b1 = s_ball[1];
+        __syncthreads();
+        const unsigned above = b0 | b1;
         if (above == 0u) {
-            dlo = __shfl_sync(0xffffffffu, x1, 31);
+            dlo = dlo + (2 * 31 + 2) * step;
         } else {
             const int l = __ffs(above) - 1;
-            const bool first = __shfl_sync(0xffffffffu, c0 > idx, l);
-            const double a0 = __shfl_sync(0xffffffffu, x0, l);
-            const double a1 = __shfl_sync(0xffffffffu, x1, l);
-            const double pl = __shfl_sync(0xffffffffu, x1, l > 0 ? l - 1 : 0);
+            const bool first = (b0 >> l) & 1u;
+            const double a0 = dlo + (2 * l + 1) * step;
+            const double a1 = dlo + (2 * l + 2) * step;
+            const double pl = dlo + (2 * (l > 0 ? l - 1 : 0) + 2) * step;
             if (first) {
                 if (l > 0) dlo = pl;
                 dhi = a0;
@@ -495,7 +521,7 @@ __global__ void __launch_bounds__(32) k_bisect(int n, const double* __restrict__
             }
         }
     }
-    if (lane == 0) w[gw] = 0.5 * (dlo + dhi) * tn;
+    if (threadIdx.x == 0) w[gw] = 0.5 * (dlo + dhi) * tn;
 }
 
 __global__ void k_square_off(int n, const double* eoff, double* e2) {
@@ -1076,7 +1102,7 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     {
         ProfScope prof("bisect", s);
         // one warp per CTA: the FP64 pipe of one SM is narrow, so the warps are spread over SMs
-        k_bisect<<<nv, 32, bsm, s>>>(n, ws->dgl, ws->eoff, il, nv, w);
+        k_bisect<<<nv, 64, bsm, s>>>(n, ws->dgl, ws->eoff, il, nv, w);
         EDA_LAUNCHED();
     }
     return EDA_OK;
@@ -1209,7 +1235,7 @@ int lanczos_top(int n, const double* A, int lda, int m, uint64_t seed, SymEigWor
     const int nv = m >= 2 ? 2 : 1;
     double* w = ws->vbuf;                       // nv values
     double* zt = ws->lu + 5 * (size_t)m;        // the eigenvector (m entries) after the 5 m factor entries
-    k_bisect<<<nv, 32, 3 * (size_t)m * sizeof(double), s>>>(m, ws->dgl, ws->eoff, m - nv, nv, w);
+    k_bisect<<<nv, 64, 3 * (size_t)m * sizeof(double), s>>>(m, ws->dgl, ws->eoff, m - nv, nv, w);
     EDA_LAUNCHED();
     k_invit<<<1, 32, 0, s>>>(m, 1, ws->dgl, ws->eoff, w + nv - 1, ws->lu, zt, seed);
     EDA_LAUNCHED();
