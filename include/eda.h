@@ -83,7 +83,7 @@ typedef struct {
     int32_t basis_cols;          /* final basis width m                                      */
     int32_t refills;             /* rank-deficient columns replaced by fresh random vectors  */
     int32_t checks;              /* Rayleigh-Ritz checks performed                            */
-    int32_t refine_iters;        /* FP64 refinement iterations (mixed precision only)         */
+    int32_t refine_iters;        /* FP64 refinement rounds: mixed precision, or FP64 after refills */
     int32_t reserved0;
     double c2, lmax_w, lmax_b;   /* scale and the two largest Gram eigenvalues               */
     double max_relres_est;       /* max_i ||B_{m+1} S_{m,i}|| / theta_i over the t pairs      */
@@ -143,7 +143,9 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
  *   Y      : optional d x t output, the orthonormal Ritz vectors y_i of M.
  * tol is the relative residual ||M y - theta y|| <= tol * theta of each of the t
  * pairs (Remark 3.4). Returns EDA_ERR_NOT_CONVERGED (outputs still written)
- * when the basis limit is reached first. */
+ * when the basis limit is reached first. When the Krylov phase replaced lost directions by fresh
+ * ones (refills > 0), the FP64 solver ends with a Rayleigh-Ritz / residual-expansion phase on true
+ * FP64 residuals (refine_iters rounds), as the residual estimate cannot see such losses. */
 int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0,
               double* V, double* lambda, double* Y, eda_solve_info* info, void* stream);
 
