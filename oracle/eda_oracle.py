@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring). Nothing here is tuned;
 each function follows the paper's definitions in the paper's order. Library
 primitives used as single steps: numpy matmul, ``numpy.linalg.eigh`` (a
 symmetric eigendecomposition), ``numpy.linalg.qr`` (Householder QR),
-``numpy.linalg.svd`` and ``numpy.linalg.cholesky``.
+``numpy.linalg.svd``, ``numpy.linalg.cholesky`` and ``numpy.linalg.eig`` (the
+small Hessenberg matrix of the Arnoldi method).
 
 Notation (Section 1, Table 1.1): X = [chi_1 .. chi_n] is d x n, k classes,
 n_j samples in class j, mu_j class centroids, mu the global centroid, t the
@@ -28,6 +29,12 @@ Pins (what each function is checked against, in tests/test_oracle_*.py):
                        form; Theorem 3.3 bounds; Theorem 3.7 unit-eigenvalue
                        count; Cholesky route on d <= 8
   eda_projected ...... equality with eda_dense on d <= 256
+  n_apply ............ the dense product exp(-c^2 S_W) exp(c^2 S_B) X
+  eda_arnoldi ........ eigenvalues and eigenvector span of the symmetric route
+                       (similarity N = E_W^{-1/2} M E_W^{1/2}); commuting
+                       diagonal closed form; all d eigenvalues of the dense N
+                       on d <= 12 (no GPU counterpart yet: the nonsymmetric
+                       form is a next step of the library)
   nn_classify ........ brute force on tiny sets; Theorem 3.8 bound
 None of the functions is "parity unpinned".
 """
@@ -41,7 +48,7 @@ __all__ = [
     "segment", "scatter_factors", "gram", "jacobi_eigh", "expm_taylor", "sym_fun",
     "lowrank_exp_apply", "dense_exp_apply", "phi", "phi_operator", "scale_c2",
     "m_apply", "eda_dense", "eda_projected", "eda", "project", "nn_classify",
-    "sin_angle", "orth", "eda_cholesky_route", "trace_ratio",
+    "sin_angle", "orth", "eda_cholesky_route", "trace_ratio", "n_apply", "eda_arnoldi",
 ]
 
 
@@ -267,6 +274,66 @@ def m_apply(HW, HB, c2, X):
     Y = lowrank_exp_apply(HW, -0.5 * c2, X)
     Y = lowrank_exp_apply(HB, c2, Y)
     return lowrank_exp_apply(HW, -0.5 * c2, Y)
+
+
+def n_apply(HW, HB, c2, X):
+    """w = exp(-c^2 S_W) exp(c^2 S_B) v, the nonsymmetric operator of Eq. (26) (Section 3.1), as the
+    two Theorem 3.1 products of Algorithm 2's Arnoldi branch (steps 6A-10A: exp(c^2 S_B) first, then
+    exp(-c^2 S_W))."""
+    Y = lowrank_exp_apply(HB, c2, X)
+    return lowrank_exp_apply(HW, -c2, Y)
+
+
+def eda_arnoldi(HW, HB, t, c2, tol=1e-10, m_max=None, seed=0):
+    """t dominant eigenpairs of exp(-c^2 S_W) exp(c^2 S_B) x = lambda x (Eq. (26)) by the Arnoldi
+    method (Section 3.1), with no recovery step: the Ritz vectors are the x of Eq. (2.02) directly.
+
+    From a seeded unit start vector v_1: w = N v_j (n_apply), orthogonalised against v_1 .. v_j by
+    modified Gram-Schmidt, applied twice, the coefficients summed into column j of the upper
+    Hessenberg H; h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}. After each step the Ritz pairs
+    (theta, V_j s) come from the eigenpairs of H_j (numpy.linalg.eig), taken by decreasing real part,
+    and the residual of a unit Ritz vector is h_{j+1,j} |e_j^T s| (the Arnoldi relation); the method
+    stops once the t largest have residual <= tol |theta|, or when w vanishes (an invariant
+    subspace). N - I maps into span([H_W, H_B]), so the space is exhausted after at most n + k + 1
+    steps (the default m_max). N is similar to the symmetric M (N = E_W^{-1/2} M E_W^{1/2}), so its
+    eigenvalues are real; the real parts are returned. Returns lam_t (descending), X_t (unit Ritz
+    vectors), V = orth(X_t), the residuals and the number of steps.
+    """
+    d = HW.shape[0]
+    if m_max is None:
+        m_max = min(d, HW.shape[1] + HB.shape[1] + 1)
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(d)
+    Vb = np.zeros((d, m_max + 1))
+    Hh = np.zeros((m_max + 1, m_max))
+    Vb[:, 0] = v / np.linalg.norm(v)
+    best = None
+    for j in range(m_max):
+        w = n_apply(HW, HB, c2, Vb[:, j:j + 1])[:, 0]
+        for _ in range(2):
+            for i in range(j + 1):
+                hij = Vb[:, i] @ w
+                Hh[i, j] += hij
+                w = w - hij * Vb[:, i]
+        hnext = np.linalg.norm(w)
+        m = j + 1
+        theta, S = np.linalg.eig(Hh[:m, :m])
+        order = np.argsort(-theta.real, kind="stable")[: min(t, m)]
+        th = theta[order].real
+        Sm = S[:, order]
+        # a real eigenvector for each (real) Ritz value: remove the phase of its largest entry
+        piv = np.argmax(np.abs(Sm), axis=0)
+        Sm = (Sm * np.exp(-1j * np.angle(Sm[piv, np.arange(Sm.shape[1])]))).real
+        Sm = Sm / np.linalg.norm(Sm, axis=0)
+        res = hnext * np.abs(Sm[m - 1, :])
+        best = (th, Vb[:, :m] @ Sm, res, m)
+        done = m >= t and np.all(res <= tol * np.abs(th))
+        if done or hnext <= 1e-14 * max(1.0, np.abs(Hh[:m, :m]).max()) or m == m_max:
+            break
+        Hh[m, j] = hnext
+        Vb[:, m] = w / hnext
+    th, Xt, res, m = best
+    return dict(lam_t=th, Xt=Xt, V=orth(Xt), relres=res / np.abs(th), steps=m)
 
 
 # --------------------------------------------------------------------------

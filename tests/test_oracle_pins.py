@@ -262,6 +262,70 @@ def test_commuting_diagonal_closed_form():
         assert O.sin_angle(E, sol["V"]) < 1e-12
 
 
+# ---------------------------------------------------------------- Section 3.1, Eq. (26): Arnoldi form
+
+def test_n_apply_matches_dense_product():
+    # N X = exp(-c^2 S_W) exp(c^2 S_B) X by two Theorem 3.1 products against the dense Taylor exponentials
+    p = synth.gaussian_clusters(d=40, k=3, n_per_class=[4, 2, 5], seed=21)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((40, 3))
+    c2 = 0.4
+    dense = O.dense_exp_apply(f["HW"], -c2, O.dense_exp_apply(f["HB"], c2, X))
+    got = O.n_apply(f["HW"], f["HB"], c2, X)
+    assert np.abs(got - dense).max() <= 1e-12 * np.abs(dense).max()
+
+
+@pytest.mark.parametrize("spec", [(90, 4, [5, 3, 6, 4], 12), (150, 6, 3, 13), (64, 2, [7, 1], 14)])
+def test_arnoldi_eda_matches_symmetric_route(spec):
+    # N = E_W^{-1/2} M E_W^{1/2} (Eq. (26) against the symmetric form of Section 3.2): the same
+    # eigenvalues, and x = E_W^{-1/2} y, so the same span of the t eigenvectors
+    d, k, nj, seed = spec
+    p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=seed)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    HW, HB = f["HW"], f["HB"]
+    c2 = O.scale_c2(np.linalg.eigvalsh(O.gram(HW))[-1], np.linalg.eigvalsh(O.gram(HB))[-1], 10.0)
+    t = k - 1
+    ref = O.eda_dense(HW, HB, t, c2)
+    a = O.eda_arnoldi(HW, HB, t, c2)
+    assert np.all(np.abs(a["lam_t"] - ref["lam_t"]) <= 1e-10 * ref["lam_t"])
+    assert O.sin_angle(ref["V"], a["V"]) <= 1e-8
+    assert a["steps"] <= HW.shape[1] + HB.shape[1] + 1
+
+
+def test_arnoldi_eda_commuting_closed_form():
+    # the diagonal factors of test_commuting_diagonal_closed_form: lambda = exp(c^2 (b_i - w_i)), axes
+    d = 12
+    w = np.array([0.5, 2.0, 0.0, 1.0, 3.0])
+    b = np.array([4.0, 1.0, 2.5, 0.0, 0.2])
+    HW = np.zeros((d, 5)); HB = np.zeros((d, 5))
+    for i in range(5):
+        HW[i, i] = math.sqrt(w[i]); HB[i, i] = math.sqrt(b[i])
+    c2 = 0.7
+    t = 2
+    a = O.eda_arnoldi(HW, HB, t, c2, m_max=d)
+    expect = np.sort(np.exp(c2 * (b - w)))[::-1][:t]
+    assert np.allclose(a["lam_t"], expect, rtol=1e-12, atol=0)
+    top = np.argsort(-(b - w))[:t]
+    E = np.zeros((d, t)); E[top, np.arange(t)] = 1.0
+    assert O.sin_angle(E, a["V"]) < 1e-10
+
+
+def test_arnoldi_eda_full_spectrum_tiny():
+    # full-rank factors of a 6-dimensional problem: the Arnoldi method run to m = d returns every
+    # eigenvalue of the dense nonsymmetric N
+    rng = np.random.default_rng(31)
+    d = 6
+    HW = 0.6 * rng.standard_normal((d, d))
+    HB = 0.8 * rng.standard_normal((d, 3))
+    c2 = 0.5
+    N = O.dense_exp_apply(HW, -c2, O.dense_exp_apply(HB, c2, np.eye(d)))
+    ev = np.sort(np.linalg.eigvals(N).real)[::-1]
+    a = O.eda_arnoldi(HW, HB, d, c2, tol=0.0, m_max=d)
+    assert a["steps"] == d
+    assert np.allclose(a["lam_t"], ev, rtol=1e-11, atol=0)
+
+
 def _load_golden(name):
     out = {}
     with open(os.path.join(GOLDEN, name)) as fh:
