@@ -358,8 +358,8 @@ __device__ __forceinline__ int sturm_count_f32(int n, const float* d, const floa
     return cnt;
 }
 
-// The same count in double precision without divisions, for two shifts at once (independent
-// chains hide the FP64 latency): the leading principal minors p_i = det(T_i - x I) obey
+// The same count in double precision without divisions: the leading principal minors
+// p_i = det(T_i - x I) obey
 // p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}, and the number of sign changes along
 // p_0 = 1, p_1, ..., p_n is the number of eigenvalues below x (Sturm). Sign tests use the sign
 // bit (integer pipe); an exact zero takes the sign opposite to its predecessor (a sign change,
@@ -380,30 +380,7 @@ __device__ __forceinline__ void rescale_pair(double& pc, double& pm) {
     }
 }
 
-__device__ __forceinline__ void sturm_count2_f64(int n, const double* d, const double* e2, double x0, double x1,
-                                                 int& c0, int& c1) {
-    double pm0 = 1.0, pm1 = 1.0;
-    double pc0 = fix_zero(d[0] - x0, 1.0), pc1 = fix_zero(d[0] - x1, 1.0);
-    c0 = (int)((unsigned)__double2hiint(pc0) >> 31);
-    c1 = (int)((unsigned)__double2hiint(pc1) >> 31);
-    for (int i = 1; i < n; ++i) {
-        const double di = d[i], ei = e2[i - 1];
-        const double pn0 = fix_zero(fma(di - x0, pc0, -ei * pm0), pc0);
-        const double pn1 = fix_zero(fma(di - x1, pc1, -ei * pm1), pc1);
-        c0 += (int)(((unsigned)__double2hiint(pn0) ^ (unsigned)__double2hiint(pc0)) >> 31);
-        c1 += (int)(((unsigned)__double2hiint(pn1) ^ (unsigned)__double2hiint(pc1)) >> 31);
-        pm0 = pc0;
-        pc0 = pn0;
-        pm1 = pc1;
-        pc1 = pn1;
-        if ((i & 3) == 0) {
-            rescale_pair(pc0, pm0);
-            rescale_pair(pc1, pm1);
-        }
-    }
-}
-
-// One chain of sturm_count2_f64: the same operations in the same order, so the same count.
+// The number of eigenvalues below x0 by that recurrence (one shift per thread).
 __device__ __forceinline__ int sturm_count1_f64(int n, const double* d, const double* e2, double x0) {
     double pm0 = 1.0;
     double pc0 = fix_zero(d[0] - x0, 1.0);
@@ -522,11 +499,6 @@ __global__ void __launch_bounds__(64) k_bisect(int n, const double* __restrict__
         }
     }
     if (threadIdx.x == 0) w[gw] = 0.5 * (dlo + dhi) * tn;
-}
-
-__global__ void k_square_off(int n, const double* eoff, double* e2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) e2[i] = (i + 1 < n) ? eoff[i] * eoff[i] : 0.0;
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
