@@ -1,11 +1,11 @@
 /*
  * eda.h - C ABI of the GB300 (sm_103a) library for exponential discriminant
  * analysis (EDA): the t dominant eigenpairs of the pencil
- *     exp(c^2 S_B) x = lambda exp(c^2 S_W) x                       (Eq. 2.02)
+ *     exp(c^2 S_B) x = lambda exp(c^2 S_W) x                       (Eq. (1.7))
  * solved in the symmetric form M y = lambda y with
- *     M = exp(-c^2 S_W / 2) exp(c^2 S_B) exp(-c^2 S_W / 2)        (Eq. 3.2, eqn315)
+ *     M = exp(-c^2 S_W / 2) exp(c^2 S_B) exp(-c^2 S_W / 2)        (Eqs. (3.13), (3.15))
  * by block Lanczos (Algorithm 3), where S_W = H_W H_W^T and S_B = H_B H_B^T
- * (Eq. eqn1, eqn2) are never formed: every exponential is applied through
+ * (Eqs. (1.1), (1.2)) are never formed: every exponential is applied through
  * Theorem 3.1 as
  *     exp(alpha H H^T) X = X + H K(alpha) (H^T X),
  *     K(alpha) = alpha phi(alpha H^T H),  phi(z) = (e^z - 1) / z.
@@ -70,7 +70,7 @@ typedef struct {
     uint64_t seed;               /* seed of the counter-based start block / refill vectors  */
     int32_t true_residuals;      /* 1: eda_solve also reports true FP64 residuals            */
     int32_t m_form;              /* FP64 M-apply: 0 = the three products of the symmetric     */
-                                 /* form one after another (Eq. 3.20); 1 = their composed     */
+                                 /* form one after another (Eq. (3.16)); 1 = their composed  */
                                  /* form M = I + Z C Z^T, Z = [H_W H_B] (Theorem 3.1 for each  */
                                  /* factor; two sweeps over Z instead of six over H_W, H_B)   */
     int32_t reserved[6];
@@ -138,7 +138,7 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
 /* The t dominant eigenpairs (Algorithm 3, steps 5-6).
  *   V0     : optional d x b0 start block (NULL: seeded counter-based Gaussian block).
  *   V      : d x t output, orthonormal basis of the t generalized eigenvectors
- *            x_i = exp(-c^2 S_W / 2) y_i (Eq. eqn311), orthonormalised.
+ *            x_i = exp(-c^2 S_W / 2) y_i (Eq. (3.14)), orthonormalised.
  *   lambda : t output eigenvalues, descending.
  *   Y      : optional d x t output, the orthonormal Ritz vectors y_i of M.
  * tol is the relative residual ||M y - theta y|| <= tol * theta of each of the t
@@ -161,14 +161,17 @@ int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_
  * loops where cudaMalloc/cudaFree (which may synchronise the device) cannot be used.
  *   H : d x m, K : m x m (for exp(alpha H H^T) pass K = alpha phi(alpha H^T H), e.g. the KW or
  *       KB matrices returned by eda_get_factors), X, Y : d x b, all FP64, leading dimension ld
- *       (H uses ld = d). X and Y must not overlap.
+ *       (H uses ld = d). Y must not overlap X, H or K (EDA_ERR_INVALID_ARG otherwise).
  * Temporaries live in one fixed 4 MiB device array inside the library (held on every GPU that
  * loads it until the process exits): m * b must not exceed 174762 (2^19 / 3 doubles), larger
  * sizes return EDA_ERR_INVALID_ARG before any device work. The first call on a device looks up
  * that array's device address with the device current; make that first call before any stream
- * capture. All calls share the array, so calls whose work overlaps on the GPU (different
- * streams, or other host threads) race and must be serialised by the caller. Nothing carries
- * over between calls: every scratch value read is written earlier in the same call. */
+ * capture. The address is kept together with the identity of the device's context and looked up
+ * again when that context changes (after cudaDeviceReset the module, and with it the array, is
+ * loaded anew; the next call on that device is again a first call). All calls share the array,
+ * so calls whose work overlaps on the GPU (different streams, or other host threads) race and
+ * must be serialised by the caller. Nothing carries over between calls: every scratch value
+ * read is written earlier in the same call. */
 int eda_lowrank_exp_apply_noalloc(const double* H, int64_t d, int32_t m, const double* K,
                                   const double* X, double* Y, int64_t ld, int32_t b, void* stream);
 

@@ -88,7 +88,7 @@ def segment(labels, k):
 
 
 def scatter_factors(X, labels, k):
-    """H_W (d x n) and H_B (d x k) of Eq. (eqn1) and Eq. (eqn2).
+    """H_W (d x n) and H_B (d x k) of Eqs. (1.1) and (1.2).
 
     mu_j = (sum of the class-j samples, added one by one in input order) / n_j
     mu   = (sum of all samples, added one by one in input order) / n
@@ -122,7 +122,7 @@ def scatter_factors(X, labels, k):
 
 
 def gram(H):
-    """G = H^T H, the small Gram matrix whose spectrum is D = Sigma^2 of Eq. (3.11)-(3.13)."""
+    """G = H^T H, the small Gram matrix whose spectrum is D = Sigma^2 of Eqs. (3.4)-(3.6)."""
     return H.T @ H
 
 
@@ -217,7 +217,7 @@ def phi(z):
 def phi_operator(G, alpha):
     """K(alpha) = alpha * phi(alpha G) for a symmetric PSD Gram G.
 
-    With H = Q~ Sigma V^T (Eq. (3.10)-(3.13)) and G = H^T H = V Sigma^2 V^T,
+    With H = Q~ Sigma V^T (Eqs. (3.3)-(3.6)) and G = H^T H = V Sigma^2 V^T,
     Theorem 3.1 gives exp(alpha H H^T) = I + H K(alpha) H^T. Eigenvalues of G
     that round below zero are clamped to 0.
     """
@@ -270,14 +270,14 @@ def scale_c2(lmax_w, lmax_b, tau):
 
 
 def m_apply(HW, HB, c2, X):
-    """w = M v for M of Eq. (eqn315), as the three products (iii)-(v) of Eq. (320)."""
+    """w = M v for M of Eq. (3.15), as the three products (iii)-(v) of Eq. (3.16)."""
     Y = lowrank_exp_apply(HW, -0.5 * c2, X)
     Y = lowrank_exp_apply(HB, c2, Y)
     return lowrank_exp_apply(HW, -0.5 * c2, Y)
 
 
 def n_apply(HW, HB, c2, X):
-    """w = exp(-c^2 S_W) exp(c^2 S_B) v, the nonsymmetric operator of Eq. (26) (Section 3.1), as the
+    """w = exp(-c^2 S_W) exp(c^2 S_B) v, the nonsymmetric operator of Eq. (3.1) (Section 3.1), as the
     two Theorem 3.1 products of Algorithm 2's Arnoldi branch (steps 6A-10A: exp(c^2 S_B) first, then
     exp(-c^2 S_W))."""
     Y = lowrank_exp_apply(HB, c2, X)
@@ -285,8 +285,8 @@ def n_apply(HW, HB, c2, X):
 
 
 def eda_arnoldi(HW, HB, t, c2, tol=1e-10, m_max=None, seed=0):
-    """t dominant eigenpairs of exp(-c^2 S_W) exp(c^2 S_B) x = lambda x (Eq. (26)) by the Arnoldi
-    method (Section 3.1), with no recovery step: the Ritz vectors are the x of Eq. (2.02) directly.
+    """t dominant eigenpairs of exp(-c^2 S_W) exp(c^2 S_B) x = lambda x (Eq. (3.1)) by the Arnoldi
+    method (Section 3.1), with no recovery step: the Ritz vectors are the x of Eq. (1.7) directly.
 
     From a seeded unit start vector v_1: w = N v_j (n_apply), orthogonalised against v_1 .. v_j by
     modified Gram-Schmidt, applied twice, the coefficients summed into column j of the upper
@@ -349,9 +349,9 @@ def orth(Xt):
 def _solve_small(SW, SB, t, c2, route):
     """Steps shared by both tiers on (small or full) symmetric S_W, S_B.
 
-    E_W^{-1/2} = exp(-c^2 S_W / 2) (Eq. (318)), E_B = exp(c^2 S_B) (Eq. (317)),
-    M = E_W^{-1/2} E_B E_W^{-1/2} (Eq. (eqn315)); the t largest eigenpairs
-    (lambda, y) of M (Eq. (3.2)), x = E_W^{-1/2} y (Eq. (eqn311)).
+    E_W^{-1/2} = exp(-c^2 S_W / 2) (Eq. (3.11)), E_B = exp(c^2 S_B) (Eq. (3.9)),
+    M = E_W^{-1/2} E_B E_W^{-1/2} (Eq. (3.15)); the t largest eigenpairs
+    (lambda, y) of M (Eq. (3.13)), x = E_W^{-1/2} y (Eq. (3.14)).
     """
     EWmh = sym_fun(c2 * SW, lambda w: np.exp(-0.5 * w), route=route)
     EB = sym_fun(c2 * SB, np.exp, route=route)
@@ -369,9 +369,9 @@ def _solve_small(SW, SB, t, c2, route):
 
 
 def eda_dense(HW, HB, t, c2, route="eigh"):
-    """Tier A: the dense EDA of Algorithm 1 in the symmetric form of Eq. (3.2).
+    """Tier A: the dense EDA of Algorithm 1 in the symmetric form of Eq. (3.13).
 
-    Forms S_W = H_W H_W^T and S_B = H_B H_B^T (Eq. (eqn1), (eqn2)) as d x d
+    Forms S_W = H_W H_W^T and S_B = H_B H_B^T (Eqs. (1.1), (1.2)) as d x d
     matrices. Returns lam (all d eigenvalues of M, descending), Y_t, X_t and
     V = orth(X_t).
     """
@@ -425,7 +425,7 @@ def eda(X, labels, k, t, tau=None, c2=None, tier="auto"):
 
 
 def eda_cholesky_route(HW, HB, t, c2):
-    """Second route for the pencil (exp(c^2 S_B), exp(c^2 S_W)) of Eq. (2.02) (small d only).
+    """Second route for the pencil (exp(c^2 S_B), exp(c^2 S_W)) of Eq. (1.7) (small d only).
 
     E_W = L L^T (Cholesky); the eigenvalues of L^{-1} E_B L^{-T} are those of the
     pencil. The exponentials come from the Taylor route, not from an
@@ -445,7 +445,7 @@ def eda_cholesky_route(HW, HB, t, c2):
 
 
 def trace_ratio(V, HW, HB, c2):
-    """rho(V) = tr((V^T exp(c^2 S_W) V)^{-1} (V^T exp(c^2 S_B) V)), Eq. (2.01), small d only."""
+    """rho(V) = tr((V^T exp(c^2 S_W) V)^{-1} (V^T exp(c^2 S_B) V)), Eq. (1.6), small d only."""
     EW = sym_fun(c2 * (HW @ HW.T), np.exp)
     EB = sym_fun(c2 * (HB @ HB.T), np.exp)
     return float(np.trace(np.linalg.solve(V.T @ EW @ V, V.T @ EB @ V)))

@@ -1,4 +1,4 @@
-// Build step: class segmentation, centroids and the scatter factors H_W, H_B (Eq. eqn1, eqn2),
+// Build step: class segmentation, centroids and the scatter factors H_W, H_B (Eqs. (1.1), (1.2)),
 // finite checks, and the small operator K(alpha) = alpha phi(alpha G) of Theorem 3.1.
 #include "eda_internal.cuh"
 

@@ -1,5 +1,5 @@
 // FP64 symmetric eigensolver for the small matrices of the method: the Gram matrices
-// G = H^T H (the spectra D = Sigma^2 of Eq. 3.11-3.13) and the block-tridiagonal Lanczos
+// G = H^T H (the spectra D = Sigma^2 of Eqs. (3.4)-(3.6)) and the block-tridiagonal Lanczos
 // matrix T of the Rayleigh-Ritz step.
 //
 // Route: Householder reduction to tridiagonal form (one cooperative launch, rows owned

@@ -1,7 +1,7 @@
 // Block Lanczos for the t dominant eigenpairs of M (Algorithm 3, step 5, Lanczos form) with
 // full CGS2 reorthogonalisation, CholQR2 block normalisation, Rayleigh-Ritz on the block
 // tridiagonal T and the residual test of Remark 3.4; then recovery x = exp(-c^2 S_W / 2) y
-// (Eq. eqn311) and orthonormalisation (Algorithm 3, step 6).
+// (Eq. (3.14)) and orthonormalisation (Algorithm 3, step 6).
 //
 // M - I has rank at most n - 1 (Theorem 3.1: it maps into span[H_W, H_B]), so the block Krylov
 // space is exhausted after about (n - 1) / b + 1 blocks. With the basis sized to n + k + b
@@ -150,7 +150,7 @@ template <> struct HStore<float> {
 int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY, int64_t ldm, double* PQ,
                      double* U, double* ZtY, double* part, size_t pcap, cudaStream_t s);
 
-// Y = M X = E_W^{-1/2} E_B E_W^{-1/2} X, the three products (iii)-(v) of Eq. (320); in FP64 with
+// Y = M X = E_W^{-1/2} E_B E_W^{-1/2} X, the three products (iii)-(v) of Eq. (3.16); in FP64 with
 // m_form = 1 (and allow_composed) their composed form instead. P and Q hold (n + k) x b doubles.
 template <class T>
 int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* tmp, double* P, double* Q,
@@ -340,7 +340,7 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
 
 }  // namespace
 
-// M Y in FP64 for p columns through the composed form of the three products of Eq. (3.20): with
+// M Y in FP64 for p columns through the composed form of the three products of Eq. (3.16): with
 // Theorem 3.1 for each factor and the Grams G_W, G_WB = H_W^T H_B, only two sweeps over
 // Z = [H_W H_B] remain:
 //     [p; q] = Z^T y

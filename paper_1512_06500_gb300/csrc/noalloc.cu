@@ -16,32 +16,81 @@ namespace {
 constexpr size_t kNoAllocScratchDoubles = size_t(1) << 19;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
-// Device address of the scratch array, looked up once per device. In host code the array's
-// name is only a host-side stand-in and must never be handed to a kernel.
+// Device address of the scratch array, looked up with the device current and kept per device
+// together with the identity of the context it was looked up in. In host code the array's name
+// is only a host-side stand-in and must never be handed to a kernel. A device reset (or a
+// primary context released and created again) reloads the module, and the array may then sit
+// at another address: the lookup is repeated whenever the current context is not the one the
+// cached address belongs to.
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;   // 0: nothing cached
+    double* addr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identity of the calling thread's current context (0 when there is none or the driver does not
+// offer context identities, in which case nothing is cached and every call looks the address up).
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 int scratch_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
-        eda::note_cuda_error(e);
+        eda::note_cuda_error(e, __FILE__, __LINE__);
         return EDA_ERR_CUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) return EDA_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // with device `dev` current
-        if (e != cudaSuccess || p == nullptr) {
-            eda::note_cuda_error(e);
-            return EDA_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = static_cast<double*>(p);
+    ScratchSlot& slot = g_scratch[dev];
+    const unsigned long long id = current_ctx_id();
+    if (id != 0 && slot.ctx_id == id && slot.addr) {
+        *out = slot.addr;
+        return EDA_OK;
     }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // with device `dev` current
+    if (e != cudaSuccess || p == nullptr) {
+        eda::note_cuda_error(e, __FILE__, __LINE__);
+        return EDA_ERR_CUDA;
+    }
+    slot.addr = static_cast<double*>(p);
+    slot.ctx_id = current_ctx_id();   // the lookup has made the device's primary context current
+    *out = slot.addr;
     return EDA_OK;
+}
+
+// True when the byte ranges [a, a + na) and [b, b + nb) intersect.
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    return pa < pb + nb && pb < pa + na;
 }
 
 }  // namespace
@@ -52,10 +101,12 @@ extern "C" int eda_lowrank_exp_apply_noalloc(const double* H, int64_t d, int32_t
     const size_t mb = (size_t)m * (size_t)b;
     // P and Q take m*b doubles each; the partial sums need at least one more m*b slice.
     if (mb > kNoAllocScratchDoubles / 3) return EDA_ERR_INVALID_ARG;
-    const char* xb = reinterpret_cast<const char*>(X);
-    const char* yb = reinterpret_cast<const char*>(Y);
-    const size_t span = ((size_t)(b - 1) * ld + d) * sizeof(double);
-    if (xb < yb + span && yb < xb + span) return EDA_ERR_INVALID_ARG;
+    // Y is written while X, H and K are still being read (by other CTAs, and K after sweep 1):
+    // it may overlap none of them.
+    const size_t yspan = ((size_t)(b - 1) * ld + d) * sizeof(double);
+    if (overlaps(Y, yspan, X, yspan) || overlaps(Y, yspan, H, (size_t)d * m * sizeof(double)) ||
+        overlaps(Y, yspan, K, (size_t)m * m * sizeof(double)))
+        return EDA_ERR_INVALID_ARG;
     double* scratch = nullptr;
     if (int rc = scratch_address(&scratch)) return rc;
     double* P = scratch;

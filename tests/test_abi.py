@@ -126,3 +126,21 @@ def test_library_has_no_undefined_internal_symbols(lib):
     out = subprocess.run(["nm", "-D", "--undefined-only", path], capture_output=True, text=True, check=True).stdout
     undefined = [line.split()[-1] for line in out.splitlines() if "_ZN3eda" in line or " eda_" in line]
     assert not undefined, undefined
+
+
+def test_noalloc_rejects_overlaps_and_oversize_before_device_work(lib):
+    """The no-allocation product checks its arguments on the host, before any CUDA call: Y may overlap
+    none of X, H, K (it is written while they are still read), and m * b is bounded by the fixed
+    scratch. The pointers here are never dereferenced."""
+    L, _ = lib
+    fn = L.eda_lowrank_exp_apply_noalloc
+    d, m, b = 1000, 10, 4
+    H, K, X, Y = 1 << 20, 1 << 24, 1 << 28, 1 << 32          # disjoint address ranges
+    P = ctypes.c_void_p
+    # Y inside H, inside K, inside X
+    assert fn(P(H), d, m, P(K), P(X), P(H + 8 * 64), d, b, None) == -1
+    assert fn(P(H), d, m, P(K), P(X), P(K), d, b, None) == -1
+    assert fn(P(H), d, m, P(K), P(X), P(X + 8), d, b, None) == -1
+    # m * b above the scratch (2^19 / 3 doubles), and ld < d
+    assert fn(P(H), d, 2000, P(K), P(X), P(Y), d, 100, None) == -1
+    assert fn(P(H), d, m, P(K), P(X), P(Y), d - 1, b, None) == -1

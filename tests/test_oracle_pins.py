@@ -262,7 +262,7 @@ def test_commuting_diagonal_closed_form():
         assert O.sin_angle(E, sol["V"]) < 1e-12
 
 
-# ---------------------------------------------------------------- Section 3.1, Eq. (26): Arnoldi form
+# ---------------------------------------------------------------- Section 3.1, Eq. (3.1): Arnoldi form
 
 def test_n_apply_matches_dense_product():
     # N X = exp(-c^2 S_W) exp(c^2 S_B) X by two Theorem 3.1 products against the dense Taylor exponentials
@@ -278,7 +278,7 @@ def test_n_apply_matches_dense_product():
 
 @pytest.mark.parametrize("spec", [(90, 4, [5, 3, 6, 4], 12), (150, 6, 3, 13), (64, 2, [7, 1], 14)])
 def test_arnoldi_eda_matches_symmetric_route(spec):
-    # N = E_W^{-1/2} M E_W^{1/2} (Eq. (26) against the symmetric form of Section 3.2): the same
+    # N = E_W^{-1/2} M E_W^{1/2} (Eq. (3.1) against the symmetric form of Section 3.2): the same
     # eigenvalues, and x = E_W^{-1/2} y, so the same span of the t eigenvectors
     d, k, nj, seed = spec
     p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=seed)
@@ -444,6 +444,134 @@ def test_tier_a_equals_tier_b(d):
     b = O.eda_projected(f["HW"], f["HB"], t, c2)
     assert np.allclose(a["lam"], b["lam"], rtol=1e-11, atol=0)
     assert O.sin_angle(a["V"], b["V"]) < 1e-9
+
+
+def _gap_bound(lam_all, t, lam1):
+    """The subspace tolerance of two FP64 routes: eps lambda_1 over the gap lambda_t - lambda_{t+1}
+    (lambda_{t+1} = 1, Theorem 3.7), times a safety factor for the d-dimensional products."""
+    gap = lam_all[t - 1] - lam_all[t]
+    return 1e3 * np.finfo(float).eps * lam1 / gap
+
+
+@pytest.mark.parametrize("d,k,nj", [(1024, 20, 5), (4096, 40, 5)])
+def test_tier_a_equals_tier_b_large(d, k, nj):
+    # the projected route (tier B) carries every GPU parity check at d >= 4096; here it is held to the
+    # dense definition (tier A: d x d scatter matrices, their exponentials and M formed explicitly) at
+    # the benchmark's d = 4096 and at 1024, on the benchmark's kind of problem (t = k - 1)
+    p, f, c2 = _random_problem(d, k, nj, seed=d + 1, tau=10.0)
+    t = k - 1
+    a = O.eda_dense(f["HW"], f["HB"], t, c2)
+    b = O.eda_projected(f["HW"], f["HB"], t, c2)
+    rel = np.abs(a["lam_t"] - b["lam_t"]) / b["lam_t"]
+    assert rel.max() <= 1e-12, rel.max()
+    # every eigenvalue of M, not only the wanted ones: d - (n + k) ones and the n + k of the projection
+    assert np.abs(a["lam"] - b["lam"]).max() <= 1e-12 * b["lam"][0]
+    assert O.sin_angle(a["V"], b["V"]) <= _gap_bound(b["lam"], t, b["lam"][0])
+
+
+@pytest.mark.parametrize("d", [64, 96])
+def test_jacobi_route_equals_eigh_route(d):
+    # the oracle's default symmetric eigen route (LAPACK eigh) against its own cyclic Jacobi sweeps,
+    # through the whole dense solve (three eigendecompositions: E_W^{-1/2}, E_B and M)
+    p, f, c2 = _random_problem(d, 6, 4, seed=40 + d, tau=10.0)
+    t = 5
+    a = O.eda_dense(f["HW"], f["HB"], t, c2, route="jacobi")
+    b = O.eda_dense(f["HW"], f["HB"], t, c2, route="eigh")
+    assert np.abs(a["lam"] - b["lam"]).max() <= 1e-12 * b["lam"][0]
+    assert O.sin_angle(a["V"], b["V"]) <= _gap_bound(b["lam"], t, b["lam"][0])
+
+
+def test_scale_c2_hand_values():
+    # c^2 = tau / max(lambda_max(G_W), lambda_max(G_B)) (reading A1), by hand
+    assert O.scale_c2(4.0, 2.5, 10.0) == 2.5
+    assert O.scale_c2(1.0, 8.0, 20.0) == 2.5
+    assert O.scale_c2(0.0, 5.0, 10.0) == 2.0
+    with pytest.raises(ValueError):
+        O.scale_c2(0.0, 0.0, 10.0)
+
+
+@pytest.mark.parametrize("w_max,b_max", [(1.0, 4.0), (4.0, 1.0)])
+def test_scale_c2_sets_theorem_3_3_bound(w_max, b_max):
+    # Commuting factors on disjoint coordinates: S_W = diag(w) on the first axes, S_B = diag(b) on the
+    # next ones. Then M = exp(c^2 S_B) exp(-c^2 S_W) is diagonal and lambda_1(M) = e^{c^2 max b}
+    # (Theorem 3.3 with nu_d = 0: lambda_1 <= e^{c^2 mu_1}, attained here). With the scale rule,
+    # c^2 max(w_max, b_max) = tau, so lambda_1 = e^tau exactly when the between-class Gram dominates
+    # and e^{tau b_max / w_max} below it otherwise. Using min instead of max, or tau * lambda_max,
+    # changes lambda_1 by orders of magnitude.
+    d, tau = 16, 6.0
+    w = np.array([w_max, 0.5, 0.25])
+    b = np.array([b_max, 0.75, 0.1])
+    HW = np.zeros((d, 3))
+    HB = np.zeros((d, 3))
+    for i in range(3):
+        HW[i, i] = np.sqrt(w[i])
+        HB[3 + i, i] = np.sqrt(b[i])
+    lw = np.linalg.eigvalsh(O.gram(HW))[-1]
+    lb = np.linalg.eigvalsh(O.gram(HB))[-1]
+    c2 = O.scale_c2(lw, lb, tau)
+    sol = O.eda_dense(HW, HB, 2, c2)
+    expect = math.exp(tau * b_max / max(w_max, b_max))
+    assert abs(sol["lam"][0] - expect) <= 1e-12 * expect
+    assert sol["lam"][0] <= math.exp(tau) * (1 + 1e-12)
+
+
+def test_scale_c2_example_1_1_tight():
+    # n_j = 1 (Example 1.1): H_W = 0, so lambda_max(G_W) = 0, c^2 = tau / lambda_max(G_B) and the top
+    # eigenvalue of M is e^{c^2 lambda_max(G_B)} = e^tau exactly
+    rng = np.random.default_rng(41)
+    d, k, tau = 24, 5, 7.0
+    X = rng.standard_normal((k, d))
+    lab = np.arange(k, dtype=np.int32)
+    sol = O.eda(X, lab, k, k - 1, tau=tau, tier="dense")
+    assert sol["lmax_w"] == 0.0
+    assert abs(sol["lam"][0] - math.exp(tau)) <= 1e-12 * math.exp(tau)
+
+
+def _angle_pair(rng, d, theta):
+    """Orthonormal V, Vt (d x t) whose principal angles are exactly theta: V = Q_1 R_1 and
+    Vt = (Q_1 diag(cos theta) + Q_2 diag(sin theta)) R_2 with [Q_1 Q_2] orthonormal and R_1, R_2
+    random rotations (so V^T Vt is not symmetric)."""
+    t = len(theta)
+    Q, _ = np.linalg.qr(rng.standard_normal((d, 2 * t)))
+    R1, _ = np.linalg.qr(rng.standard_normal((t, t)))
+    R2, _ = np.linalg.qr(rng.standard_normal((t, t)))
+    V = Q[:, :t] @ R1
+    Vt = (Q[:, :t] * np.cos(theta) + Q[:, t:] * np.sin(theta)) @ R2
+    return V, Vt
+
+
+def test_sin_angle_known_principal_angles():
+    # Theorem 3.8 measures the subspace error by the sine of the largest principal angle,
+    # ||(I - V V^T) Vt||_2. On a pair with prescribed angles it must return max sin(theta_i).
+    rng = np.random.default_rng(42)
+    theta = np.array([1e-9, 1e-5, 0.3, 1.3, 0.8])
+    V, Vt = _angle_pair(rng, 40, theta)
+    expect = np.sin(theta).max()
+    assert abs(O.sin_angle(V, Vt) - expect) <= 1e-15
+    assert abs(O.sin_angle(Vt, V) - expect) <= 1e-15        # symmetric in its arguments
+    # tiny angles, which 1 - cos cannot resolve: the direct formula keeps them
+    theta = np.array([1e-12, 3e-10, 2e-9])
+    V, Vt = _angle_pair(rng, 30, theta)
+    assert abs(O.sin_angle(V, Vt) - np.sin(2e-9)) <= 1e-6 * 2e-9
+    # the same span in another basis: angle 0
+    V, _ = _angle_pair(rng, 30, np.zeros(4))
+    R, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    assert O.sin_angle(V, V @ R) <= 1e-15
+
+
+def test_sin_angle_pin_rejects_plausible_slips():
+    # mistakes planted in copies of the oracle's formula (on the CPU): the prescribed-angle pin above
+    # rejects each of them by far
+    rng = np.random.default_rng(43)
+    theta = np.array([0.05, 0.2, 0.6])
+    V, Vt = _angle_pair(rng, 25, theta)
+    expect = np.sin(theta).max()
+    transposed = float(np.linalg.norm(Vt - V @ (Vt.T @ V), 2))          # (V^T Vt)^T in place of V^T Vt
+    frobenius = float(np.linalg.norm(Vt - V @ (V.T @ Vt)))              # Frobenius in place of the 2-norm
+    cosines = float(np.sqrt(max(0.0, 1 - np.linalg.svd(V.T @ Vt, compute_uv=False).max() ** 2)))  # smallest angle
+    for wrong in (transposed, frobenius, cosines):
+        assert abs(wrong - expect) > 1e-2, wrong
+    assert abs(O.sin_angle(V, Vt) - expect) <= 1e-15
 
 
 def test_scale_invariance():
