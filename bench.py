@@ -1,8 +1,10 @@
 """Benchmark: one EDA pass (build, block-Lanczos solve to rel-res 1e-6, recovery, projection).
 
-A step is the whole hot path on one synthetic problem shaped like a 64x64 face set with 40
-classes of 5 images (d = 4096, n = 200, t = 39, block size 8), inputs resident in HBM. The L2
-cache is flushed (a 256 MB write) before every step, outside the timed events.
+A step is the whole hot path on one synthetic problem shaped like the largest face workload that fits
+one GPU: 256x256 images, 200 classes of 10 images (d = 65536, n = 2000, t = 199, block size 32,
+tau = 20), plain FP64, inputs resident in HBM (1.05 GB of samples: larger than the 129 MB L2, which is
+also flushed by a 256 MB write before every step, outside the timed events). The d = 4096, k = 40
+workload (64x64 images) is timed beside it under "small_config".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--workload NAME]
 
@@ -29,9 +31,11 @@ from paper_1512_06500_gb300 import synth  # noqa: E402
 
 METRIC = "EDA solve time to t Ritz pairs @rel-res 1e-6; exp-apply GB/s vs HBM peak"
 NOMINAL_FP64_TFLOPS = 1.25          # GB300 FP64 (non-tensor), profiling recipe
-# DRAM bytes (read + write) of the G_W Gram launch of one d4096_k40 build from one ncu capture
-# (profiles/gram_gemm_d4096_k40.md): H_W is read once, the product stays in L2
-GRAM_TRAFFIC_BYTES = 6565120
+HEADLINE = "d65536_k200"
+SMALL = "d4096_k40"
+# DRAM bytes (read + write) of one launch of the Gram SYRK kernel, k_gemm_tn_partial<32, double, SYRK>,
+# per workload, from ncu captures (profiles/); None until captured for the current kernel
+GRAM_TRAFFIC_BYTES = {}
 FALLBACK_HBM_GBS = 6800.0           # profiling recipe fallback when no measured peaks exist
 FALLBACK_BF16_TFLOPS = 1900.0
 
@@ -39,10 +43,11 @@ FALLBACK_BF16_TFLOPS = 1900.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="d4096_k40", choices=list(synth.CONFIGS) + ["batched64"])
+    ap.add_argument("--workload", default=HEADLINE, choices=list(synth.CONFIGS) + ["batched64"])
+    ap.add_argument("--small-steps", type=int, default=20, help="steps of the d4096_k40 leg (0: skip it)")
     ap.add_argument("--workers", type=int, default=32, help="host workers of the batched solve")
     ap.add_argument("--m-form", type=int, default=1, choices=[0, 1],
                     help="FP64 M-apply: 0 = the three products one after another, 1 = their composed form")
@@ -53,6 +58,9 @@ def parse():
     ap.add_argument("--profile-exp-apply", default=None, metavar="D,K,NJ,B",
                     help="profiling driver: build a bf16 handle on a d x (K*NJ) Gaussian-cluster problem "
                          "and run three W exp-applies of width B, nothing else")
+    ap.add_argument("--profile-build", default=None, metavar="WORKLOAD",
+                    help="profiling driver: one FP64 build of the named workload (its first split-K launch is "
+                         "the Gram SYRK G_W = H_W^T H_W), nothing else")
     return ap.parse_args()
 
 
@@ -117,18 +125,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload_config(args):
-    if args.workload == "batched64":
+def workload_config(args, name=None):
+    name = name or args.workload
+    if name == "batched64":
         return {"workload": "batched64: 64 independent problems, d in {1024, 4096, 16384}, k ~ U[10, 100], "
                             f"n_j ~ U[3, 10] per class, t = k - 1, tau = {synth.BATCHED['tau']}, tol={args.tol}",
                 "l2": "flushed (256 MB write) before every step",
                 "precision": "plain FP64 sweeps and small steps; block size tuned per problem shape",
                 "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form],
                 "workers": args.workers}
-    c = synth.CONFIGS[args.workload]
-    return {"workload": f"{args.workload}: d={c['d']}, k={c['k']}, n_j={c['n_j']} (n={c['k'] * c['n_j']}), "
+    c = synth.CONFIGS[name]
+    return {"workload": f"{name}: d={c['d']}, k={c['k']}, n_j={c['n_j']} (n={c['k'] * c['n_j']}), "
                         f"t={c['t']}, b={c['b']}, tau={c['tau']}, tol={args.tol}",
-            "l2": "flushed (256 MB write) before every step",
+            "l2": "flushed (256 MB write) before every step; the samples (d n 8 bytes) are read from HBM",
             "precision": "plain FP64 sweeps and small steps",
             "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form]}
 
@@ -406,35 +415,34 @@ def run_gpu_batched(args, rank, world, local_rank):
     return line, ps
 
 
-def run_gpu(args, rank, world, local_rank):
+def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e=True):
+    """W untimed and K timed steps of one workload (build, solve, recovery, projection of the held-out
+    set) with CUDA events on the launching stream, the L2 flushed before every step; optional end-to-end
+    steps from pinned host buffers. Returns the per-step ms (max over ranks), the region timers read
+    inside the timed region, the solve infos, the launch count and the end-to-end figures."""
     import torch
-    from paper_1512_06500_gb300 import build_lib, eda
+    from paper_1512_06500_gb300 import eda
 
-    build_lib.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    c = synth.CONFIGS[args.workload]
-    p = rank_problem(args.workload, rank)
+    c = synth.CONFIGS[name]
+    p = rank_problem(name, rank)
     X = torch.from_numpy(p.X).to(dev)
     lab = torch.from_numpy(p.labels).to(dev)
     Xt = torch.from_numpy(p.Xtest).to(dev)
-    cfg = eda.config(block_b=c["b"], tau=c["tau"], check_every=1, m_form=args.m_form)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    cfg = eda.config(block_b=c["b"], tau=c["tau"], check_every=1, m_form=m_form)
     stream = torch.cuda.current_stream()
 
     def step():
         h = eda.build(X, lab, p.k, cfg)
-        V, lam, _, info, code = h.solve(c["t"], args.tol)
-        P = h.project(V, Xt)
+        V, lam, _, info, code = h.solve(c["t"], tol)
+        h.project(V, Xt)
         h.close()
         if code != 0:
-            raise RuntimeError(f"solve did not converge: {info}")
+            raise RuntimeError(f"{name}: solve did not converge: {info}")
         return info
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -442,13 +450,13 @@ def run_gpu(args, rank, world, local_rank):
     eda.profile_reset()
     eda.profile_enable(True)
     launches0 = eda.kernel_launches()
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     wall0 = time.perf_counter()
     infos = []
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
         infos.append(step())
@@ -460,77 +468,40 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     eda.profile_enable(False)
     launches = eda.kernel_launches() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    ms = max_over_ranks(ms, dev)
-
-    # ---- rooflines measured inside the timed region (library event pairs + its own work counts) ----
-    regions = {r: eda.profile_read(r) for r in ("exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
-                                                  "tridiag", "bisect", "invit", "backtransform", "symeig", "gram",
-                                                  "lanczos", "phi_squaring", "rr", "reorth", "refine")}
-    pk = peaks()
-    # dominant kernel of the step (ncu launch list): k_gemm_tn_partial<32, double>, whose largest launch
-    # is the FP64 Gram G_W = H_W^T H_W of the build (2 d n^2 flops, timed as the library's "gram" region;
-    # G_B runs beside it on a second stream); FP64-ALU bound
-    g_ms, g_calls = regions["gram"]
-    g_flops, _ = eda.profile_work("gram")
-    g_tf = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else float("nan")
-    roofline = {
-        "kernel": "k_gemm_tn_partial<32, double>: FP64 Gram G_W = H_W^T H_W (2 d n^2 flops per build)",
-        "bound": "alu", "achieved": g_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-        "frac": g_tf / NOMINAL_FP64_TFLOPS, "traffic": GRAM_TRAFFIC_BYTES,
-        "peak_source": "nominal FP64 rate of the profiling recipe (own probe measured 1.19 TFLOP/s)",
-        "avg_call_us": g_ms * 1e3 / max(g_calls, 1), "calls": g_calls,
-        "flops_per_step": g_flops / args.steps,
-    }
-    tri_ms, tri_calls = regions["tridiag"]
-    tri_flops, _ = eda.profile_work("tridiag")
-    latency_bound = {
-        "kernel": "k_tridiag_cluster: Householder tridiagonalisation (4/3 n^3 flops) of the Rayleigh-Ritz matrices",
-        "achieved_tflops": tri_flops / (tri_ms / 1e3) / 1e12 if tri_ms > 0 else None,
-        "avg_call_us": tri_ms * 1e3 / max(tri_calls, 1), "calls": tri_calls,
-        "note": "latency-bound: n dependent column steps, each a chain of FP64 instructions (64 cycles per warp "
-                "instruction on an SM sub-partition) and cluster barriers",
-    }
-    # FP64 products of the Krylov phase: the composed M-apply (two sweeps over [H_W H_B]) with
-    # --m-form 1, else the W exp-applies of the three-product form; flops and bytes counted by the library
-    region = "m_apply_composed" if args.m_form == 1 else "exp_apply_w"
-    ew_ms, ew_calls = eda.profile_read(region)
-    ew_flops, ew_bytes = eda.profile_work(region)
-    ew_s = ew_ms / 1e3 if ew_ms > 0 else float("nan")
-    exp_apply_fp64 = {
-        "kernel": ("composed M-apply (FP64): M X = X + Z C Z^T X, Z = [H_W H_B]" if args.m_form == 1
-                   else "exp_apply (H_W, FP64 sweeps): Y = X + H_W K (H_W^T X)"),
-        "bound": "alu",
-        "achieved_tflops": ew_flops / ew_s / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
-        "frac": ew_flops / ew_s / 1e12 / NOMINAL_FP64_TFLOPS,
-        "achieved_gbs": ew_bytes / ew_s / 1e9, "hbm_peak_gbs": pk["hbm"], "hbm_peak_source": pk["source"],
-        "avg_call_us": ew_ms * 1e3 / max(ew_calls, 1), "calls": ew_calls,
-    }
-
-    # ---- end to end through the public API with host buffers ----
-    d = p.d
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dev)
+    regions = {r: eda.profile_read(r) for r in REGIONS}
+    work = {r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "m_apply_composed", "exp_apply_w",
+                                             "tridiag")}
+    out = dict(p=p, c=c, ms=ms, regions=regions, work=work, infos=infos, launches=launches, clocks=clk,
+               wall=wall)
+    if not e2e:
+        return out
+    # end to end through the public API: samples, labels and the held-out set from pinned host memory,
+    # V, lambda and the projected held-out set back to pinned host memory, inside the timed region
     Xh = torch.from_numpy(p.X).pin_memory()
     labh = torch.from_numpy(p.labels).pin_memory()
     Xth = torch.from_numpy(p.Xtest).pin_memory()
-    Vh = torch.empty((c["t"], d), dtype=torch.float64).pin_memory()
+    Vh = torch.empty((c["t"], p.d), dtype=torch.float64).pin_memory()
     lamh = torch.empty(c["t"], dtype=torch.float64).pin_memory()
     Ph = torch.empty((p.Xtest.shape[0], c["t"]), dtype=torch.float64).pin_memory()
+    del X, Xt
 
     def e2e_step():
         Xd = Xh.to(dev, non_blocking=True)
         labd = labh.to(dev, non_blocking=True)
         Xtd = Xth.to(dev, non_blocking=True)
         h = eda.build(Xd, labd, p.k, cfg)
-        V, lam, _, info, code = h.solve(c["t"], args.tol)
+        V, lam, _, info, code = h.solve(c["t"], tol)
         P = h.project(V, Xtd)
         Vh.copy_(V, non_blocking=True)
         lamh.copy_(lam, non_blocking=True)
         Ph.copy_(P, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         h.close()
+        if code != 0:
+            raise RuntimeError(f"{name}: solve did not converge: {info}")
 
-    e2e_steps = max(2, args.steps // 4)
+    e2e_steps = max(2, steps // 4)
     for _ in range(2):
         e2e_step()
     e2e_ms = []
@@ -544,35 +515,148 @@ def run_gpu(args, rank, world, local_rank):
         e2e_ms.append(a.elapsed_time(bb))
     h2d = Xh.numel() * 8 + labh.numel() * 4 + Xth.numel() * 8
     d2h = Vh.numel() * 8 + lamh.numel() * 8 + Ph.numel() * 8
-    e2e_v = sum(e2e_ms) / len(e2e_ms)
-    e2e_v = max_over_ranks(e2e_v, dev)
+    out["e2e"] = {"value": max_over_ranks(sum(e2e_ms) / len(e2e_ms), dev), "unit": "ms",
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    return out
 
+
+REGIONS = ("gram", "tn_f64", "nn_f64", "cluster_orth", "exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
+           "tridiag", "bisect", "invit", "backtransform", "symeig", "lanczos", "phi_squaring", "rr", "reorth",
+           "refine")
+
+
+def rate(flops, ms):
+    return flops / (ms / 1e3) / 1e12 if ms > 0 else float("nan")
+
+
+def roofline_of(name, r, steps):
+    """The step's dominant kernel, k_gemm_tn_partial<32, double> (the split-K A^T B product; largest share of
+    the ncu launch list at d65536_k200 and d4096_k40), on its largest launch: the Gram SYRK
+    G_W = H_W^T H_W of the build, d n (n + 1) flops (one triangle), timed as the library's "gram" region
+    (the SYRK and its split reduction) inside the timed region. FP64-ALU bound: its flops per byte of H_W
+    (n / 8) are far above GB300's FP64 ridge point."""
+    g_ms, g_calls = r["regions"]["gram"]
+    g_flops, g_bytes = r["work"]["gram"]
+    tn_ms, tn_calls = r["regions"]["tn_f64"]
+    tn_flops, _ = r["work"]["tn_f64"]
+    nn_ms, nn_calls = r["regions"]["nn_f64"]
+    nn_flops, _ = r["work"]["nn_f64"]
+    ach = rate(g_flops, g_ms)
+    per_launch_flops = g_flops / max(g_calls, 1)
+    return {
+        "kernel": "k_gemm_tn_partial<32, double, SYRK> + split reduction: FP64 Gram G_W = H_W^T H_W, "
+                  "d n (n + 1) flops per launch",
+        "bound": "alu", "achieved": ach, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+        "frac": ach / NOMINAL_FP64_TFLOPS,
+        "traffic": GRAM_TRAFFIC_BYTES.get(name),
+        "algorithmic_bytes_per_launch": g_bytes / max(g_calls, 1),
+        "flops_per_launch": per_launch_flops, "avg_launch_us": g_ms * 1e3 / max(g_calls, 1), "launches": g_calls,
+        "peak_source": "nominal FP64 (non-tensor) rate of the profiling recipe; MEASURED_PEAKS.json has no FP64 "
+                       "figure (own dependent-chain probe: 1.06-1.19 TFLOP/s attainable)",
+        "all_launches": {
+            "tn_f64": {"kernel": "k_gemm_tn_partial<*, double> (every split-K A^T B product of the step)",
+                       "achieved_tflops": rate(tn_flops, tn_ms), "launches": tn_calls,
+                       "ms_per_step": tn_ms / steps},
+            "nn_f64": {"kernel": "k_gemm_nn<*, double> (every tall A B product of the step)",
+                       "achieved_tflops": rate(nn_flops, nn_ms), "launches": nn_calls,
+                       "ms_per_step": nn_ms / steps},
+        },
+    }
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1512_06500_gb300 import build_lib, eda
+
+    build_lib.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    r = time_workload(args.workload, args.steps, args.warmup, args.m_form, args.tol, dev, flush, rank, world)
+    p, c = r["p"], r["c"]
+    ms = r["ms"]
+    regions = r["regions"]
+    pk = peaks()
+    roofline = roofline_of(args.workload, r, args.steps)
+    tri_ms, tri_calls = regions["tridiag"]
+    tri_flops, _ = r["work"]["tridiag"]
+    latency_bound = {
+        "kernel": "k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the Gram "
+                  "(n > 256) and of the Rayleigh-Ritz matrices",
+        "achieved_tflops": rate(tri_flops, tri_ms) if tri_ms > 0 else None,
+        "avg_call_us": tri_ms * 1e3 / max(tri_calls, 1), "calls": tri_calls,
+        "note": "latency-bound: n dependent column steps, each a chain of FP64 instructions (64 cycles per warp "
+                "instruction on an SM sub-partition) and grid or cluster barriers",
+    }
+    region = "m_apply_composed" if args.m_form == 1 else "exp_apply_w"
+    ew_ms, ew_calls = regions[region]
+    ew_flops, ew_bytes = r["work"][region]
+    ew_s = ew_ms / 1e3 if ew_ms > 0 else float("nan")
+    exp_apply_fp64 = {
+        "kernel": ("composed M-apply (FP64): M X = X + Z C Z^T X, Z = [H_W H_B]" if args.m_form == 1
+                   else "exp_apply (H_W, FP64 sweeps): Y = X + H_W K (H_W^T X)"),
+        "bound": "alu",
+        "achieved_tflops": ew_flops / ew_s / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
+        "frac": ew_flops / ew_s / 1e12 / NOMINAL_FP64_TFLOPS,
+        "achieved_gbs": ew_bytes / ew_s / 1e9, "hbm_peak_gbs": pk["hbm"], "hbm_peak_source": pk["source"],
+        "avg_call_us": ew_ms * 1e3 / max(ew_calls, 1), "calls": ew_calls,
+    }
+    small = None
+    if args.small_steps > 0 and args.workload != SMALL and rank == 0:
+        rs = time_workload(SMALL, args.small_steps, 5, args.m_form, args.tol, dev, flush, rank, 1)
+        small = {"workload": workload_config(args, SMALL)["workload"], "ms_per_step": rs["ms"], "unit": "ms",
+                 "e2e_ms": rs["e2e"]["value"], "gpu_launches_per_step": rs["launches"] / args.small_steps,
+                 "roofline": roofline_of(SMALL, rs, args.small_steps),
+                 "solve_info": {kk: rs["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols",
+                                                                   "refills", "max_relres_est")}}
     exp_leg = None
     if not args.no_exp_apply and rank == 0:
         exp_leg = exp_apply_leg(dev, flush, args.exp_apply_reps)
-
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Gaussian class clusters clipped to [0, 1]; stands in for 64x64 face sets)",
+        "data": ("synthetic (seeded low-rank smooth images plus noise; stands in for 256x256 face sets)"
+                 if c["gen"] == "lowrank" else
+                 "synthetic (seeded Gaussian class clusters clipped to [0, 1]; stands in for face sets)"),
         "config": dict(workload_config(args), solves_per_s=1e3 * world / ms),
-        "clocks": clk, "gpu_launches": launches,
-        "e2e": {"value": e2e_v, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "clocks": r["clocks"], "gpu_launches": r["launches"],
+        "e2e": r["e2e"],
         "roofline": roofline,
         "tridiag": latency_bound,
         "exp_apply_fp64": exp_apply_fp64,
         "exp_apply_bf16": exp_leg,
-        "breakdown_ms_per_step": {r: v[0] / args.steps for r, v in regions.items()},
-        "solve_info": {kk: infos[-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols", "max_relres_est")},
-        "wall_s": wall,
+        "small_config": small,
+        "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in regions.items()},
+        "solve_info": {kk: r["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols", "refills",
+                                                         "refine_iters", "max_relres_est")},
+        "wall_s": r["wall"],
     }
     return line, p, c
+
+
+def profile_build(name):
+    """Small driver for ncu: one FP64 build of the named workload, nothing else."""
+    import torch
+    from paper_1512_06500_gb300 import build_lib, eda
+
+    build_lib.build()
+    c = synth.CONFIGS[name]
+    p = synth.config_problem(name)
+    X = torch.from_numpy(p.X).cuda()
+    lab = torch.from_numpy(p.labels).cuda()
+    h = eda.build(X, lab, p.k, eda.config(block_b=c["b"], tau=c["tau"], m_form=1))
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "profile-build", "workload": name, "c2": h.c2}))
+    h.close()
 
 
 def main():
     args = parse()
     if args.profile_exp_apply:
         profile_exp_apply(args.profile_exp_apply)
+        return
+    if args.profile_build:
+        profile_build(args.profile_build)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

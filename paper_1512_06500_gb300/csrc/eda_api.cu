@@ -419,22 +419,19 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         if (!partB) return EDA_ERR_OOM;
         EDA_TRY(aux.fork());
         {
-            // algorithmic work of G_W: 2 d n^2 flops, reading H_W once
-            ProfScope prof("gram", s, 2.0 * (double)d * n * n, 8.0 * (double)d * n);
-            EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
-            EDA_TRY(symmetrize_f64(n, h->GW, n, s));
+            // algorithmic work of the SYRK G_W = H_W^T H_W: d n (n + 1) flops (one triangle), reading H_W once
+            ProfScope prof("gram", s, (double)d * n * (n + 1.0), 8.0 * (double)d * n);
+            EDA_TRY(syrk_f64(d, n, 1.0, h->HW, d, 0.0, h->GW, n, part, pcap, s));
         }
-        EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, partB, pcapB, aux.aux));
-        EDA_TRY(symmetrize_f64(k, h->GB, k, aux.aux));
+        EDA_TRY(syrk_f64(d, k, 1.0, h->HB, d, 0.0, h->GB, k, partB, pcapB, aux.aux));
         EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
         EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, aux.aux));
     } else {
         {
-            ProfScope prof("gram", s, 2.0 * (double)d * ((double)n * n + (double)k * k), 8.0 * (double)d * (n + k));
-            EDA_TRY(gemm_tn_f64(d, n, n, 1.0, h->HW, d, h->HW, d, 0.0, h->GW, n, part, pcap, s));
-            EDA_TRY(symmetrize_f64(n, h->GW, n, s));
-            EDA_TRY(gemm_tn_f64(d, k, k, 1.0, h->HB, d, h->HB, d, 0.0, h->GB, k, part, pcap, s));
-            EDA_TRY(symmetrize_f64(k, h->GB, k, s));
+            ProfScope prof("gram", s, (double)d * ((double)n * (n + 1.0) + (double)k * (k + 1.0)),
+                           8.0 * (double)d * (n + k));
+            EDA_TRY(syrk_f64(d, n, 1.0, h->HW, d, 0.0, h->GW, n, part, pcap, s));
+            EDA_TRY(syrk_f64(d, k, 1.0, h->HB, d, 0.0, h->GB, k, part, pcap, s));
         }
         EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
         EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));

@@ -94,6 +94,12 @@ struct GridBarrier {
 int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda,
                 const double* B, int64_t ldb, double beta, double* C, int ldc,
                 double* partial, size_t partial_cap, cudaStream_t s);
+// Symmetric C (m x m) = alpha * A^T A (+ beta * C), A: d x m: only the tiles of the lower triangle are
+// computed and each result is written to both triangles (bitwise symmetric).
+int syrk_f64(int64_t d, int m, double alpha, const double* A, int64_t lda, double beta, double* C, int ldc,
+             double* partial, size_t partial_cap, cudaStream_t s);
+// Streaming multiprocessors of the current device (queried once per process).
+int sm_count();
 // C (d x p) = beta * C0 + alpha * A B, A: d x m (lda), B: m x p (ldb); C may equal C0 (same ld).
 int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda,
                 const double* B, int ldb, double beta, const double* C0, int64_t ldc0,
@@ -121,6 +127,9 @@ int col_norms_f64(int64_t rows, int cols, const double* A, int64_t lda, double* 
 template <class T>
 int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const T* B, int64_t ldb, double beta,
             double* C, int ldc, void* partial_buf, size_t partial_cap, cudaStream_t s);
+template <class T>
+int syrk_tn(int64_t d, int m, double alpha, const T* A, int64_t lda, double beta, double* C, int ldc,
+            void* partial_buf, size_t partial_cap, cudaStream_t s);
 template <class T>
 int gemm_nn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const double* B, int ldb, double beta,
             const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s);

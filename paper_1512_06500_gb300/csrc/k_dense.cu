@@ -3,6 +3,8 @@
 #include "eda_internal.cuh"
 
 #include <cmath>
+#include <mutex>
+#include <type_traits>
 
 namespace eda {
 
@@ -12,15 +14,30 @@ constexpr int TN_KB = 32;       // rows of A/B staged per pass
 constexpr int TN_TM = 32;       // output tile rows
 constexpr int TN_THREADS = 256;
 
-// partial[s][j][i] = sum over rows r of split s of A[r, i0+i] * B[r, j0+j]
-template <int TP, class T>
+// Tile (bx, by) with bx >= by of the lower triangle of a T x T tile grid from its index
+// q = bx (bx + 1) / 2 + by (row by row).
+__device__ __forceinline__ void tri_tile(int q, int& bx, int& by) {
+    int x = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
+    while ((x + 1) * (x + 2) / 2 <= q) ++x;
+    while (x * (x + 1) / 2 > q) --x;
+    bx = x;
+    by = q - x * (x + 1) / 2;
+}
+
+// partial[s][j][i] = sum over rows r of split s of A[r, i0+i] * B[r, j0+j]. SYM (A = B, m = p, TP = TN_TM):
+// only the tiles with i0 >= j0 are launched (blockIdx.x runs over the lower triangle of the tile grid);
+// a diagonal tile computes entries (i, j) and (j, i) from the same products in the same order, so it is
+// exactly symmetric.
+template <int TP, class T, bool SYM = false>
 __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m, int p, const T* __restrict__ A,
                                                                 int64_t lda, const T* __restrict__ B, int64_t ldb,
                                                                 int64_t rows_per_split, T* __restrict__ partial) {
     __shared__ T As[TN_KB][TN_TM + 1];
     __shared__ T Bs[TN_KB][TP + 1];
-    const int i0 = blockIdx.x * TN_TM;
-    const int j0 = blockIdx.y * TP;
+    int bx = blockIdx.x, by = blockIdx.y;
+    if (SYM) tri_tile(blockIdx.x, bx, by);
+    const int i0 = bx * TN_TM;
+    const int j0 = by * TP;
     const int s = blockIdx.z;
     const int64_t r_begin = (int64_t)s * rows_per_split;
     const int64_t r_end = min(d, r_begin + rows_per_split);
@@ -102,26 +119,39 @@ __global__ void __launch_bounds__(TN_THREADS) k_gemm_tn_partial(int64_t d, int m
 // C[i, j] = alpha * sum_s partial[s][j][i] + beta * C[i, j]. Small split counts: one thread per
 // output, splits summed in order. Large split counts: one warp per output, lane l sums splits
 // l, l + 32, ... in order, then a fixed butterfly across lanes (deterministic either way).
-template <class T>
-__global__ void k_gemm_tn_reduce(int m, int p, int splits, const T* __restrict__ partial, double alpha,
-                                 double beta, double* __restrict__ C, int ldc) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)m * p) return;
-    const int i = (int)(e % m), j = (int)(e / m);
-    double acc = 0.0;
-    for (int s = 0; s < splits; ++s) acc += (double)partial[(int64_t)s * m * p + e];
+// SYM: only entries with i >= j are summed; each is written to (i, j) and mirrored to (j, i).
+__device__ __forceinline__ void tn_store(double* C, int ldc, int i, int j, double acc, double alpha, double beta,
+                                         bool sym) {
     double v = alpha * acc;
     if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
     C[(int64_t)j * ldc + i] = v;
+    if (sym && i != j) {
+        double w = alpha * acc;
+        if (beta != 0.0) w = fma(beta, C[(int64_t)i * ldc + j], w);
+        C[(int64_t)i * ldc + j] = w;
+    }
+}
+
+template <class T>
+__global__ void k_gemm_tn_reduce(int m, int p, int splits, const T* __restrict__ partial, double alpha,
+                                 double beta, double* __restrict__ C, int ldc, bool sym) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * p) return;
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (sym && i < j) return;
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) acc += (double)partial[(int64_t)s * m * p + e];
+    tn_store(C, ldc, i, j, acc, alpha, beta, sym);
 }
 
 template <class T>
 __global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const T* __restrict__ partial, double alpha,
-                                      double beta, double* __restrict__ C, int ldc) {
+                                      double beta, double* __restrict__ C, int ldc, bool sym) {
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (e >= (int64_t)m * p) return;
     const int i = (int)(e % m), j = (int)(e / m);
+    if (sym && i < j) return;
     const int64_t mp = (int64_t)m * p;
     double a0 = 0.0, a1 = 0.0;
     int s = lane;
@@ -132,11 +162,7 @@ __global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const T* __restr
     if (s < splits) a0 += (double)partial[(int64_t)s * mp + e];
     double acc = a0 + a1;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-        double v = alpha * acc;
-        if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
-        C[(int64_t)j * ldc + i] = v;
-    }
+    if (lane == 0) tn_store(C, ldc, i, j, acc, alpha, beta, sym);
 }
 
 // C[r, c] = beta * C0[r, c] + alpha * sum_l A[r, l] B[l, c] for tall A (d x m) and small B
@@ -560,28 +586,39 @@ __global__ void k_col_norms(int64_t rows, const T* __restrict__ A, int64_t lda, 
 
 }  // namespace
 
+namespace {
+
+int g_sm_count = 0;   // streaming multiprocessors of the device the split counts are sized for
+
 template <class T>
-int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const T* B, int64_t ldb, double beta,
-            double* C, int ldc, void* partial_buf, size_t partial_cap, cudaStream_t s) {
+int gemm_tn_impl(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const T* B, int64_t ldb,
+                 double beta, double* C, int ldc, void* partial_buf, size_t partial_cap, bool sym, cudaStream_t s) {
     if (m <= 0 || p <= 0) return EDA_OK;
     T* partial = static_cast<T*>(partial_buf);
-    const int TP = p <= 8 ? 8 : (p <= 16 ? 16 : 32);
-    const int tiles = ceil_div(m, TN_TM) * ceil_div(p, TP);
+    const int TP = sym ? TN_TM : (p <= 8 ? 8 : (p <= 16 ? 16 : 32));
+    const int tm = ceil_div(m, TN_TM);
+    const int tiles = sym ? tm * (tm + 1) / 2 : tm * ceil_div(p, TP);
+    const int nsm = sm_count();
+    // algorithmic work of this product, by the definition (one triangle for the symmetric case):
+    // flops 2 d m p (SYRK: d m (m + 1)), bytes: A and B read once, C written once, in the storage type
+    const double flops = sym ? (double)d * m * (m + 1.0) : 2.0 * (double)d * m * p;
+    const double bytes = (double)sizeof(T) * (double)d * (sym ? m : (double)m + p) + 8.0 * m * p;
+    ProfScope prof(std::is_same<T, double>::value ? "tn_f64" : "tn_f32", s, flops, bytes);
     // Split count: the kernel is FP64- or bandwidth-bound per SM, so an SM holding one CTA more than
     // the others sets the time. Among counts giving 1.8 to 4 CTAs per SM (after rounding the split
-    // rows to TN_KB), take the one that fills the 152 SMs most evenly, tiles * splits over
-    // 152 * ceil(tiles * splits / 152), preferring fewer splits unless another fills 2 % better.
+    // rows to TN_KB), take the one that fills the SMs most evenly, tiles * splits over
+    // nsm * ceil(tiles * splits / nsm), preferring fewer splits unless another fills 2 % better.
     int splits = 1;
     {
-        const int smax = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(4 * 152, tiles), (d + 63) / 64));
-        const int smin = std::min(smax, std::max(1, (int)std::ceil(1.8 * 152 / tiles)));
+        const int smax = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(4 * nsm, tiles), (d + 63) / 64));
+        const int smin = std::min(smax, std::max(1, (int)std::ceil(1.8 * nsm / tiles)));
         double best = -1.0;
         for (int s0 = smin; s0 <= smax; ++s0) {
             int64_t rw = (d + s0 - 1) / s0;
             rw = (rw + TN_KB - 1) / TN_KB * TN_KB;
             const int sc = (int)std::max<int64_t>(1, (d + rw - 1) / rw);
             const int64_t ctas = (int64_t)tiles * sc;
-            const double fill = (double)ctas / (152.0 * (double)((ctas + 151) / 152));
+            const double fill = (double)ctas / ((double)nsm * (double)((ctas + nsm - 1) / nsm));
             if (fill > best + 0.02) {
                 best = fill;
                 splits = sc;
@@ -593,28 +630,66 @@ int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, cons
     int64_t rows = (d + splits - 1) / splits;
     rows = (rows + TN_KB - 1) / TN_KB * TN_KB;
     splits = (int)std::max<int64_t>(1, (d + rows - 1) / rows);
-    dim3 grid(ceil_div(m, TN_TM), ceil_div(p, TP), splits);
     if (d > 0) {
-        if (TP == 8) k_gemm_tn_partial<8, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
-        else if (TP == 16) k_gemm_tn_partial<16, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
-        else k_gemm_tn_partial<32, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        if (sym) {
+            dim3 grid(tiles, 1, splits);
+            k_gemm_tn_partial<32, T, true><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        } else {
+            dim3 grid(tm, ceil_div(p, TP), splits);
+            if (TP == 8) k_gemm_tn_partial<8, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+            else if (TP == 16) k_gemm_tn_partial<16, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+            else k_gemm_tn_partial<32, T><<<grid, TN_THREADS, 0, s>>>(d, m, p, A, lda, B, ldb, rows, partial);
+        }
         EDA_LAUNCHED();
     } else {
         splits = 0;
     }
     const int64_t tot = (int64_t)m * p;
     if (splits >= 16 && tot <= 65536)
-        k_gemm_tn_reduce_warp<T><<<ceil_div(tot * 32, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
+        k_gemm_tn_reduce_warp<T><<<ceil_div(tot * 32, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc,
+                                                                          sym);
     else
-        k_gemm_tn_reduce<T><<<ceil_div(tot, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc);
+        k_gemm_tn_reduce<T><<<ceil_div(tot, 256), 256, 0, s>>>(m, p, splits, partial, alpha, beta, C, ldc, sym);
     EDA_LAUNCHED();
     return EDA_OK;
+}
+
+}  // namespace
+
+int sm_count() {
+    // queried once per process for the current device (every handle of a process uses one GPU type)
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            g_sm_count = n;
+        else
+            g_sm_count = 148;
+        cudaGetLastError();
+    });
+    return g_sm_count;
+}
+
+template <class T>
+int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const T* B, int64_t ldb, double beta,
+            double* C, int ldc, void* partial_buf, size_t partial_cap, cudaStream_t s) {
+    return gemm_tn_impl<T>(d, m, p, alpha, A, lda, B, ldb, beta, C, ldc, partial_buf, partial_cap, false, s);
+}
+
+template <class T>
+int syrk_tn(int64_t d, int m, double alpha, const T* A, int64_t lda, double beta, double* C, int ldc,
+            void* partial_buf, size_t partial_cap, cudaStream_t s) {
+    return gemm_tn_impl<T>(d, m, m, alpha, A, lda, A, lda, beta, C, ldc, partial_buf, partial_cap, true, s);
 }
 
 template <class T>
 int gemm_nn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const double* B, int ldb, double beta,
             const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s) {
     if (d <= 0 || p <= 0) return EDA_OK;
+    // algorithmic work: 2 d m p flops; A read once, C0 read (beta != 0) and C written once
+    ProfScope prof(std::is_same<T, double>::value ? "nn_f64" : "nn_f32", s, 2.0 * (double)d * m * p,
+                   (double)sizeof(T) * (double)d * (m + (beta != 0.0 ? 2.0 : 1.0) * p) + 8.0 * m * p);
     const int rowblocks = ceil_div(d, 32);
     // columns per thread: as many as possible while at least ~one CTA per SM stays busy
     if (p >= 6 && (int64_t)rowblocks * ceil_div(p, 8) >= 120) {
@@ -658,6 +733,10 @@ template int gemm_tn<double>(int64_t, int, int, double, const double*, int64_t, 
                              double*, int, void*, size_t, cudaStream_t);
 template int gemm_tn<float>(int64_t, int, int, double, const float*, int64_t, const float*, int64_t, double,
                             double*, int, void*, size_t, cudaStream_t);
+template int syrk_tn<double>(int64_t, int, double, const double*, int64_t, double, double*, int, void*, size_t,
+                             cudaStream_t);
+template int syrk_tn<float>(int64_t, int, double, const float*, int64_t, double, double*, int, void*, size_t,
+                            cudaStream_t);
 template int gemm_nn<double>(int64_t, int, int, double, const double*, int64_t, const double*, int, double,
                              const double*, int64_t, double*, int64_t, cudaStream_t);
 template int gemm_nn<float>(int64_t, int, int, double, const float*, int64_t, const double*, int, double,
@@ -674,6 +753,11 @@ template int col_norms<float>(int64_t, int, const float*, int64_t, double*, cuda
 int gemm_tn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                 double beta, double* C, int ldc, double* partial, size_t partial_cap, cudaStream_t s) {
     return gemm_tn<double>(d, m, p, alpha, A, lda, B, ldb, beta, C, ldc, partial, partial_cap, s);
+}
+
+int syrk_f64(int64_t d, int m, double alpha, const double* A, int64_t lda, double beta, double* C, int ldc,
+             double* partial, size_t partial_cap, cudaStream_t s) {
+    return syrk_tn<double>(d, m, alpha, A, lda, beta, C, ldc, partial, partial_cap, s);
 }
 
 int gemm_nn_f64(int64_t d, int m, int p, double alpha, const double* A, int64_t lda, const double* B, int ldb,

@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <climits>
 #include <cfloat>
 #include <cmath>
 
@@ -877,8 +878,11 @@ __global__ void k_copy_sq(int n, const double* A, int lda, double* B) {
 
 }  // namespace
 
-int symeig_finish_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, double cluster_rel,
-                          cudaStream_t s);
+constexpr int kBlockClusterMin = 48;   // clusters of this many columns or more: block Gram-Schmidt
+constexpr int kClusterRedo = 1;        // internal status: a block lost rank, orthogonalise column by column
+int symeig_orth_clusters(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, double cluster_rel,
+                         int maxc, cudaStream_t s);
+int symeig_backtransform(int n, int nv, double* Z, int ldz, SymEigWork* ws, cudaStream_t s);
 
 size_t symeig_work_bytes(int n, int nv) {
     const size_t nn = (size_t)n * n;
@@ -1080,9 +1084,9 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     return EDA_OK;
 }
 
-int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, uint64_t seed,
-                   double cluster_rel, cudaStream_t s) {
-    if (nv <= 0) return EDA_OK;
+namespace {
+// Inverse iteration for the nv eigenvalues w of the tridiagonal in ws, vectors into Z (n x nv, ldz).
+int invit_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, uint64_t seed, cudaStream_t s) {
     double* lu = ws->lu;
     double* Zt = ws->lu + 5 * (size_t)n * nv;
     {
@@ -1092,7 +1096,23 @@ int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWor
     }
     k_transpose_out<<<ceil_div((int64_t)n * nv, 256), 256, 0, s>>>(n, nv, Zt, Z, ldz);
     EDA_LAUNCHED();
-    return symeig_finish_vectors(n, nv, w, Z, ldz, ws, cluster_rel, s);
+    return EDA_OK;
+}
+}  // namespace
+
+int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, uint64_t seed,
+                   double cluster_rel, cudaStream_t s) {
+    if (nv <= 0) return EDA_OK;
+    EDA_TRY(invit_vectors(n, nv, w, Z, ldz, ws, seed, s));
+    int rc = symeig_orth_clusters(n, nv, w, Z, ldz, ws, cluster_rel, kBlockClusterMin, s);
+    if (rc == kClusterRedo) {
+        // a large cluster lost rank in its block orthogonalisation: recompute the (deterministic) inverse
+        // iteration vectors and orthogonalise every cluster column by column instead
+        EDA_TRY(invit_vectors(n, nv, w, Z, ldz, ws, seed, s));
+        rc = symeig_orth_clusters(n, nv, w, Z, ldz, ws, cluster_rel, INT_MAX, s);
+    }
+    EDA_TRY(rc);
+    return symeig_backtransform(n, nv, Z, ldz, ws, s);
 }
 
 int symeig_f64(int n, const double* A, int lda, int il, int iu, double* w, double* Z, int ldz, SymEigWork* ws,
@@ -1112,7 +1132,10 @@ __global__ void k_cluster_scale(int nv, const double* lam, double rel, double* o
         out[0] = rel * m;
     }
 }
-__global__ void k_cluster_mgs_dev(int n, int nv, const double* lam, const double* ctol_dev, double* Z, int ldz) {
+// Modified Gram-Schmidt (two passes) inside each run of eigenvalues whose consecutive gaps are <= ctol,
+// one warp per run; runs of maxc or more columns are left to the block path.
+__global__ void k_cluster_mgs_dev(int n, int nv, const double* lam, const double* ctol_dev, double* Z, int ldz,
+                                  int maxc) {
     const double ctol = ctol_dev[0];
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -1120,7 +1143,7 @@ __global__ void k_cluster_mgs_dev(int n, int nv, const double* lam, const double
     if (q > 0 && lam[q] - lam[q - 1] <= ctol) return;
     int end = q + 1;
     while (end < nv && lam[end] - lam[end - 1] <= ctol) ++end;
-    if (end - q < 2) return;
+    if (end - q < 2 || end - q >= maxc) return;
     for (int c = q + 1; c < end; ++c) {
         double* zc = Z + (int64_t)c * ldz;
         for (int pass = 0; pass < 2; ++pass) {
@@ -1141,17 +1164,78 @@ __global__ void k_cluster_mgs_dev(int n, int nv, const double* lam, const double
 }
 }  // namespace
 
-// Cluster orthogonalisation (tridiagonal basis) and back-transformation; call after symeig_f64
-// with the same workspace while the reflectors are still in it.
-int symeig_finish_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, double cluster_rel,
-                          cudaStream_t s) {
+// Orthogonalisation of the inverse-iteration vectors inside eigenvalue clusters (runs whose consecutive
+// gaps are <= cluster_rel * max |w|), in the tridiagonal basis. Runs shorter than maxc columns: modified
+// Gram-Schmidt by one warp each (k_cluster_mgs_dev). Longer runs (when eigenvalues span many orders of
+// magnitude, every value near the bottom of the spectrum falls within one such run): block Gram-Schmidt
+// in blocks of 32 columns with the multi-CTA products, CGS2 against the earlier blocks of the run and
+// CholQR2 inside the block; in exact arithmetic both give the same basis (Gram-Schmidt in column order).
+// The cluster bounds are found on the host with the device's criterion and operations. Returns
+// kClusterRedo when a block lost rank (the caller recomputes the vectors and uses maxc = INT_MAX).
+int symeig_orth_clusters(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, double cluster_rel,
+                         int maxc, cudaStream_t s) {
     double* ctol = ws->vbuf + 2 * n;
     k_cluster_scale<<<1, 32, 0, s>>>(nv, w, cluster_rel, ctol);
     EDA_LAUNCHED();
-    k_cluster_mgs_dev<<<ceil_div((int64_t)nv * 32, 256), 256, 0, s>>>(n, nv, w, ctol, Z, ldz);
+    k_cluster_mgs_dev<<<ceil_div((int64_t)nv * 32, 256), 256, 0, s>>>(n, nv, w, ctol, Z, ldz, maxc);
     EDA_LAUNCHED();
-    if (n >= 3) {
+    if (maxc == INT_MAX || nv < maxc) return EDA_OK;
+    std::vector<double> wh(nv);
+    EDA_CUDA_TRY(cudaMemcpyAsync(wh.data(), w, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaStreamSynchronize(s));
+    double mx = 0.0;
+    for (int i = 0; i < nv; ++i) mx = std::fmax(mx, std::fabs(wh[i]));
+    const double tol = cluster_rel * mx;
+    std::vector<std::pair<int, int>> big;
+    for (int q = 0; q < nv;) {
+        int end = q + 1;
+        while (end < nv && wh[end] - wh[end - 1] <= tol) ++end;
+        if (end - q >= maxc) big.emplace_back(q, end);
+        q = end;
+    }
+    if (big.empty()) return EDA_OK;
+    ProfScope prof("cluster_orth", s);
+    // scratch in the inverse-iteration factors (free once the vectors are in Z)
+    constexpr int BS = 32;
+    double* T = ws->lu;                                   // n x BS
+    double* C = T + (size_t)n * BS;                       // nv x BS
+    double* G = C + (size_t)nv * BS;                      // BS x BS
+    double* Ri = G + BS * BS;                             // BS x BS
+    int* st = reinterpret_cast<int*>(Ri + BS * BS);       // status word (8 doubles reserved)
+    double* part = Ri + BS * BS + 8;
+    const size_t used = (size_t)n * BS + (size_t)nv * BS + 2 * BS * BS + 8;
+    const size_t cap = 6 * (size_t)n * nv;
+    if (used + (size_t)nv * BS > cap) return EDA_ERR_INVALID_ARG;
+    const size_t pcap = cap - used;
+    EDA_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int), s));
+    for (const auto& cl : big) {
+        const int q = cl.first, end = cl.second;
+        double* Zq = Z + (size_t)q * ldz;
+        for (int j0 = q; j0 < end; j0 += BS) {
+            const int bs = std::min(BS, end - j0);
+            double* Zj = Z + (size_t)j0 * ldz;
+            const int prev = j0 - q;
+            for (int pass = 0; pass < 2 && prev > 0; ++pass) {
+                EDA_TRY(gemm_tn_f64(n, prev, bs, 1.0, Zq, ldz, Zj, ldz, 0.0, C, prev, part, pcap, s));
+                EDA_TRY(gemm_nn_f64(n, prev, bs, -1.0, Zq, ldz, C, prev, 1.0, Zj, ldz, Zj, ldz, s));
+            }
+            for (int pass = 0; pass < 2; ++pass) {
+                EDA_TRY(syrk_f64(n, bs, 1.0, Zj, ldz, 0.0, G, bs, part, pcap, s));
+                EDA_TRY(chol_inv_small(bs, G, bs, Ri, 1e-28, 0.0, st, nullptr, s));
+                EDA_TRY(gemm_nn_f64(n, bs, bs, 1.0, Zj, ldz, Ri, bs, 0.0, nullptr, 0, T, n, s));
+                EDA_TRY(copy_mat_f64(n, bs, T, n, Zj, ldz, s));
+            }
+        }
+    }
+    int sth = 0;
+    EDA_CUDA_TRY(cudaMemcpyAsync(&sth, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaStreamSynchronize(s));
+    return (sth & ST_RANKLOSS) ? kClusterRedo : EDA_OK;
+}
 
+// Householder back-transformation of the tridiagonal eigenvectors Z (reflectors still in ws).
+int symeig_backtransform(int n, int nv, double* Z, int ldz, SymEigWork* ws, cudaStream_t s) {
+    if (n >= 3) {
         ProfScope prof("backtransform", s);
         if (n <= 256) k_backtransform_reg<8><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
         else if (n <= 512) k_backtransform_reg<16><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
@@ -1167,7 +1251,7 @@ int newton_schulz_f64(int n, int nv, double* Z, int ldz, int steps, double* tmp,
     double* G = tmp;                       // nv x nv
     double* Zn = tmp + (size_t)nv * nv;    // n x nv
     for (int it = 0; it < steps; ++it) {
-        EDA_TRY(gemm_tn_f64(n, nv, nv, 1.0, Z, ldz, Z, ldz, 0.0, G, nv, partial, partial_cap, s));
+        EDA_TRY(syrk_f64(n, nv, 1.0, Z, ldz, 0.0, G, nv, partial, partial_cap, s));
         // Zn = 1.5 Z - 0.5 Z G
         EDA_TRY(gemm_nn_f64(n, nv, nv, -0.5, Z, ldz, G, nv, 1.5, Z, ldz, Zn, n, s));
         EDA_TRY(copy_mat_f64(n, nv, Zn, n, Z, ldz, s));

@@ -586,7 +586,7 @@ int launch_tc(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, i
     // sweep 1 over split ranges of whole stages
     const int tiles = ceil_div(m, TC_M);
     const int kst = (int)(f.ldh / TC_KS);
-    int splits = std::max(1, std::min(kst, ceil_div(2 * 152, tiles)));
+    int splits = std::max(1, std::min(kst, ceil_div(2 * sm_count(), tiles)));
     while (splits > 1 && (size_t)splits * m * b > partial_cap) --splits;
     if ((size_t)splits * m * b > partial_cap) return EDA_ERR_INVALID_ARG;
     const int rows = ceil_div(kst, splits) * TC_KS;
@@ -656,7 +656,7 @@ int tc_factor_make(const double* H, int64_t d, int m, const double* K, __nv_bflo
     return rc;
 }
 
-size_t tc_partial_floats(int m_max) { return (size_t)(2 * 152 + ceil_div(m_max, TC_M)) * TC_M * 32; }
+size_t tc_partial_floats(int m_max) { return (size_t)(2 * sm_count() + ceil_div(m_max, TC_M)) * TC_M * 32; }
 
 int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, __nv_bfloat16* Qhi,
                     __nv_bfloat16* Qlo, float* partial, size_t partial_cap, TcBuffers* b) {

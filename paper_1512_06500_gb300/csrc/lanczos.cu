@@ -116,7 +116,7 @@ struct SolveWs {
 template <class T>
 int cholqr_pass(int64_t d, int b, T* X, int64_t ldx, double* Rm, double* Rinv, T* out, double piv_min2, int* status,
                 int* lost, SolveWs<T>& w, cudaStream_t s) {
-    EDA_TRY(gemm_tn<T>(d, b, b, 1.0, X, ldx, X, ldx, 0.0, Rm, b, w.part, w.pcap, s));
+    EDA_TRY(syrk_tn<T>(d, b, 1.0, X, ldx, 0.0, Rm, b, w.part, w.pcap, s));
     EDA_TRY(chol_inv_small(b, Rm, b, Rinv, 1e-28, piv_min2, status, lost, s));
     EDA_TRY(gemm_nn<T>(d, b, b, 1.0, X, ldx, Rinv, b, 0.0, nullptr, 0, out, ldx, s));
     return EDA_OK;
@@ -378,7 +378,7 @@ template <class T>
 int cholqr_f64(int64_t d, int p, double* X, double* tmpX, SolveWs<T>& w, int passes, int* status, cudaStream_t s) {
     double* part = static_cast<double*>(w.part);
     for (int q = 0; q < passes; ++q) {
-        EDA_TRY(gemm_tn_f64(d, p, p, 1.0, X, d, X, d, 0.0, w.Rt, p, part, w.pcap, s));
+        EDA_TRY(syrk_f64(d, p, 1.0, X, d, 0.0, w.Rt, p, part, w.pcap, s));
         EDA_TRY(chol_inv_small(p, w.Rt, p, w.Rti, 1e-28, 0.0, status, nullptr, s));
         EDA_TRY(gemm_nn_f64(d, p, p, 1.0, X, d, w.Rti, p, 0.0, nullptr, 0, tmpX, d, s));
         EDA_TRY(copy_mat_f64(d, p, tmpX, d, X, d, s));
@@ -626,10 +626,10 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     // V = orth(X_t): CholQR2
     {
         double* part = static_cast<double*>(w.part);
-        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Xt, d, w.Xt, d, 0.0, w.Rt, t, part, w.pcap, s));
+        EDA_TRY(syrk_f64(d, t, 1.0, w.Xt, d, 0.0, w.Rt, t, part, w.pcap, s));
         EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
         EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Xt, d, w.Rti, t, 0.0, nullptr, 0, Vout, d, s));
-        EDA_TRY(gemm_tn_f64(d, t, t, 1.0, Vout, d, Vout, d, 0.0, w.Rt, t, part, w.pcap, s));
+        EDA_TRY(syrk_f64(d, t, 1.0, Vout, d, 0.0, w.Rt, t, part, w.pcap, s));
         EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
         EDA_TRY(gemm_nn_f64(d, t, t, 1.0, Vout, d, w.Rti, t, 0.0, nullptr, 0, w.Xt, d, s));
         EDA_TRY(copy_mat_f64(d, t, w.Xt, d, Vout, d, s));

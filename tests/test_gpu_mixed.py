@@ -32,6 +32,7 @@ def _dev(a):
 
 
 def _run(eda, p, t, b, tau, tol, prec):
+    # returns the library's c^2 only to check it against the oracle's own (no oracle input comes from it)
     cfg = eda.config(prec=prec, block_b=b, tau=tau, true_residuals=1)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         V, lam, _, info, code = h.solve(t, tol)
@@ -51,7 +52,8 @@ def test_mixed_precision_solver(eda, name, tol, eig_tol, angle_tol):
     c2, lam, V, info, Ptr, Pte = _run(eda, p, c["t"], c["b"], c["tau"], tol, eda.EDA_F32)
     assert info["refine_iters"] >= 1
     assert info["max_relres_true"] <= 10 * tol
-    ref = O.eda(p.X, p.labels, p.k, c["t"], c2=c2, tier="projected")
+    ref = O.eda(p.X, p.labels, p.k, c["t"], tau=c["tau"], tier="projected")
+    assert abs(c2 - ref["c2"]) <= 1e-13 * ref["c2"]
     rel = np.abs(lam - ref["lam_t"]) / ref["lam_t"]
     assert rel.max() <= eig_tol, rel.max()
     assert O.sin_angle(ref["V"], V) <= angle_tol
@@ -76,34 +78,45 @@ def _bf16_round(a):
     return t.to(torch.float64).numpy()
 
 
+def _colwise(Y, Yr):
+    """Per column: max_i |Y - Yr|_ij / max_i |Yr|_ij (an error in a few rows cannot hide in a norm)."""
+    return float(np.max(np.abs(Y - Yr).max(axis=0) / np.abs(Yr).max(axis=0)))
+
+
 @pytest.mark.parametrize("d,k,nj,b", [(4096, 40, 5, 8), (1000, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 16), (2048, 20, 7, 32),
                                       (777, 5, 3, 40)])
 def test_tc_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
     # The tensor-core product is X + bf16(H K) (bf16(H)^T X): H and the precomputed d x m product H K
-    # are stored in bf16, X and P = H^T X enter as hi + lo bf16 pairs, accumulation is FP32. Against an
-    # FP64 evaluation of that expression the error is the hi + lo rounding (2^-17 relative), FP32
-    # accumulation, and the rare entries of H K whose FP32 and FP64 values round to different bf16
-    # neighbours, so 1e-4 relative is a sharp bound that any operand or layout mistake (a transposed
-    # core matrix, a wrong swizzle, a wrong K step) violates by orders of magnitude.
+    # are stored in bf16, X and P = H^T X enter as hi + lo bf16 pairs, accumulation is FP32. The
+    # reference takes H from the oracle's scatter factors and K = alpha phi(alpha G) from the oracle's
+    # Gram and scale, applies the same bf16 roundings in FP64 and is compared element by element, per
+    # column against the column's largest entry. What separates the two: the hi + lo rounding of X and P
+    # (2^-17 relative), FP32 accumulation, and the rare entries of H K whose FP32 and FP64 values round
+    # to different bf16 neighbours; 1e-4 is a sharp bound that any operand or layout mistake (a
+    # transposed core matrix, a wrong swizzle, a wrong K step, a lost tile edge at a ragged d) violates.
     p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=500 + d)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    GW, GB = O.gram(f["HW"]), O.gram(f["HB"])
+    c2 = O.scale_c2(np.linalg.eigvalsh(GW)[-1], np.linalg.eigvalsh(GB)[-1], 10.0)
     cfg = eda.config(prec=eda.EDA_BF16, block_b=min(b, 16), tau=10.0)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
-        f = h.factors()
+        assert abs(h.c2 - c2) <= 1e-13 * c2
         rng = np.random.default_rng(d + b)
         Xb = rng.standard_normal((b, d)).astype(np.float32)
-        for op, H, K, alpha in ((eda.OP_SW, f["HW"], f["KW"], -0.5 * h.c2), (eda.OP_SB, f["HB"], f["KB"], h.c2)):
-            Y = h.apply_exp(op, _dev(Xb), alpha=alpha).cpu().numpy().astype(np.float64)
-            Hn = H.cpu().numpy()                       # (m, d): rows are the columns of H
-            Hb = _bf16_round(Hn)
-            Kn = K.cpu().numpy()
-            HKb = _bf16_round(Hb.T @ Kn)               # (d, m)
+        # the library's alpha selects its stored bf16 operators
+        for op, H, G, a_lib, a_ref in ((eda.OP_SW, f["HW"], GW, -0.5 * h.c2, -0.5 * c2),
+                                       (eda.OP_SB, f["HB"], GB, h.c2, c2)):
+            Y = h.apply_exp(op, _dev(Xb), alpha=a_lib).cpu().numpy().astype(np.float64)
+            K = O.phi_operator(G, a_ref)
+            Hb = _bf16_round(H.T)                      # (m, d): rows are the columns of H
+            HKb = _bf16_round(Hb.T @ K)                # (d, m)
             X64 = Xb.astype(np.float64)
             ref = X64 + (HKb @ (Hb @ X64.T)).T
-            err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+            err = _colwise(Y.T, ref.T)
             assert err <= 1e-4, (op, err)
-            # and against the exact FP64 operator: the bf16 rounding of H and H K (2^-9) sets the scale
-            exact = X64 + ((Hn.T @ (Kn @ (Hn @ X64.T))).T)
-            assert np.linalg.norm(Y - exact) / np.linalg.norm(exact) <= 2e-2
+            # against the exact FP64 operator: the bf16 rounding of H and H K (2^-9) sets the scale
+            exact = O.lowrank_exp_apply(H, a_ref, X64.T).T
+            assert _colwise(Y.T, exact.T) <= 2e-2, op
 
 
 @pytest.mark.parametrize("name,tol,eig_tol", [("d4096_k40", 1e-8, 1e-6), ("d16384_k100", 1e-8, 1e-6)])
@@ -113,7 +126,8 @@ def test_bf16_tensor_core_solver(eda, name, tol, eig_tol):
     c2, lam, V, info, Ptr, Pte = _run(eda, p, c["t"], c["b"], c["tau"], tol, eda.EDA_BF16)
     assert info["refine_iters"] >= 1
     assert info["max_relres_true"] <= 10 * tol
-    ref = O.eda(p.X, p.labels, p.k, c["t"], c2=c2, tier="projected")
+    ref = O.eda(p.X, p.labels, p.k, c["t"], tau=c["tau"], tier="projected")
+    assert abs(c2 - ref["c2"]) <= 1e-13 * ref["c2"]
     rel = np.abs(lam - ref["lam_t"]) / ref["lam_t"]
     assert rel.max() <= eig_tol, rel.max()
     lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)

@@ -75,31 +75,51 @@ def test_gram_eigen_and_phi_operator(eda):
         assert abs(h.lmax_w - ew[-1]) <= 64 * EPS * ew[-1]
         c2 = O.scale_c2(ew[-1], np.linalg.eigvalsh(GB)[-1], 10.0)
         assert abs(h.c2 - c2) <= 1e-13 * c2
-        KW = O.phi_operator(GW, -0.5 * h.c2)
-        KB = O.phi_operator(GB, h.c2)
+        KW = O.phi_operator(GW, -0.5 * c2)
+        KB = O.phi_operator(GB, c2)
         assert np.abs(f["KW"].cpu().numpy() - KW).max() <= 1e-12 * np.abs(KW).max()
         assert np.abs(f["KB"].cpu().numpy() - KB).max() <= 1e-12 * np.abs(KB).max()
 
 
 # ----------------------------------------------------------------- exp-vector products
 
-@pytest.mark.parametrize("d,k,nj,b", [(256, 8, 6, 1), (777, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 5), (4096, 40, 5, 8)])
+def _oracle_c2(ref, tau):
+    """c^2 from the oracle's own Grams (reading A1), never from the library."""
+    lw = float(np.linalg.eigvalsh(O.gram(ref["HW"]))[-1])
+    lb = float(np.linalg.eigvalsh(O.gram(ref["HB"]))[-1])
+    return O.scale_c2(lw, lb, tau)
+
+
+def _colwise(Y, Yr):
+    """max over columns j of max_i |Y - Yr|_ij / max_i |Yr|_ij: an error confined to a few rows (a tile
+    edge at a ragged d) cannot hide under a norm of the whole block."""
+    return float(np.max(np.abs(Y - Yr).max(axis=0) / np.abs(Yr).max(axis=0)))
+
+
+@pytest.mark.parametrize("d,k,nj,b", [(256, 8, 6, 1), (777, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 5), (4096, 40, 5, 8),
+                                      (1000, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 33)])
 def test_apply_exp_matches_theorem_3_1(eda, d, k, nj, b):
+    # element by element against the oracle's product through the paper's own QR / SVD route
+    # (Algorithm 2), with the oracle's own factors and scale; ragged d and block widths
     p = _problem(d, k, nj, seed=200 + d)
     rng = np.random.default_rng(d)
     Xb = rng.standard_normal((d, b))
+    ref = O.scatter_factors(p.X, p.labels, p.k)
+    c2 = _oracle_c2(ref, 10.0)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(block_b=2, tau=10.0)) as h:
-        ref = O.scatter_factors(p.X, p.labels, p.k)
+        assert abs(h.c2 - c2) <= 1e-13 * c2
         Xt = _dev(Xb.T)
-        for op, H, alpha in [(eda.OP_SW, ref["HW"], -0.5 * h.c2), (eda.OP_SB, ref["HB"], h.c2),
-                             (eda.OP_SW, ref["HW"], 0.8 * h.c2), (eda.OP_SB, ref["HB"], -1.3 * h.c2)]:
-            Y = h.apply_exp(op, Xt, alpha=alpha).cpu().numpy().T
-            Yr = O.lowrank_exp_apply(H, alpha, Xb)
-            err = np.linalg.norm(Y - Yr) / np.linalg.norm(Yr)
-            assert err <= 1e-12, (op, alpha, err)
+        # the library's alpha selects its stored operators (the first two) or forms K(alpha) anew
+        for op, H, a_lib, a_ref in [(eda.OP_SW, ref["HW"], -0.5 * h.c2, -0.5 * c2), (eda.OP_SB, ref["HB"], h.c2, c2),
+                                    (eda.OP_SW, ref["HW"], 0.8 * c2, 0.8 * c2),
+                                    (eda.OP_SB, ref["HB"], -1.3 * c2, -1.3 * c2)]:
+            Y = h.apply_exp(op, Xt, alpha=a_lib).cpu().numpy().T
+            Yr = O.lowrank_exp_apply(H, a_ref, Xb)
+            err = _colwise(Y, Yr)
+            assert err <= 1e-12, (op, a_ref, err)
         Y = h.apply_exp(eda.OP_M, Xt).cpu().numpy().T
-        Yr = O.m_apply(ref["HW"], ref["HB"], h.c2, Xb)
-        assert np.linalg.norm(Y - Yr) <= 1e-12 * np.linalg.norm(Yr)
+        Yr = O.m_apply(ref["HW"], ref["HB"], c2, Xb)
+        assert _colwise(Y, Yr) <= 1e-12
 
 
 def test_apply_exp_zero_factor_is_identity(eda):
@@ -145,7 +165,7 @@ def test_phi_by_squaring_matches_oracle(eda, tau):
         assert abs(h.lmax_b - lb) <= 64 * EPS * lb
         c2 = O.scale_c2(lw, lb, tau)
         assert abs(h.c2 - c2) <= 1e-13 * c2
-        for key, G, a in (("KW", GW, -0.5 * h.c2), ("KB", GB, h.c2)):
+        for key, G, a in (("KW", GW, -0.5 * c2), ("KB", GB, c2)):
             K = O.phi_operator(G, a)
             assert np.abs(f[key].cpu().numpy() - K).max() <= 1e-12 * np.abs(K).max(), key
 
@@ -175,7 +195,8 @@ def _solve_and_compare(eda, p, t, b, tau, tol=1e-12, tier="auto", check_every=1,
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         V, lam, Y, info, code = h.solve(t, tol, want_y=True, relres=True)
         assert code == 0, info
-        ref = O.eda(p.X, p.labels, p.k, t, c2=h.c2, tier=tier)
+        ref = O.eda(p.X, p.labels, p.k, t, tau=tau, tier=tier)
+        assert abs(h.c2 - ref["c2"]) <= 1e-13 * ref["c2"]
         lam = lam.cpu().numpy()
         rel = np.abs(lam - ref["lam_t"]) / ref["lam_t"]
         assert rel.max() <= 1e-10, rel.max()
@@ -235,7 +256,8 @@ def test_solve_every_block_size_small_problems(eda, spec):
         cfg = eda.config(block_b=b, tau=10.0, true_residuals=1)
         with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
             if ref is None:
-                ref = O.eda(p.X, p.labels, p.k, t, c2=h.c2, tier="projected")
+                ref = O.eda(p.X, p.labels, p.k, t, tau=10.0, tier="projected")
+            assert abs(h.c2 - ref["c2"]) <= 1e-13 * ref["c2"]
             V, lam, _, info, code = h.solve(t, 1e-12, check=False)
             assert code == 0, (b, info)
             assert info["max_relres_true"] <= 1e-11, (b, info)
@@ -295,9 +317,11 @@ def test_example_1_1_one_sample_per_class(eda):
     with eda.build(_dev(X), _dev(labels), k, eda.config(block_b=1, tau=4.0)) as h:
         f = O.scatter_factors(X, labels, k)
         mu = np.sort(np.linalg.eigvalsh(f["HB"].T @ f["HB"]))[::-1][: k - 1]
+        c2 = O.scale_c2(0.0, mu[0], 4.0)
+        assert abs(h.c2 - c2) <= 1e-13 * c2
         V, lam, _, info, code = h.solve(k - 1, 1e-13)
         assert code == 0
-        assert np.allclose(lam.cpu().numpy(), np.exp(h.c2 * mu), rtol=1e-11, atol=0)
+        assert np.allclose(lam.cpu().numpy(), np.exp(c2 * mu), rtol=1e-11, atol=0)
 
 
 # ----------------------------------------------------------------- error paths (host-detected)

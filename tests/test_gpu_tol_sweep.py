@@ -47,12 +47,13 @@ def test_tolerance_sweep_against_nearest_neighbour(eda, name):
             V, lam, _, info, code = h.solve(c["t"], tol)
             assert code == 0, (tol, info)
             if ref is None:
-                ref = O.eda(p.X, p.labels, p.k, c["t"], c2=h.c2, tier="projected")
+                ref = O.eda(p.X, p.labels, p.k, c["t"], tau=c["tau"], tier="projected")
                 Ptr_o = O.project(ref["V"], p.X)
                 Pte_o = O.project(ref["V"], p.Xtest)
                 lab_o, _, margin = O.nn_classify(Ptr_o, p.labels, Pte_o)
                 zmax = max(np.linalg.norm(p.X[i] - p.Xtest[j]) for i in range(p.X.shape[0])
                            for j in range(p.Xtest.shape[0]))
+            assert abs(h.c2 - ref["c2"]) <= 1e-13 * ref["c2"]
             Ptr = h.project(V, X).cpu().numpy()
             Pte = h.project(V, Xt).cpu().numpy()
         assert info["max_relres_true"] <= 10 * tol, (tol, info["max_relres_true"])
