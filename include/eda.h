@@ -48,7 +48,11 @@ typedef enum {
     EDA_F64 = 0,                 /* IEEE double                                              */
     EDA_F32 = 1,                 /* IEEE single                                              */
     EDA_BF16 = 2,                /* bfloat16 storage, FP32 accumulation                      */
-    EDA_BF16X2 = 3               /* hi + lo bfloat16 split of an FP32 value                  */
+    EDA_BF16X2 = 3,              /* hi + lo bfloat16 split of an FP32 value (not accepted)   */
+    EDA_F64_TC = 4               /* FP64-accurate products on the bf16 tensor cores: each    */
+                                 /* operand split exactly into 7 bf16 digit planes with a   */
+                                 /* power-of-two scale per row, 28 plane products with exact */
+                                 /* integer accumulation (error-free splitting)             */
 } eda_prec;
 
 typedef enum {
@@ -59,6 +63,8 @@ typedef enum {
 
 typedef struct {
     int32_t prec;                /* eda_prec of the Krylov sweeps: EDA_F64 (plain FP64),      */
+                                 /* EDA_F64_TC (FP64 solver whose M-apply sweeps over        */
+                                 /* [H_W H_B] run as FP64-accurate tensor-core products),    */
                                  /* EDA_F32 (single-precision H, basis and sweeps) or         */
                                  /* EDA_BF16 (bf16 H on the tensor cores, single-precision    */
                                  /* basis); the last two end with FP64 refinement to tol      */

@@ -408,7 +408,8 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     // GPU) instead of the eigensolver's sequential column steps; the eigenpairs follow on request.
     // The B half (G_B, its Lanczos run, its K, the cross Gram) runs on a second stream beside the W half.
     const bool by_squaring = n <= kLanczosMaxN && k <= kLanczosMaxN;
-    const bool cross = h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16 || h->cfg.m_form == 1;
+    const bool cross = h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16 || h->cfg.prec == EDA_F64_TC ||
+                       h->cfg.m_form == 1;
     AuxStream aux;
     double* partB = nullptr;
     size_t pcapB = 0;
@@ -481,6 +482,20 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
     }
     if (cross && !by_squaring) EDA_TRY(ensure_cross_gram(h, part, pcap, s));
+    if (h->cfg.prec == EDA_F64_TC) {
+        // Z = [H_W H_B] (d x (n + k), one allocation) split into bf16 digit planes twice: scaled per column
+        // for Z^T Y and per row for Z U; the narrow staging sized for both reduction lengths
+        const int nk = n + k;
+        const size_t bT = align256(oz_operand_bytes(nk, d)), bN = align256(oz_operand_bytes(d, nk));
+        const size_t bS = align256(oz_narrow_bytes(std::max<int64_t>(d, nk), sm_count(), nk));
+        void* p = nullptr;
+        EDA_CUDA_TRY(cudaMalloc(&p, bT + bN + bS));
+        h->ozblock = p;
+        char* c = static_cast<char*>(p);
+        EDA_TRY(oz_operand_make(h->HW, d, nk, d, true, c, &h->ozT, s));
+        EDA_TRY(oz_operand_make(h->HW, d, d, nk, false, c + bT, &h->ozN, s));
+        EDA_TRY(oz_narrow_make(std::max<int64_t>(d, nk), sm_count(), nk, c + bT + bN, &h->oznb));
+    }
     if (h->cfg.prec == EDA_BF16) {
         // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
         // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)
@@ -519,7 +534,8 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
 
 bool valid_cfg(const eda_config& c) {
     return c.block_b >= 1 && c.check_every >= 1 && (c.c2 > 0.0 || c.tau > 0.0) &&
-           (c.prec == EDA_F64 || c.prec == EDA_F32 || c.prec == EDA_BF16) && (c.m_form == 0 || c.m_form == 1);
+           (c.prec == EDA_F64 || c.prec == EDA_F32 || c.prec == EDA_BF16 || c.prec == EDA_F64_TC) &&
+           (c.m_form == 0 || c.m_form == 1);
 }
 
 }  // namespace
@@ -736,6 +752,7 @@ void eda_destroy(eda_handle h) {
     if (h->ws) cudaFree(h->ws);
     if (h->kblock) cudaFree(h->kblock);
     if (h->xblock) cudaFree(h->xblock);
+    if (h->ozblock) cudaFree(h->ozblock);
     if (h->block32) cudaFree(h->block32);
     if (h->block) cudaFree(h->block);
     delete h;

@@ -254,6 +254,40 @@ enum : int { TC_X_SPLIT_READY = 1, TC_EMIT_SPLIT = 2 };
 int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
                  float* Y, int64_t ldy, int flags, int* status, cudaStream_t s);
 
+// ---------------------------------------------------------------- FP64-accurate products on the tensor cores
+// An FP64 operand split once into kOzSlices bf16 digit planes with a power-of-two scale per M row
+// (error-free splitting), each plane in the pre-tiled swizzled layout: M rows are the columns of the
+// source matrix (operand of A^T B) or its rows (operand of A B), K runs along the reduction index.
+constexpr int kOzSlices = 7;
+struct OzOperand {
+    __nv_bfloat16* tiles = nullptr;   // plane q at tiles + q * slice
+    int64_t slice = 0;                // elements between planes
+    int* exps = nullptr;              // M scale exponents
+    int64_t M = 0, K = 0;
+    int kbs = 0, mtiles = 0;          // 64-wide K tiles per 128-row band; bands
+};
+// Staging of the narrow operand (at most 32 columns, split on every call), its tensor map, and the
+// split-K partial sums.
+struct OzNarrow {
+    CUtensorMap map;
+    __nv_bfloat16* planes = nullptr;  // [7][32][ldmax]
+    int* exps = nullptr;              // 32
+    double* partial = nullptr;
+    size_t pcap = 0;                  // doubles
+    int64_t ldmax = 0, map_ld = 0;
+};
+size_t oz_operand_bytes(int64_t M, int64_t K);
+// Split A (lda) into the operand: rows_are_cols = true: M = columns of A (d x M matrix, K = d rows);
+// false: M = rows of A (M x K matrix). mem: oz_operand_bytes(M, K) bytes, 256-byte aligned.
+int oz_operand_make(const double* A, int64_t lda, int64_t M, int64_t K, bool rows_are_cols, void* mem,
+                    OzOperand* op, cudaStream_t s);
+size_t oz_narrow_bytes(int64_t Kmax, int max_splits, int64_t Mmax);
+int oz_narrow_make(int64_t Kmax, int max_splits, int64_t Mmax, void* mem, OzNarrow* nb);
+// D (M x p, ldd) = alpha * op(A) B + beta * C0 (ldc0), op(A) the M x K split operand, B: K x p (ldb),
+// p <= 32, in FP64 accuracy on the bf16 tensor cores. D may equal C0 (same ld).
+int oz_gemm(const OzOperand& A, OzNarrow& nb, int p, const double* B, int64_t ldb, double alpha, double beta,
+            const double* C0, int64_t ldc0, double* D, int64_t ldd, int* status, cudaStream_t s);
+
 }  // namespace eda
 
 // The handle.
@@ -292,6 +326,10 @@ struct eda_ctx {
     // the mixed-precision refinement (allocated on first use)
     void* xblock = nullptr;
     double *GWB = nullptr, *GBW = nullptr;
+    // prec = EDA_F64_TC: Z = [H_W H_B] split for Z^T Y (ozT) and for Z U (ozN), and the narrow staging
+    void* ozblock = nullptr;
+    eda::OzOperand ozT, ozN;
+    eda::OzNarrow oznb;
     // solve workspace (grown on demand)
     void* ws = nullptr;
     size_t ws_bytes = 0;

@@ -1,0 +1,437 @@
+// FP64-accurate tall-skinny products on the bf16 tensor cores by error-free splitting of the operands
+// into integer digit planes (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications", Numerical
+// Algorithms 59, 2012), arranged for tcgen05.
+//
+// Splitting. Each row i of an operand (the rows of the MMA's M or N side; the reduction index k runs
+// along it) gets a power-of-two scale 2^{e_i} with |a_ik| < 2^{e_i}. Then
+//     a_ik = 2^{e_i - 7} (s_0 + 2^-8 s_1 + ... + 2^-48 s_6) + tail,   |tail| <= 2^{e_i - 57},
+// with integer digits s_q in [-128, 128] from the exact recurrence x_0 = a 2^{7 - e}, s_q = rint(x_q),
+// x_{q+1} = 256 (x_q - s_q) (every step is exact in FP64). A digit is exact in bf16 (8 significant bits).
+//
+// Products. For D = A B^T over the reduction index (A: M x K, B: N x K, both split),
+//     D_ij = 2^{e_i + f_j - 14} sum_q 2^{-8q} L_q,    L_q = sum_{a + b = q} sum_k s^A_{a,ik} s^B_{b,jk},
+// truncated at q <= 6 (28 digit-plane products; the dropped terms and both tails are below 2^-53 of
+// max_k |a_ik| sum_k |b_jk|). A level L_q summed over a chunk of 128 values of k is an integer below
+// (q + 1) 128 2^14 < 2^24, so the tensor cores' FP32 accumulation of a chunk is exact. Each chunk's
+// seven levels are read out of tensor memory, converted to integers and folded into two 64-bit
+// integer sums per output (G_0 = L_0 2^16 + L_1 2^8 + L_2 and G_1 = L_3 2^24 + L_4 2^16 + L_5 2^8 + L_6),
+// so the reduction over k is exact as well; the only roundings are the final conversion to FP64 and the
+// 2^-56 truncation of the digits.
+//
+// Kernel. One CTA per (128-row band of M, split of K), 256 threads: thread 0 issues the bulk copies of
+// the pre-tiled digit planes of A (one contiguous 16 KB swizzled tile per K stage of 64 and plane) and
+// the TMA boxes of the seven planes of B; thread 32 issues tcgen05.mma (M = 128, N = 32, K = 16) into one
+// of two accumulator sets of seven levels in tensor memory (7 x 32 columns each), switching sets every
+// chunk of two K stages; warps 4-7 drain a finished set (tcgen05.ld, integer fold) while the tensor
+// cores fill the other. Every wait is bounded (ST_TIMEOUT on give-up).
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+#include <mutex>
+
+namespace eda {
+
+using namespace tc;
+
+namespace {
+
+constexpr int OZ_S = kOzSlices;       // digit planes
+constexpr int OZ_N = 32;              // N of every MMA: the narrow operand's columns per launch
+constexpr int OZ_AST = 8;             // A ring slots (one 16 KB tile of one plane each)
+constexpr int OZ_BST = 2;             // B ring slots (the seven 32 x 64 planes of one K stage)
+constexpr int OZ_THREADS = 256;
+constexpr int OZ_SET_COLS = 256;      // tensor-memory columns of one accumulator set (7 levels x 32)
+
+struct OzRing {
+    __nv_bfloat16 A[OZ_AST][TC_M * TC_KS];            // 8 x 16 KB
+    __nv_bfloat16 B[OZ_BST][OZ_S][OZ_N * TC_KS];      // 2 x 7 x 4 KB
+    uint64_t fullA[OZ_AST], emptyA[OZ_AST];
+    uint64_t fullB[OZ_BST], emptyB[OZ_BST];
+    uint64_t accFull[2], accEmpty[2];
+    uint32_t tbase;
+    int fail;
+};
+constexpr size_t oz_smem_bytes() { return sizeof(OzRing) + 1024; }
+
+__device__ __forceinline__ OzRing& oz_ring(unsigned char* raw) {
+    const uint32_t mis = smem_u32(raw) & 1023u;
+    return *reinterpret_cast<OzRing*>(raw + ((1024u - mis) & 1023u));
+}
+
+// D[i, j] (i < M, j < N) = alpha * sum_k A_ik B_jk + beta * C0[i, j]; D, C0 column-major (ld ldd, ldc0),
+// the split-th slice of D at D + split * split_stride. A: digit planes at At + q * aslice, pre-tiled
+// (128-row bands, kbs tiles of 64 along K per band), row scales expA. B: digit planes read through tmB
+// (inner = K, outer = 7 x 32 rows: plane q is rows 32 q .. 32 q + 31), row scales expB. K stages
+// [split * kps, min(kst, (split + 1) * kps)).
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_gemm(const __nv_bfloat16* __restrict__ At, int64_t aslice, int kbs, const __grid_constant__ CUtensorMap tmB,
+              const int* __restrict__ expA, const int* __restrict__ expB, int M, int N, int kst, int kps,
+              double alpha, double beta, const double* C0, int64_t ldc0, double* D, int64_t ldd,
+              int64_t split_stride, int* status) {
+    extern __shared__ unsigned char smraw[];
+    OzRing& sm = oz_ring(smraw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int band = blockIdx.x, split = blockIdx.y;
+    const int ks0 = split * kps;
+    const int nks = max(0, min(kst, ks0 + kps) - ks0);
+    const int nchunks = (nks + 1) >> 1;
+    if (warp == 0) {
+        tmem_alloc(&sm.tbase, 2 * OZ_SET_COLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < OZ_AST; ++i) {
+            mbar_init(&sm.fullA[i], 1);
+            mbar_init(&sm.emptyA[i], 1);
+        }
+        for (int i = 0; i < OZ_BST; ++i) {
+            mbar_init(&sm.fullB[i], 1);
+            mbar_init(&sm.emptyB[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.accFull[i], 1);
+            mbar_init(&sm.accEmpty[i], 128);
+        }
+        fence_mbar_init();
+        sm.fail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tbase;
+
+    int issuedA = 0, issuedB = 0;   // producer: copies requested (for the drain after a give-up)
+    bool ok = true;
+    if (tid == 0) {
+        // ---- producer ----
+        constexpr uint32_t abytes = TC_M * TC_KS * 2;
+        constexpr uint32_t bbytes = OZ_S * OZ_N * TC_KS * 2;
+        for (int s = 0; s < nks && ok; ++s) {
+            const int kstage = ks0 + s;
+            const int bslot = s % OZ_BST;
+            if (s >= OZ_BST && !(ok = mbar_wait(&sm.emptyB[bslot], ((s / OZ_BST) - 1) & 1, status))) break;
+            mbar_expect_tx(&sm.fullB[bslot], bbytes);
+#pragma unroll
+            for (int q = 0; q < OZ_S; ++q) tma_load_2d(sm.B[bslot][q], &tmB, kstage * TC_KS, q * OZ_N, &sm.fullB[bslot]);
+            issuedB = s + 1;
+            for (int a = 0; a < OZ_S; ++a) {
+                const int idx = s * OZ_S + a;
+                const int slot = idx % OZ_AST;
+                if (idx >= OZ_AST && !(ok = mbar_wait(&sm.emptyA[slot], ((idx / OZ_AST) - 1) & 1, status))) break;
+                mbar_expect_tx(&sm.fullA[slot], abytes);
+                bulk_load(sm.A[slot], At + a * aslice + ((int64_t)((int64_t)band * kbs + kstage) << 13), abytes,
+                          &sm.fullA[slot]);
+                issuedA = idx + 1;
+            }
+        }
+    } else if (tid == 32) {
+        // ---- MMA issuer ----
+        constexpr uint32_t idesc = idesc_bf16(TC_M, OZ_N);
+        for (int s = 0; s < nks && ok; ++s) {
+            const int chunk = s >> 1, set = chunk & 1;
+            const bool first = (s & 1) == 0;
+            if (first && chunk >= 2 && !(ok = mbar_wait(&sm.accEmpty[set], ((chunk >> 1) - 1) & 1, status))) break;
+            const int bslot = s % OZ_BST;
+            if (!(ok = mbar_wait(&sm.fullB[bslot], (s / OZ_BST) & 1, status))) break;
+            for (int a = 0; a < OZ_S; ++a) {
+                const int idx = s * OZ_S + a;
+                const int slot = idx % OZ_AST;
+                if (!(ok = mbar_wait(&sm.fullA[slot], (idx / OZ_AST) & 1, status))) break;
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sm.A[slot]);
+                for (int b = 0; b < OZ_S - a; ++b) {
+                    const uint32_t b0 = smem_u32(sm.B[bslot][b]);
+                    const uint32_t col = (uint32_t)(set * OZ_SET_COLS + (a + b) * OZ_N);
+#pragma unroll
+                    for (int kk = 0; kk < TC_KS / 16; ++kk) {
+                        // the first product of level a + b in this chunk (a = 0, first K step) overwrites
+                        const uint32_t acc = (first && a == 0 && kk == 0) ? 0u : 1u;
+                        mma_bf16(tmem + col, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                                 acc);
+                    }
+                }
+                mma_commit(&sm.emptyA[slot]);
+            }
+            if (!ok) break;
+            mma_commit(&sm.emptyB[bslot]);
+            if ((s & 1) || s == nks - 1) mma_commit(&sm.accFull[set]);
+        }
+    }
+    // ---- epilogue: warps 4-7 fold each finished chunk into exact 64-bit integer sums ----
+    long long g0[OZ_N], g1[OZ_N];
+#pragma unroll
+    for (int c = 0; c < OZ_N; ++c) g0[c] = g1[c] = 0;
+    bool eok = true;
+    if (warp >= 4) {
+        const int ew = warp - 4;
+        const uint32_t lanebase = tmem + ((uint32_t)(32 * ew) << 16);
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int set = ch & 1;
+            if (!(eok = mbar_wait(&sm.accFull[set], (ch >> 1) & 1, status))) break;
+            tc_fence_after();
+#pragma unroll
+            for (int c0 = 0; c0 < OZ_N; c0 += 8) {
+                uint32_t r[OZ_S][8];
+#pragma unroll
+                for (int q = 0; q < OZ_S; ++q) tmem_ld8(lanebase + set * OZ_SET_COLS + q * OZ_N + c0, r[q]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    long long L[OZ_S];
+#pragma unroll
+                    for (int q = 0; q < OZ_S; ++q) L[q] = (long long)__float2int_rn(__uint_as_float(r[q][c]));
+                    g0[c0 + c] += L[0] * 65536LL + L[1] * 256LL + L[2];
+                    g1[c0 + c] += ((L[3] * 256LL + L[4]) * 256LL + L[5]) * 256LL + L[6];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sm.accEmpty[set]);
+        }
+    }
+    __shared__ int s_ok;
+    if ((tid == 0 || tid == 32) && !ok) sm.fail = 1;
+    if (warp >= 4 && !eok) sm.fail = 1;
+    __syncthreads();
+    if (tid == 0) s_ok = sm.fail == 0 ? 1 : 0;
+    if (tid == 0 && sm.fail) {
+        // after a give-up, wait (bounded again) for this CTA's copies that may still be in flight, so
+        // that none lands after the CTA's shared memory is released
+        for (int i = max(0, issuedA - OZ_AST); i < issuedA; ++i)
+            mbar_wait(&sm.fullA[i % OZ_AST], (i / OZ_AST) & 1, status);
+        for (int i = max(0, issuedB - OZ_BST); i < issuedB; ++i)
+            mbar_wait(&sm.fullB[i % OZ_BST], (i / OZ_BST) & 1, status);
+    }
+    __syncthreads();
+    if (warp >= 4) {
+        const int i = band * TC_M + 32 * (warp - 4) + lane;
+        if (i < M) {
+            const int ea = expA[i];
+            double* Ds = D + (int64_t)split * split_stride;
+#pragma unroll
+            for (int c = 0; c < OZ_N; ++c) {
+                if (c >= N) break;
+                const int e = ea + expB[c];
+                double v = (s_ok && nks > 0) ? ldexp((double)g0[c], e - 30) + ldexp((double)g1[c], e - 62) : 0.0;
+                if (!s_ok) v = nan("");
+                double out = alpha * v;
+                if (beta != 0.0) out = fma(beta, C0[(int64_t)c * ldc0 + i], out);
+                Ds[(int64_t)c * ldd + i] = out;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 2 * OZ_SET_COLS);
+}
+
+// Digits of x_0 = v 2^{7 - e}: s_q = rint(x_q), x_{q+1} = 256 (x_q - s_q); all steps exact in FP64.
+__device__ __forceinline__ void oz_digits(double v, int e, __nv_bfloat16 (&s)[OZ_S]) {
+    double x = ldexp(v, 7 - e);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) {
+        const double d = rint(x);
+        s[q] = __float2bfloat16_rn((float)d);
+        x = (x - d) * 256.0;
+    }
+}
+
+// e_i with max_k |A_ik| < 2^{e_i} (frexp exponent of the largest magnitude; 0 for a zero row).
+__device__ __forceinline__ int oz_scale_exp(double mx) {
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    return e;
+}
+
+// Row scales of a split operand whose M rows are the COLUMNS of A (d x m, lda): block per column.
+__global__ void k_oz_exp_cols(int64_t rows, const double* __restrict__ A, int64_t lda, int* __restrict__ e) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double mx = 0.0;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) mx = fmax(mx, fabs(A[(int64_t)c * lda + r]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        e[c] = oz_scale_exp(m);
+    }
+}
+
+// Row scales of a split operand whose M rows are the ROWS of A (d x m, lda): thread per row.
+__global__ void k_oz_exp_rows(int64_t rows, int cols, const double* __restrict__ A, int64_t lda,
+                              int* __restrict__ e) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double mx = 0.0;
+    for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(A[(int64_t)c * lda + r]));
+    e[r] = oz_scale_exp(mx);
+}
+
+// The seven digit planes of a big operand in the pre-tiled layout (tile_off): element (i, k) of the
+// operand is A[k + i lda] (rows_are_cols = 1: M rows are the columns of A, K runs down them) or
+// A[i + k lda] (rows_are_cols = 0: M rows are the rows of A, K runs along them); zero outside M x K.
+__global__ void k_oz_split_tiled(const double* __restrict__ A, int64_t lda, int64_t Mrows, int64_t Kcols,
+                                 int rows_are_cols, const int* __restrict__ e, int kbs, int64_t total,
+                                 __nv_bfloat16* __restrict__ out, int64_t slice) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int64_t tile = t >> 13;
+    const int within = (int)(t & 8191);
+    const int rr = within >> 6, pc = (within >> 3) & 7, el = within & 7;
+    const int c = pc ^ (rr & 7);
+    const int64_t i = (tile / kbs) * TC_M + rr;
+    const int64_t k = (tile % kbs) * TC_KS + c * 8 + el;
+    double v = 0.0;
+    int ex = 0;
+    if (i < Mrows && k < Kcols) {
+        v = rows_are_cols ? A[i * lda + k] : A[k * lda + i];
+        ex = e[i];
+    }
+    __nv_bfloat16 s[OZ_S];
+    oz_digits(v, ex, s);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) out[q * slice + t] = s[q];
+}
+
+// The seven digit planes of a narrow operand B (K x p, ldb; its columns are the N rows of the product),
+// planes [7][32][ld] (plane q, row j at (32 q + j) ld), zero for j >= p or k >= K.
+__global__ void k_oz_split_narrow(int64_t K, int p, const double* __restrict__ B, int64_t ldb,
+                                  const int* __restrict__ e, int64_t ld, __nv_bfloat16* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)OZ_N * ld) return;
+    const int j = (int)(t / ld);
+    const int64_t k = t % ld;
+    double v = 0.0;
+    int ex = 0;
+    if (j < p && k < K) {
+        v = B[(int64_t)j * ldb + k];
+        ex = e[j];
+    }
+    __nv_bfloat16 s[OZ_S];
+    oz_digits(v, ex, s);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) out[(int64_t)q * OZ_N * ld + t] = s[q];
+}
+
+// D[i, j] = alpha * sum_s P[s][j][i] + beta * D[i, j], splits added in order (deterministic).
+__global__ void k_oz_reduce(int M, int N, int splits, const double* __restrict__ P, int64_t sstride, double alpha,
+                            double beta, const double* C0, int64_t ldc0, double* D, int64_t ldd) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)M * N) return;
+    const int i = (int)(t % M), j = (int)(t / M);
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) acc += P[(int64_t)s * sstride + (int64_t)j * M + i];
+    double v = alpha * acc;
+    if (beta != 0.0) v = fma(beta, C0[(int64_t)j * ldc0 + i], v);
+    D[(int64_t)j * ldd + i] = v;
+}
+
+int oz_attr() {
+    static std::once_flag once;
+    static cudaError_t rc = cudaSuccess;
+    std::call_once(once, [] {
+        rc = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    });
+    EDA_CUDA_TRY(rc);
+    return EDA_OK;
+}
+
+}  // namespace
+
+size_t oz_operand_bytes(int64_t M, int64_t K) {
+    const int64_t mt = (M + TC_M - 1) / TC_M, kb = (K + TC_KS - 1) / TC_KS;
+    const size_t plane = (size_t)mt * kb * TC_M * TC_KS * 2;
+    return OZ_S * ((plane + 255) / 256 * 256) + ((size_t)M * 4 + 255) / 256 * 256;
+}
+
+int oz_operand_make(const double* A, int64_t lda, int64_t M, int64_t K, bool rows_are_cols, void* mem,
+                    OzOperand* op, cudaStream_t s) {
+    const int64_t mt = (M + TC_M - 1) / TC_M, kb = (K + TC_KS - 1) / TC_KS;
+    const int64_t plane = mt * kb * TC_M * TC_KS;
+    const int64_t slice = ((plane * 2 + 255) / 256 * 256) / 2;
+    op->tiles = static_cast<__nv_bfloat16*>(mem);
+    op->slice = slice;
+    op->exps = reinterpret_cast<int*>(static_cast<char*>(mem) + OZ_S * slice * 2);
+    op->M = M;
+    op->K = K;
+    op->kbs = (int)kb;
+    op->mtiles = (int)mt;
+    if (rows_are_cols) {
+        k_oz_exp_cols<<<(unsigned)M, 256, 0, s>>>(K, A, lda, op->exps);
+    } else {
+        k_oz_exp_rows<<<ceil_div(M, 256), 256, 0, s>>>(M, (int)K, A, lda, op->exps);
+    }
+    EDA_LAUNCHED();
+    k_oz_split_tiled<<<ceil_div(plane, 256), 256, 0, s>>>(A, lda, M, K, rows_are_cols ? 1 : 0, op->exps, (int)kb,
+                                                          plane, op->tiles, slice);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+size_t oz_narrow_bytes(int64_t Kmax, int max_splits, int64_t Mmax) {
+    const int64_t ld = (Kmax + TC_KS - 1) / TC_KS * TC_KS;
+    return ((size_t)OZ_S * OZ_N * ld * 2 + 255) / 256 * 256 + 256 +
+           ((size_t)max_splits * OZ_N * Mmax * 8 + 255) / 256 * 256;
+}
+
+int oz_narrow_make(int64_t Kmax, int max_splits, int64_t Mmax, void* mem, OzNarrow* nb) {
+    const int64_t ld = (Kmax + TC_KS - 1) / TC_KS * TC_KS;
+    char* p = static_cast<char*>(mem);
+    nb->planes = reinterpret_cast<__nv_bfloat16*>(p);
+    p += ((size_t)OZ_S * OZ_N * ld * 2 + 255) / 256 * 256;
+    nb->exps = reinterpret_cast<int*>(p);
+    p += 256;
+    nb->partial = reinterpret_cast<double*>(p);
+    nb->pcap = (size_t)max_splits * OZ_N * Mmax;
+    nb->ldmax = ld;
+    nb->map_ld = 0;
+    return EDA_OK;
+}
+
+int oz_gemm(const OzOperand& A, OzNarrow& nb, int p, const double* B, int64_t ldb, double alpha, double beta,
+            const double* C0, int64_t ldc0, double* D, int64_t ldd, int* status, cudaStream_t s) {
+    if (p < 1 || p > OZ_N) return EDA_ERR_INVALID_ARG;
+    const int64_t ld = (A.K + TC_KS - 1) / TC_KS * TC_KS;
+    if (ld > nb.ldmax) return EDA_ERR_INVALID_ARG;
+    EDA_TRY(oz_attr());
+    if (nb.map_ld != ld) {
+        EDA_TRY(make_map(&nb.map, nb.planes, (uint64_t)ld, (uint64_t)OZ_S * OZ_N, (uint64_t)ld, OZ_N));
+        nb.map_ld = ld;
+    }
+    // algorithmic work, as for the FP64 product it replaces: 2 M K p flops; A read once (seven bf16
+    // digit planes), B read and D written once in FP64
+    ProfScope prof("oz_gemm", s, 2.0 * (double)A.M * A.K * p,
+                   2.0 * OZ_S * (double)A.M * A.K + 8.0 * (double)A.K * p + 8.0 * (double)A.M * p);
+    k_oz_exp_cols<<<p, 256, 0, s>>>(A.K, B, ldb, nb.exps);
+    EDA_LAUNCHED();
+    k_oz_split_narrow<<<ceil_div((int64_t)OZ_N * ld, 256), 256, 0, s>>>(A.K, p, B, ldb, nb.exps, ld, nb.planes);
+    EDA_LAUNCHED();
+    const int kst = (int)(ld / TC_KS);
+    // K splits: fill the SMs with one CTA each (the kernel holds all of an SM's tensor memory)
+    const int nsm = sm_count();
+    int splits = std::max(1, std::min(kst / 2, nsm / std::max(1, A.mtiles)));
+    while (splits > 1 && (size_t)splits * p * A.M > nb.pcap) --splits;
+    const int kps = ceil_div(kst, splits);
+    splits = ceil_div(kst, kps);
+    const dim3 grid((unsigned)A.mtiles, (unsigned)splits);
+    if (splits == 1) {
+        k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps,
+                                                            (int)A.M, p, kst, kps, alpha, beta, C0, ldc0, D, ldd, 0,
+                                                            status);
+        EDA_LAUNCHED();
+        return EDA_OK;
+    }
+    const int64_t sstride = (int64_t)p * A.M;
+    k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps, (int)A.M,
+                                                        p, kst, kps, 1.0, 0.0, nullptr, 0, nb.partial, A.M, sstride,
+                                                        status);
+    EDA_LAUNCHED();
+    k_oz_reduce<<<ceil_div((int64_t)A.M * p, 256), 256, 0, s>>>((int)A.M, p, splits, nb.partial, sstride, alpha,
+                                                                 beta, C0, ldc0, D, ldd);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+}  // namespace eda

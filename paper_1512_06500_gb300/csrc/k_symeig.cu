@@ -879,7 +879,6 @@ __global__ void k_copy_sq(int n, const double* A, int lda, double* B) {
 }  // namespace
 
 constexpr int kBlockClusterMin = 48;   // clusters of this many columns or more: block Gram-Schmidt
-constexpr int kClusterRedo = 1;        // internal status: a block lost rank, orthogonalise column by column
 int symeig_orth_clusters(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, double cluster_rel,
                          int maxc, cudaStream_t s);
 int symeig_backtransform(int n, int nv, double* Z, int ldz, SymEigWork* ws, cudaStream_t s);
@@ -1104,14 +1103,7 @@ int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWor
                    double cluster_rel, cudaStream_t s) {
     if (nv <= 0) return EDA_OK;
     EDA_TRY(invit_vectors(n, nv, w, Z, ldz, ws, seed, s));
-    int rc = symeig_orth_clusters(n, nv, w, Z, ldz, ws, cluster_rel, kBlockClusterMin, s);
-    if (rc == kClusterRedo) {
-        // a large cluster lost rank in its block orthogonalisation: recompute the (deterministic) inverse
-        // iteration vectors and orthogonalise every cluster column by column instead
-        EDA_TRY(invit_vectors(n, nv, w, Z, ldz, ws, seed, s));
-        rc = symeig_orth_clusters(n, nv, w, Z, ldz, ws, cluster_rel, INT_MAX, s);
-    }
-    EDA_TRY(rc);
+    EDA_TRY(symeig_orth_clusters(n, nv, w, Z, ldz, ws, cluster_rel, kBlockClusterMin, s));
     return symeig_backtransform(n, nv, Z, ldz, ws, s);
 }
 
@@ -1132,6 +1124,51 @@ __global__ void k_cluster_scale(int nv, const double* lam, double rel, double* o
         out[0] = rel * m;
     }
 }
+// Columns Z[:, 0 .. bs) (bs <= 16), already orthogonal to every earlier column of their cluster: each column
+// against the earlier ones of the block by classical Gram-Schmidt applied twice (the dot products of a pass
+// on one warp each, the update on all threads), then normalised. Computed from the vectors themselves (not
+// their Gram matrix), like the column-by-column loop it replaces, so nearly dependent inverse-iteration
+// vectors of a tight cluster keep their content above the rounding level.
+constexpr int kClusterBlock = 16;
+__global__ void __launch_bounds__(512) k_cluster_block_cgs2(int n, double* Z, int ldz, int bs) {
+    __shared__ double dots[kClusterBlock];
+    __shared__ double red[16];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int c = 0; c < bs; ++c) {
+        double* zc = Z + (int64_t)c * ldz;
+        for (int pass = 0; pass < 2 && c > 0; ++pass) {
+            if (warp < c) {
+                const double* zw = Z + (int64_t)warp * ldz;
+                double dot = 0.0;
+                for (int i = lane; i < n; i += 32) dot = fma(zw[i], zc[i], dot);
+                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                if (lane == 0) dots[warp] = dot;
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += blockDim.x) {
+                double acc = 0.0;
+                for (int w = 0; w < c; ++w) acc = fma(dots[w], Z[(int64_t)w * ldz + i], acc);
+                zc[i] -= acc;
+            }
+            __syncthreads();
+        }
+        double nrm = 0.0;
+        for (int i = tid; i < n; i += blockDim.x) nrm = fma(zc[i], zc[i], nrm);
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if (lane == 0) red[warp] = nrm;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            red[0] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+        }
+        __syncthreads();
+        const double sc = red[0];
+        for (int i = tid; i < n; i += blockDim.x) zc[i] *= sc;
+        __syncthreads();
+    }
+}
+
 // Modified Gram-Schmidt (two passes) inside each run of eigenvalues whose consecutive gaps are <= ctol,
 // one warp per run; runs of maxc or more columns are left to the block path.
 __global__ void k_cluster_mgs_dev(int n, int nv, const double* lam, const double* ctol_dev, double* Z, int ldz,
@@ -1166,12 +1203,13 @@ __global__ void k_cluster_mgs_dev(int n, int nv, const double* lam, const double
 
 // Orthogonalisation of the inverse-iteration vectors inside eigenvalue clusters (runs whose consecutive
 // gaps are <= cluster_rel * max |w|), in the tridiagonal basis. Runs shorter than maxc columns: modified
-// Gram-Schmidt by one warp each (k_cluster_mgs_dev). Longer runs (when eigenvalues span many orders of
-// magnitude, every value near the bottom of the spectrum falls within one such run): block Gram-Schmidt
-// in blocks of 32 columns with the multi-CTA products, CGS2 against the earlier blocks of the run and
-// CholQR2 inside the block; in exact arithmetic both give the same basis (Gram-Schmidt in column order).
-// The cluster bounds are found on the host with the device's criterion and operations. Returns
-// kClusterRedo when a block lost rank (the caller recomputes the vectors and uses maxc = INT_MAX).
+// Gram-Schmidt (two passes) by one warp each (k_cluster_mgs_dev). Longer runs (when eigenvalues span many
+// orders of magnitude, every value near the bottom of the spectrum falls within one such run): blocks of
+// kClusterBlock columns in order, each first made orthogonal to the earlier blocks of its run by block
+// classical Gram-Schmidt applied twice with the multi-CTA products, then orthonormalised column by column
+// (k_cluster_block_cgs2). In exact arithmetic this is the same Gram-Schmidt basis as the column loop, and
+// like it every step works on the vectors, never on their Gram matrix. The cluster bounds are found on the
+// host with the device's criterion and operations.
 int symeig_orth_clusters(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, double cluster_rel,
                          int maxc, cudaStream_t s) {
     double* ctol = ws->vbuf + 2 * n;
@@ -1196,18 +1234,12 @@ int symeig_orth_clusters(int n, int nv, const double* w, double* Z, int ldz, Sym
     if (big.empty()) return EDA_OK;
     ProfScope prof("cluster_orth", s);
     // scratch in the inverse-iteration factors (free once the vectors are in Z)
-    constexpr int BS = 32;
-    double* T = ws->lu;                                   // n x BS
-    double* C = T + (size_t)n * BS;                       // nv x BS
-    double* G = C + (size_t)nv * BS;                      // BS x BS
-    double* Ri = G + BS * BS;                             // BS x BS
-    int* st = reinterpret_cast<int*>(Ri + BS * BS);       // status word (8 doubles reserved)
-    double* part = Ri + BS * BS + 8;
-    const size_t used = (size_t)n * BS + (size_t)nv * BS + 2 * BS * BS + 8;
+    constexpr int BS = kClusterBlock;
+    double* C = ws->lu;                                   // nv x BS
+    double* part = C + (size_t)nv * BS;
     const size_t cap = 6 * (size_t)n * nv;
-    if (used + (size_t)nv * BS > cap) return EDA_ERR_INVALID_ARG;
-    const size_t pcap = cap - used;
-    EDA_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int), s));
+    if ((size_t)nv * BS * 2 > cap) return EDA_ERR_INVALID_ARG;
+    const size_t pcap = cap - (size_t)nv * BS;
     for (const auto& cl : big) {
         const int q = cl.first, end = cl.second;
         double* Zq = Z + (size_t)q * ldz;
@@ -1219,18 +1251,11 @@ int symeig_orth_clusters(int n, int nv, const double* w, double* Z, int ldz, Sym
                 EDA_TRY(gemm_tn_f64(n, prev, bs, 1.0, Zq, ldz, Zj, ldz, 0.0, C, prev, part, pcap, s));
                 EDA_TRY(gemm_nn_f64(n, prev, bs, -1.0, Zq, ldz, C, prev, 1.0, Zj, ldz, Zj, ldz, s));
             }
-            for (int pass = 0; pass < 2; ++pass) {
-                EDA_TRY(syrk_f64(n, bs, 1.0, Zj, ldz, 0.0, G, bs, part, pcap, s));
-                EDA_TRY(chol_inv_small(bs, G, bs, Ri, 1e-28, 0.0, st, nullptr, s));
-                EDA_TRY(gemm_nn_f64(n, bs, bs, 1.0, Zj, ldz, Ri, bs, 0.0, nullptr, 0, T, n, s));
-                EDA_TRY(copy_mat_f64(n, bs, T, n, Zj, ldz, s));
-            }
+            k_cluster_block_cgs2<<<1, 512, 0, s>>>(n, Zj, ldz, bs);
+            EDA_LAUNCHED();
         }
     }
-    int sth = 0;
-    EDA_CUDA_TRY(cudaMemcpyAsync(&sth, st, sizeof(int), cudaMemcpyDeviceToHost, s));
-    EDA_CUDA_TRY(cudaStreamSynchronize(s));
-    return (sth & ST_RANKLOSS) ? kClusterRedo : EDA_OK;
+    return EDA_OK;
 }
 
 // Householder back-transformation of the tridiagonal eigenvectors Z (reflectors still in ws).

@@ -17,7 +17,7 @@
 // hi and lo per step, each K-step a 32-byte advance of the descriptor start inside the swizzle
 // atom) and commits each stage to the stage's "empty" mbarrier; the four warps read the 128 x N
 // FP32 accumulator out of tensor memory at the end. Every wait is bounded (ST_TIMEOUT on give-up).
-#include "eda_internal.cuh"
+#include "tc_ptx.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -26,119 +26,48 @@
 
 namespace eda {
 
+using namespace tc;
+
+// ---- tensor maps ------------------------------------------------------------------------------------------------
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D bf16 tensor: inner extent `inner` (contiguous, a multiple of 64), `outer` rows of stride `ld`
+// elements; box of 64 inner elements (128 bytes) x `box_rows` rows, 128-byte swizzle; reads outside
+// the extents return zeros.
+namespace tc {
+int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_rows) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return EDA_ERR_CUDA;
+    if (inner % TC_KS || ld % TC_KS || (reinterpret_cast<uintptr_t>(base) & 15)) return EDA_ERR_INVALID_ARG;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {TC_KS, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? EDA_OK : EDA_ERR_CUDA;
+}
+}  // namespace tc
+
 namespace {
-
-constexpr int TC_M = 128;        // MMA rows (tensor-memory lanes)
-constexpr int TC_KS = 64;        // K per stage (4 MMAs of K = 16)
-constexpr int TC_STAGES = 4;
-constexpr long long TC_SPIN = 1LL << 24;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(mbar)), "r"(parity)
-        : "memory");
-    return ok;
-}
-// bounded wait; returns false (and records the timeout) when it gives up
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int* status) {
-    long long it = 0;
-    while (!mbar_try_wait(mbar, parity)) {
-        if (++it > TC_SPIN) {
-            atomicOr(status, ST_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(mbar))
-        : "memory");
-}
-// Contiguous global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-        : "memory");
-}
-// Programmatic dependent launch: wait for the preceding grid (and, transitively, all earlier work
-// in the stream) to complete; allow the next grid to start its independent prologue.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor for a K-major operand in the 128-byte-swizzled layout: start
-// address, leading-dimension offset (unused inside one swizzle atom, encoded 1), stride-dimension
-// offset 1024 bytes (between 8-row groups), version 1, layout type 2 (128-byte swizzle).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-// Instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Pre-tiled operand layout in HBM: the operand is cut into 128-row x 64-element tiles, each stored as
-// one contiguous 16 KB block that is byte-for-byte the 128-byte-swizzled shared-memory image (row rr
-// at rr * 128 bytes, 16-byte chunk c at chunk c ^ (rr mod 8)); tiles of one 128-row band follow each
-// other along K (kbs tiles per band). A stage of the main loop is then one contiguous bulk copy.
-__host__ __device__ __forceinline__ int64_t tile_off(int64_t r, int64_t kk, int kbs) {
-    const int64_t rt = r >> 7, rr = r & 127, kb = kk >> 6, kc = kk & 63;
-    const int64_t c = kc >> 3, e = kc & 7;
-    return ((rt * kbs + kb) << 13) + rr * 64 + ((c ^ (rr & 7)) << 3) + e;
-}
 
 // The ring; every tile starts on a 1024-byte boundary (the swizzle pattern repeats every 8 rows of
 // 128 bytes), which holds because the struct is placed on such a boundary and every member size is a
@@ -495,43 +424,6 @@ __global__ void k_tile_bf16(int64_t d, int m, const double* __restrict__ H, int 
         if (r < d && kk < m) v = H[kk * d + r];
     }
     out[e] = __float2bfloat16_rn((float)v);
-}
-
-// ---- tensor maps ------------------------------------------------------------------------------------------------
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encoder() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-        cudaGetLastError();
-    });
-    return fn;
-}
-
-// 2-D bf16 tensor: inner extent `inner` (contiguous, a multiple of 64), `outer` rows of stride `ld`
-// elements; box of 64 inner elements (128 bytes) x `box_rows` rows, 128-byte swizzle; reads outside
-// the extents return zeros.
-int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_rows) {
-    EncodeTiledFn enc = encoder();
-    if (!enc) return EDA_ERR_CUDA;
-    if (inner % TC_KS || ld % TC_KS || (reinterpret_cast<uintptr_t>(base) & 15)) return EDA_ERR_INVALID_ARG;
-    const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {ld * 2};
-    const cuuint32_t box[2] = {TC_KS, box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? EDA_OK : EDA_ERR_CUDA;
 }
 
 // Launch with programmatic stream serialisation: the kernel may start while the preceding kernel of

@@ -156,7 +156,8 @@ template <class T>
 int m_apply_t(eda_ctx* h, int b, const T* X, int64_t ldx, T* Y, int64_t ldy, T* tmp, double* P, double* Q,
               void* partial, size_t partial_cap, cudaStream_t s, bool allow_composed = true) {
     ProfScope prof("m_apply", s);
-    if (std::is_same<T, double>::value && allow_composed && h->cfg.m_form == 1 && h->GWB)
+    if (std::is_same<T, double>::value && allow_composed && (h->cfg.m_form == 1 || h->cfg.prec == EDA_F64_TC) &&
+        h->GWB)
         return m_apply_composed(h, b, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<double*>(Y), ldy, P,
                                 Q, nullptr, static_cast<double*>(partial), partial_cap, s);
     const int64_t d = h->d;
@@ -354,7 +355,15 @@ int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY
     const int n = (int)h->n, k = h->k, nk = n + k;
     ProfScope prof("m_apply_composed", s, 4.0 * d * nk * p + 2.0 * p * (3.0 * n * n + 2.0 * n * k + k * k),
                    8.0 * (2.0 * d * nk + 3.0 * d * p));
-    EDA_TRY(gemm_tn_f64(d, nk, p, 1.0, h->HW, d, Y, ldy, 0.0, PQ, nk, part, pcap, s));
+    const bool tc = h->cfg.prec == EDA_F64_TC && h->ozblock;
+    if (tc) {
+        // FP64-accurate sweeps on the tensor cores (error-free splitting), 32 columns at a time
+        for (int c0 = 0; c0 < p; c0 += 32)
+            EDA_TRY(oz_gemm(h->ozT, h->oznb, std::min(32, p - c0), Y + (size_t)c0 * ldy, ldy, 1.0, 0.0, nullptr, 0,
+                            PQ + (size_t)c0 * nk, nk, h->status, s));
+    } else {
+        EDA_TRY(gemm_tn_f64(d, nk, p, 1.0, h->HW, d, Y, ldy, 0.0, PQ, nk, part, pcap, s));
+    }
     if (ZtY) EDA_TRY(copy_mat_f64(nk, p, PQ, nk, ZtY, nk, s));   // keep Z^T y (coordinates) for the caller
     double* Pw = PQ;
     double* Qb = PQ + n;
@@ -366,6 +375,12 @@ int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY
     EDA_TRY(gemm_small_f64(false, false, k, p, k, 1.0, h->KB, k, Qb, nk, 0.0, Ub, nk, s));   // v
     EDA_TRY(gemm_small_f64(false, false, n, p, k, 1.0, h->GWB, n, Ub, nk, 1.0, Pw, nk, s));  // H_W^T y2
     EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->KW, n, Pw, nk, 1.0, Uw, nk, s));   // u1 + u3
+    if (tc) {
+        for (int c0 = 0; c0 < p; c0 += 32)
+            EDA_TRY(oz_gemm(h->ozN, h->oznb, std::min(32, p - c0), U + (size_t)c0 * nk, nk, 1.0, 1.0,
+                            Y + (size_t)c0 * ldy, ldy, MY + (size_t)c0 * ldm, ldm, h->status, s));
+        return EDA_OK;
+    }
     EDA_TRY(gemm_nn_f64(d, nk, p, 1.0, h->HW, d, U, nk, 1.0, Y, ldy, MY, ldm, s));
     return EDA_OK;
 }
@@ -691,7 +706,8 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
 
 int solve_impl(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vout, double* lambda, double* Yout,
                eda_solve_info* info, cudaStream_t s) {
-    if (h->cfg.prec == EDA_F64) return solve_t<double>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
+    if (h->cfg.prec == EDA_F64 || h->cfg.prec == EDA_F64_TC)
+        return solve_t<double>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
     if (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16)
         return solve_t<float>(h, t, tol, V0, b0, Vout, lambda, Yout, info, s);
     return EDA_ERR_INVALID_ARG;

@@ -19,7 +19,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libeda_gb300.so")
 
-EDA_F64, EDA_F32, EDA_BF16, EDA_BF16X2 = 0, 1, 2, 3
+EDA_F64, EDA_F32, EDA_BF16, EDA_BF16X2, EDA_F64_TC = 0, 1, 2, 3, 4
 OP_SW, OP_SB, OP_M = 0, 1, 2
 
 STATUS = {
