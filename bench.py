@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=HEADLINE, choices=list(synth.CONFIGS) + ["batched64"])
     ap.add_argument("--small-steps", type=int, default=20, help="steps of the d4096_k40 leg (0: skip it)")
+    ap.add_argument("--prec", default="tc", choices=["tc", "f64"],
+                    help="tc: FP64 solver whose sweeps over [H_W H_B], Grams and recovery run as FP64-accurate "
+                         "tensor-core products (error-free splitting); f64: plain FP64 throughout")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the plain FP64 comparison leg on the same workload (0: skip it)")
     ap.add_argument("--workers", type=int, default=32, help="host workers of the batched solve")
     ap.add_argument("--m-form", type=int, default=1, choices=[0, 1],
                     help="FP64 M-apply: 0 = the three products one after another, 1 = their composed form")
@@ -138,7 +143,10 @@ def workload_config(args, name=None):
     return {"workload": f"{name}: d={c['d']}, k={c['k']}, n_j={c['n_j']} (n={c['k'] * c['n_j']}), "
                         f"t={c['t']}, b={c['b']}, tau={c['tau']}, tol={args.tol}",
             "l2": "flushed (256 MB write) before every step; the samples (d n 8 bytes) are read from HBM",
-            "precision": "plain FP64 sweeps and small steps",
+            "precision": ("FP64 solver; the products with [H_W H_B] (Grams, M-apply sweeps, recovery) as FP64-accurate "
+                          "tensor-core products: operands split exactly into 7 bf16 digit planes, exact integer "
+                          "accumulation" if getattr(args, "prec", "f64") == "tc" else
+                          "plain FP64 sweeps and small steps"),
             "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form]}
 
 
@@ -415,7 +423,10 @@ def run_gpu_batched(args, rank, world, local_rank):
     return line, ps
 
 
-def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e=True):
+PRECS = {"tc": 4, "f64": 0}   # eda_prec codes: EDA_F64_TC, EDA_F64
+
+
+def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e=True, prec="tc"):
     """W untimed and K timed steps of one workload (build, solve, recovery, projection of the held-out
     set) with CUDA events on the launching stream, the L2 flushed before every step; optional end-to-end
     steps from pinned host buffers. Returns the per-step ms (max over ranks), the region timers read
@@ -428,7 +439,7 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     X = torch.from_numpy(p.X).to(dev)
     lab = torch.from_numpy(p.labels).to(dev)
     Xt = torch.from_numpy(p.Xtest).to(dev)
-    cfg = eda.config(block_b=c["b"], tau=c["tau"], check_every=1, m_form=m_form)
+    cfg = eda.config(prec=PRECS[prec], block_b=c["b"], tau=c["tau"], check_every=1, m_form=m_form)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -470,8 +481,8 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     launches = eda.kernel_launches() - launches0
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dev)
     regions = {r: eda.profile_read(r) for r in REGIONS}
-    work = {r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "m_apply_composed", "exp_apply_w",
-                                             "tridiag")}
+    work = {r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "oz_gemm", "m_apply_composed",
+                                             "exp_apply_w", "tridiag")}
     out = dict(p=p, c=c, ms=ms, regions=regions, work=work, infos=infos, launches=launches, clocks=clk,
                wall=wall)
     if not e2e:
@@ -520,7 +531,7 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     return out
 
 
-REGIONS = ("gram", "tn_f64", "nn_f64", "cluster_orth", "exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
+REGIONS = ("gram", "tn_f64", "nn_f64", "oz_gemm", "cluster_orth", "exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
            "tridiag", "bisect", "invit", "backtransform", "symeig", "lanczos", "phi_squaring", "rr", "reorth",
            "refine")
 
@@ -560,6 +571,12 @@ def roofline_of(name, r, steps):
             "nn_f64": {"kernel": "k_gemm_nn<*, double> (every tall A B product of the step)",
                        "achieved_tflops": rate(nn_flops, nn_ms), "launches": nn_calls,
                        "ms_per_step": nn_ms / steps},
+            "oz_gemm": {"kernel": "k_oz_gemm (+ splits of the narrow operand, reduction): FP64-accurate "
+                                  "tensor-core products of the split Z (Grams, sweeps, recovery)",
+                        "achieved_fp64_equivalent_tflops": rate(r["work"]["oz_gemm"][0], r["regions"]["oz_gemm"][0]),
+                        "achieved_gbs": (r["work"]["oz_gemm"][1] / (r["regions"]["oz_gemm"][0] / 1e3) / 1e9
+                                         if r["regions"]["oz_gemm"][0] > 0 else None),
+                        "launches": r["regions"]["oz_gemm"][1], "ms_per_step": r["regions"]["oz_gemm"][0] / steps},
         },
     }
 
@@ -572,7 +589,8 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    r = time_workload(args.workload, args.steps, args.warmup, args.m_form, args.tol, dev, flush, rank, world)
+    r = time_workload(args.workload, args.steps, args.warmup, args.m_form, args.tol, dev, flush, rank, world,
+                      prec=args.prec)
     p, c = r["p"], r["c"]
     ms = r["ms"]
     regions = r["regions"]
@@ -603,12 +621,22 @@ def run_gpu(args, rank, world, local_rank):
     }
     small = None
     if args.small_steps > 0 and args.workload != SMALL and rank == 0:
-        rs = time_workload(SMALL, args.small_steps, 5, args.m_form, args.tol, dev, flush, rank, 1)
+        rs = time_workload(SMALL, args.small_steps, 5, args.m_form, args.tol, dev, flush, rank, 1, prec=args.prec)
         small = {"workload": workload_config(args, SMALL)["workload"], "ms_per_step": rs["ms"], "unit": "ms",
                  "e2e_ms": rs["e2e"]["value"], "gpu_launches_per_step": rs["launches"] / args.small_steps,
                  "roofline": roofline_of(SMALL, rs, args.small_steps),
                  "solve_info": {kk: rs["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols",
                                                                    "refills", "max_relres_est")}}
+    fp64_leg = None
+    if args.prec != "f64" and args.fp64_steps > 0 and rank == 0:
+        # the plain FP64 GPU solver on the same workload, for the speedup at equal accuracy (both forms meet
+        # the same oracle parity bars in the GPU tests)
+        rf = time_workload(args.workload, args.fp64_steps, 1, args.m_form, args.tol, dev, flush, rank, 1, e2e=False,
+                           prec="f64")
+        fp64_leg = {"ms_per_step": rf["ms"], "speedup_of_tc_over_fp64": rf["ms"] / ms,
+                    "breakdown_ms_per_step": {k: v[0] / args.fp64_steps for k, v in rf["regions"].items()},
+                    "solve_info": {kk: rf["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols",
+                                                                     "refills", "refine_iters")}}
     exp_leg = None
     if not args.no_exp_apply and rank == 0:
         exp_leg = exp_apply_leg(dev, flush, args.exp_apply_reps)
@@ -626,6 +654,7 @@ def run_gpu(args, rank, world, local_rank):
         "exp_apply_fp64": exp_apply_fp64,
         "exp_apply_bf16": exp_leg,
         "small_config": small,
+        "fp64_plain": fp64_leg,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in regions.items()},
         "solve_info": {kk: r["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols", "refills",
                                                          "refine_iters", "max_relres_est")},

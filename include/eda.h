@@ -79,7 +79,11 @@ typedef struct {
                                  /* form one after another (Eq. (3.16)); 1 = their composed  */
                                  /* form M = I + Z C Z^T, Z = [H_W H_B] (Theorem 3.1 for each  */
                                  /* factor; two sweeps over Z instead of six over H_W, H_B)   */
-    int32_t reserved[6];
+    int32_t wait_limit;          /* polls of a grid-wide barrier wait (the cooperative        */
+                                 /* symmetric eigensolver, n > 512) before it gives up and    */
+                                 /* the call returns EDA_ERR_TIMEOUT; <= 0: the default,      */
+                                 /* 20,000,000 (about 1-2 s)                                  */
+    int32_t reserved[5];
 } eda_config;
 
 typedef struct {
@@ -101,7 +105,7 @@ typedef struct {
 typedef struct eda_ctx* eda_handle;
 
 /* Fill *cfg with defaults: F64, b = 8, m_max = 0 (n + k + b), check_every = 1,
- * tau = 10, c2 = 0, seed = 1, true_residuals = 0, m_form = 0. */
+ * tau = 10, c2 = 0, seed = 1, true_residuals = 0, m_form = 0, wait_limit = 0. */
 int eda_config_default(eda_config* cfg);
 
 /* Build a handle from labelled samples (Section 1; Algorithm 2 step 1 with the

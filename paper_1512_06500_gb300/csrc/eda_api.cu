@@ -85,6 +85,9 @@ constexpr double kLmaxAccept = 8.0;  // accept its theta_1 when its residual is 
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+int tc_operands(eda_ctx* h, cudaStream_t s);
+int tc_grams(eda_ctx* h, cudaStream_t s);
+
 int read_status(eda_ctx* h, cudaStream_t s, int* out) {
     EDA_CUDA_TRY(cudaMemcpyAsync(out, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     EDA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -164,7 +167,7 @@ int alloc_handle(eda_ctx* h, bool with_labels) {
     h->KB = a.take<double>(k * k);
     h->status = a.take<int>(64);
     unsigned* bar = a.take<unsigned>(64);
-    h->bar = GridBarrier{bar, bar + 32};
+    h->bar = GridBarrier{bar, bar + 32, h->cfg.wait_limit > 0 ? (long long)h->cfg.wait_limit : kGridSpinDefault};
     h->build_arena_off = a.used;
     if (!h->KB || !bar) return EDA_ERR_OOM;
     EDA_CUDA_TRY(cudaMemset(h->status, 0, 256));
@@ -413,7 +416,21 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     AuxStream aux;
     double* partB = nullptr;
     size_t pcapB = 0;
-    if (by_squaring) {
+    const bool tc = h->cfg.prec == EDA_F64_TC;
+    if (tc) {
+        // every Gram as a block of Z^T Z on the tensor cores, from the split Z the sweeps use as well
+        EDA_TRY(tc_operands(h, s));
+        EDA_TRY(tc_grams(h, s));
+        EDA_TRY(check_finite_f64(n, n, h->GW, n, h->status, s));
+        EDA_TRY(check_finite_f64(k, k, h->GB, k, h->status, s));
+        if (by_squaring) {
+            EDA_TRY(aux.open(s));
+            pcapB = std::max<size_t>(1u << 17, 64 * (size_t)k * k);
+            partB = scratch.take<double>(pcapB);
+            if (!partB) return EDA_ERR_OOM;
+            EDA_TRY(aux.fork());
+        }
+    } else if (by_squaring) {
         EDA_TRY(aux.open(s));
         pcapB = std::max<size_t>(1u << 17, 64 * (size_t)k * k);
         partB = scratch.take<double>(pcapB);
@@ -482,20 +499,6 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
     }
     if (cross && !by_squaring) EDA_TRY(ensure_cross_gram(h, part, pcap, s));
-    if (h->cfg.prec == EDA_F64_TC) {
-        // Z = [H_W H_B] (d x (n + k), one allocation) split into bf16 digit planes twice: scaled per column
-        // for Z^T Y and per row for Z U; the narrow staging sized for both reduction lengths
-        const int nk = n + k;
-        const size_t bT = align256(oz_operand_bytes(nk, d)), bN = align256(oz_operand_bytes(d, nk));
-        const size_t bS = align256(oz_narrow_bytes(std::max<int64_t>(d, nk), sm_count(), nk));
-        void* p = nullptr;
-        EDA_CUDA_TRY(cudaMalloc(&p, bT + bN + bS));
-        h->ozblock = p;
-        char* c = static_cast<char*>(p);
-        EDA_TRY(oz_operand_make(h->HW, d, nk, d, true, c, &h->ozT, s));
-        EDA_TRY(oz_operand_make(h->HW, d, d, nk, false, c + bT, &h->ozN, s));
-        EDA_TRY(oz_narrow_make(std::max<int64_t>(d, nk), sm_count(), nk, c + bT + bN, &h->oznb));
-    }
     if (h->cfg.prec == EDA_BF16) {
         // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
         // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)
@@ -530,6 +533,57 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     int st = 0;
     EDA_TRY(read_status(h, s, &st));
     return status_to_code(st);
+}
+
+// prec = EDA_F64_TC: Z = [H_W H_B] (d x (n + k), one allocation) split into bf16 digit planes twice, scaled
+// per column for Z^T Y and per row for Z U, and the narrow staging sized for both reduction lengths.
+int tc_operands(eda_ctx* h, cudaStream_t s) {
+    const int64_t d = h->d;
+    const int nk = (int)h->n + h->k;
+    const size_t bT = align256(oz_operand_bytes(nk, d)), bN = align256(oz_operand_bytes(d, nk));
+    const size_t bS = align256(oz_narrow_bytes(std::max<int64_t>(d, nk), sm_count(), nk));
+    void* p = nullptr;
+    EDA_CUDA_TRY(cudaMalloc(&p, bT + bN + bS));
+    h->ozblock = p;
+    char* c = static_cast<char*>(p);
+    EDA_TRY(oz_operand_make(h->HW, d, nk, d, true, c, &h->ozT, s));
+    EDA_TRY(oz_operand_make(h->HW, d, d, nk, false, c + bT, &h->ozN, s));
+    EDA_TRY(oz_narrow_make(std::max<int64_t>(d, nk), sm_count(), nk, c + bT + bN, &h->oznb));
+    return EDA_OK;
+}
+
+// prec = EDA_F64_TC: the Grams G_W, G_B and the cross Grams G_WB, G_BW as the blocks of Z^T Z, computed with
+// the FP64-accurate tensor-core products 32 columns at a time. A column of Z has the same scale and digits
+// as an operand of either side, so Z^T Z comes out exactly symmetric.
+int tc_grams(eda_ctx* h, cudaStream_t s) {
+    const int64_t d = h->d;
+    const int n = (int)h->n, k = h->k, nk = n + k;
+    ProfScope prof("gram", s, (double)d * nk * (nk + 1.0), 8.0 * (double)d * nk);
+    double* GZ = nullptr;
+    EDA_CUDA_TRY(cudaMalloc(&GZ, (size_t)nk * nk * 8));
+    int rc = EDA_OK;
+    for (int j0 = 0; j0 < nk && rc == EDA_OK; j0 += 32)
+        rc = oz_gemm(h->ozT, h->oznb, std::min(32, nk - j0), h->HW + (size_t)j0 * d, d, 1.0, 0.0, nullptr, 0,
+                     GZ + (size_t)j0 * nk, nk, h->status, s);
+    if (rc == EDA_OK && !h->GWB) {
+        const size_t xb = ((size_t)n * k * 8 + 255) & ~size_t(255);
+        void* xp = nullptr;
+        if (cudaMalloc(&xp, 2 * xb) != cudaSuccess) {
+            cudaGetLastError();
+            rc = EDA_ERR_OOM;
+        } else {
+            h->xblock = xp;
+            h->GWB = static_cast<double*>(xp);
+            h->GBW = reinterpret_cast<double*>(static_cast<char*>(xp) + xb);
+        }
+    }
+    if (rc == EDA_OK) rc = copy_mat_f64(n, n, GZ, nk, h->GW, n, s);
+    if (rc == EDA_OK) rc = copy_mat_f64(k, k, GZ + (size_t)n * nk + n, nk, h->GB, k, s);
+    if (rc == EDA_OK) rc = copy_mat_f64(n, k, GZ + (size_t)n * nk, nk, h->GWB, n, s);
+    if (rc == EDA_OK) rc = copy_mat_f64(k, n, GZ + n, nk, h->GBW, k, s);
+    cudaStreamSynchronize(s);   // GZ is released below
+    cudaFree(GZ);
+    return rc;
 }
 
 bool valid_cfg(const eda_config& c) {

@@ -82,10 +82,13 @@ struct Arena {
     void reset() { used = 0; }
 };
 
-// Grid barrier state in device memory (zeroed at allocation).
+// Grid barrier state in device memory (zeroed at allocation) and the number of polls a wait makes
+// before it gives up (ST_TIMEOUT).
+constexpr long long kGridSpinDefault = 20000000;   // about 1-2 s of polling
 struct GridBarrier {
     unsigned int* count;
     unsigned int* gen;
+    long long spin_limit = kGridSpinDefault;
 };
 
 // ---------------------------------------------------------------- dense FP64 ops

@@ -22,7 +22,6 @@ namespace eda {
 namespace {
 
 constexpr int TRI_THREADS = 256;
-constexpr long long SPIN_LIMIT = 20000000;   // ~1-2 s of polling before a barrier gives up
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -49,7 +48,7 @@ __device__ void grid_sync(GridBarrier bar, int* status) {
         } else {
             long long it = 0;
             while (ld_acquire_u32(bar.gen) == g) {
-                if (++it > SPIN_LIMIT) {
+                if (++it > bar.spin_limit) {
                     atomicOr(status, ST_TIMEOUT);
                     break;
                 }

@@ -240,7 +240,8 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     // Rayleigh-Ritz schedule: the first check once the basis has t + 2b columns (block Lanczos needs
     // about two blocks beyond the t wanted directions; an earlier check costs a small eigensolve and
     // rarely succeeds); later checks at the basis width where the geometric rate seen between the last
-    // two checks predicts convergence (never sooner than check_every blocks, always at the last block).
+    // two checks predicts convergence (never sooner than check_every blocks, never more than a quarter of
+    // the current basis width later, always at the last block).
     int next_check = t + 2 * b;
     int prev_check_cols = 0;
     double prev_check_rel = 0.0;
@@ -322,6 +323,10 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
                 const double need = std::log(tol / st.max_rel) / std::log(rate);           // blocks to go
                 if (std::isfinite(need) && need > 1.0) gap = std::max(gap, b * (int)std::floor(0.8 * need));
             }
+            // the rate comes from residual estimates that refilled directions make noisy: never let it push the
+            // next check further than a quarter of the basis built so far (an extra check costs one small
+            // eigensolve, a missed one whole blocks of M-applies and reorthogonalisation)
+            gap = std::min(gap, std::max(b * h->cfg.check_every, (cols / 4) / b * b));
             prev_check_cols = cols;
             prev_check_rel = st.max_rel;
             next_check = cols + gap;
@@ -634,6 +639,22 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
         EDA_TRY(gemm_nn_f64(d, n, t, 1.0, h->HW, d, w.PQ, n, 1.0, w.Y, d, w.Z2, d, s));
         k_reverse_cols<<<ceil_div((int64_t)d * t, 256), 256, 0, s>>>(d, t, w.Z2, d, w.Xt, d);
         EDA_LAUNCHED();
+    } else if (h->cfg.prec == EDA_F64_TC && h->ozblock) {
+        // the same product with the FP64-accurate tensor-core sweeps: H_W is the first n columns of the
+        // split Z (the first n rows of its column-scaled operand, the first n of the reduction index of the
+        // row-scaled one; the digits beyond meet zero rows of the narrow operand)
+        ProfScope prof("exp_apply_w", s, 4.0 * d * n * t + 2.0 * (double)n * n * t, 8.0 * (2.0 * d * n + 3.0 * d * t));
+        OzOperand AT = h->ozT, AN = h->ozN;
+        AT.M = n;
+        AT.mtiles = ceil_div(n, 128);
+        AN.K = n;
+        for (int c0 = 0; c0 < t; c0 += 32)
+            EDA_TRY(oz_gemm(AT, h->oznb, std::min(32, t - c0), w.Y2 + (size_t)c0 * d, d, 1.0, 0.0, nullptr, 0,
+                            w.P + (size_t)c0 * n, n, h->status, s));
+        EDA_TRY(gemm_small_f64(false, false, n, t, n, 1.0, h->KW, n, w.P, n, 0.0, w.Q, n, s));
+        for (int c0 = 0; c0 < t; c0 += 32)
+            EDA_TRY(oz_gemm(AN, h->oznb, std::min(32, t - c0), w.Q + (size_t)c0 * n, n, 1.0, 1.0,
+                            w.Y2 + (size_t)c0 * d, d, w.Xt + (size_t)c0 * d, d, h->status, s));
     } else {
         EDA_TRY(exp_apply<double>(d, h->HW, h->KW, n, "exp_apply_w", t, w.Y2, d, w.Xt, d, w.P, w.Q, w.part, w.pcap,
                                   s));

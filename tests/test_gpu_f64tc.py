@@ -138,3 +138,21 @@ def test_solve_tc_d65536_k200_matches_oracle(eda):
     ref = O.eda(p.X, p.labels, p.k, c["t"], tau=c["tau"], tier="projected")
     s, info = _solve_compare(eda, p, c["t"], c["b"], c["tau"], 1e-6, ref)
     print(f"\nd65536_k200 (tensor-core FP64 sweeps): sin {s:.2e}, blocks {info['iters']}, refills {info['refills']}")
+
+
+@pytest.mark.parametrize("d,k,nj", [(777, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1]), (4096, 40, 5), (2000, 70, 4)])
+def test_grams_tc_match_oracle(eda, d, k, nj):
+    # the build's Grams as blocks of Z^T Z from the split Z: element by element within the FP64 bound of a
+    # length-d dot product, exactly symmetric, and the cross Gram G_WB enters the composed M-apply (checked
+    # above through M); n + k = 310 at the last size takes the eigenpair route for K
+    p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=640 + d)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(prec=eda.EDA_F64_TC, block_b=4, tau=10.0)) as h:
+        g = h.factors()
+        for key, H in (("GW", f["HW"]), ("GB", f["HB"])):
+            G = g[key].cpu().numpy()
+            Gr = O.gram(H)
+            assert np.array_equal(G, G.T), key
+            assert np.abs(G - Gr).max() <= 64 * d * EPS * np.abs(Gr).max(), key
+        c2 = _oracle_c2(f, 10.0)
+        assert abs(h.c2 - c2) <= 1e-13 * c2
