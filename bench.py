@@ -663,8 +663,9 @@ def run_gpu(args, rank, world, local_rank):
     return line, p, c
 
 
-def profile_build(name):
-    """Small driver for ncu: one FP64 build of the named workload, nothing else."""
+def profile_build(name, prec="f64"):
+    """Small driver for ncu: one build of the named workload (FP64, or the tensor-core FP64 mode whose Grams
+    are k_oz_gemm launches), nothing else."""
     import torch
     from paper_1512_06500_gb300 import build_lib, eda
 
@@ -673,9 +674,9 @@ def profile_build(name):
     p = synth.config_problem(name)
     X = torch.from_numpy(p.X).cuda()
     lab = torch.from_numpy(p.labels).cuda()
-    h = eda.build(X, lab, p.k, eda.config(block_b=c["b"], tau=c["tau"], m_form=1))
+    h = eda.build(X, lab, p.k, eda.config(prec=PRECS[prec], block_b=c["b"], tau=c["tau"], m_form=1))
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "profile-build", "workload": name, "c2": h.c2}))
+    print(json.dumps({"mode": "profile-build", "workload": name, "prec": prec, "c2": h.c2}))
     h.close()
 
 
@@ -685,7 +686,7 @@ def main():
         profile_exp_apply(args.profile_exp_apply)
         return
     if args.profile_build:
-        profile_build(args.profile_build)
+        profile_build(args.profile_build, args.prec)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
