@@ -58,7 +58,9 @@ typedef enum {
 typedef enum {
     EDA_OP_SW = 0,               /* Y = exp(alpha S_W) X                                     */
     EDA_OP_SB = 1,               /* Y = exp(alpha S_B) X                                     */
-    EDA_OP_M = 2                 /* Y = M X with the handle's c^2 (alpha ignored)            */
+    EDA_OP_M = 2,                /* Y = M X with the handle's c^2 (alpha ignored)            */
+    EDA_OP_N = 3                 /* Y = exp(-c^2 S_W) exp(c^2 S_B) X, the nonsymmetric form  */
+                                 /* of Eq. (3.1) (alpha ignored; FP64 io only)               */
 } eda_op;
 
 typedef struct {
@@ -158,6 +160,22 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
  * FP64 residuals (refine_iters rounds), as the residual estimate cannot see such losses. */
 int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0,
               double* V, double* lambda, double* Y, eda_solve_info* info, void* stream);
+
+/* The t dominant eigenpairs of the nonsymmetric form of the pencil, Eq. (3.1):
+ *     exp(-c^2 S_W) exp(c^2 S_B) x = lambda x,
+ * by block Arnoldi (Section 3.1; Algorithm 2 steps 6A-10A for the products; Algorithm 3 step 5, Arnoldi
+ * form). Each step applies the operator once (two Theorem 3.1 products, as two sweeps over [H_W H_B]);
+ * the basis is kept orthonormal by full reorthogonalisation (as for eda_solve). The Ritz pairs are the
+ * real eigenpairs of the Galerkin condition with test space exp(c^2 S_W) V on the Arnoldi subspace V
+ * (a symmetric-definite projected pencil). There is no recovery step: the Ritz vectors are the
+ * generalized eigenvectors x themselves.
+ *   V      : d x t output, orthonormal basis of the t generalized eigenvectors.
+ *   lambda : t output eigenvalues, descending.
+ * tol bounds ||N x - theta x|| / (theta ||x||) for each pair (from the Arnoldi relation). The handle's
+ * prec selects FP64 or tensor-core FP64 sweeps (EDA_F64, EDA_F64_TC); block size, basis limit, check
+ * schedule and seed come from its configuration. Errors as for eda_solve. */
+int eda_solve_arnoldi(eda_handle h, int32_t t, double tol, double* V, double* lambda, eda_solve_info* info,
+                      void* stream);
 
 /* P = V^T Xq (t x m, column-major, ld t): the projected samples of the
  * nearest-neighbour classifier (Section 3.3, d_ij = ||V^T (x_i - y_j)||).

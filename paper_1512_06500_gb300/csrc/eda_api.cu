@@ -47,6 +47,7 @@ int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t 
             double* Q, double* partial, size_t partial_cap, cudaStream_t s);
 int m_apply_f32(eda_ctx* h, int b, const float* X, int64_t ldx, float* Y, int64_t ldy, float* tmp, double* P,
                 double* Q, double* partial, size_t partial_cap, cudaStream_t s);
+int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, eda_solve_info* info, cudaStream_t s);
 
 namespace {
 // B (k x n) = A^T for A (n x k), both column-major.
@@ -687,7 +688,8 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
     if (io_dtype != EDA_F64 && !(io_dtype == EDA_F32 && (h->cfg.prec == EDA_F32 || h->cfg.prec == EDA_BF16)))
         return EDA_ERR_INVALID_ARG;
     const size_t esz = io_dtype == EDA_F64 ? sizeof(double) : sizeof(float);
-    if (op != EDA_OP_SW && op != EDA_OP_SB && op != EDA_OP_M) return EDA_ERR_INVALID_ARG;
+    if (op != EDA_OP_SW && op != EDA_OP_SB && op != EDA_OP_M && op != EDA_OP_N) return EDA_ERR_INVALID_ARG;
+    if (op == EDA_OP_N && io_dtype != EDA_F64) return EDA_ERR_INVALID_ARG;
     const char* xb = static_cast<const char*>(X);
     const char* yb = static_cast<const char*>(Y);
     const size_t span = ((size_t)(b - 1) * ldx + h->d) * esz;
@@ -722,6 +724,16 @@ int eda_apply_exp(eda_handle h, int32_t op, double alpha, const void* X, void* Y
                                 ldx, P, Q, part, pcap, s);
     }
     if (op == EDA_OP_M) return m_apply(h, b, x, ldx, y, ldx, tmp, P, Q, part, pcap, s);
+    if (op == EDA_OP_N) {
+        EDA_TRY(ensure_n_operators(h, s));
+        // ensure_n_operators may have grown the workspace: take the temporaries again
+        EDA_TRY(eda::ensure_workspace(h, need));
+        Arena a2{static_cast<char*>(h->ws), h->ws_bytes, 0};
+        double* P2 = a2.take<double>((size_t)N * b);
+        double* Q2 = a2.take<double>((size_t)N * b);
+        double* part2 = a2.take<double>(pcap);
+        return n_apply_composed(h, b, x, ldx, y, ldx, P2, Q2, nullptr, part2, pcap, s);
+    }
     // K(alpha) for the requested alpha: rebuild from the stored eigenpairs when alpha differs
     const bool isW = (op == EDA_OP_SW);
     const int m = isW ? (int)h->n : h->k;
@@ -751,6 +763,13 @@ int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0,
               eda_solve_info* info, void* stream) {
     if (!h || !V || !lambda || t < 1 || !(tol > 0.0) || (V0 && b0 < 1)) return EDA_ERR_INVALID_ARG;
     return solve_impl(h, t, tol, V0, b0, V, lambda, Y, info, static_cast<cudaStream_t>(stream));
+}
+
+int eda_solve_arnoldi(eda_handle h, int32_t t, double tol, double* V, double* lambda, eda_solve_info* info,
+                      void* stream) {
+    if (!h || !V || !lambda || t < 1 || !(tol > 0.0)) return EDA_ERR_INVALID_ARG;
+    if (h->cfg.prec != EDA_F64 && h->cfg.prec != EDA_F64_TC) return EDA_ERR_INVALID_ARG;
+    return arnoldi_impl(h, t, tol, V, lambda, info, static_cast<cudaStream_t>(stream));
 }
 
 int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_t xq_dtype, int64_t m, int64_t ldq,
@@ -807,6 +826,7 @@ void eda_destroy(eda_handle h) {
     if (h->kblock) cudaFree(h->kblock);
     if (h->xblock) cudaFree(h->xblock);
     if (h->ozblock) cudaFree(h->ozblock);
+    if (h->nblock) cudaFree(h->nblock);
     if (h->block32) cudaFree(h->block32);
     if (h->block) cudaFree(h->block);
     delete h;

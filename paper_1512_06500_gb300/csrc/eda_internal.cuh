@@ -333,6 +333,10 @@ struct eda_ctx {
     void* ozblock = nullptr;
     eda::OzOperand ozT, ozN;
     eda::OzNarrow oznb;
+    // K(-c^2) and K(+c^2) for H_W, the operators of the nonsymmetric form exp(-c^2 S_W) exp(c^2 S_B) and of
+    // exp(c^2 S_W) (allocated on first use by the Arnoldi solver)
+    void* nblock = nullptr;
+    double *KWm = nullptr, *KWp = nullptr;
     // solve workspace (grown on demand)
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -341,6 +345,17 @@ struct eda_ctx {
 namespace eda {
 // Grow the handle's solve workspace to at least `bytes` (contents are not preserved).
 int ensure_workspace(eda_ctx* h, size_t bytes);
+// The two sweeps over Z = [H_W H_B] of a composed product (FP64, or the tensor-core FP64 products when the
+// handle was built with EDA_F64_TC): PQ = Z^T Y, and OUT = Y + Z U.
+int sweep_zt(eda_ctx* h, int p, const double* Y, int64_t ldy, double* PQ, double* part, size_t pcap, cudaStream_t s);
+int sweep_z(eda_ctx* h, int p, const double* U, const double* Y, int64_t ldy, double* OUT, int64_t ldo,
+            cudaStream_t s);
+// The nonsymmetric operator of Eq. (3.1): NY = exp(-c^2 S_W) exp(c^2 S_B) Y in composed form; PQ, U: (n + k) x p;
+// ZtY ((n + k) x p, optional) receives Z^T Y.
+int n_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* NY, int64_t ldn, double* PQ, double* U,
+                     double* ZtY, double* part, size_t pcap, cudaStream_t s);
+// K(-c^2) and K(+c^2) of H_W (and the cross Grams) for the nonsymmetric form.
+int ensure_n_operators(eda_ctx* h, cudaStream_t s);
 // Form the cross Grams G_WB, G_BW of the handle if they are not there yet.
 int ensure_cross_gram(eda_ctx* h, double* part, size_t pcap, cudaStream_t s);
 }  // namespace eda

@@ -134,21 +134,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             if (first && chunk >= 2 && !(ok = mbar_wait(&sm.accEmpty[set], ((chunk >> 1) - 1) & 1, status))) break;
             const int bslot = s % OZ_BST;
             if (!(ok = mbar_wait(&sm.fullB[bslot], (s / OZ_BST) & 1, status))) break;
+            // descriptors differ only in their start-address field (address / 16): a K step of 16 elements
+            // is +2, the next B plane (4 KB further) +256; computed once per stage and tile
+            const uint64_t bdesc = smem_desc_sw128(smem_u32(sm.B[bslot][0]));
+            const uint32_t dset = tmem + (uint32_t)(set * OZ_SET_COLS);
+#pragma unroll
             for (int a = 0; a < OZ_S; ++a) {
                 const int idx = s * OZ_S + a;
                 const int slot = idx % OZ_AST;
                 if (!(ok = mbar_wait(&sm.fullA[slot], (idx / OZ_AST) & 1, status))) break;
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(sm.A[slot]);
+                const uint64_t adesc = smem_desc_sw128(smem_u32(sm.A[slot]));
+#pragma unroll
                 for (int b = 0; b < OZ_S - a; ++b) {
-                    const uint32_t b0 = smem_u32(sm.B[bslot][b]);
-                    const uint32_t col = (uint32_t)(set * OZ_SET_COLS + (a + b) * OZ_N);
+                    const uint32_t dcol = dset + (uint32_t)((a + b) * OZ_N);
 #pragma unroll
                     for (int kk = 0; kk < TC_KS / 16; ++kk) {
                         // the first product of level a + b in this chunk (a = 0, first K step) overwrites
-                        const uint32_t acc = (first && a == 0 && kk == 0) ? 0u : 1u;
-                        mma_bf16(tmem + col, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
-                                 acc);
+                        const uint32_t acc = (a == 0 && kk == 0 && first) ? 0u : 1u;
+                        mma_bf16(dcol, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(b * 256 + kk * 2), idesc, acc);
                     }
                 }
                 mma_commit(&sm.emptyA[slot]);

@@ -360,15 +360,7 @@ int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY
     const int n = (int)h->n, k = h->k, nk = n + k;
     ProfScope prof("m_apply_composed", s, 4.0 * d * nk * p + 2.0 * p * (3.0 * n * n + 2.0 * n * k + k * k),
                    8.0 * (2.0 * d * nk + 3.0 * d * p));
-    const bool tc = h->cfg.prec == EDA_F64_TC && h->ozblock;
-    if (tc) {
-        // FP64-accurate sweeps on the tensor cores (error-free splitting), 32 columns at a time
-        for (int c0 = 0; c0 < p; c0 += 32)
-            EDA_TRY(oz_gemm(h->ozT, h->oznb, std::min(32, p - c0), Y + (size_t)c0 * ldy, ldy, 1.0, 0.0, nullptr, 0,
-                            PQ + (size_t)c0 * nk, nk, h->status, s));
-    } else {
-        EDA_TRY(gemm_tn_f64(d, nk, p, 1.0, h->HW, d, Y, ldy, 0.0, PQ, nk, part, pcap, s));
-    }
+    EDA_TRY(sweep_zt(h, p, Y, ldy, PQ, part, pcap, s));
     if (ZtY) EDA_TRY(copy_mat_f64(nk, p, PQ, nk, ZtY, nk, s));   // keep Z^T y (coordinates) for the caller
     double* Pw = PQ;
     double* Qb = PQ + n;
@@ -380,14 +372,33 @@ int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY
     EDA_TRY(gemm_small_f64(false, false, k, p, k, 1.0, h->KB, k, Qb, nk, 0.0, Ub, nk, s));   // v
     EDA_TRY(gemm_small_f64(false, false, n, p, k, 1.0, h->GWB, n, Ub, nk, 1.0, Pw, nk, s));  // H_W^T y2
     EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->KW, n, Pw, nk, 1.0, Uw, nk, s));   // u1 + u3
-    if (tc) {
+    return sweep_z(h, p, U, Y, ldy, MY, ldm, s);
+}
+
+// PQ ((n + k) x p) = Z^T Y, Z = [H_W H_B]: the first sweep of a composed product; FP64-accurate tensor-core
+// products (error-free splitting, 32 columns at a time) for prec EDA_F64_TC, FP64 otherwise.
+int sweep_zt(eda_ctx* h, int p, const double* Y, int64_t ldy, double* PQ, double* part, size_t pcap, cudaStream_t s) {
+    const int nk = (int)h->n + h->k;
+    if (h->cfg.prec == EDA_F64_TC && h->ozblock) {
         for (int c0 = 0; c0 < p; c0 += 32)
-            EDA_TRY(oz_gemm(h->ozN, h->oznb, std::min(32, p - c0), U + (size_t)c0 * nk, nk, 1.0, 1.0,
-                            Y + (size_t)c0 * ldy, ldy, MY + (size_t)c0 * ldm, ldm, h->status, s));
+            EDA_TRY(oz_gemm(h->ozT, h->oznb, std::min(32, p - c0), Y + (size_t)c0 * ldy, ldy, 1.0, 0.0, nullptr, 0,
+                            PQ + (size_t)c0 * nk, nk, h->status, s));
         return EDA_OK;
     }
-    EDA_TRY(gemm_nn_f64(d, nk, p, 1.0, h->HW, d, U, nk, 1.0, Y, ldy, MY, ldm, s));
-    return EDA_OK;
+    return gemm_tn_f64(h->d, nk, p, 1.0, h->HW, h->d, Y, ldy, 0.0, PQ, nk, part, pcap, s);
+}
+
+// OUT (d x p) = Y + Z U, U ((n + k) x p, ld n + k): the second sweep of a composed product.
+int sweep_z(eda_ctx* h, int p, const double* U, const double* Y, int64_t ldy, double* OUT, int64_t ldo,
+            cudaStream_t s) {
+    const int nk = (int)h->n + h->k;
+    if (h->cfg.prec == EDA_F64_TC && h->ozblock) {
+        for (int c0 = 0; c0 < p; c0 += 32)
+            EDA_TRY(oz_gemm(h->ozN, h->oznb, std::min(32, p - c0), U + (size_t)c0 * nk, nk, 1.0, 1.0,
+                            Y + (size_t)c0 * ldy, ldy, OUT + (size_t)c0 * ldo, ldo, h->status, s));
+        return EDA_OK;
+    }
+    return gemm_nn_f64(h->d, nk, p, 1.0, h->HW, h->d, U, nk, 1.0, Y, ldy, OUT, ldo, s);
 }
 
 namespace {

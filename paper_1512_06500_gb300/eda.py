@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libeda_gb300.so")
 
 EDA_F64, EDA_F32, EDA_BF16, EDA_BF16X2, EDA_F64_TC = 0, 1, 2, 3, 4
-OP_SW, OP_SB, OP_M = 0, 1, 2
+OP_SW, OP_SB, OP_M, OP_N = 0, 1, 2, 3
 
 STATUS = {
     0: "EDA_OK", -1: "EDA_ERR_INVALID_ARG", -2: "EDA_ERR_BAD_LABELS", -3: "EDA_ERR_NONFINITE",
@@ -34,7 +34,7 @@ EXPORTS = [
     "eda_project", "eda_get_factors", "eda_get_dims", "eda_destroy", "eda_strerror",
     "eda_last_cuda_error", "eda_last_cuda_error_string", "eda_kernel_launches",
     "eda_profile_enable", "eda_profile_reset", "eda_profile_read", "eda_profile_work",
-    "eda_lowrank_exp_apply_noalloc", "eda_solve_batched",
+    "eda_lowrank_exp_apply_noalloc", "eda_solve_batched", "eda_solve_arnoldi",
 ]
 
 
@@ -113,6 +113,7 @@ def load(path: str | None = None):
         "eda_profile_work": ([ctypes.c_char_p, P(f64), P(f64)], ctypes.c_int),
         "eda_lowrank_exp_apply_noalloc": ([vp, i64, i32, vp, vp, vp, i64, i32, vp], ctypes.c_int),
         "eda_solve_batched": ([P(Problem), i32, P(Config), i32, vp], ctypes.c_int),
+        "eda_solve_arnoldi": ([vp, i32, f64, vp, vp, P(SolveInfo), vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -286,6 +287,24 @@ class Handle:
         if rr is not None:
             out["relres"] = list(rr)
         return V, lam, Y, out, code
+
+    def solve_arnoldi(self, t, tol, relres=False, stream=None, check=True):
+        """t dominant pairs of the nonsymmetric form (block Arnoldi): returns (V (t, d), lam (t,), info, status)."""
+        dev = self.device
+        V = torch.empty((t, self.d), dtype=torch.float64, device=dev)
+        lam = torch.empty(t, dtype=torch.float64, device=dev)
+        info = SolveInfo()
+        rr = (ctypes.c_double * t)() if relres else None
+        if rr is not None:
+            info.relres = ctypes.cast(rr, ctypes.POINTER(ctypes.c_double))
+        code = load().eda_solve_arnoldi(self._h, t, float(tol), _ptr(V), _ptr(lam), ctypes.byref(info),
+                                        _stream(stream))
+        if check and code not in (0, -8):
+            raise EdaError(code, "eda_solve_arnoldi")
+        out = info.as_dict()
+        if rr is not None:
+            out["relres"] = list(rr)
+        return V, lam, out, code
 
     def project(self, V, Xq, stream=None):
         """P = V^T Xq; V: (t, d) float64, Xq: (m, d) float64 -> P (m, t)."""

@@ -110,12 +110,14 @@ def lowrank_images(d, k, n_per_class, rank=20, noise=0.05, seed=0, n_test_per_cl
                    {"generator": "lowrank_images", "rank": rank, "noise": noise, "seed": seed})
 
 
-# The five workload shapes. tau is the scale target (largest c^2 * lambda_max of the two Grams).
+# The workload shapes. tau is the scale target (largest c^2 * lambda_max of the two Grams).
 CONFIGS = {
     "d256_k8":    dict(d=256,   k=8,   n_j=6,  t=7,   b=1,  tau=10.0, test=5, gen="clusters"),
     "d4096_k40":  dict(d=4096,  k=40,  n_j=5,  t=39,  b=8,  tau=10.0, test=5, gen="clusters"),
     "d16384_k100": dict(d=16384, k=100, n_j=7, t=99,  b=16, tau=20.0, test=3, gen="clusters"),
     "d65536_k200": dict(d=65536, k=200, n_j=10, t=199, b=32, tau=20.0, test=3, gen="lowrank"),
+    # CMU-PIE-sized images (486 x 640 pixels), 10 classes of 8 training images (Section 4, Table 4.6)
+    "d311040_k10": dict(d=311040, k=10, n_j=8, t=9, b=8, tau=10.0, test=3, gen="clusters"),
 }
 
 

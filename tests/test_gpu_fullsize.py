@@ -129,3 +129,25 @@ def test_fp64_d65536_k200_sampled_pairs_three_products(eda, oracle_solutions):
     assert np.all(res <= tol + floor), (res, floor)
     rq = np.einsum("ij,ij->j", Ys, MY)
     assert np.all(np.abs(rq - lam[idx]) / lam[idx] <= 1e-9 + floor)
+
+
+@pytest.mark.parametrize("prec", ["f64", "tc"])
+def test_d311040_k10_matches_oracle(eda, prec, oracle_solutions):
+    # the paper's largest images (CMU-PIE, 486 x 640 pixels, Section 4): the factors (311040 x 90, 0.2 GB)
+    # stay resident in HBM, no streaming; both precision modes to the FP64 bars at tau = 10
+    name = "d311040_k10"
+    c = synth.CONFIGS[name]
+    p, ref = oracle_solutions(name)
+    cfg = eda.config(prec=eda.EDA_F64 if prec == "f64" else eda.EDA_F64_TC, block_b=c["b"], tau=c["tau"],
+                     true_residuals=1)
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        assert abs(h.c2 - ref["c2"]) <= 1e-13 * ref["c2"]
+        V, lam, _, info, code = h.solve(c["t"], 1e-12)
+        assert code == 0, info
+        Ptr = h.project(V, _dev(p.X)).cpu().numpy()
+        Pte = h.project(V, _dev(p.Xtest)).cpu().numpy()
+    rel = np.abs(lam.cpu().numpy() - ref["lam_t"]) / ref["lam_t"]
+    assert rel.max() <= 1e-10, rel.max()
+    assert O.sin_angle(ref["V"], V.cpu().numpy().T) <= 1e-8
+    lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
+    assert np.array_equal(lab_g, ref["lab"])
