@@ -226,7 +226,7 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
     add((size_t)d * tw * 2);           // X, X2
     add((size_t)nk * m_max);           // Wz
     add((size_t)m_max * m_max);        // H
-    add((size_t)m_max * b * 2);        // C
+    add((size_t)m_max * b * 4);        // C: the two passes' coefficients, and those of a refill
     for (int i = 0; i < 5; ++i) add((size_t)b * b);
     add((size_t)nk * b * 2);           // PQ, U
     for (int i = 0; i < 4; ++i) add((size_t)m_max * m_max);   // AW, AB, Cm, Ri
@@ -245,7 +245,7 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
     w.X2 = a.take<double>((size_t)d * tw);
     w.Wz = a.take<double>((size_t)nk * m_max);
     w.H = a.take<double>((size_t)m_max * m_max);
-    w.C = a.take<double>((size_t)m_max * b * 2);
+    w.C = a.take<double>((size_t)m_max * b * 4);
     w.R1 = a.take<double>((size_t)b * b);
     w.R1i = a.take<double>((size_t)b * b);
     w.R2 = a.take<double>((size_t)b * b);
@@ -319,7 +319,9 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
                     for (int q = 0; q < lostc && rc == EDA_OK; ++q)
                         rc = fill_gaussian_f64(d, 1, w.W1 + (size_t)lost_h[q] * d, d, h->cfg.seed,
                                                1000 + (uint64_t)iters * 64 + q, s);
-                    if (rc == EDA_OK) rc = cgs2_f64(d, cols, b, w.V, w.W1, C2, C2 + (size_t)cols * b, w, s);
+                    // refilled directions against the basis (their coefficients are not part of H)
+                    double* C3 = w.C + 2 * (size_t)m_max * b;
+                    if (rc == EDA_OK) rc = cgs2_f64(d, cols, b, w.V, w.W1, C3, C3 + (size_t)m_max * b, w, s);
                     if (rc != EDA_OK) break;
                 }
                 double* Vn = w.V + (size_t)cols * d;
