@@ -274,7 +274,9 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
                 for (int q = 0; q < lostc; ++q)
                     EDA_TRY(fill_gaussian<T>(d, 1, w.W1 + (size_t)lost_h[q] * d, d, h->cfg.seed,
                                              1000 + (uint64_t)st.iters * 64 + q, s));
-                EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W1, d, C2, C2 + (size_t)cols * b, w, s));
+                // the refilled directions against the basis (their coefficients are not part of T)
+                double* C3 = w.C + (size_t)m_max * tw * 2;
+                EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W1, d, C3, C3 + (size_t)m_max * b, w, s));
             }
             T* Vn = w.V + (size_t)cols * d;
             EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
@@ -543,7 +545,7 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     addT((size_t)d * tw);              // tmp
     addT((size_t)d * t);               // Yt
     add((size_t)m_max * m_max);        // Tm
-    add((size_t)m_max * tw * 2);       // C
+    add((size_t)m_max * tw * 2 + (size_t)m_max * b * 2);   // C: both passes, and a refill's coefficients
     for (int i = 0; i < 7; ++i) add((size_t)b * b);
     add((size_t)(n + k) * tw * 2);     // P, Q (also the (n + k) x b coordinates of the composed M-apply)
     add(w.pcap);                       // partial (double-sized slots hold either type)
@@ -567,7 +569,7 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     w.tmp = a.take<T>((size_t)d * tw);
     w.Yt = a.take<T>((size_t)d * t);
     w.Tm = a.take<double>((size_t)m_max * m_max);
-    w.C = a.take<double>((size_t)m_max * tw * 2);
+    w.C = a.take<double>((size_t)m_max * tw * 2 + (size_t)m_max * b * 2);
     w.R1 = a.take<double>((size_t)b * b);
     w.R1i = a.take<double>((size_t)b * b);
     w.R2 = a.take<double>((size_t)b * b);
