@@ -12,9 +12,14 @@
 //     (V^T exp(c^2 S_B) V) s = theta (V^T exp(c^2 S_W) V) s,
 // a symmetric-definite pencil (so theta is real, as the eigenvalues of Eq. (3.1) are), formed from the
 // coordinates Z^T V that every N-apply produces anyway: V^T exp(c^2 S_B) V = I + (H_B^T V)^T K_B (H_B^T V) and
-// V^T exp(c^2 S_W) V = I + (H_W^T V)^T K_W(c^2) (H_W^T V). The residual of a Ritz pair (theta, x = V s)
-// follows from the Arnoldi relation N V = V H + W E^T (W the reorthogonalised remainder of the last block):
-// ||N x - theta x||^2 = ||H s - theta s||^2 + ||W s_last||^2.
+// V^T exp(c^2 S_W) V = I + (H_W^T V)^T K_W(c^2) (H_W^T V). (With y = exp(c^2 S_W / 2) x this is the Rayleigh-Ritz
+// step of the symmetric form on span(exp(c^2 S_W / 2) V).) The residual r = N x - theta x of a Ritz pair
+// (theta, x = V s) follows from the Arnoldi relation N V = V H + W E^T (W the reorthogonalised remainder of the
+// last block): r = V (H s - theta s) + W s_last. It is measured in the exp(c^2 S_W) norm, the norm in which it
+// equals the symmetric form's residual M y - theta y (so tol means the same for eda_solve and this solver):
+// ||r||^2 = ||H s - theta s||^2 + ||W s_last||^2 + (H_W^T r)^T K_W(c^2) (H_W^T r), with H_W^T r from the
+// coordinates Z^T V and Z^T W = Z^T N V_last - (Z^T V) H_last and ||y|| = 1 (s = R^{-1} y, y a unit
+// eigenvector of the projected symmetric matrix).
 #include "eda_internal.cuh"
 
 #include <algorithm>
@@ -57,13 +62,23 @@ __global__ void k_arn_sub_scaled(int rows, int t, double* R, int ldr, const doub
     R[(int64_t)c * ldr + r] = fma(-theta[c], S[(int64_t)c * lds + r], R[(int64_t)c * ldr + r]);
 }
 
-// relres[i] = sqrt(a[i]^2 + b[i]^2) / (|theta[i]| snorm[i])
-__global__ void k_arn_relres(int t, const double* a, const double* b, const double* snorm, const double* theta,
+// relres[i] = sqrt(a[i]^2 + b[i]^2 + q[i]) / |theta[i]|
+__global__ void k_arn_relres(int t, const double* a, const double* b, const double* q, const double* theta,
                              double* relres) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= t) return;
-    const double den = fabs(theta[i]) * snorm[i];
-    relres[i] = den > 0.0 ? sqrt(fma(a[i], a[i], b[i] * b[i])) / den : INFINITY;
+    const double den = fabs(theta[i]);
+    relres[i] = den > 0.0 ? sqrt(fmax(0.0, fma(a[i], a[i], fma(b[i], b[i], q[i])))) / den : INFINITY;
+}
+
+// q[c] = sum_r X[r, c] Y[r, c] (one warp per column)
+__global__ void k_arn_coldot(int rows, int t, const double* X, int ldx, const double* Y, int ldy, double* q) {
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x;
+    double acc = 0.0;
+    for (int r = lane; r < rows; r += 32) acc = fma(X[(int64_t)c * ldx + r], Y[(int64_t)c * ldy + r], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) q[c] = acc;
 }
 
 __global__ void k_arn_reverse_cols(int64_t rows, int t, const double* in, int64_t ldi, double* out, int64_t ldo) {
@@ -82,6 +97,7 @@ __global__ void k_arn_reverse_vec(int t, const double* in, double* out) {
 struct ArnWs {
     double *V, *W, *W1, *X, *X2, *Wz, *H, *C, *R1, *R1i, *R2, *R2i, *Bm, *PQ, *U;
     double *AW, *AB, *Cm, *Ri, *T1, *S, *HS, *theta, *relres, *n1, *n2, *sn, *lamd;
+    double *ZW, *T2, *T3;   // Z^T W of the last block; n x t temporaries of the residual
     double* part;
     size_t pcap;
     int* lost;
@@ -106,6 +122,20 @@ int cgs2_f64(int64_t d, int cols, int b, const double* V, double* X, double* C1,
         EDA_TRY(gemm_nn_f64(d, cols, b, -1.0, V, d, C, cols, 1.0, X, d, X, d, s));
     }
     return EDA_OK;
+}
+
+// Z^T W for the remainder W = N V_j - V_{:cols} H[:cols, j0:j0+b] of the block just applied: N V_j = V_j + Z U
+// gives Z^T N V_j = Z^T V_j + (Z^T Z) U with the Grams G_W, G_WB, G_BW, G_B.
+int arn_ztw(eda_ctx* h, int cols, int j0, int ldh, int b, ArnWs& w, cudaStream_t s) {
+    const int n = (int)h->n, k = h->k, nk = n + k;
+    const double* Uw = w.U;
+    const double* Ub = w.U + n;
+    EDA_TRY(copy_mat_f64(nk, b, w.Wz + (size_t)j0 * nk, nk, w.ZW, nk, s));
+    EDA_TRY(gemm_small_f64(false, false, n, b, n, 1.0, h->GW, n, Uw, nk, 1.0, w.ZW, nk, s));
+    EDA_TRY(gemm_small_f64(false, false, n, b, k, 1.0, h->GWB, n, Ub, nk, 1.0, w.ZW, nk, s));
+    EDA_TRY(gemm_small_f64(false, false, k, b, n, 1.0, h->GBW, k, Uw, nk, 1.0, w.ZW + n, nk, s));
+    EDA_TRY(gemm_small_f64(false, false, k, b, k, 1.0, h->GB, k, Ub, nk, 1.0, w.ZW + n, nk, s));
+    return gemm_small_f64(false, false, nk, b, cols, -1.0, w.Wz, nk, w.H + (size_t)j0 * ldh, ldh, 1.0, w.ZW, nk, s);
 }
 
 // Rayleigh-Ritz on span(V[:, :m]) with the E_W-Galerkin condition: theta (t, ascending), S (m x t), and the
@@ -134,14 +164,19 @@ int arn_ritz(eda_ctx* h, int m, int ldh, int t, int b, ArnWs& w, std::vector<dou
     EDA_TRY(symmetrize_f64(m, w.Cm, m, s));
     EDA_TRY(symeig_f64(m, w.Cm, m, m - t, m - 1, w.theta, w.T1, m, &w.eig, h->status, h->cfg.seed + 17, 1e-7, s));
     EDA_TRY(gemm_small_f64(false, false, m, t, m, 1.0, w.Ri, m, w.T1, m, 0.0, w.S, m, s));
-    // residuals: ||H s - theta s|| and ||W s_last|| (the reorthogonalised remainder of the last block)
+    // residuals in the exp(c^2 S_W) norm: ||H s - theta s||^2 + ||W s_last||^2 + (H_W^T r)^T K_W(c^2) (H_W^T r)
     EDA_TRY(gemm_small_f64(false, false, m, t, m, 1.0, w.H, ldh, w.S, m, 0.0, w.HS, m, s));
     k_arn_sub_scaled<<<ceil_div((int64_t)m * t, 256), 256, 0, s>>>(m, t, w.HS, m, w.S, m, w.theta);
     EDA_LAUNCHED();
     EDA_TRY(col_norms_f64(m, t, w.HS, m, w.n1, s));
     EDA_TRY(gemm_nn_f64(d, b, t, 1.0, w.W, d, w.S + (m - b), m, 0.0, nullptr, 0, w.X, d, s));
     EDA_TRY(col_norms_f64(d, t, w.X, d, w.n2, s));
-    EDA_TRY(col_norms_f64(m, t, w.S, m, w.sn, s));
+    // H_W^T r = Q_W (H s - theta s) + (H_W^T W) s_last
+    EDA_TRY(gemm_small_f64(false, false, n, t, m, 1.0, QW, nk, w.HS, m, 0.0, w.T2, n, s));
+    EDA_TRY(gemm_small_f64(false, false, n, t, b, 1.0, w.ZW, nk, w.S + (m - b), m, 1.0, w.T2, n, s));
+    EDA_TRY(gemm_small_f64(false, false, n, t, n, 1.0, h->KWp, n, w.T2, n, 0.0, w.T3, n, s));
+    k_arn_coldot<<<t, 32, 0, s>>>(n, t, w.T2, n, w.T3, n, w.sn);
+    EDA_LAUNCHED();
     k_arn_relres<<<ceil_div(t, 128), 128, 0, s>>>(t, w.n1, w.n2, w.sn, w.theta, w.relres);
     EDA_LAUNCHED();
     EDA_CUDA_TRY(cudaMemcpyAsync(relres_h.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -232,6 +267,7 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
     for (int i = 0; i < 4; ++i) add((size_t)m_max * m_max);   // AW, AB, Cm, Ri
     add((size_t)std::max<size_t>((size_t)m_max * m_max, (size_t)n * m_max));   // T1
     add((size_t)m_max * t * 2);        // S, HS
+    add((size_t)nk * b + 2 * (size_t)n * t);   // ZW, T2, T3
     for (int i = 0; i < 6; ++i) add(t);
     add(w.pcap);
     add(b + 64);                       // lost (ints)
@@ -260,6 +296,9 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
     w.T1 = a.take<double>(std::max<size_t>((size_t)m_max * m_max, (size_t)n * m_max));
     w.S = a.take<double>((size_t)m_max * t);
     w.HS = a.take<double>((size_t)m_max * t);
+    w.ZW = a.take<double>((size_t)nk * b);
+    w.T2 = a.take<double>((size_t)n * t);
+    w.T3 = a.take<double>((size_t)n * t);
     w.theta = a.take<double>(t);
     w.relres = a.take<double>(t);
     w.n1 = a.take<double>(t);
@@ -336,6 +375,7 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
             if ((cols >= next_check && cols >= t + 1) || (last && cols >= t)) {
                 ++checks;
                 rr_cols = cols;
+                if ((rc = arn_ztw(h, cols, j0, m_max, b, w, s)) != EDA_OK) break;
                 if ((rc = arn_ritz(h, cols, m_max, t, b, w, relres_h, s)) != EDA_OK) break;
                 max_rel = 0.0;
                 conv = 0;

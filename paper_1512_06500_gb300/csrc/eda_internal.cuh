@@ -284,6 +284,13 @@ size_t oz_operand_bytes(int64_t M, int64_t K);
 // false: M = rows of A (M x K matrix). mem: oz_operand_bytes(M, K) bytes, 256-byte aligned.
 int oz_operand_make(const double* A, int64_t lda, int64_t M, int64_t K, bool rows_are_cols, void* mem,
                     OzOperand* op, cudaStream_t s);
+// A growing operand (the Krylov basis): room for Mcap rows and Kcap reduction values, planes zeroed.
+// oz_append_cols: split columns i0 .. i1 of A (d x ., lda) as rows i0 .. i1 of a column-scaled operand
+// (K = d). oz_resplit_rows: split all of A (M x K) afresh as a row-scaled operand (row scales over the K
+// columns present).
+int oz_operand_init(int64_t Mcap, int64_t Kcap, void* mem, OzOperand* op, cudaStream_t s);
+int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOperand* op, cudaStream_t s);
+int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperand* op, cudaStream_t s);
 size_t oz_narrow_bytes(int64_t Kmax, int max_splits, int64_t Mmax);
 int oz_narrow_make(int64_t Kmax, int max_splits, int64_t Mmax, void* mem, OzNarrow* nb);
 // D (M x p, ldd) = alpha * op(A) B + beta * C0 (ldc0), op(A) the M x K split operand, B: K x p (ldb),

@@ -319,6 +319,62 @@ __global__ void k_oz_split_narrow(int64_t K, int p, const double* __restrict__ B
     for (int q = 0; q < OZ_S; ++q) out[(int64_t)q * OZ_N * ld + t] = s[q];
 }
 
+// Digit planes of the columns i0 .. i1 of A (d x m, lda) as M rows of a split operand whose K index runs down
+// the columns (rows_are_cols layout), 8 consecutive k per thread: one 64-byte read of A and one 16-byte
+// store per plane. e: the scales of those columns (e[i - i0]).
+__global__ void k_oz_split_cols8(const double* __restrict__ A, int64_t lda, int i0, int i1, int64_t K,
+                                 const int* __restrict__ e, int kbs, int64_t ld, __nv_bfloat16* __restrict__ out,
+                                 int64_t slice) {
+    const int64_t groups = ld / 8;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)(i1 - i0) * groups) return;
+    const int i = i0 + (int)(t / groups);
+    const int64_t k0 = (t % groups) * 8;
+    const int ex = e[i - i0];
+    __align__(16) __nv_bfloat16 dg[OZ_S][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const double v = (k0 + u < K) ? A[(int64_t)i * lda + k0 + u] : 0.0;
+        __nv_bfloat16 sq[OZ_S];
+        oz_digits(v, ex, sq);
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q) dg[q][u] = sq[q];
+    }
+    const int64_t off = tile_off(i, k0, kbs);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q)
+        *reinterpret_cast<uint4*>(out + q * slice + off) = *reinterpret_cast<const uint4*>(dg[q]);
+}
+
+// Digit planes of the rows of A (M x K, lda; M rows = rows of A, K along its columns k0 .. k1, k0 a multiple
+// of 8), 8 consecutive k per thread: eight reads, each coalesced across the threads of a warp (consecutive
+// rows), and one 16-byte store per plane. Columns at or beyond Kvalid are taken as zero.
+__global__ void k_oz_split_rows8(const double* __restrict__ A, int64_t lda, int64_t M, int64_t k0, int64_t k1,
+                                 int64_t Kvalid, const int* __restrict__ e, int kbs, __nv_bfloat16* __restrict__ out,
+                                 int64_t slice) {
+    const int64_t mpad = (M + TC_M - 1) / TC_M * TC_M;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t groups = (k1 - k0 + 7) / 8;
+    if (t >= mpad * groups) return;
+    const int64_t i = t % mpad;
+    const int64_t kg = k0 + (t / mpad) * 8;
+    const int ex = i < M ? e[i] : 0;
+    __align__(16) __nv_bfloat16 dg[OZ_S][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int64_t k = kg + u;
+        const double v = (i < M && k < Kvalid) ? A[k * lda + i] : 0.0;
+        __nv_bfloat16 sq[OZ_S];
+        oz_digits(v, ex, sq);
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q) dg[q][u] = sq[q];
+    }
+    const int64_t off = tile_off(i, kg, kbs);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q)
+        *reinterpret_cast<uint4*>(out + q * slice + off) = *reinterpret_cast<const uint4*>(dg[q]);
+}
+
 // D[i, j] = alpha * sum_s P[s][j][i] + beta * D[i, j], splits added in order (deterministic).
 __global__ void k_oz_reduce(int M, int N, int splits, const double* __restrict__ P, int64_t sstride, double alpha,
                             double beta, const double* C0, int64_t ldc0, double* D, int64_t ldd) {
@@ -371,6 +427,51 @@ int oz_operand_make(const double* A, int64_t lda, int64_t M, int64_t K, bool row
     k_oz_split_tiled<<<ceil_div(plane, 256), 256, 0, s>>>(A, lda, M, K, rows_are_cols ? 1 : 0, op->exps, (int)kb,
                                                           plane, op->tiles, slice);
     EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+// A split operand with room for Mcap rows (columns of a d x Mcap matrix, K = d) or for Kcap values of K
+// (rows_are_cols = false: M = d rows, K up to Kcap columns), planes zeroed, no row filled yet.
+int oz_operand_init(int64_t Mcap, int64_t Kcap, void* mem, OzOperand* op, cudaStream_t s) {
+    const int64_t mt = (Mcap + TC_M - 1) / TC_M, kb = (Kcap + TC_KS - 1) / TC_KS;
+    const int64_t plane = mt * kb * TC_M * TC_KS;
+    const int64_t slice = ((plane * 2 + 255) / 256 * 256) / 2;
+    op->tiles = static_cast<__nv_bfloat16*>(mem);
+    op->slice = slice;
+    op->exps = reinterpret_cast<int*>(static_cast<char*>(mem) + OZ_S * slice * 2);
+    op->M = 0;
+    op->K = 0;
+    op->kbs = (int)kb;
+    op->mtiles = 0;
+    EDA_CUDA_TRY(cudaMemsetAsync(mem, 0, (size_t)OZ_S * slice * 2, s));
+    return EDA_OK;
+}
+
+int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOperand* op, cudaStream_t s) {
+    if (i1 <= i0) return EDA_OK;
+    k_oz_exp_cols<<<(unsigned)(i1 - i0), 256, 0, s>>>(K, A + (int64_t)i0 * lda, lda, op->exps + i0);
+    EDA_LAUNCHED();
+    const int64_t ld = (int64_t)op->kbs * TC_KS;
+    k_oz_split_cols8<<<ceil_div((int64_t)(i1 - i0) * (ld / 8), 256), 256, 0, s>>>(A, lda, i0, i1, K, op->exps + i0,
+                                                                               op->kbs, ld, op->tiles, op->slice);
+    EDA_LAUNCHED();
+    op->M = i1;
+    op->K = K;
+    op->mtiles = ceil_div(i1, TC_M);
+    return EDA_OK;
+}
+
+int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperand* op, cudaStream_t s) {
+    k_oz_exp_rows<<<ceil_div(M, 256), 256, 0, s>>>(M, (int)K, A, lda, op->exps);
+    EDA_LAUNCHED();
+    const int64_t kpad = (K + TC_KS - 1) / TC_KS * TC_KS;
+    const int64_t mpad = (M + TC_M - 1) / TC_M * TC_M;
+    k_oz_split_rows8<<<ceil_div(mpad * (kpad / 8), 256), 256, 0, s>>>(A, lda, M, 0, kpad, K, op->exps, op->kbs,
+                                                                      op->tiles, op->slice);
+    EDA_LAUNCHED();
+    op->M = M;
+    op->K = K;
+    op->mtiles = ceil_div(M, TC_M);
     return EDA_OK;
 }
 

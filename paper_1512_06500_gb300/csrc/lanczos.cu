@@ -111,7 +111,44 @@ struct SolveWs {
     int* lost;
     size_t pcap;
     SymEigWork eig;
+    // prec = EDA_F64_TC: the basis split for V^T X (column scales, appended block by block) and for V C (row
+    // scales over the current columns, split afresh whenever a block is added)
+    bool oz = false;
+    OzOperand VT, VN;
 };
+
+// tc products with the split basis, 32 columns at a time: C (cols x p, ldc) = V^T X, and X -= V C
+template <class T>
+int oz_basis_tn(eda_ctx* h, SolveWs<T>& w, int cols, int p, const double* X, int64_t ldx, double* C, int ldc,
+                cudaStream_t s) {
+    OzOperand A = w.VT;
+    A.M = cols;
+    A.mtiles = ceil_div(cols, 128);
+    for (int c0 = 0; c0 < p; c0 += 32)
+        EDA_TRY(oz_gemm(A, h->oznb, std::min(32, p - c0), X + (size_t)c0 * ldx, ldx, 1.0, 0.0, nullptr, 0,
+                        C + (size_t)c0 * ldc, ldc, h->status, s));
+    return EDA_OK;
+}
+template <class T>
+int oz_basis_nn(eda_ctx* h, SolveWs<T>& w, int cols, int p, const double* C, int ldc, double alpha, double beta,
+                const double* X0, int64_t ldx0, double* X, int64_t ldx, cudaStream_t s) {
+    OzOperand A = w.VN;
+    A.K = cols;
+    for (int c0 = 0; c0 < p; c0 += 32)
+        EDA_TRY(oz_gemm(A, h->oznb, std::min(32, p - c0), C + (size_t)c0 * ldc, ldc, alpha, beta,
+                        X0 ? X0 + (size_t)c0 * ldx0 : nullptr, ldx0, X + (size_t)c0 * ldx, ldx, h->status, s));
+    return EDA_OK;
+}
+
+// The basis has grown from cols0 to cols1 columns: append their column-scaled digit planes and split the
+// whole basis afresh with row scales over all its columns.
+template <class T>
+int oz_basis_grow(SolveWs<T>& w, int64_t d, int cols0, int cols1, cudaStream_t s) {
+    if (!w.oz) return EDA_OK;
+    const double* V = reinterpret_cast<const double*>(w.V);
+    EDA_TRY(oz_append_cols(V, d, cols0, cols1, d, &w.VT, s));
+    return oz_resplit_rows(V, d, d, cols1, &w.VN, s);
+}
 
 template <class T>
 int cholqr_pass(int64_t d, int b, T* X, int64_t ldx, double* Rm, double* Rinv, T* out, double piv_min2, int* status,
@@ -122,12 +159,22 @@ int cholqr_pass(int64_t d, int b, T* X, int64_t ldx, double* Rm, double* Rinv, T
     return EDA_OK;
 }
 
-// CGS2: X <- X - V (V^T X), twice; the first coefficients are left in Cfirst (cols x b).
+// CGS2: X <- X - V (V^T X), twice; the first coefficients are left in Cfirst (cols x b). With the split
+// basis (tensor-core FP64 mode) both products of each pass run on the tensor cores.
 template <class T>
 int cgs2(int64_t d, int cols, int b, const T* V, T* X, int64_t ldx, double* Cfirst, double* C2, SolveWs<T>& w,
-         cudaStream_t s) {
+         cudaStream_t s, eda_ctx* h = nullptr) {
     if (cols <= 0) return EDA_OK;
     ProfScope prof("reorth", s);
+    if (w.oz && h) {
+        double* Xd = reinterpret_cast<double*>(X);
+        for (int pass = 0; pass < 2; ++pass) {
+            double* C = pass == 0 ? Cfirst : C2;
+            EDA_TRY(oz_basis_tn(h, w, cols, b, Xd, ldx, C, cols, s));
+            EDA_TRY(oz_basis_nn(h, w, cols, b, C, cols, -1.0, 1.0, Xd, ldx, Xd, ldx, s));
+        }
+        return EDA_OK;
+    }
     EDA_TRY(gemm_tn<T>(d, cols, b, 1.0, V, d, X, ldx, 0.0, Cfirst, cols, w.part, w.pcap, s));
     EDA_TRY(gemm_nn<T>(d, cols, b, -1.0, V, d, Cfirst, cols, 1.0, X, ldx, X, ldx, s));
     EDA_TRY(gemm_tn<T>(d, cols, b, 1.0, V, d, X, ldx, 0.0, C2, cols, w.part, w.pcap, s));
@@ -228,6 +275,7 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     }
     EDA_TRY(cholqr_pass<T>(d, b, w.V, d, w.R1, w.R1i, w.W1, 0.0, h->status, w.lost, w, s));
     EDA_TRY(cholqr_pass<T>(d, b, w.W1, d, w.R2, w.R2i, w.V, 0.0, h->status, w.lost, w, s));
+    EDA_TRY(oz_basis_grow<T>(w, d, 0, b, s));
     {
         int lostc = 0;
         EDA_CUDA_TRY(cudaMemcpyAsync(&lostc, w.lost + b, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -254,7 +302,7 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
         ++st.iters;
         double* C1 = w.C;
         double* C2 = w.C + (size_t)m_max * tw;
-        EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W, d, C1, C2, w, s));
+        EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W, d, C1, C2, w, s, h));
         k_set_col_block<<<ceil_div(cols * b, 256), 256, 0, s>>>(w.Tm, m_max, cols, j0, b, C1, C2);
         EDA_LAUNCHED();
         // CholQR2 of W with rank detection: W = V_{j+1} B_{j+1}
@@ -276,11 +324,12 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
                                              1000 + (uint64_t)st.iters * 64 + q, s));
                 // the refilled directions against the basis (their coefficients are not part of T)
                 double* C3 = w.C + (size_t)m_max * tw * 2;
-                EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W1, d, C3, C3 + (size_t)m_max * b, w, s));
+                EDA_TRY(cgs2<T>(d, cols, b, w.V, w.W1, d, C3, C3 + (size_t)m_max * b, w, s, h));
             }
             T* Vn = w.V + (size_t)cols * d;
             EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
             EDA_TRY(cholqr_pass<T>(d, b, w.W1, d, w.R2, w.R2i, Vn, 0.0, h->status, w.lost, w, s));
+            EDA_TRY(oz_basis_grow<T>(w, d, cols, cols + b, s));
             EDA_TRY(gemm_small_f64(false, false, b, b, b, 1.0, w.R2, b, w.R1, b, 0.0, w.Bm, b, s));   // B = R2 R1
         } else {
             EDA_TRY(copy_mat_f64(b, b, w.R1, b, w.Bm, b, s));   // basis full: residual estimate only
@@ -342,6 +391,9 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     }
     if (st.rr_cols == 0) return EDA_ERR_NOT_CONVERGED;
     // Ritz vectors Y = V_{:rr} S (ascending theta)
+    if (w.oz)
+        return oz_basis_nn(h, w, st.rr_cols, t, w.S, st.rr_cols, 1.0, 0.0, nullptr, 0, reinterpret_cast<double*>(w.Yt),
+                           d, s);
     EDA_TRY(gemm_nn<T>(d, st.rr_cols, t, 1.0, w.V, d, w.S, st.rr_cols, 0.0, nullptr, 0, w.Yt, d, s));
     return EDA_OK;
 }
@@ -561,6 +613,9 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     add(t);                            // lamd
     add(b + 64);                       // lost (ints)
     need += symeig_work_bytes(eig_n, t) + 16384;
+    const bool oz = !mixed && h->cfg.prec == EDA_F64_TC && h->ozblock;
+    const size_t ozT_bytes = oz ? a256(oz_operand_bytes(m_max, d)) : 0, ozN_bytes = oz ? a256(oz_operand_bytes(d, m_max)) : 0;
+    need += ozT_bytes + ozN_bytes;
     EDA_TRY(ensure_workspace(h, need));
     Arena a{static_cast<char*>(h->ws), h->ws_bytes, 0};
     w.V = a.take<T>((size_t)d * m_max);
@@ -604,6 +659,14 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     w.lost = a.take<int>(b + 64);
     EDA_TRY(symeig_work_carve(a, eig_n, t, h->bar, &w.eig));
     if (!w.lost) return EDA_ERR_OOM;
+    if (oz) {
+        char* mT = a.take<char>(ozT_bytes);
+        char* mN = a.take<char>(ozN_bytes);
+        if (!mT || !mN) return EDA_ERR_OOM;
+        EDA_TRY(oz_operand_init(m_max, d, mT, &w.VT, s));
+        EDA_TRY(oz_operand_init(d, m_max, mN, &w.VN, s));
+        w.oz = true;
+    }
     EDA_CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), s));
     EDA_CUDA_TRY(cudaMemsetAsync(w.Tm, 0, (size_t)m_max * m_max * 8, s));
 
