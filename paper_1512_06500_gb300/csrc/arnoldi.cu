@@ -18,8 +18,8 @@
 // last block): r = V (H s - theta s) + W s_last. It is measured in the exp(c^2 S_W) norm, the norm in which it
 // equals the symmetric form's residual M y - theta y (so tol means the same for eda_solve and this solver):
 // ||r||^2 = ||H s - theta s||^2 + ||W s_last||^2 + (H_W^T r)^T K_W(c^2) (H_W^T r), with H_W^T r from the
-// coordinates Z^T V and Z^T W = Z^T N V_last - (Z^T V) H_last and ||y|| = 1 (s = R^{-1} y, y a unit
-// eigenvector of the projected symmetric matrix).
+// coordinates Z^T V and one sweep Z^T W at each check, and ||y|| = 1 (s = R^{-1} y, y a unit eigenvector of
+// the projected symmetric matrix).
 #include "eda_internal.cuh"
 
 #include <algorithm>
@@ -98,6 +98,7 @@ struct ArnWs {
     double *V, *W, *W1, *X, *X2, *Wz, *H, *C, *R1, *R1i, *R2, *R2i, *Bm, *PQ, *U;
     double *AW, *AB, *Cm, *Ri, *T1, *S, *HS, *theta, *relres, *n1, *n2, *sn, *lamd;
     double *ZW, *T2, *T3;   // Z^T W of the last block; n x t temporaries of the residual
+    double* CW;             // blocked Cholesky work
     double* part;
     size_t pcap;
     int* lost;
@@ -108,7 +109,8 @@ struct ArnWs {
 int cholqr_once(int64_t d, int p, double* X, double* X2, double* R, double* Ri, double piv_min2, int* status, int* lost,
                 ArnWs& w, cudaStream_t s) {
     EDA_TRY(syrk_f64(d, p, 1.0, X, d, 0.0, R, p, w.part, w.pcap, s));
-    EDA_TRY(chol_inv_small(p, R, p, Ri, 1e-28, piv_min2, status, lost, s));
+    if (lost || piv_min2 > 0.0) EDA_TRY(chol_inv_small(p, R, p, Ri, 1e-28, piv_min2, status, lost, s));
+    else EDA_TRY(chol_inv_auto(p, R, p, Ri, 1e-28, status, w.CW, w.part, w.pcap, s));
     EDA_TRY(gemm_nn_f64(d, p, p, 1.0, X, d, Ri, p, 0.0, nullptr, 0, X2, d, s));
     return EDA_OK;
 }
@@ -124,18 +126,11 @@ int cgs2_f64(int64_t d, int cols, int b, const double* V, double* X, double* C1,
     return EDA_OK;
 }
 
-// Z^T W for the remainder W = N V_j - V_{:cols} H[:cols, j0:j0+b] of the block just applied: N V_j = V_j + Z U
-// gives Z^T N V_j = Z^T V_j + (Z^T Z) U with the Grams G_W, G_WB, G_BW, G_B.
-int arn_ztw(eda_ctx* h, int cols, int j0, int ldh, int b, ArnWs& w, cudaStream_t s) {
-    const int n = (int)h->n, k = h->k, nk = n + k;
-    const double* Uw = w.U;
-    const double* Ub = w.U + n;
-    EDA_TRY(copy_mat_f64(nk, b, w.Wz + (size_t)j0 * nk, nk, w.ZW, nk, s));
-    EDA_TRY(gemm_small_f64(false, false, n, b, n, 1.0, h->GW, n, Uw, nk, 1.0, w.ZW, nk, s));
-    EDA_TRY(gemm_small_f64(false, false, n, b, k, 1.0, h->GWB, n, Ub, nk, 1.0, w.ZW, nk, s));
-    EDA_TRY(gemm_small_f64(false, false, k, b, n, 1.0, h->GBW, k, Uw, nk, 1.0, w.ZW + n, nk, s));
-    EDA_TRY(gemm_small_f64(false, false, k, b, k, 1.0, h->GB, k, Ub, nk, 1.0, w.ZW + n, nk, s));
-    return gemm_small_f64(false, false, nk, b, cols, -1.0, w.Wz, nk, w.H + (size_t)j0 * ldh, ldh, 1.0, w.ZW, nk, s);
+// Z^T W for the reorthogonalised remainder W of the block just applied, by one sweep over Z. (Forming it
+// from Z^T N V_j - (Z^T V) H[:, j] cancels: both terms are of size ||N|| ~ e^tau while W is small, and the
+// cancellation leaves an error far above the residuals the solver must resolve.)
+int arn_ztw(eda_ctx* h, ArnWs& w, int b, cudaStream_t s) {
+    return sweep_zt(h, b, w.W, h->d, w.ZW, w.part, w.pcap, s);
 }
 
 // Rayleigh-Ritz on span(V[:, :m]) with the E_W-Galerkin condition: theta (t, ascending), S (m x t), and the
@@ -158,7 +153,7 @@ int arn_ritz(eda_ctx* h, int m, int ldh, int t, int b, ArnWs& w, std::vector<dou
     EDA_TRY(symmetrize_f64(m, w.AW, m, s));
     EDA_TRY(symmetrize_f64(m, w.AB, m, s));
     // A_W = R^T R; the symmetric C = R^{-T} A_B R^{-1} has the pencil's eigenvalues; s = R^{-1} y
-    EDA_TRY(chol_inv_small(m, w.AW, m, w.Ri, 1e-28, 0.0, h->status, nullptr, s));
+    EDA_TRY(chol_inv_auto(m, w.AW, m, w.Ri, 1e-28, h->status, w.CW, w.part, w.pcap, s));
     EDA_TRY(gemm_small_f64(false, false, m, m, m, 1.0, w.AB, m, w.Ri, m, 0.0, w.T1, m, s));
     EDA_TRY(gemm_small_f64(true, false, m, m, m, 1.0, w.Ri, m, w.T1, m, 0.0, w.Cm, m, s));
     EDA_TRY(symmetrize_f64(m, w.Cm, m, s));
@@ -268,6 +263,7 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
     add((size_t)std::max<size_t>((size_t)m_max * m_max, (size_t)n * m_max));   // T1
     add((size_t)m_max * t * 2);        // S, HS
     add((size_t)nk * b + 2 * (size_t)n * t);   // ZW, T2, T3
+    add(chol_inv_blocked_doubles(m_max));        // CW
     for (int i = 0; i < 6; ++i) add(t);
     add(w.pcap);
     add(b + 64);                       // lost (ints)
@@ -299,6 +295,7 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
     w.ZW = a.take<double>((size_t)nk * b);
     w.T2 = a.take<double>((size_t)n * t);
     w.T3 = a.take<double>((size_t)n * t);
+    w.CW = a.take<double>(chol_inv_blocked_doubles(m_max));
     w.theta = a.take<double>(t);
     w.relres = a.take<double>(t);
     w.n1 = a.take<double>(t);
@@ -375,7 +372,7 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
             if ((cols >= next_check && cols >= t + 1) || (last && cols >= t)) {
                 ++checks;
                 rr_cols = cols;
-                if ((rc = arn_ztw(h, cols, j0, m_max, b, w, s)) != EDA_OK) break;
+                if ((rc = arn_ztw(h, w, b, s)) != EDA_OK) break;
                 if ((rc = arn_ritz(h, cols, m_max, t, b, w, relres_h, s)) != EDA_OK) break;
                 max_rel = 0.0;
                 conv = 0;

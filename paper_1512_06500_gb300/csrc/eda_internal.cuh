@@ -116,6 +116,17 @@ int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const d
 // and ST_RANKLOSS is or-ed into *status; lost pivots are listed in lost[0..], lost[b] = count.
 int chol_inv_small(int b, double* G, int ldg, double* Rinv, double rank_tol, double piv_min2,
                    int* status, int* lost, cudaStream_t s);
+// The same factorisation for any m, blocked: one-CTA factorisations of kCholBlock x kCholBlock diagonal
+// blocks and multi-CTA products for the panels, trailing updates and the inverse. Rank detection
+// (rank_tol) applies within each diagonal block; no lost list. work: chol_inv_blocked_doubles(m) doubles;
+// partial: split-K partials (at least m * m doubles).
+constexpr int kCholBlock = 64;
+size_t chol_inv_blocked_doubles(int m);
+int chol_inv_blocked(int m, double* G, int ldg, double* Rinv, int ldr, double rank_tol, int* status, double* work,
+                     double* partial, size_t pcap, cudaStream_t s);
+// chol_inv_small (one CTA) up to b = 90, chol_inv_blocked beyond (Rinv with ld b); no lost list, no pivot floor.
+int chol_inv_auto(int b, double* G, int ldg, double* Rinv, double rank_tol, int* status, double* work, double* partial,
+                  size_t pcap, cudaStream_t s);
 // Copy / scale / symmetrise helpers.
 int copy_mat_f64(int64_t rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb,
                  cudaStream_t s);

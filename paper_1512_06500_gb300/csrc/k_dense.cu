@@ -2,6 +2,7 @@
 // split-K reduction, small products, Cholesky with inverse, and seeded Gaussian blocks.
 #include "eda_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -798,6 +799,73 @@ int chol_inv_small(int b, double* G, int ldg, double* Rinv, double rank_tol, dou
     }
     EDA_LAUNCHED();
     return EDA_OK;
+}
+
+namespace {
+// B (rows x cols, ldb) = 0 below the diagonal (strict lower triangle of a square or tall block)
+__global__ void k_zero_lower(int m, double* A, int lda) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int r = (int)(e % m), c = (int)(e / m);
+    if (r > c) A[(int64_t)c * lda + r] = 0.0;
+}
+__global__ void k_zero_all(int m, double* A, int lda) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    A[(int64_t)(e / m) * lda + e % m] = 0.0;
+}
+}  // namespace
+
+size_t chol_inv_blocked_doubles(int m) { return (size_t)kCholBlock * m + (size_t)kCholBlock * kCholBlock; }
+
+// Right-looking blocked Cholesky G = R^T R (R upper, in place, strict lower triangle zeroed) and R^{-1}, in
+// blocks of kCholBlock: the diagonal block by the one-CTA factorisation (with its rank detection), the row
+// panel R12 = R11^{-T} G12 and the trailing update G22 -= R12^T R12 as multi-CTA products; then R^{-1} block
+// column by block column, X[:j, j] = -X[:j, :j] R[:j, j] R_jj^{-1}. work: chol_inv_blocked_doubles(m);
+// partial: split-K partials of at least m * m doubles.
+int chol_inv_blocked(int m, double* G, int ldg, double* Rinv, int ldr, double rank_tol, int* status, double* work,
+                     double* partial, size_t pcap, cudaStream_t s) {
+    constexpr int NB = kCholBlock;
+    double* T = work;                          // NB x m
+    double* Dinv = work + (size_t)NB * m;      // NB x NB
+    // R^{-1} starts as zero: its blocks below the block diagonal are never written and are read as zeros
+    k_zero_all<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, Rinv, ldr);
+    EDA_LAUNCHED();
+    for (int j0 = 0; j0 < m; j0 += NB) {
+        const int nb = std::min(NB, m - j0);
+        double* G11 = G + (int64_t)j0 * ldg + j0;
+        EDA_TRY(chol_inv_small(nb, G11, ldg, Dinv, rank_tol, 0.0, status, nullptr, s));
+        // R^{-1} diagonal block
+        EDA_TRY(copy_mat_f64(nb, nb, Dinv, nb, Rinv + (int64_t)j0 * ldr + j0, ldr, s));
+        const int r = m - j0 - nb;
+        if (r > 0) {
+            double* G12 = G + (int64_t)(j0 + nb) * ldg + j0;
+            double* G22 = G + (int64_t)(j0 + nb) * ldg + j0 + nb;
+            // R12 = R11^{-T} G12
+            EDA_TRY(gemm_small_f64(true, false, nb, r, nb, 1.0, Dinv, nb, G12, ldg, 0.0, T, nb, s));
+            EDA_TRY(copy_mat_f64(nb, r, T, nb, G12, ldg, s));
+            // G22 -= R12^T R12 (a product reduced over the nb rows of R12)
+            EDA_TRY(gemm_tn_f64(nb, r, r, -1.0, G12, ldg, G12, ldg, 1.0, G22, ldg, partial, pcap, s));
+        }
+    }
+    k_zero_lower<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, G, ldg);
+    EDA_LAUNCHED();
+    // off-diagonal blocks of R^{-1}: X[:j0, j-block] = -X[:j0, :j0] (R[:j0, j-block] R_jj^{-1})
+    for (int j0 = NB; j0 < m; j0 += NB) {
+        const int nb = std::min(NB, m - j0);
+        const double* Rj = G + (int64_t)j0 * ldg;                       // R[:j0, j-block]
+        const double* Xjj = Rinv + (int64_t)j0 * ldr + j0;              // R_jj^{-1}
+        EDA_TRY(gemm_small_f64(false, false, j0, nb, nb, 1.0, Rj, ldg, Xjj, ldr, 0.0, T, j0, s));
+        EDA_TRY(gemm_small_f64(false, false, j0, nb, j0, -1.0, Rinv, ldr, T, j0, 0.0, Rinv + (int64_t)j0 * ldr, ldr,
+                               s));
+    }
+    return EDA_OK;
+}
+
+int chol_inv_auto(int b, double* G, int ldg, double* Rinv, double rank_tol, int* status, double* work, double* partial,
+                  size_t pcap, cudaStream_t s) {
+    if (b <= 90) return chol_inv_small(b, G, ldg, Rinv, rank_tol, 0.0, status, nullptr, s);
+    return chol_inv_blocked(b, G, ldg, Rinv, b, rank_tol, status, work, partial, pcap, s);
 }
 
 int copy_mat_f64(int64_t rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb, cudaStream_t s) {

@@ -106,6 +106,7 @@ struct SolveWs {
     double *Y, *Z, *Y2, *Z2, *Xt, *Gt, *Rt, *Rti, *lamd, *tmp64;
     double *R, *MR, *A2, *PQ, *Uc;   // refinement: [Y R] and [MY MR] adjacent; (2t)^2; (n + k) x t twice
     double* ZY;                      // refinement: Z^T [Y R], (n + k) x 2t
+    double* CW;                      // blocked Cholesky work (t > 90)
     int* idx;                        // refinement: unconverged columns
     void* part;
     int* lost;
@@ -464,7 +465,7 @@ int cholqr_f64(int64_t d, int p, double* X, double* tmpX, SolveWs<T>& w, int pas
     double* part = static_cast<double*>(w.part);
     for (int q = 0; q < passes; ++q) {
         EDA_TRY(syrk_f64(d, p, 1.0, X, d, 0.0, w.Rt, p, part, w.pcap, s));
-        EDA_TRY(chol_inv_small(p, w.Rt, p, w.Rti, 1e-28, 0.0, status, nullptr, s));
+        EDA_TRY(chol_inv_auto(p, w.Rt, p, w.Rti, 1e-28, status, w.CW, part, w.pcap, s));
         EDA_TRY(gemm_nn_f64(d, p, p, 1.0, X, d, w.Rti, p, 0.0, nullptr, 0, tmpX, d, s));
         EDA_TRY(copy_mat_f64(d, p, tmpX, d, X, d, s));
     }
@@ -612,6 +613,7 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     add((size_t)t * t * 4);            // Gt, Rt, Rti
     add(t);                            // lamd
     add(b + 64);                       // lost (ints)
+    add(chol_inv_blocked_doubles(std::max(t, b)));   // CW
     need += symeig_work_bytes(eig_n, t) + 16384;
     const bool oz = !mixed && h->cfg.prec == EDA_F64_TC && h->ozblock;
     const size_t ozT_bytes = oz ? a256(oz_operand_bytes(m_max, d)) : 0, ozN_bytes = oz ? a256(oz_operand_bytes(d, m_max)) : 0;
@@ -657,6 +659,7 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     (void)a.take<double>((size_t)t * t);
     w.lamd = a.take<double>(t);
     w.lost = a.take<int>(b + 64);
+    w.CW = a.take<double>(chol_inv_blocked_doubles(std::max(t, b)));
     EDA_TRY(symeig_work_carve(a, eig_n, t, h->bar, &w.eig));
     if (!w.lost) return EDA_ERR_OOM;
     if (oz) {
@@ -739,10 +742,10 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     {
         double* part = static_cast<double*>(w.part);
         EDA_TRY(syrk_f64(d, t, 1.0, w.Xt, d, 0.0, w.Rt, t, part, w.pcap, s));
-        EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
+        EDA_TRY(chol_inv_auto(t, w.Rt, t, w.Rti, 1e-28, h->status, w.CW, part, w.pcap, s));
         EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Xt, d, w.Rti, t, 0.0, nullptr, 0, Vout, d, s));
         EDA_TRY(syrk_f64(d, t, 1.0, Vout, d, 0.0, w.Rt, t, part, w.pcap, s));
-        EDA_TRY(chol_inv_small(t, w.Rt, t, w.Rti, 1e-28, 0.0, h->status, nullptr, s));
+        EDA_TRY(chol_inv_auto(t, w.Rt, t, w.Rti, 1e-28, h->status, w.CW, part, w.pcap, s));
         EDA_TRY(gemm_nn_f64(d, t, t, 1.0, Vout, d, w.Rti, t, 0.0, nullptr, 0, w.Xt, d, s));
         EDA_TRY(copy_mat_f64(d, t, w.Xt, d, Vout, d, s));
     }
