@@ -380,7 +380,9 @@ int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, ed
                     if (relres_h[i] <= tol) ++conv;
                     max_rel = std::max(max_rel, relres_h[i]);
                 }
-                int gap = b * h->cfg.check_every;
+                // no usable rate (no progress since the last check): wait an eighth of the basis width
+                int gap = (prev_cols > 0 && !(max_rel < prev_rel)) ? std::max(b * h->cfg.check_every, (cols / 8) / b * b)
+                                                                   : b * h->cfg.check_every;
                 if (prev_cols > 0 && max_rel > 0.0 && prev_rel > 0.0 && max_rel < prev_rel && std::isfinite(max_rel)) {
                     const double rate = std::pow(max_rel / prev_rel, 1.0 / ((double)(cols - prev_cols) / b));
                     const double need_b = std::log(tol / max_rel) / std::log(rate);

@@ -367,7 +367,10 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
                 st.max_rel = std::max(st.max_rel, st.relres[i]);
             }
             if (st.conv_count == t) st.converged = true;
-            int gap = b * h->cfg.check_every;
+            // no usable rate (no progress since the last check): wait an eighth of the basis width
+            int gap = (prev_check_cols > 0 && !(st.max_rel < prev_check_rel))
+                          ? std::max(b * h->cfg.check_every, (cols / 8) / b * b)
+                          : b * h->cfg.check_every;
             if (prev_check_cols > 0 && st.max_rel > 0.0 && prev_check_rel > 0.0 && st.max_rel < prev_check_rel &&
                 std::isfinite(st.max_rel)) {
                 const double blocks = (double)(cols - prev_check_cols) / b;
