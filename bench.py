@@ -2,9 +2,12 @@
 
 A step is the whole hot path on one synthetic problem shaped like the largest face workload that fits
 one GPU: 256x256 images, 200 classes of 10 images (d = 65536, n = 2000, t = 199, block size 32,
-tau = 20), plain FP64, inputs resident in HBM (1.05 GB of samples: larger than the 129 MB L2, which is
-also flushed by a 256 MB write before every step, outside the timed events). The d = 4096, k = 40
-workload (64x64 images) is timed beside it under "small_config".
+tau = 20), inputs resident in HBM (1.05 GB of samples: larger than the 129 MB L2, which is also flushed
+by a 256 MB write before every step, outside the timed events). The solver is FP64 throughout; by
+default (--prec tc) its products with [H_W H_B] and with the Krylov basis run as FP64-accurate
+tensor-core products (error-free splitting into bf16 digit planes), --prec f64 keeps them on the FP64
+pipe. The plain FP64 solver is timed beside it ("fp64_plain"), and the d = 4096, k = 40 workload (64x64
+images) under "small_config".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--workload NAME]
 
@@ -36,6 +39,9 @@ SMALL = "d4096_k40"
 # DRAM bytes (read + write) of one launch of the Gram SYRK kernel, k_gemm_tn_partial<32, double, SYRK>,
 # per workload, from ncu captures (profiles/); None until captured for the current kernel
 GRAM_TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch of k_oz_gemm, averaged over the launches of one step of the
+# workload, from an ncu capture of the same command (profiles/); None until captured for the current kernel
+OZ_TRAFFIC_BYTES = {}
 FALLBACK_HBM_GBS = 6800.0           # profiling recipe fallback when no measured peaks exist
 FALLBACK_BF16_TFLOPS = 1900.0
 
@@ -63,6 +69,8 @@ def parse():
     ap.add_argument("--profile-exp-apply", default=None, metavar="D,K,NJ,B",
                     help="profiling driver: build a bf16 handle on a d x (K*NJ) Gaussian-cluster problem "
                          "and run three W exp-applies of width B, nothing else")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--profile-build", default=None, metavar="WORKLOAD",
                     help="profiling driver: one FP64 build of the named workload (its first split-K launch is "
                          "the Gram SYRK G_W = H_W^T H_W), nothing else")
@@ -426,7 +434,8 @@ def run_gpu_batched(args, rank, world, local_rank):
 PRECS = {"tc": 4, "f64": 0}   # eda_prec codes: EDA_F64_TC, EDA_F64
 
 
-def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e=True, prec="tc"):
+def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e=True, prec="tc",
+                  profile_timed=False):
     """W untimed and K timed steps of one workload (build, solve, recovery, projection of the held-out
     set) with CUDA events on the launching stream, the L2 flushed before every step; optional end-to-end
     steps from pinned host buffers. Returns the per-step ms (max over ranks), the region timers read
@@ -467,12 +476,16 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     wall0 = time.perf_counter()
     infos = []
+    if profile_timed:
+        torch.cuda.profiler.start()
     for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
         infos.append(step())
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    if profile_timed:
+        torch.cuda.profiler.stop()
     wall = time.perf_counter() - wall0
     if dist is not None:
         dist.barrier()
@@ -481,7 +494,7 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     launches = eda.kernel_launches() - launches0
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dev)
     regions = {r: eda.profile_read(r) for r in REGIONS}
-    work = {r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "oz_gemm", "m_apply_composed",
+    work = {r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "m_apply_composed",
                                              "exp_apply_w", "tridiag")}
     out = dict(p=p, c=c, ms=ms, regions=regions, work=work, infos=infos, launches=launches, clocks=clk,
                wall=wall)
@@ -531,7 +544,7 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     return out
 
 
-REGIONS = ("gram", "tn_f64", "nn_f64", "oz_gemm", "cluster_orth", "exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
+REGIONS = ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "cluster_orth", "exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
            "tridiag", "bisect", "invit", "backtransform", "symeig", "lanczos", "phi_squaring", "rr", "reorth",
            "refine")
 
@@ -540,20 +553,60 @@ def rate(flops, ms):
     return flops / (ms / 1e3) / 1e12 if ms > 0 else float("nan")
 
 
-def roofline_of(name, r, steps):
-    """The step's dominant kernel, k_gemm_tn_partial<32, double> (the split-K A^T B product; largest share of
-    the ncu launch list at d65536_k200 and d4096_k40), on its largest launch: the Gram SYRK
-    G_W = H_W^T H_W of the build, d n (n + 1) flops (one triangle), timed as the library's "gram" region
-    (the SYRK and its split reduction) inside the timed region. FP64-ALU bound: its flops per byte of H_W
-    (n / 8) are far above GB300's FP64 ridge point."""
+def _all_launches(r, steps):
+    tn_ms, tn_calls = r["regions"]["tn_f64"]
+    nn_ms, nn_calls = r["regions"]["nn_f64"]
+    oz_ms, oz_calls = r["regions"]["oz_kernel"]
+    oz_flops, oz_bytes = r["work"]["oz_kernel"]
+    return {
+        "tn_f64": {"kernel": "k_gemm_tn_partial<*, double> (every FP64 split-K A^T B product of the step)",
+                   "achieved_tflops": rate(r["work"]["tn_f64"][0], tn_ms), "launches": tn_calls,
+                   "ms_per_step": tn_ms / steps},
+        "nn_f64": {"kernel": "k_gemm_nn<*, double> (every FP64 tall A B product of the step)",
+                   "achieved_tflops": rate(r["work"]["nn_f64"][0], nn_ms), "launches": nn_calls,
+                   "ms_per_step": nn_ms / steps},
+        "oz_kernel": {"kernel": "k_oz_gemm (tensor-core digit-plane products; the split of the narrow operand and "
+                                "the K-split reduction excluded)",
+                      "achieved_gbs": oz_bytes / (oz_ms / 1e3) / 1e9 if oz_ms > 0 else None,
+                      "tensor_tflops_bf16": rate(oz_flops, oz_ms) if oz_ms > 0 else None,
+                      "launches": oz_calls, "ms_per_step": oz_ms / steps},
+    }
+
+
+def roofline_of(name, r, steps, prec, pk):
+    """The dominant kernel of the step, on its launches inside the timed region (CUDA events around each
+    launch, averaged).
+
+    prec tc: k_oz_gemm, the FP64-accurate tensor-core product (largest share of the ncu launch list of
+    the tensor-core step). Per launch it must read the seven bf16 digit planes of its split operand
+    (14 M K bytes: Z^T or Z for the Grams and sweeps, the Krylov basis for its products) and of the
+    narrow operand (14 K p) and write the M x p result (8 M p); its 28 digit-plane MMAs per 64 values of
+    K (2 x 28 x 128 x 32 x 64 flops per 14 x 128 x 64 bytes of A: 128 flops per byte) sit below the bf16
+    ridge point of 1866 TFLOP/s / 6768 GB/s = 276 flops per byte, so it is HBM-bound.
+
+    prec f64: k_gemm_tn_partial<32, double, SYRK> + its split reduction on its largest launch, the Gram
+    SYRK G_W = H_W^T H_W of the build, d n (n + 1) flops (one triangle), timed as the library's "gram"
+    region. FP64-ALU bound: its flops per byte of H_W (n / 8) are far above GB300's FP64 ridge point."""
+    if prec == "tc":
+        ms, calls = r["regions"]["oz_kernel"]
+        flops, nbytes = r["work"]["oz_kernel"]
+        ach = nbytes / (ms / 1e3) / 1e9 if ms > 0 else float("nan")
+        return {
+            "kernel": "k_oz_gemm: FP64-accurate tensor-core product (7 bf16 digit planes per operand, tcgen05.mma "
+                      "M=128 N=32 K=16 into tensor memory, exact integer folding), every Gram, sweep and basis "
+                      "product of the step",
+            "bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s", "frac": ach / pk["hbm"],
+            "traffic": OZ_TRAFFIC_BYTES.get(name),
+            "algorithmic_bytes_per_launch": nbytes / max(calls, 1),
+            "avg_launch_us": ms * 1e3 / max(calls, 1), "launches": calls,
+            "tensor_tflops_bf16": rate(flops, ms),
+            "peak_source": f"{pk['source']} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                           if pk["source"] == "measured" else "profiling recipe fallback",
+            "all_launches": _all_launches(r, steps),
+        }
     g_ms, g_calls = r["regions"]["gram"]
     g_flops, g_bytes = r["work"]["gram"]
-    tn_ms, tn_calls = r["regions"]["tn_f64"]
-    tn_flops, _ = r["work"]["tn_f64"]
-    nn_ms, nn_calls = r["regions"]["nn_f64"]
-    nn_flops, _ = r["work"]["nn_f64"]
     ach = rate(g_flops, g_ms)
-    per_launch_flops = g_flops / max(g_calls, 1)
     return {
         "kernel": "k_gemm_tn_partial<32, double, SYRK> + split reduction: FP64 Gram G_W = H_W^T H_W, "
                   "d n (n + 1) flops per launch",
@@ -561,23 +614,11 @@ def roofline_of(name, r, steps):
         "frac": ach / NOMINAL_FP64_TFLOPS,
         "traffic": GRAM_TRAFFIC_BYTES.get(name),
         "algorithmic_bytes_per_launch": g_bytes / max(g_calls, 1),
-        "flops_per_launch": per_launch_flops, "avg_launch_us": g_ms * 1e3 / max(g_calls, 1), "launches": g_calls,
+        "flops_per_launch": g_flops / max(g_calls, 1), "avg_launch_us": g_ms * 1e3 / max(g_calls, 1),
+        "launches": g_calls,
         "peak_source": "nominal FP64 (non-tensor) rate of the profiling recipe; MEASURED_PEAKS.json has no FP64 "
                        "figure (own dependent-chain probe: 1.06-1.19 TFLOP/s attainable)",
-        "all_launches": {
-            "tn_f64": {"kernel": "k_gemm_tn_partial<*, double> (every split-K A^T B product of the step)",
-                       "achieved_tflops": rate(tn_flops, tn_ms), "launches": tn_calls,
-                       "ms_per_step": tn_ms / steps},
-            "nn_f64": {"kernel": "k_gemm_nn<*, double> (every tall A B product of the step)",
-                       "achieved_tflops": rate(nn_flops, nn_ms), "launches": nn_calls,
-                       "ms_per_step": nn_ms / steps},
-            "oz_gemm": {"kernel": "k_oz_gemm (+ splits of the narrow operand, reduction): FP64-accurate "
-                                  "tensor-core products of the split Z (Grams, sweeps, recovery)",
-                        "achieved_fp64_equivalent_tflops": rate(r["work"]["oz_gemm"][0], r["regions"]["oz_gemm"][0]),
-                        "achieved_gbs": (r["work"]["oz_gemm"][1] / (r["regions"]["oz_gemm"][0] / 1e3) / 1e9
-                                         if r["regions"]["oz_gemm"][0] > 0 else None),
-                        "launches": r["regions"]["oz_gemm"][1], "ms_per_step": r["regions"]["oz_gemm"][0] / steps},
-        },
+        "all_launches": _all_launches(r, steps),
     }
 
 
@@ -590,12 +631,12 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     r = time_workload(args.workload, args.steps, args.warmup, args.m_form, args.tol, dev, flush, rank, world,
-                      prec=args.prec)
+                      prec=args.prec, profile_timed=args.profile_timed)
     p, c = r["p"], r["c"]
     ms = r["ms"]
     regions = r["regions"]
     pk = peaks()
-    roofline = roofline_of(args.workload, r, args.steps)
+    roofline = roofline_of(args.workload, r, args.steps, args.prec, pk)
     tri_ms, tri_calls = regions["tridiag"]
     tri_flops, _ = r["work"]["tridiag"]
     latency_bound = {
@@ -610,21 +651,32 @@ def run_gpu(args, rank, world, local_rank):
     ew_ms, ew_calls = regions[region]
     ew_flops, ew_bytes = r["work"][region]
     ew_s = ew_ms / 1e3 if ew_ms > 0 else float("nan")
-    exp_apply_fp64 = {
-        "kernel": ("composed M-apply (FP64): M X = X + Z C Z^T X, Z = [H_W H_B]" if args.m_form == 1
-                   else "exp_apply (H_W, FP64 sweeps): Y = X + H_W K (H_W^T X)"),
-        "bound": "alu",
-        "achieved_tflops": ew_flops / ew_s / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
-        "frac": ew_flops / ew_s / 1e12 / NOMINAL_FP64_TFLOPS,
-        "achieved_gbs": ew_bytes / ew_s / 1e9, "hbm_peak_gbs": pk["hbm"], "hbm_peak_source": pk["source"],
-        "avg_call_us": ew_ms * 1e3 / max(ew_calls, 1), "calls": ew_calls,
-    }
+    if args.prec == "tc":
+        # the sweeps read the seven bf16 digit planes of Z (14 bytes per entry) once each: HBM-bound
+        m_apply = {
+            "kernel": "composed M-apply on the tensor cores: M X = X + Z C Z^T X, Z = [H_W H_B], both sweeps "
+                      "FP64-accurate digit-plane products (k_oz_gemm), C applied in FP64",
+            "bound": "hbm", "achieved_gbs": ew_bytes / ew_s / 1e9, "peak_gbs": pk["hbm"],
+            "frac": ew_bytes / ew_s / 1e9 / pk["hbm"], "peak_source": pk["source"],
+            "fp64_equivalent_tflops": ew_flops / ew_s / 1e12,
+            "avg_call_us": ew_ms * 1e3 / max(ew_calls, 1), "calls": ew_calls,
+        }
+    else:
+        m_apply = {
+            "kernel": ("composed M-apply (FP64): M X = X + Z C Z^T X, Z = [H_W H_B]" if args.m_form == 1
+                       else "exp_apply (H_W, FP64 sweeps): Y = X + H_W K (H_W^T X)"),
+            "bound": "alu",
+            "achieved_tflops": ew_flops / ew_s / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
+            "frac": ew_flops / ew_s / 1e12 / NOMINAL_FP64_TFLOPS,
+            "achieved_gbs": ew_bytes / ew_s / 1e9, "hbm_peak_gbs": pk["hbm"], "hbm_peak_source": pk["source"],
+            "avg_call_us": ew_ms * 1e3 / max(ew_calls, 1), "calls": ew_calls,
+        }
     small = None
     if args.small_steps > 0 and args.workload != SMALL and rank == 0:
         rs = time_workload(SMALL, args.small_steps, 5, args.m_form, args.tol, dev, flush, rank, 1, prec=args.prec)
         small = {"workload": workload_config(args, SMALL)["workload"], "ms_per_step": rs["ms"], "unit": "ms",
                  "e2e_ms": rs["e2e"]["value"], "gpu_launches_per_step": rs["launches"] / args.small_steps,
-                 "roofline": roofline_of(SMALL, rs, args.small_steps),
+                 "roofline": roofline_of(SMALL, rs, args.small_steps, args.prec, pk),
                  "solve_info": {kk: rs["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols",
                                                                    "refills", "max_relres_est")}}
     fp64_leg = None
@@ -651,7 +703,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": r["e2e"],
         "roofline": roofline,
         "tridiag": latency_bound,
-        "exp_apply_fp64": exp_apply_fp64,
+        "m_apply": m_apply,
         "exp_apply_bf16": exp_leg,
         "small_config": small,
         "fp64_plain": fp64_leg,

@@ -521,18 +521,22 @@ int oz_gemm(const OzOperand& A, OzNarrow& nb, int p, const double* B, int64_t ld
     const int kps = ceil_div(kst, splits);
     splits = ceil_div(kst, kps);
     const dim3 grid((unsigned)A.mtiles, (unsigned)splits);
-    if (splits == 1) {
-        k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps,
-                                                            (int)A.M, p, kst, kps, alpha, beta, C0, ldc0, D, ldd, 0,
-                                                            status);
+    const int64_t sstride = splits == 1 ? 0 : (int64_t)p * A.M;
+    {
+        // the tensor-core kernel alone: it must read the seven digit planes of A and of B once and write D
+        ProfScope kprof("oz_kernel", s, 2.0 * OZ_S * OZ_S * (double)A.M * A.K * p,
+                        2.0 * OZ_S * ((double)A.M * A.K + (double)A.K * p) + 8.0 * (double)A.M * p);
+        if (splits == 1)
+            k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps,
+                                                                (int)A.M, p, kst, kps, alpha, beta, C0, ldc0, D, ldd,
+                                                                0, status);
+        else
+            k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps,
+                                                                (int)A.M, p, kst, kps, 1.0, 0.0, nullptr, 0,
+                                                                nb.partial, A.M, sstride, status);
         EDA_LAUNCHED();
-        return EDA_OK;
     }
-    const int64_t sstride = (int64_t)p * A.M;
-    k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps, (int)A.M,
-                                                        p, kst, kps, 1.0, 0.0, nullptr, 0, nb.partial, A.M, sstride,
-                                                        status);
-    EDA_LAUNCHED();
+    if (splits == 1) return EDA_OK;
     k_oz_reduce<<<ceil_div((int64_t)A.M * p, 256), 256, 0, s>>>((int)A.M, p, splits, nb.partial, sstride, alpha,
                                                                  beta, C0, ldc0, D, ldd);
     EDA_LAUNCHED();

@@ -116,6 +116,7 @@ struct SolveWs {
     // scales over the current columns, split afresh whenever a block is added)
     bool oz = false;
     OzOperand VT, VN;
+    int oz_cap = 0;                  // columns the basis operands hold (m_max)
 };
 
 // tc products with the split basis, 32 columns at a time: C (cols x p, ldc) = V^T X, and X -= V C
@@ -416,8 +417,11 @@ int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY
                      double* U, double* ZtY, double* part, size_t pcap, cudaStream_t s) {
     const int64_t d = h->d;
     const int n = (int)h->n, k = h->k, nk = n + k;
+    // bytes: Z read once per sweep (FP64, or its seven bf16 digit planes on the tensor-core path), Y read
+    // twice and MY written
+    const double zbytes = (h->cfg.prec == EDA_F64_TC && h->ozblock) ? 14.0 : 8.0;
     ProfScope prof("m_apply_composed", s, 4.0 * d * nk * p + 2.0 * p * (3.0 * n * n + 2.0 * n * k + k * k),
-                   8.0 * (2.0 * d * nk + 3.0 * d * p));
+                   2.0 * zbytes * d * nk + 8.0 * 3.0 * d * p);
     EDA_TRY(sweep_zt(h, p, Y, ldy, PQ, part, pcap, s));
     if (ZtY) EDA_TRY(copy_mat_f64(nk, p, PQ, nk, ZtY, nk, s));   // keep Z^T y (coordinates) for the caller
     double* Pw = PQ;
@@ -461,15 +465,53 @@ int sweep_z(eda_ctx* h, int p, const double* U, const double* Y, int64_t ldy, do
 
 namespace {
 
+// Products of the FP64 finish (refinement, final CholQR2) with d-long operands. With the tensor-core
+// FP64 mode they run as FP64-accurate digit-plane products, the d-long operand split afresh into the
+// solve's basis-operand buffers (free once the Krylov phase has ended); otherwise on the FP64 pipe.
+// C (m x p, ldc) = A^T B, A d x m (ld d), B d x p (ldb).
+template <class T>
+int fin_tn(eda_ctx* h, SolveWs<T>& w, int m, int p, const double* A, const double* B, int64_t ldb, double* C,
+           int ldc, cudaStream_t s) {
+    const int64_t d = h->d;
+    if (w.oz && m <= w.oz_cap) {
+        OzOperand op;
+        EDA_TRY(oz_operand_make(A, d, m, d, true, w.VT.tiles, &op, s));
+        for (int c0 = 0; c0 < p; c0 += 32)
+            EDA_TRY(oz_gemm(op, h->oznb, std::min(32, p - c0), B + (size_t)c0 * ldb, ldb, 1.0, 0.0, nullptr, 0,
+                            C + (size_t)c0 * ldc, ldc, h->status, s));
+        return EDA_OK;
+    }
+    return gemm_tn_f64(d, m, p, 1.0, A, d, B, ldb, 0.0, C, ldc, static_cast<double*>(w.part), w.pcap, s);
+}
+// OUT (d x p, ld d) = alpha A Bs + beta X0, A d x m (ld d), Bs m x p (ldbs), X0 ld d (may be OUT).
+template <class T>
+int fin_nn(eda_ctx* h, SolveWs<T>& w, int m, int p, double alpha, const double* A, const double* Bs, int ldbs,
+           double beta, const double* X0, double* OUT, cudaStream_t s) {
+    const int64_t d = h->d;
+    if (w.oz && m <= w.oz_cap) {
+        OzOperand op;
+        EDA_TRY(oz_operand_make(A, d, d, m, false, w.VN.tiles, &op, s));
+        for (int c0 = 0; c0 < p; c0 += 32)
+            EDA_TRY(oz_gemm(op, h->oznb, std::min(32, p - c0), Bs + (size_t)c0 * ldbs, ldbs, alpha, beta,
+                            X0 ? X0 + (size_t)c0 * d : nullptr, d, OUT + (size_t)c0 * d, d, h->status, s));
+        return EDA_OK;
+    }
+    return gemm_nn_f64(d, m, p, alpha, A, d, Bs, ldbs, beta, X0, d, OUT, d, s);
+}
+
 // X (d x p) <- orth(X) by CholQR in FP64, `passes` times (columns at the rank threshold come out
 // zero). One pass suffices for an input that is orthonormal to single precision.
 template <class T>
-int cholqr_f64(int64_t d, int p, double* X, double* tmpX, SolveWs<T>& w, int passes, int* status, cudaStream_t s) {
+int cholqr_f64(eda_ctx* h, int p, double* X, double* tmpX, SolveWs<T>& w, int passes, cudaStream_t s) {
+    const int64_t d = h->d;
     double* part = static_cast<double*>(w.part);
     for (int q = 0; q < passes; ++q) {
-        EDA_TRY(syrk_f64(d, p, 1.0, X, d, 0.0, w.Rt, p, part, w.pcap, s));
-        EDA_TRY(chol_inv_auto(p, w.Rt, p, w.Rti, 1e-28, status, w.CW, part, w.pcap, s));
-        EDA_TRY(gemm_nn_f64(d, p, p, 1.0, X, d, w.Rti, p, 0.0, nullptr, 0, tmpX, d, s));
+        if (w.oz && p <= w.oz_cap)
+            EDA_TRY(fin_tn(h, w, p, p, X, X, d, w.Rt, p, s));
+        else
+            EDA_TRY(syrk_f64(d, p, 1.0, X, d, 0.0, w.Rt, p, part, w.pcap, s));
+        EDA_TRY(chol_inv_auto(p, w.Rt, p, w.Rti, 1e-28, h->status, w.CW, part, w.pcap, s));
+        EDA_TRY(fin_nn(h, w, p, p, 1.0, X, w.Rti, p, 0.0, nullptr, tmpX, s));
         EDA_TRY(copy_mat_f64(d, p, tmpX, d, X, d, s));
     }
     return EDA_OK;
@@ -516,14 +558,14 @@ int refine_f64(eda_ctx* h, int t, double tol, SolveWs<T>& w, int max_iter, int* 
     double* part = static_cast<double*>(w.part);
     if (!h->GWB) return EDA_ERR_INVALID_ARG;   // cross Grams are formed at build for mixed handles
     // span(Y): orthonormalise (Y is orthonormal to single precision: one CholQR pass), M Y, Rayleigh-Ritz
-    EDA_TRY(cholqr_f64<T>(d, t, w.Y, w.Y2, w, 1, h->status, s));
+    EDA_TRY(cholqr_f64<T>(h, t, w.Y, w.Y2, w, 1, s));
     EDA_TRY(m_apply_composed(h, t, w.Y, d, w.Z, d, w.PQ, w.Uc, w.ZY, part, w.pcap, s));
     *mapplies += (t + b - 1) / b;
-    EDA_TRY(gemm_tn_f64(d, t, t, 1.0, w.Y, d, w.Z, d, 0.0, w.Gt, t, part, w.pcap, s));
+    EDA_TRY(fin_tn(h, w, t, t, w.Y, w.Z, d, w.Gt, t, s));
     EDA_TRY(symmetrize_f64(t, w.Gt, t, s));
     EDA_TRY(symeig_f64(t, w.Gt, t, 0, t - 1, w.theta, w.S, t, &w.eig, h->status, h->cfg.seed + 11, 1e-7, s));
-    EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Y, d, w.S, t, 0.0, nullptr, 0, w.Y2, d, s));
-    EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Z, d, w.S, t, 0.0, nullptr, 0, w.Z2, d, s));
+    EDA_TRY(fin_nn(h, w, t, t, 1.0, w.Y, w.S, t, 0.0, nullptr, w.Y2, s));
+    EDA_TRY(fin_nn(h, w, t, t, 1.0, w.Z, w.S, t, 0.0, nullptr, w.Z2, s));
     EDA_TRY(copy_mat_f64(d, t, w.Y2, d, w.Y, d, s));
     EDA_TRY(copy_mat_f64(d, t, w.Z2, d, w.Z, d, s));
     EDA_TRY(gemm_small_f64(false, false, nk, t, t, 1.0, w.ZY, nk, w.S, t, 0.0, w.PQ, nk, s));
@@ -544,19 +586,19 @@ int refine_f64(eda_ctx* h, int t, double tol, SolveWs<T>& w, int max_iter, int* 
         EDA_LAUNCHED();
         EDA_TRY(copy_mat_f64(d, r, w.Y2, d, w.R, d, s));
         for (int pass = 0; pass < 2; ++pass) {
-            EDA_TRY(gemm_tn_f64(d, t, r, 1.0, w.Y, d, w.R, d, 0.0, w.Gt, t, part, w.pcap, s));
-            EDA_TRY(gemm_nn_f64(d, t, r, -1.0, w.Y, d, w.Gt, t, 1.0, w.R, d, w.R, d, s));
+            EDA_TRY(fin_tn(h, w, t, r, w.Y, w.R, d, w.Gt, t, s));
+            EDA_TRY(fin_nn(h, w, t, r, -1.0, w.Y, w.Gt, t, 1.0, w.R, w.R, s));
         }
-        EDA_TRY(cholqr_f64<T>(d, r, w.R, w.Y2, w, 2, h->status, s));
+        EDA_TRY(cholqr_f64<T>(h, r, w.R, w.Y2, w, 2, s));
         // M R_u, then Rayleigh-Ritz on [Y R_u] (adjacent in memory, as are [MY M R_u] and their coordinates)
         EDA_TRY(m_apply_composed(h, r, w.R, d, w.MR, d, w.PQ, w.Uc, w.ZY + (size_t)nk * t, part, w.pcap, s));
         *mapplies += (r + b - 1) / b;
-        EDA_TRY(gemm_tn_f64(d, tr, tr, 1.0, w.Y, d, w.Z, d, 0.0, w.A2, tr, part, w.pcap, s));
+        EDA_TRY(fin_tn(h, w, tr, tr, w.Y, w.Z, d, w.A2, tr, s));
         EDA_TRY(symmetrize_f64(tr, w.A2, tr, s));
         EDA_TRY(symeig_f64(tr, w.A2, tr, r, tr - 1, w.theta, w.S, tr, &w.eig, h->status, h->cfg.seed + 13 + it,
                            1e-7, s));
-        EDA_TRY(gemm_nn_f64(d, tr, t, 1.0, w.Y, d, w.S, tr, 0.0, nullptr, 0, w.Y2, d, s));
-        EDA_TRY(gemm_nn_f64(d, tr, t, 1.0, w.Z, d, w.S, tr, 0.0, nullptr, 0, w.Z2, d, s));
+        EDA_TRY(fin_nn(h, w, tr, t, 1.0, w.Y, w.S, tr, 0.0, nullptr, w.Y2, s));
+        EDA_TRY(fin_nn(h, w, tr, t, 1.0, w.Z, w.S, tr, 0.0, nullptr, w.Z2, s));
         EDA_TRY(copy_mat_f64(d, t, w.Y2, d, w.Y, d, s));
         EDA_TRY(copy_mat_f64(d, t, w.Z2, d, w.Z, d, s));
         EDA_TRY(gemm_small_f64(false, false, nk, t, tr, 1.0, w.ZY, nk, w.S, tr, 0.0, w.PQ, nk, s));
@@ -672,6 +714,7 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
         EDA_TRY(oz_operand_init(m_max, d, mT, &w.VT, s));
         EDA_TRY(oz_operand_init(d, m_max, mN, &w.VN, s));
         w.oz = true;
+        w.oz_cap = m_max;
     }
     EDA_CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), s));
     EDA_CUDA_TRY(cudaMemsetAsync(w.Tm, 0, (size_t)m_max * m_max * 8, s));
@@ -741,17 +784,8 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
         EDA_TRY(exp_apply<double>(d, h->HW, h->KW, n, "exp_apply_w", t, w.Y2, d, w.Xt, d, w.P, w.Q, w.part, w.pcap,
                                   s));
     }
-    // V = orth(X_t): CholQR2
-    {
-        double* part = static_cast<double*>(w.part);
-        EDA_TRY(syrk_f64(d, t, 1.0, w.Xt, d, 0.0, w.Rt, t, part, w.pcap, s));
-        EDA_TRY(chol_inv_auto(t, w.Rt, t, w.Rti, 1e-28, h->status, w.CW, part, w.pcap, s));
-        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, w.Xt, d, w.Rti, t, 0.0, nullptr, 0, Vout, d, s));
-        EDA_TRY(syrk_f64(d, t, 1.0, Vout, d, 0.0, w.Rt, t, part, w.pcap, s));
-        EDA_TRY(chol_inv_auto(t, w.Rt, t, w.Rti, 1e-28, h->status, w.CW, part, w.pcap, s));
-        EDA_TRY(gemm_nn_f64(d, t, t, 1.0, Vout, d, w.Rti, t, 0.0, nullptr, 0, w.Xt, d, s));
-        EDA_TRY(copy_mat_f64(d, t, w.Xt, d, Vout, d, s));
-    }
+    // V = orth(X_t): CholQR2 (leaves V in both)
+    EDA_TRY(cholqr_f64<T>(h, t, w.Xt, Vout, w, 2, s));
     double true_max = -1.0;
     if (h->cfg.true_residuals) {
         // R = M Y - Y diag(theta) in FP64, in blocks of at most tw columns
