@@ -206,8 +206,10 @@ int ensure_n_operators(eda_ctx* h, cudaStream_t s) {
         EDA_TRY(phi_operator(n, ns, lam, h->evecs_w, n, c2, h->KWp, work, s));
     } else {
         // by scaling and squaring of G_W (the build's route for small Grams)
-        EDA_TRY(phi_by_squaring(n, h->GW, -c2, h->lmax_w, h->KWm, work, s));
-        EDA_TRY(phi_by_squaring(n, h->GW, c2, h->lmax_w, h->KWp, work, s));
+        const OzSquare oz{&h->oznb, h->ozsmall, h->status};
+        const OzSquare* pz = h->ozsmall ? &oz : nullptr;
+        EDA_TRY(phi_by_squaring(n, h->GW, -c2, h->lmax_w, h->KWm, work, s, pz));
+        EDA_TRY(phi_by_squaring(n, h->GW, c2, h->lmax_w, h->KWp, work, s, pz));
     }
     return EDA_OK;
 }

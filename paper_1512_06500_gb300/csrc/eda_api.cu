@@ -83,6 +83,7 @@ constexpr int kEigClusterMaxN = 512;   // the eigensolver's cluster path (no gri
 constexpr double kSigRel = 32.0;   // eigenvalues <= kSigRel * n * eps * lambda_max are the Gram's null space
 constexpr int kLanczosSteps = 64;  // steps of the largest-eigenvalue Lanczos run on a Gram
 constexpr double kLmaxAccept = 8.0;  // accept its theta_1 when its residual is <= kLmaxAccept * eps * theta_1
+constexpr int kLanczosStepsLarge = 160;   // the same run on a large Gram (n >= kOzSmallMinN, tensor-core mode)
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -328,6 +329,33 @@ double lmax_accepted(const double* o) {
     return std::max(t1, 0.0);
 }
 
+// lambda_max of one Gram (m x m) by a Lanczos run of kLanczosStepsLarge steps, falling back to the full
+// eigensolver's largest eigenvalue (into w) when the residual does not accept the estimate.
+int gram_lmax_one(eda_ctx* h, int m, const double* G, double* w, Arena& scratch, double* lmax, cudaStream_t s) {
+    SymEigWork ws{};
+    EDA_TRY(symeig_work_carve(scratch, m, 1, h->bar, &ws));
+    double* out = scratch.take<double>(4);
+    if (!out) return EDA_ERR_OOM;
+    EDA_TRY(lanczos_top(m, G, m, std::min(m, kLanczosStepsLarge), h->cfg.seed, &ws, out, s));
+    double o[4];
+    EDA_CUDA_TRY(cudaMemcpyAsync(o, out, sizeof(o), cudaMemcpyDeviceToHost, s));
+    EDA_CUDA_TRY(cudaStreamSynchronize(s));
+    double l = lmax_accepted(o);
+    if (l < 0.0) {
+        EDA_TRY(symeig_values(m, G, m, m - 1, m - 1, w, &ws, h->status, s));
+        double top = 0.0;
+        EDA_CUDA_TRY(cudaMemcpyAsync(&top, w, sizeof(double), cudaMemcpyDeviceToHost, s));
+        EDA_CUDA_TRY(cudaStreamSynchronize(s));
+        int st = 0;
+        EDA_TRY(read_status(h, s, &st));
+        if (int c = status_to_code(st)) return c;
+        if (!std::isfinite(top)) return EDA_ERR_NONFINITE;
+        l = std::max(top, 0.0);
+    }
+    *lmax = l;
+    return EDA_OK;
+}
+
 // lambda_max of G_W and G_B without their eigenvectors: one Lanczos run per Gram, side by side on two
 // streams (aux is already forked from s and holds the G_B product), one host wait for both; a Gram
 // whose residual does not accept its estimate falls back to the full eigensolver's largest eigenvalue.
@@ -418,6 +446,17 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     double* partB = nullptr;
     size_t pcapB = 0;
     const bool tc = h->cfg.prec == EDA_F64_TC;
+    // Large G_W in tensor-core mode: lambda_max by Lanczos and K_W by scaling and squaring with
+    // FP64-accurate tensor-core products, instead of the n-step tridiagonalisation and the
+    // back-transformation of the eigensolver; G_B keeps its route.
+    const bool sq_w_tc = tc && !by_squaring && n >= kOzSmallMinN;
+    if (sq_w_tc) {
+        // three n x n split operands: the squaring's left factors, then K_W and G_W for the solves
+        const size_t b1 = align256(oz_operand_bytes(n, n));
+        void* p = nullptr;
+        EDA_CUDA_TRY(cudaMalloc(&p, 3 * b1));
+        h->ozsmall = p;
+    }
     if (tc) {
         // every Gram as a block of Z^T Z on the tensor cores, from the split Z the sweeps use as well
         EDA_TRY(tc_operands(h, s));
@@ -459,6 +498,11 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     int nsw = 0, nsb = 0, first_w = 0, first_b = 0;
     if (by_squaring) {
         EDA_TRY(gram_lmax_pair(h, scratch, aux, s));
+    } else if (sq_w_tc) {
+        EDA_TRY(gram_lmax_one(h, n, h->GW, h->evals_w, scratch, &h->lmax_w, s));
+        scratch.used = mark;
+        EDA_TRY(gram_eigen(h, k, h->GB, h->evals_b, h->evecs_b, scratch, part, pcap, &h->lmax_b, &nsb, s));
+        first_b = h->nsig_first;
     } else if (n <= kEigClusterMaxN && k <= kEigClusterMaxN) {
         // both on the cluster path (no grid barrier): solve side by side
         EDA_TRY(gram_eigen_pair(h, scratch, part, pcap, &nsw, &nsb, &first_w, &first_b, s));
@@ -472,7 +516,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     scratch.used = mark;
     h->nsig_w = nsw;
     h->nsig_b = nsb;
-    h->eig_ready = !by_squaring;
+    h->eig_ready = !by_squaring && !sq_w_tc;
     if (h->cfg.c2 > 0.0) {
         h->c2 = h->cfg.c2;
     } else {
@@ -496,10 +540,25 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     } else {
         double* tmp = scratch.take<double>(N * N + 64);
         if (!tmp) return EDA_ERR_OOM;
-        EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
+        if (sq_w_tc) {
+            double* workW = scratch.take<double>(6 * (size_t)n * n);
+            if (!workW) return EDA_ERR_OOM;
+            ProfScope prof("phi_squaring", s);
+            const OzSquare oz{&h->oznb, h->ozsmall, h->status};
+            EDA_TRY(phi_by_squaring(n, h->GW, -0.5 * h->c2, h->lmax_w, h->KW, workW, s, &oz));
+        } else {
+            EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
+        }
         EDA_TRY(phi_operator(k, nsb, h->evals_b + first_b, h->evecs_b, k, h->c2, h->KB, tmp, s));
     }
     if (cross && !by_squaring) EDA_TRY(ensure_cross_gram(h, part, pcap, s));
+    if (sq_w_tc) {
+        // K_W and G_W are symmetric: column i is row i, so the column-scaled split serves as the left factor
+        const size_t b1 = align256(oz_operand_bytes(n, n));
+        char* p = static_cast<char*>(h->ozsmall);
+        EDA_TRY(oz_operand_make(h->KW, n, n, n, true, p + b1, &h->ozKW, h->status, s));
+        EDA_TRY(oz_operand_make(h->GW, n, n, n, true, p + 2 * b1, &h->ozGW, h->status, s));
+    }
     if (h->cfg.prec == EDA_BF16) {
         // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
         // buffers of X and P with their tensor maps (zeroed: padded rows are read as zeros)
@@ -547,8 +606,8 @@ int tc_operands(eda_ctx* h, cudaStream_t s) {
     EDA_CUDA_TRY(cudaMalloc(&p, bT + bN + bS));
     h->ozblock = p;
     char* c = static_cast<char*>(p);
-    EDA_TRY(oz_operand_make(h->HW, d, nk, d, true, c, &h->ozT, s));
-    EDA_TRY(oz_operand_make(h->HW, d, d, nk, false, c + bT, &h->ozN, s));
+    EDA_TRY(oz_operand_make(h->HW, d, nk, d, true, c, &h->ozT, h->status, s));
+    EDA_TRY(oz_operand_make(h->HW, d, d, nk, false, c + bT, &h->ozN, h->status, s));
     EDA_TRY(oz_narrow_make(std::max<int64_t>(d, nk), sm_count(), nk, c + bT + bN, &h->oznb));
     return EDA_OK;
 }
@@ -826,6 +885,7 @@ void eda_destroy(eda_handle h) {
     if (h->kblock) cudaFree(h->kblock);
     if (h->xblock) cudaFree(h->xblock);
     if (h->ozblock) cudaFree(h->ozblock);
+    if (h->ozsmall) cudaFree(h->ozsmall);
     if (h->nblock) cudaFree(h->nblock);
     if (h->block32) cudaFree(h->block32);
     if (h->block) cudaFree(h->block);

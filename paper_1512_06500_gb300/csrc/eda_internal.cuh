@@ -182,12 +182,14 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
 int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, uint64_t seed,
                    double cluster_rel, cudaStream_t s);
 // Lanczos estimate of the largest eigenvalue of a symmetric positive semidefinite n x n matrix A
-// (n <= kLanczosMaxN): m steps of the three-term recurrence in one thread-block cluster, then the
+// (n <= kLanczosMaxN: in one thread-block cluster with the matrix in shared memory; beyond: two
+// launches per step, the matrix read from global memory): m steps of the three-term recurrence, then the
 // two largest eigenvalues of the m x m tridiagonal and the last entry of the unit eigenvector of the
 // largest. out (device, 4 doubles): theta_1, theta_2 (-DBL_MAX when m = 1), |z_m|, beta_m; the
 // distance from theta_1 to an eigenvalue of A is at most beta_m |z_m|, and at most
 // (beta_m z_m)^2 / (theta_1 - theta_2 - beta_m |z_m|) when that gap is positive. ws: carved for n.
 constexpr int kLanczosMaxN = 256;
+constexpr int kOzSmallMinN = 512;     // n from which K_W and G_W products run on the tensor cores
 int lanczos_top(int n, const double* A, int lda, int m, uint64_t seed, SymEigWork* ws, double* out,
                 cudaStream_t s);
 // Orthonormalise the columns of Z (n x nv) against each other by Newton-Schulz steps
@@ -208,10 +210,6 @@ int check_finite_f64(int64_t rows, int cols, const double* A, int64_t lda, int* 
 // and phi(0) = 1. tmp: n * ns doubles.
 int phi_operator(int n, int ns, const double* lam, const double* W, int ldw, double alpha,
                  double* K, double* tmp, cudaStream_t s);
-// The same K(alpha) = alpha phi(alpha G) from G itself by scaling and squaring (dense products
-// only), given lmax >= the largest eigenvalue of G. work: 6 m^2 doubles.
-int phi_by_squaring(int m, const double* G, double alpha, double lmax, double* K, double* work,
-                    cudaStream_t s);
 
 // ---------------------------------------------------------------- exp-apply
 struct ExpOp {
@@ -293,21 +291,34 @@ struct OzNarrow {
 size_t oz_operand_bytes(int64_t M, int64_t K);
 // Split A (lda) into the operand: rows_are_cols = true: M = columns of A (d x M matrix, K = d rows);
 // false: M = rows of A (M x K matrix). mem: oz_operand_bytes(M, K) bytes, 256-byte aligned.
+// Splitting flags ST_NONFINITE in *status when it meets Inf or NaN.
 int oz_operand_make(const double* A, int64_t lda, int64_t M, int64_t K, bool rows_are_cols, void* mem,
-                    OzOperand* op, cudaStream_t s);
+                    OzOperand* op, int* status, cudaStream_t s);
 // A growing operand (the Krylov basis): room for Mcap rows and Kcap reduction values, planes zeroed.
 // oz_append_cols: split columns i0 .. i1 of A (d x ., lda) as rows i0 .. i1 of a column-scaled operand
 // (K = d). oz_resplit_rows: split all of A (M x K) afresh as a row-scaled operand (row scales over the K
 // columns present).
 int oz_operand_init(int64_t Mcap, int64_t Kcap, void* mem, OzOperand* op, cudaStream_t s);
-int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOperand* op, cudaStream_t s);
-int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperand* op, cudaStream_t s);
+int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOperand* op, int* status,
+                   cudaStream_t s);
+int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperand* op, int* status, cudaStream_t s);
 size_t oz_narrow_bytes(int64_t Kmax, int max_splits, int64_t Mmax);
 int oz_narrow_make(int64_t Kmax, int max_splits, int64_t Mmax, void* mem, OzNarrow* nb);
 // D (M x p, ldd) = alpha * op(A) B + beta * C0 (ldc0), op(A) the M x K split operand, B: K x p (ldb),
 // p <= 32, in FP64 accuracy on the bf16 tensor cores. D may equal C0 (same ld).
 int oz_gemm(const OzOperand& A, OzNarrow& nb, int p, const double* B, int64_t ldb, double alpha, double beta,
             const double* C0, int64_t ldc0, double* D, int64_t ldd, int* status, cudaStream_t s);
+
+// K(alpha) = alpha phi(alpha G) from G itself by scaling and squaring (dense products only), given
+// lmax >= the largest eigenvalue of G. work: 6 m^2 doubles. With oz the m x m products run on the
+// tensor cores: abuf holds oz_operand_bytes(m, m) bytes, nb a narrow staging area for K = m.
+struct OzSquare {
+    OzNarrow* nb = nullptr;
+    void* abuf = nullptr;
+    int* status = nullptr;
+};
+int phi_by_squaring(int m, const double* G, double alpha, double lmax, double* K, double* work,
+                    cudaStream_t s, const OzSquare* oz = nullptr);
 
 }  // namespace eda
 
@@ -351,6 +362,11 @@ struct eda_ctx {
     void* ozblock = nullptr;
     eda::OzOperand ozT, ozN;
     eda::OzNarrow oznb;
+    // prec = EDA_F64_TC and n >= kOzSmallMinN: the left-factor split of the scaling and squaring that
+    // forms K_W (and, for the nonsymmetric form, K(-c^2) and K(+c^2)), then K_W and G_W split for
+    // their products with the n x p coordinates inside the composed M-apply and the recovery
+    void* ozsmall = nullptr;
+    eda::OzOperand ozKW, ozGW;
     // K(-c^2) and K(+c^2) for H_W, the operators of the nonsymmetric form exp(-c^2 S_W) exp(c^2 S_B) and of
     // exp(c^2 S_W) (allocated on first use by the Arnoldi solver)
     void* nblock = nullptr;

@@ -5,9 +5,10 @@
 //
 // Splitting. Each row i of an operand (the rows of the MMA's M or N side; the reduction index k runs
 // along it) gets a power-of-two scale 2^{e_i} with |a_ik| < 2^{e_i}. Then
-//     a_ik = 2^{e_i - 7} (s_0 + 2^-8 s_1 + ... + 2^-48 s_6) + tail,   |tail| <= 2^{e_i - 57},
-// with integer digits s_q in [-128, 128] from the exact recurrence x_0 = a 2^{7 - e}, s_q = rint(x_q),
-// x_{q+1} = 256 (x_q - s_q) (every step is exact in FP64). A digit is exact in bf16 (8 significant bits).
+//     a_ik = 2^{e_i - 7} (s_0 + 2^-8 s_1 + ... + 2^-48 s_6) + tail,   |tail| <= 2^{e_i - 56},
+// with integer digits s_q in [-128, 128]: the balanced base-256 digits of the integer nearest to
+// a 2^{55 - e}, extracted with integer operations from the bits of a. A digit is exact in bf16 (8
+// significant bits).
 //
 // Products. For D = A B^T over the reduction index (A: M x K, B: N x K, both split),
 //     D_ij = 2^{e_i + f_j - 14} sum_q 2^{-8q} L_q,    L_q = sum_{a + b = q} sum_k s^A_{a,ik} s^B_{b,jk},
@@ -21,10 +22,11 @@
 //
 // Kernel. One CTA per (128-row band of M, split of K), 256 threads: thread 0 issues the bulk copies of
 // the pre-tiled digit planes of A (one contiguous 16 KB swizzled tile per K stage of 64 and plane) and
-// the TMA boxes of the seven planes of B; thread 32 issues tcgen05.mma (M = 128, N = 32, K = 16) into one
-// of two accumulator sets of seven levels in tensor memory (7 x 32 columns each), switching sets every
-// chunk of two K stages; warps 4-7 drain a finished set (tcgen05.ld, integer fold) while the tensor
-// cores fill the other. Every wait is bounded (ST_TIMEOUT on give-up).
+// the TMA boxes of the seven planes of B; thread 32 issues tcgen05.mma (M = 128, K = 16, N = 32 (7 - a) for
+// digit plane a of A against planes 0 .. 6 - a of B at once) into one of two accumulator sets of seven
+// levels in tensor memory (7 x 32 columns each), switching sets every chunk of two K stages; warps 4-7
+// drain a finished set (tcgen05.ld, integer fold) while the tensor cores fill the other. Every wait is
+// bounded (ST_TIMEOUT on give-up).
 #include "tc_ptx.cuh"
 
 #include <algorithm>
@@ -127,7 +129,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
     } else if (tid == 32) {
         // ---- MMA issuer ----
-        constexpr uint32_t idesc = idesc_bf16(TC_M, OZ_N);
         for (int s = 0; s < nks && ok; ++s) {
             const int chunk = s >> 1, set = chunk & 1;
             const bool first = (s & 1) == 0;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const int bslot = s % OZ_BST;
             if (!(ok = mbar_wait(&sm.fullB[bslot], (s / OZ_BST) & 1, status))) break;
             // descriptors differ only in their start-address field (address / 16): a K step of 16 elements
-            // is +2, the next B plane (4 KB further) +256; computed once per stage and tile
+            // is +2; computed once per stage and tile
             const uint64_t bdesc = smem_desc_sw128(smem_u32(sm.B[bslot][0]));
             const uint32_t dset = tmem + (uint32_t)(set * OZ_SET_COLS);
 #pragma unroll
@@ -145,15 +146,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 if (!(ok = mbar_wait(&sm.fullA[slot], (idx / OZ_AST) & 1, status))) break;
                 tc_fence_after();
                 const uint64_t adesc = smem_desc_sw128(smem_u32(sm.A[slot]));
+                // A plane a against B planes 0 .. 6 - a in one MMA per K step: those planes are consecutive
+                // in shared memory, one operand of N = 32 (7 - a) rows, and the product with plane b lands
+                // 32 b columns into the accumulator, so starting it at level column 32 a puts it in level
+                // a + b. A is read from shared memory once per K step instead of once per B plane.
+                const uint32_t idesc = idesc_bf16(TC_M, OZ_N * (OZ_S - a));
+                const uint32_t dcol = dset + (uint32_t)(a * OZ_N);
 #pragma unroll
-                for (int b = 0; b < OZ_S - a; ++b) {
-                    const uint32_t dcol = dset + (uint32_t)((a + b) * OZ_N);
-#pragma unroll
-                    for (int kk = 0; kk < TC_KS / 16; ++kk) {
-                        // the first product of level a + b in this chunk (a = 0, first K step) overwrites
-                        const uint32_t acc = (a == 0 && kk == 0 && first) ? 0u : 1u;
-                        mma_bf16(dcol, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(b * 256 + kk * 2), idesc, acc);
-                    }
+                for (int kk = 0; kk < TC_KS / 16; ++kk) {
+                    // the chunk's first MMA (a = 0, first K step) covers all seven levels and overwrites
+                    const uint32_t acc = (a == 0 && kk == 0 && first) ? 0u : 1u;
+                    mma_bf16(dcol, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, acc);
                 }
                 mma_commit(&sm.emptyA[slot]);
             }
@@ -229,117 +232,131 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, 2 * OZ_SET_COLS);
 }
 
-// Digits of x_0 = v 2^{7 - e}: s_q = rint(x_q), x_{q+1} = 256 (x_q - s_q); all steps exact in FP64.
-__device__ __forceinline__ void oz_digits(double v, int e, __nv_bfloat16 (&s)[OZ_S]) {
-    double x = ldexp(v, 7 - e);
+// frexp exponent of |v| (|v| = f 2^e, f in [0.5, 1)) read from the bits of v; kOzExpZero for v = 0.
+// Inf and NaN give 1025.
+constexpr int kOzExpZero = -1061109568;   // every byte 0xC0: the fill of a scale array before its maxima
+__device__ __forceinline__ int oz_frexp_exp(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    if (b == 0) return kOzExpZero;
+    const int ef = (int)(b >> 52);
+    return ef ? ef - 1022 : -1010 - __clzll((long long)b);   // subnormal: b is the mantissa
+}
+
+// Digits of x_0 = v 2^{7 - e} (|v| < 2^e). N = v 2^{55 - e} rounded to an integer (|N| <= 2^55, the
+// rounding error at most half a unit of 2^{e - 55}), written in balanced base 256: s_6 .. s_1 are its
+// low bytes taken as residues in [-128, 127] from the low end, s_0 what remains (|s_0| <= 128, since
+// the low digits sum to less than 2^47 in magnitude). Then x_0 = sum_q 2^{-8q} s_q up to 2^{-49}, the
+// same precision as the rounding recurrence x_{q+1} = 256 (x_q - rint(x_q)). Integer operations only
+// (the mantissa and exponent come from the bits of v), so the split runs at memory speed rather than
+// at the FP64 rate. Returns false for Inf or NaN (digits zero).
+__device__ __forceinline__ bool oz_digits(double v, int e, __nv_bfloat16 (&s)[OZ_S]) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+    long long N = 0;
+    if (ef != 0x7FF) {
+        int ex = -1074;                       // |v| = m 2^ex
+        if (ef) {
+            m |= 1ull << 52;
+            ex = ef - 1075;
+        }
+        const int sh = ex + 55 - e;           // <= 2 whenever |v| < 2^e
+        if (m != 0) {
+            if (sh >= 0)
+                N = (long long)(m << sh);
+            else if (sh > -56)
+                N = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+        }
+        if (bits >> 63) N = -N;
+    }
 #pragma unroll
-    for (int q = 0; q < OZ_S; ++q) {
-        const double d = rint(x);
-        s[q] = __float2bfloat16_rn((float)d);
-        x = (x - d) * 256.0;
+    for (int q = OZ_S - 1; q >= 1; --q) {
+        const int dq = (int)((N + 128) & 255) - 128;
+        s[q] = __float2bfloat16_rn((float)dq);
+        N = (N - dq) >> 8;                    // exact: N - dq is a multiple of 256
     }
+    s[0] = __float2bfloat16_rn((float)N);
+    return ef != 0x7FF;
 }
 
-// e_i with max_k |A_ik| < 2^{e_i} (frexp exponent of the largest magnitude; 0 for a zero row).
-__device__ __forceinline__ int oz_scale_exp(double mx) {
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
-    return e;
-}
-
-// Row scales of a split operand whose M rows are the COLUMNS of A (d x m, lda): block per column.
+// Column scales: e[c] = max over rows r of the frexp exponent of A[r, c] (d x ncols, lda), kOzExpZero for
+// a zero column. One CTA per (column, chunk of kOzExpChunk rows), merged by atomicMax into e, which the
+// host fills with kOzExpZero first.
+constexpr int kOzExpChunk = 8192;
 __global__ void k_oz_exp_cols(int64_t rows, const double* __restrict__ A, int64_t lda, int* __restrict__ e) {
-    __shared__ double red[32];
     const int c = blockIdx.x;
-    double mx = 0.0;
-    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) mx = fmax(mx, fabs(A[(int64_t)c * lda + r]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-        e[c] = oz_scale_exp(m);
-    }
+    const int64_t r0 = (int64_t)blockIdx.y * kOzExpChunk;
+    const int64_t r1 = min(rows, r0 + kOzExpChunk);
+    int mx = kOzExpZero;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) mx = max(mx, oz_frexp_exp(A[(int64_t)c * lda + r]));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && mx != kOzExpZero) atomicMax(&e[c], mx);
 }
 
-// Row scales of a split operand whose M rows are the ROWS of A (d x m, lda): thread per row.
+// Row scales of a split operand whose M rows are the ROWS of A (d x m, lda): thread per row, 0 for a
+// zero row.
 __global__ void k_oz_exp_rows(int64_t rows, int cols, const double* __restrict__ A, int64_t lda,
                               int* __restrict__ e) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    double mx = 0.0;
-    for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(A[(int64_t)c * lda + r]));
-    e[r] = oz_scale_exp(mx);
-}
-
-// The seven digit planes of a big operand in the pre-tiled layout (tile_off): element (i, k) of the
-// operand is A[k + i lda] (rows_are_cols = 1: M rows are the columns of A, K runs down them) or
-// A[i + k lda] (rows_are_cols = 0: M rows are the rows of A, K runs along them); zero outside M x K.
-__global__ void k_oz_split_tiled(const double* __restrict__ A, int64_t lda, int64_t Mrows, int64_t Kcols,
-                                 int rows_are_cols, const int* __restrict__ e, int kbs, int64_t total,
-                                 __nv_bfloat16* __restrict__ out, int64_t slice) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const int64_t tile = t >> 13;
-    const int within = (int)(t & 8191);
-    const int rr = within >> 6, pc = (within >> 3) & 7, el = within & 7;
-    const int c = pc ^ (rr & 7);
-    const int64_t i = (tile / kbs) * TC_M + rr;
-    const int64_t k = (tile % kbs) * TC_KS + c * 8 + el;
-    double v = 0.0;
-    int ex = 0;
-    if (i < Mrows && k < Kcols) {
-        v = rows_are_cols ? A[i * lda + k] : A[k * lda + i];
-        ex = e[i];
-    }
-    __nv_bfloat16 s[OZ_S];
-    oz_digits(v, ex, s);
-#pragma unroll
-    for (int q = 0; q < OZ_S; ++q) out[q * slice + t] = s[q];
+    int mx = kOzExpZero;
+    for (int c = 0; c < cols; ++c) mx = max(mx, oz_frexp_exp(A[(int64_t)c * lda + r]));
+    e[r] = mx == kOzExpZero ? 0 : mx;
 }
 
 // The seven digit planes of a narrow operand B (K x p, ldb; its columns are the N rows of the product),
-// planes [7][32][ld] (plane q, row j at (32 q + j) ld), zero for j >= p or k >= K.
+// planes [7][32][ld] (plane q, row j at (32 q + j) ld), zero for j >= p or k >= K. Eight consecutive k per
+// thread: one 64-byte read and one 16-byte store per plane.
 __global__ void k_oz_split_narrow(int64_t K, int p, const double* __restrict__ B, int64_t ldb,
-                                  const int* __restrict__ e, int64_t ld, __nv_bfloat16* __restrict__ out) {
+                                  const int* __restrict__ e, int64_t ld, __nv_bfloat16* __restrict__ out,
+                                  int* __restrict__ status) {
+    const int64_t groups = ld / 8;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)OZ_N * ld) return;
-    const int j = (int)(t / ld);
-    const int64_t k = t % ld;
-    double v = 0.0;
-    int ex = 0;
-    if (j < p && k < K) {
-        v = B[(int64_t)j * ldb + k];
-        ex = e[j];
-    }
-    __nv_bfloat16 s[OZ_S];
-    oz_digits(v, ex, s);
+    if (t >= (int64_t)OZ_N * groups) return;
+    const int j = (int)(t / groups);
+    const int64_t k0 = (t % groups) * 8;
+    const int ex = j < p ? e[j] : 0;
+    __align__(16) __nv_bfloat16 dg[OZ_S][8];
+    bool fin = true;
 #pragma unroll
-    for (int q = 0; q < OZ_S; ++q) out[(int64_t)q * OZ_N * ld + t] = s[q];
+    for (int u = 0; u < 8; ++u) {
+        const double v = (j < p && k0 + u < K) ? B[(int64_t)j * ldb + k0 + u] : 0.0;
+        __nv_bfloat16 sq[OZ_S];
+        fin &= oz_digits(v, ex, sq);
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q) dg[q][u] = sq[q];
+    }
+    if (!fin) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q)
+        *reinterpret_cast<uint4*>(out + ((int64_t)q * OZ_N + j) * ld + k0) = *reinterpret_cast<const uint4*>(dg[q]);
 }
 
 // Digit planes of the columns i0 .. i1 of A (d x m, lda) as M rows of a split operand whose K index runs down
 // the columns (rows_are_cols layout), 8 consecutive k per thread: one 64-byte read of A and one 16-byte
-// store per plane. e: the scales of those columns (e[i - i0]).
-__global__ void k_oz_split_cols8(const double* __restrict__ A, int64_t lda, int i0, int i1, int64_t K,
+// store per plane. e: the scales of those columns (e[i - i0]). Rows at or beyond Mvalid (the padding of
+// the last 128-row band) are written as zeros.
+__global__ void k_oz_split_cols8(const double* __restrict__ A, int64_t lda, int i0, int i1, int Mvalid, int64_t K,
                                  const int* __restrict__ e, int kbs, int64_t ld, __nv_bfloat16* __restrict__ out,
-                                 int64_t slice) {
+                                 int64_t slice, int* __restrict__ status) {
     const int64_t groups = ld / 8;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)(i1 - i0) * groups) return;
     const int i = i0 + (int)(t / groups);
     const int64_t k0 = (t % groups) * 8;
-    const int ex = e[i - i0];
+    const bool row = i < Mvalid;
+    const int ex = row ? e[i - i0] : 0;
     __align__(16) __nv_bfloat16 dg[OZ_S][8];
+    bool fin = true;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        const double v = (k0 + u < K) ? A[(int64_t)i * lda + k0 + u] : 0.0;
+        const double v = (row && k0 + u < K) ? A[(int64_t)i * lda + k0 + u] : 0.0;
         __nv_bfloat16 sq[OZ_S];
-        oz_digits(v, ex, sq);
+        fin &= oz_digits(v, ex, sq);
 #pragma unroll
         for (int q = 0; q < OZ_S; ++q) dg[q][u] = sq[q];
     }
+    if (!fin) atomicOr(status, ST_NONFINITE);
     const int64_t off = tile_off(i, k0, kbs);
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q)
@@ -348,10 +365,10 @@ __global__ void k_oz_split_cols8(const double* __restrict__ A, int64_t lda, int 
 
 // Digit planes of the rows of A (M x K, lda; M rows = rows of A, K along its columns k0 .. k1, k0 a multiple
 // of 8), 8 consecutive k per thread: eight reads, each coalesced across the threads of a warp (consecutive
-// rows), and one 16-byte store per plane. Columns at or beyond Kvalid are taken as zero.
+// rows), and one 16-byte store per plane. Columns at or beyond Kvalid, and rows at or beyond M, are zero.
 __global__ void k_oz_split_rows8(const double* __restrict__ A, int64_t lda, int64_t M, int64_t k0, int64_t k1,
                                  int64_t Kvalid, const int* __restrict__ e, int kbs, __nv_bfloat16* __restrict__ out,
-                                 int64_t slice) {
+                                 int64_t slice, int* __restrict__ status) {
     const int64_t mpad = (M + TC_M - 1) / TC_M * TC_M;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t groups = (k1 - k0 + 7) / 8;
@@ -360,15 +377,17 @@ __global__ void k_oz_split_rows8(const double* __restrict__ A, int64_t lda, int6
     const int64_t kg = k0 + (t / mpad) * 8;
     const int ex = i < M ? e[i] : 0;
     __align__(16) __nv_bfloat16 dg[OZ_S][8];
+    bool fin = true;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int64_t k = kg + u;
         const double v = (i < M && k < Kvalid) ? A[k * lda + i] : 0.0;
         __nv_bfloat16 sq[OZ_S];
-        oz_digits(v, ex, sq);
+        fin &= oz_digits(v, ex, sq);
 #pragma unroll
         for (int q = 0; q < OZ_S; ++q) dg[q][u] = sq[q];
     }
+    if (!fin) atomicOr(status, ST_NONFINITE);
     const int64_t off = tile_off(i, kg, kbs);
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q)
@@ -406,8 +425,18 @@ size_t oz_operand_bytes(int64_t M, int64_t K) {
     return OZ_S * ((plane + 255) / 256 * 256) + ((size_t)M * 4 + 255) / 256 * 256;
 }
 
+// Column scales of columns 0 .. ncols of A (K x ncols, lda) into e.
+static int oz_col_exps(int64_t K, const double* A, int64_t lda, int ncols, int* e, cudaStream_t s) {
+    if (ncols <= 0) return EDA_OK;
+    EDA_CUDA_TRY(cudaMemsetAsync(e, 0xC0, (size_t)ncols * sizeof(int), s));   // kOzExpZero in every entry
+    const dim3 grid((unsigned)ncols, (unsigned)ceil_div(std::max<int64_t>(K, 1), kOzExpChunk));
+    k_oz_exp_cols<<<grid, 256, 0, s>>>(K, A, lda, e);
+    EDA_LAUNCHED();
+    return EDA_OK;
+}
+
 int oz_operand_make(const double* A, int64_t lda, int64_t M, int64_t K, bool rows_are_cols, void* mem,
-                    OzOperand* op, cudaStream_t s) {
+                    OzOperand* op, int* status, cudaStream_t s) {
     const int64_t mt = (M + TC_M - 1) / TC_M, kb = (K + TC_KS - 1) / TC_KS;
     const int64_t plane = mt * kb * TC_M * TC_KS;
     const int64_t slice = ((plane * 2 + 255) / 256 * 256) / 2;
@@ -418,14 +447,17 @@ int oz_operand_make(const double* A, int64_t lda, int64_t M, int64_t K, bool row
     op->K = K;
     op->kbs = (int)kb;
     op->mtiles = (int)mt;
+    const int64_t ld = kb * TC_KS, mpad = mt * TC_M;
     if (rows_are_cols) {
-        k_oz_exp_cols<<<(unsigned)M, 256, 0, s>>>(K, A, lda, op->exps);
+        EDA_TRY(oz_col_exps(K, A, lda, (int)M, op->exps, s));
+        k_oz_split_cols8<<<ceil_div(mpad * (ld / 8), 256), 256, 0, s>>>(A, lda, 0, (int)mpad, (int)M, K, op->exps,
+                                                                        (int)kb, ld, op->tiles, slice, status);
     } else {
         k_oz_exp_rows<<<ceil_div(M, 256), 256, 0, s>>>(M, (int)K, A, lda, op->exps);
+        EDA_LAUNCHED();
+        k_oz_split_rows8<<<ceil_div(mpad * (ld / 8), 256), 256, 0, s>>>(A, lda, M, 0, ld, K, op->exps, (int)kb,
+                                                                         op->tiles, slice, status);
     }
-    EDA_LAUNCHED();
-    k_oz_split_tiled<<<ceil_div(plane, 256), 256, 0, s>>>(A, lda, M, K, rows_are_cols ? 1 : 0, op->exps, (int)kb,
-                                                          plane, op->tiles, slice);
     EDA_LAUNCHED();
     return EDA_OK;
 }
@@ -447,13 +479,13 @@ int oz_operand_init(int64_t Mcap, int64_t Kcap, void* mem, OzOperand* op, cudaSt
     return EDA_OK;
 }
 
-int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOperand* op, cudaStream_t s) {
+int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOperand* op, int* status,
+                   cudaStream_t s) {
     if (i1 <= i0) return EDA_OK;
-    k_oz_exp_cols<<<(unsigned)(i1 - i0), 256, 0, s>>>(K, A + (int64_t)i0 * lda, lda, op->exps + i0);
-    EDA_LAUNCHED();
+    EDA_TRY(oz_col_exps(K, A + (int64_t)i0 * lda, lda, i1 - i0, op->exps + i0, s));
     const int64_t ld = (int64_t)op->kbs * TC_KS;
-    k_oz_split_cols8<<<ceil_div((int64_t)(i1 - i0) * (ld / 8), 256), 256, 0, s>>>(A, lda, i0, i1, K, op->exps + i0,
-                                                                               op->kbs, ld, op->tiles, op->slice);
+    k_oz_split_cols8<<<ceil_div((int64_t)(i1 - i0) * (ld / 8), 256), 256, 0, s>>>(
+        A, lda, i0, i1, i1, K, op->exps + i0, op->kbs, ld, op->tiles, op->slice, status);
     EDA_LAUNCHED();
     op->M = i1;
     op->K = K;
@@ -461,13 +493,13 @@ int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOp
     return EDA_OK;
 }
 
-int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperand* op, cudaStream_t s) {
+int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperand* op, int* status, cudaStream_t s) {
     k_oz_exp_rows<<<ceil_div(M, 256), 256, 0, s>>>(M, (int)K, A, lda, op->exps);
     EDA_LAUNCHED();
     const int64_t kpad = (K + TC_KS - 1) / TC_KS * TC_KS;
     const int64_t mpad = (M + TC_M - 1) / TC_M * TC_M;
     k_oz_split_rows8<<<ceil_div(mpad * (kpad / 8), 256), 256, 0, s>>>(A, lda, M, 0, kpad, K, op->exps, op->kbs,
-                                                                      op->tiles, op->slice);
+                                                                      op->tiles, op->slice, status);
     EDA_LAUNCHED();
     op->M = M;
     op->K = K;
@@ -509,9 +541,9 @@ int oz_gemm(const OzOperand& A, OzNarrow& nb, int p, const double* B, int64_t ld
     // digit planes), B read and D written once in FP64
     ProfScope prof("oz_gemm", s, 2.0 * (double)A.M * A.K * p,
                    2.0 * OZ_S * (double)A.M * A.K + 8.0 * (double)A.K * p + 8.0 * (double)A.M * p);
-    k_oz_exp_cols<<<p, 256, 0, s>>>(A.K, B, ldb, nb.exps);
-    EDA_LAUNCHED();
-    k_oz_split_narrow<<<ceil_div((int64_t)OZ_N * ld, 256), 256, 0, s>>>(A.K, p, B, ldb, nb.exps, ld, nb.planes);
+    EDA_TRY(oz_col_exps(A.K, B, ldb, p, nb.exps, s));
+    k_oz_split_narrow<<<ceil_div((int64_t)OZ_N * (ld / 8), 256), 256, 0, s>>>(A.K, p, B, ldb, nb.exps, ld, nb.planes,
+                                                                            status);
     EDA_LAUNCHED();
     const int kst = (int)(ld / TC_KS);
     // K splits: fill the SMs with one CTA each (the kernel holds all of an SM's tensor memory)

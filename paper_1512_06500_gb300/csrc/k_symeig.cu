@@ -857,6 +857,88 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(int n, const double* __r
     cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
+// The same recurrence for a Gram too large for one cluster's shared memory (n > kLanczosMaxN), two
+// launches per step with the matrix read from global memory (L2-resident at these sizes):
+// k_lz_matvec forms u = A v_j (one warp per row; A is symmetric, so row r is read as its contiguous
+// column r), k_lz_update the rest of the step in one CTA. The vectors rotate through three buffers
+// chosen by the host; st[0] = beta_{j-1}, st[1] = the running norm estimate, st[2] = the stop flag.
+constexpr int LZG_THREADS = 1024;
+__global__ void k_lz_start(int n, uint64_t seed, double* __restrict__ v, double* __restrict__ vprev,
+                           double* __restrict__ st) {
+    __shared__ double red[32];
+    double ss = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const uint64_t h = mix64(seed ^ mix64((uint64_t)c + 0x2545F4914F6CDD1Dull));
+        const double x = 2.0 * ((h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+        v[c] = x;
+        vprev[c] = 0.0;
+        ss = fma(x, x, ss);
+    }
+    ss = block_sum(ss, red);
+    const double inv0 = (ss > 0.0) ? 1.0 / sqrt(ss) : 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) v[c] *= inv0;
+    if (threadIdx.x == 0) {
+        st[0] = 0.0;
+        st[1] = 0.0;
+        st[2] = 0.0;
+    }
+}
+
+__global__ void k_lz_matvec(int n, const double* __restrict__ A, int lda, const double* __restrict__ v,
+                            double* __restrict__ u, const double* __restrict__ st) {
+    if (st[2] != 0.0) return;
+    const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const double* col = A + (int64_t)row * lda;
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) acc = fma(col[c], v[c], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) u[row] = acc;
+}
+
+// u <- u - beta_{j-1} v_{j-1}; alpha_j = v_j^T u; u <- u - alpha_j v_j; beta_j = ||u||;
+// v_{j+1} = u / beta_j, written over v_{j-1}. On breakdown (or after it) T's entries are zero.
+__global__ void __launch_bounds__(LZG_THREADS) k_lz_update(int n, int j, double* __restrict__ u,
+                                                           const double* __restrict__ v, double* __restrict__ vprev,
+                                                           double* __restrict__ st, double* dgl, double* eoff) {
+    __shared__ double red[32];
+    if (st[2] != 0.0) {
+        if (threadIdx.x == 0) {
+            dgl[j] = 0.0;
+            eoff[j] = 0.0;
+        }
+        return;
+    }
+    const double beta = st[0];
+    double a = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const double x = fma(-beta, vprev[c], u[c]);
+        u[c] = x;
+        a = fma(v[c], x, a);
+    }
+    a = block_sum(a, red);
+    double b2 = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const double x = fma(-a, v[c], u[c]);
+        u[c] = x;
+        b2 = fma(x, x, b2);
+    }
+    b2 = block_sum(b2, red);
+    const double rb = (b2 > 0.0) ? rsqrt(b2) : 0.0;
+    const double b = b2 * rb;
+    const double anorm = fmax(st[1], fabs(a) + b + beta);
+    const bool stop = !(b > 16.0 * DBL_EPSILON * anorm);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) vprev[c] = stop ? 0.0 : u[c] * rb;
+    __syncthreads();   // every thread has read st before thread 0 updates it
+    if (threadIdx.x == 0) {
+        dgl[j] = a;
+        eoff[j] = stop ? 0.0 : b;
+        st[0] = b;
+        st[1] = anorm;
+        st[2] = stop ? 1.0 : 0.0;
+    }
+}
+
 // (theta_1, theta_2, |z_m|, beta_m) of the Lanczos tridiagonal: its two largest eigenvalues, the last
 // entry of the unit eigenvector of theta_1, and the residual norm after the last step.
 __global__ void k_lanczos_pack(int m, const double* w, const double* z, const double* eoff, double* out) {
@@ -1285,7 +1367,36 @@ int newton_schulz_f64(int n, int nv, double* Z, int ldz, int steps, double* tmp,
 
 int lanczos_top(int n, const double* A, int lda, int m, uint64_t seed, SymEigWork* ws, double* out,
                 cudaStream_t s) {
-    if (n < 1 || n > kLanczosMaxN || m < 1 || m > n) return EDA_ERR_INVALID_ARG;
+    if (n < 1 || m < 1 || m > n) return EDA_ERR_INVALID_ARG;
+    if (n > kLanczosMaxN) {
+        // three n-vectors in vbuf (4 n doubles), the state after them in lu
+        double* buf[3] = {ws->vbuf, ws->vbuf + n, ws->vbuf + 2 * (size_t)n};
+        double* st = ws->lu;
+        {
+            ProfScope prof("lanczos", s);
+            k_lz_start<<<1, LZG_THREADS, 0, s>>>(n, seed, buf[0], buf[1], st);
+            EDA_LAUNCHED();
+            // v_j in buf[j % 2], v_{j-1} (then v_{j+1}) in buf[(j + 1) % 2], u in buf[2]
+            for (int j = 0; j < m; ++j) {
+                double* v = buf[j & 1];
+                double* vp = buf[(j + 1) & 1];
+                k_lz_matvec<<<ceil_div((int64_t)n * 32, 256), 256, 0, s>>>(n, A, lda, v, buf[2], st);
+                EDA_LAUNCHED();
+                k_lz_update<<<1, LZG_THREADS, 0, s>>>(n, j, buf[2], v, vp, st, ws->dgl, ws->eoff);
+                EDA_LAUNCHED();
+            }
+        }
+        const int nv = m >= 2 ? 2 : 1;
+        double* w = ws->vbuf + 3 * (size_t)n;       // nv values (vbuf holds 4 n doubles)
+        double* zt = ws->lu + 5 * (size_t)m;        // the eigenvector after the 5 m factor entries
+        k_bisect<<<nv, 64, 3 * (size_t)m * sizeof(double), s>>>(m, ws->dgl, ws->eoff, m - nv, nv, w);
+        EDA_LAUNCHED();
+        k_invit<<<1, 32, 0, s>>>(m, 1, ws->dgl, ws->eoff, w + nv - 1, ws->lu, zt, seed);   // st is dead here
+        EDA_LAUNCHED();
+        k_lanczos_pack<<<1, 32, 0, s>>>(m, w, zt, ws->eoff, out);
+        EDA_LAUNCHED();
+        return EDA_OK;
+    }
     const int C = (n + LZ_ROWS - 1) / LZ_ROWS;
     {
         static std::once_flag once;

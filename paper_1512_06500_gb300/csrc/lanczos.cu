@@ -145,11 +145,11 @@ int oz_basis_nn(eda_ctx* h, SolveWs<T>& w, int cols, int p, const double* C, int
 // The basis has grown from cols0 to cols1 columns: append their column-scaled digit planes and split the
 // whole basis afresh with row scales over all its columns.
 template <class T>
-int oz_basis_grow(SolveWs<T>& w, int64_t d, int cols0, int cols1, cudaStream_t s) {
+int oz_basis_grow(SolveWs<T>& w, int64_t d, int cols0, int cols1, int* status, cudaStream_t s) {
     if (!w.oz) return EDA_OK;
     const double* V = reinterpret_cast<const double*>(w.V);
-    EDA_TRY(oz_append_cols(V, d, cols0, cols1, d, &w.VT, s));
-    return oz_resplit_rows(V, d, d, cols1, &w.VN, s);
+    EDA_TRY(oz_append_cols(V, d, cols0, cols1, d, &w.VT, status, s));
+    return oz_resplit_rows(V, d, d, cols1, &w.VN, status, s);
 }
 
 template <class T>
@@ -277,7 +277,7 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
     }
     EDA_TRY(cholqr_pass<T>(d, b, w.V, d, w.R1, w.R1i, w.W1, 0.0, h->status, w.lost, w, s));
     EDA_TRY(cholqr_pass<T>(d, b, w.W1, d, w.R2, w.R2i, w.V, 0.0, h->status, w.lost, w, s));
-    EDA_TRY(oz_basis_grow<T>(w, d, 0, b, s));
+    EDA_TRY(oz_basis_grow<T>(w, d, 0, b, h->status, s));
     {
         int lostc = 0;
         EDA_CUDA_TRY(cudaMemcpyAsync(&lostc, w.lost + b, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -331,7 +331,7 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
             T* Vn = w.V + (size_t)cols * d;
             EDA_CUDA_TRY(cudaMemsetAsync(w.lost, 0, (b + 1) * sizeof(int), s));
             EDA_TRY(cholqr_pass<T>(d, b, w.W1, d, w.R2, w.R2i, Vn, 0.0, h->status, w.lost, w, s));
-            EDA_TRY(oz_basis_grow<T>(w, d, cols, cols + b, s));
+            EDA_TRY(oz_basis_grow<T>(w, d, cols, cols + b, h->status, s));
             EDA_TRY(gemm_small_f64(false, false, b, b, b, 1.0, w.R2, b, w.R1, b, 0.0, w.Bm, b, s));   // B = R2 R1
         } else {
             EDA_TRY(copy_mat_f64(b, b, w.R1, b, w.Bm, b, s));   // basis full: residual estimate only
@@ -428,12 +428,23 @@ int m_apply_composed(eda_ctx* h, int p, const double* Y, int64_t ldy, double* MY
     double* Qb = PQ + n;
     double* Uw = U;
     double* Ub = U + n;
-    EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->KW, n, Pw, nk, 0.0, Uw, nk, s));   // u1
+    // the n x n products with K_W and G_W: on the tensor cores from their splits when the handle has them
+    auto nn = [&](const OzOperand* oz, const double* M, const double* X, double beta, const double* C0,
+                  double* D) -> int {
+        if (!oz) return gemm_small_f64(false, false, n, p, n, 1.0, M, n, X, nk, beta, D, nk, s);
+        for (int c0 = 0; c0 < p; c0 += 32)
+            EDA_TRY(oz_gemm(*oz, h->oznb, std::min(32, p - c0), X + (size_t)c0 * nk, nk, 1.0, beta,
+                            C0 ? C0 + (size_t)c0 * nk : nullptr, nk, D + (size_t)c0 * nk, nk, h->status, s));
+        return EDA_OK;
+    };
+    const OzOperand* okw = h->ozsmall ? &h->ozKW : nullptr;
+    const OzOperand* ogw = h->ozsmall ? &h->ozGW : nullptr;
+    EDA_TRY(nn(okw, h->KW, Pw, 0.0, nullptr, Uw));                                               // u1
     EDA_TRY(gemm_small_f64(false, false, k, p, n, 1.0, h->GBW, k, Uw, nk, 1.0, Qb, nk, s));  // H_B^T y1
-    EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->GW, n, Uw, nk, 1.0, Pw, nk, s));   // H_W^T y1
+    EDA_TRY(nn(ogw, h->GW, Uw, 1.0, Pw, Pw));                                                    // H_W^T y1
     EDA_TRY(gemm_small_f64(false, false, k, p, k, 1.0, h->KB, k, Qb, nk, 0.0, Ub, nk, s));   // v
     EDA_TRY(gemm_small_f64(false, false, n, p, k, 1.0, h->GWB, n, Ub, nk, 1.0, Pw, nk, s));  // H_W^T y2
-    EDA_TRY(gemm_small_f64(false, false, n, p, n, 1.0, h->KW, n, Pw, nk, 1.0, Uw, nk, s));   // u1 + u3
+    EDA_TRY(nn(okw, h->KW, Pw, 1.0, Uw, Uw));                                                    // u1 + u3
     return sweep_z(h, p, U, Y, ldy, MY, ldm, s);
 }
 
@@ -475,7 +486,7 @@ int fin_tn(eda_ctx* h, SolveWs<T>& w, int m, int p, const double* A, const doubl
     const int64_t d = h->d;
     if (w.oz && m <= w.oz_cap) {
         OzOperand op;
-        EDA_TRY(oz_operand_make(A, d, m, d, true, w.VT.tiles, &op, s));
+        EDA_TRY(oz_operand_make(A, d, m, d, true, w.VT.tiles, &op, h->status, s));
         for (int c0 = 0; c0 < p; c0 += 32)
             EDA_TRY(oz_gemm(op, h->oznb, std::min(32, p - c0), B + (size_t)c0 * ldb, ldb, 1.0, 0.0, nullptr, 0,
                             C + (size_t)c0 * ldc, ldc, h->status, s));
@@ -490,7 +501,7 @@ int fin_nn(eda_ctx* h, SolveWs<T>& w, int m, int p, double alpha, const double* 
     const int64_t d = h->d;
     if (w.oz && m <= w.oz_cap) {
         OzOperand op;
-        EDA_TRY(oz_operand_make(A, d, d, m, false, w.VN.tiles, &op, s));
+        EDA_TRY(oz_operand_make(A, d, d, m, false, w.VN.tiles, &op, h->status, s));
         for (int c0 = 0; c0 < p; c0 += 32)
             EDA_TRY(oz_gemm(op, h->oznb, std::min(32, p - c0), Bs + (size_t)c0 * ldbs, ldbs, alpha, beta,
                             X0 ? X0 + (size_t)c0 * d : nullptr, d, OUT + (size_t)c0 * d, d, h->status, s));
@@ -776,7 +787,13 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
         for (int c0 = 0; c0 < t; c0 += 32)
             EDA_TRY(oz_gemm(AT, h->oznb, std::min(32, t - c0), w.Y2 + (size_t)c0 * d, d, 1.0, 0.0, nullptr, 0,
                             w.P + (size_t)c0 * n, n, h->status, s));
-        EDA_TRY(gemm_small_f64(false, false, n, t, n, 1.0, h->KW, n, w.P, n, 0.0, w.Q, n, s));
+        if (h->ozsmall) {
+            for (int c0 = 0; c0 < t; c0 += 32)
+                EDA_TRY(oz_gemm(h->ozKW, h->oznb, std::min(32, t - c0), w.P + (size_t)c0 * n, n, 1.0, 0.0, nullptr,
+                                0, w.Q + (size_t)c0 * n, n, h->status, s));
+        } else {
+            EDA_TRY(gemm_small_f64(false, false, n, t, n, 1.0, h->KW, n, w.P, n, 0.0, w.Q, n, s));
+        }
         for (int c0 = 0; c0 < t; c0 += 32)
             EDA_TRY(oz_gemm(AN, h->oznb, std::min(32, t - c0), w.Q + (size_t)c0 * n, n, 1.0, 1.0,
                             w.Y2 + (size_t)c0 * d, d, w.Xt + (size_t)c0 * d, d, h->status, s));
