@@ -39,9 +39,10 @@ SMALL = "d4096_k40"
 # DRAM bytes (read + write) of one launch of the Gram SYRK kernel, k_gemm_tn_partial<32, double, SYRK>,
 # per workload, from ncu captures (profiles/); None until captured for the current kernel
 GRAM_TRAFFIC_BYTES = {}
-# DRAM bytes (read + write) per launch of k_oz_gemm, averaged over the launches of one step of the
-# workload, from an ncu capture of the same command (profiles/); None until captured for the current kernel
-OZ_TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch of k_oz_gemm with a narrow operand, averaged over those launches of
+# one timed step of the workload, from an ncu capture of the same command (profiles/); absent until captured
+# for the current kernel
+OZ_TRAFFIC_BYTES = {"d65536_k200": 599.06e6}
 FALLBACK_HBM_GBS = 6800.0           # profiling recipe fallback when no measured peaks exist
 FALLBACK_BF16_TFLOPS = 1900.0
 
@@ -82,8 +83,9 @@ def peaks():
     if os.path.exists(p):
         with open(p) as fh:
             j = json.load(fh)
-        return dict(hbm=float(j.get("hbm_gbs", FALLBACK_HBM_GBS)), source="measured")
-    return dict(hbm=FALLBACK_HBM_GBS, source="fallback")
+        return dict(hbm=float(j.get("hbm_gbs", FALLBACK_HBM_GBS)), bf16=float(j.get("bf16_tflops", FALLBACK_BF16_TFLOPS)),
+                    bf16_sustained=float(j.get("bf16_tflops_sustained", FALLBACK_BF16_TFLOPS)), source="measured")
+    return dict(hbm=FALLBACK_HBM_GBS, bf16=FALLBACK_BF16_TFLOPS, bf16_sustained=FALLBACK_BF16_TFLOPS, source="fallback")
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -494,7 +496,7 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     launches = eda.kernel_launches() - launches0
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dev)
     regions = {r: eda.profile_read(r) for r in REGIONS}
-    work = {r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "m_apply_composed",
+    work = {r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "oz_tiled", "m_apply_composed",
                                              "exp_apply_w", "tridiag")}
     out = dict(p=p, c=c, ms=ms, regions=regions, work=work, infos=infos, launches=launches, clocks=clk,
                wall=wall)
@@ -544,7 +546,7 @@ def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e
     return out
 
 
-REGIONS = ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "cluster_orth", "exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
+REGIONS = ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "oz_tiled", "cluster_orth", "exp_apply_w", "exp_apply_b", "m_apply", "m_apply_composed",
            "tridiag", "bisect", "invit", "backtransform", "symeig", "lanczos", "phi_squaring", "rr", "reorth",
            "refine")
 
@@ -565,11 +567,17 @@ def _all_launches(r, steps):
         "nn_f64": {"kernel": "k_gemm_nn<*, double> (every FP64 tall A B product of the step)",
                    "achieved_tflops": rate(r["work"]["nn_f64"][0], nn_ms), "launches": nn_calls,
                    "ms_per_step": nn_ms / steps},
-        "oz_kernel": {"kernel": "k_oz_gemm (tensor-core digit-plane products; the split of the narrow operand and "
-                                "the K-split reduction excluded)",
+        "oz_kernel": {"kernel": "k_oz_gemm<narrow B> (tensor-core digit-plane products with a narrow operand of "
+                                "<= 32 columns; the split of the narrow operand and the K-split reduction excluded)",
                       "achieved_gbs": oz_bytes / (oz_ms / 1e3) / 1e9 if oz_ms > 0 else None,
                       "tensor_tflops_bf16": rate(oz_flops, oz_ms) if oz_ms > 0 else None,
                       "launches": oz_calls, "ms_per_step": oz_ms / steps},
+        "oz_tiled": {"kernel": "k_oz_gemm<tiled B> (both operands split: the Gram Z^T Z, the squaring's n x n "
+                               "products); tensor-bound",
+                     "tensor_tflops_bf16": rate(r["work"]["oz_tiled"][0], r["regions"]["oz_tiled"][0])
+                     if r["regions"]["oz_tiled"][0] > 0 else None,
+                     "peak_tflops_bf16": peaks()["bf16"],
+                     "launches": r["regions"]["oz_tiled"][1], "ms_per_step": r["regions"]["oz_tiled"][0] / steps},
     }
 
 

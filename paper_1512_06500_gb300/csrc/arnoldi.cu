@@ -206,10 +206,11 @@ int ensure_n_operators(eda_ctx* h, cudaStream_t s) {
         EDA_TRY(phi_operator(n, ns, lam, h->evecs_w, n, c2, h->KWp, work, s));
     } else {
         // by scaling and squaring of G_W (the build's route for small Grams)
-        const OzSquare oz{&h->oznb, h->ozsmall, h->status};
+        const size_t b1 = (oz_operand_bytes(n, n) + 255) / 256 * 256;
+        const OzSquare oz{h->ozsmall, static_cast<char*>(h->ozsmall) + b1, h->status};
         const OzSquare* pz = h->ozsmall ? &oz : nullptr;
-        EDA_TRY(phi_by_squaring(n, h->GW, -c2, h->lmax_w, h->KWm, work, s, pz));
-        EDA_TRY(phi_by_squaring(n, h->GW, c2, h->lmax_w, h->KWp, work, s, pz));
+        EDA_TRY(phi_by_squaring(n, h->GW, -c2, h->lmax_w_bound, h->KWm, work, s, pz));
+        EDA_TRY(phi_by_squaring(n, h->GW, c2, h->lmax_w_bound, h->KWp, work, s, pz));
     }
     return EDA_OK;
 }

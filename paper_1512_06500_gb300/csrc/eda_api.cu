@@ -83,7 +83,7 @@ constexpr int kEigClusterMaxN = 512;   // the eigensolver's cluster path (no gri
 constexpr double kSigRel = 32.0;   // eigenvalues <= kSigRel * n * eps * lambda_max are the Gram's null space
 constexpr int kLanczosSteps = 64;  // steps of the largest-eigenvalue Lanczos run on a Gram
 constexpr double kLmaxAccept = 8.0;  // accept its theta_1 when its residual is <= kLmaxAccept * eps * theta_1
-constexpr int kLanczosStepsLarge = 160;   // the same run on a large Gram (n >= kOzSmallMinN, tensor-core mode)
+constexpr int kLanczosStepsLarge = 64;    // the same run on a large Gram (n >= kOzSmallMinN, tensor-core mode)
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -329,9 +329,13 @@ double lmax_accepted(const double* o) {
     return std::max(t1, 0.0);
 }
 
-// lambda_max of one Gram (m x m) by a Lanczos run of kLanczosStepsLarge steps, falling back to the full
-// eigensolver's largest eigenvalue (into w) when the residual does not accept the estimate.
-int gram_lmax_one(eda_ctx* h, int m, const double* G, double* w, Arena& scratch, double* lmax, cudaStream_t s) {
+// lambda_max of one Gram (m x m) by a Lanczos run of kLanczosStepsLarge steps. Its top Ritz value theta_1
+// with residual bound r is taken when r <= kLmaxAccept eps theta_1. Otherwise, when theta_1 + r < below
+// (the other Gram's lambda_max, which then sets c^2), theta_1 is kept as the estimate and theta_1 + r as
+// an upper bound (for the squaring's scale); else the full eigensolver's largest eigenvalue (into w) is
+// taken. *lmax: the value, *lbound: an upper bound for the squaring (equal to *lmax when exact).
+int gram_lmax_one(eda_ctx* h, int m, const double* G, double* w, Arena& scratch, double below, double* lmax,
+                  double* lbound, cudaStream_t s) {
     SymEigWork ws{};
     EDA_TRY(symeig_work_carve(scratch, m, 1, h->bar, &ws));
     double* out = scratch.take<double>(4);
@@ -341,6 +345,12 @@ int gram_lmax_one(eda_ctx* h, int m, const double* G, double* w, Arena& scratch,
     EDA_CUDA_TRY(cudaMemcpyAsync(o, out, sizeof(o), cudaMemcpyDeviceToHost, s));
     EDA_CUDA_TRY(cudaStreamSynchronize(s));
     double l = lmax_accepted(o);
+    const double r = o[2] * o[3];
+    if (l < 0.0 && std::isfinite(o[0]) && std::isfinite(r) && o[0] + r < below) {
+        *lmax = std::max(o[0], 0.0);
+        *lbound = std::max(o[0] + r, 0.0);
+        return EDA_OK;
+    }
     if (l < 0.0) {
         EDA_TRY(symeig_values(m, G, m, m - 1, m - 1, w, &ws, h->status, s));
         double top = 0.0;
@@ -353,6 +363,7 @@ int gram_lmax_one(eda_ctx* h, int m, const double* G, double* w, Arena& scratch,
         l = std::max(top, 0.0);
     }
     *lmax = l;
+    *lbound = l;
     return EDA_OK;
 }
 
@@ -451,10 +462,10 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     // back-transformation of the eigensolver; G_B keeps its route.
     const bool sq_w_tc = tc && !by_squaring && n >= kOzSmallMinN;
     if (sq_w_tc) {
-        // three n x n split operands: the squaring's left factors, then K_W and G_W for the solves
+        // four n x n split operands: the squaring's two factors, then K_W and G_W for the solves
         const size_t b1 = align256(oz_operand_bytes(n, n));
         void* p = nullptr;
-        EDA_CUDA_TRY(cudaMalloc(&p, 3 * b1));
+        EDA_CUDA_TRY(cudaMalloc(&p, 4 * b1));
         h->ozsmall = p;
     }
     if (tc) {
@@ -496,13 +507,15 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     }
     const size_t mark = scratch.used;
     int nsw = 0, nsb = 0, first_w = 0, first_b = 0;
+    double lbound_w = 0.0;   // the large-G_W route: an upper bound of lambda_max(G_W) for the squaring
     if (by_squaring) {
         EDA_TRY(gram_lmax_pair(h, scratch, aux, s));
     } else if (sq_w_tc) {
-        EDA_TRY(gram_lmax_one(h, n, h->GW, h->evals_w, scratch, &h->lmax_w, s));
-        scratch.used = mark;
         EDA_TRY(gram_eigen(h, k, h->GB, h->evals_b, h->evecs_b, scratch, part, pcap, &h->lmax_b, &nsb, s));
         first_b = h->nsig_first;
+        scratch.used = mark;
+        const double below = h->cfg.c2 > 0.0 ? DBL_MAX : h->lmax_b;   // with a given c^2 nothing is compared
+        EDA_TRY(gram_lmax_one(h, n, h->GW, h->evals_w, scratch, below, &h->lmax_w, &lbound_w, s));
     } else if (n <= kEigClusterMaxN && k <= kEigClusterMaxN) {
         // both on the cluster path (no grid barrier): solve side by side
         EDA_TRY(gram_eigen_pair(h, scratch, part, pcap, &nsw, &nsb, &first_w, &first_b, s));
@@ -517,6 +530,7 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     h->nsig_w = nsw;
     h->nsig_b = nsb;
     h->eig_ready = !by_squaring && !sq_w_tc;
+    h->lmax_w_bound = sq_w_tc ? std::max(lbound_w, h->lmax_w) : h->lmax_w;
     if (h->cfg.c2 > 0.0) {
         h->c2 = h->cfg.c2;
     } else {
@@ -544,8 +558,9 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
             double* workW = scratch.take<double>(6 * (size_t)n * n);
             if (!workW) return EDA_ERR_OOM;
             ProfScope prof("phi_squaring", s);
-            const OzSquare oz{&h->oznb, h->ozsmall, h->status};
-            EDA_TRY(phi_by_squaring(n, h->GW, -0.5 * h->c2, h->lmax_w, h->KW, workW, s, &oz));
+            const size_t b1 = align256(oz_operand_bytes(n, n));
+            const OzSquare oz{h->ozsmall, static_cast<char*>(h->ozsmall) + b1, h->status};
+            EDA_TRY(phi_by_squaring(n, h->GW, -0.5 * h->c2, h->lmax_w_bound, h->KW, workW, s, &oz));
         } else {
             EDA_TRY(phi_operator(n, nsw, h->evals_w + first_w, h->evecs_w, n, -0.5 * h->c2, h->KW, tmp, s));
         }
@@ -556,8 +571,8 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         // K_W and G_W are symmetric: column i is row i, so the column-scaled split serves as the left factor
         const size_t b1 = align256(oz_operand_bytes(n, n));
         char* p = static_cast<char*>(h->ozsmall);
-        EDA_TRY(oz_operand_make(h->KW, n, n, n, true, p + b1, &h->ozKW, h->status, s));
-        EDA_TRY(oz_operand_make(h->GW, n, n, n, true, p + 2 * b1, &h->ozGW, h->status, s));
+        EDA_TRY(oz_operand_make(h->KW, n, n, n, true, p + 2 * b1, &h->ozKW, h->status, s));
+        EDA_TRY(oz_operand_make(h->GW, n, n, n, true, p + 3 * b1, &h->ozGW, h->status, s));
     }
     if (h->cfg.prec == EDA_BF16) {
         // bf16 H_W, H_B tiled for sweep 1, bf16 H K tiled for sweep 2, and the staging
@@ -613,18 +628,16 @@ int tc_operands(eda_ctx* h, cudaStream_t s) {
 }
 
 // prec = EDA_F64_TC: the Grams G_W, G_B and the cross Grams G_WB, G_BW as the blocks of Z^T Z, computed with
-// the FP64-accurate tensor-core products 32 columns at a time. A column of Z has the same scale and digits
-// as an operand of either side, so Z^T Z comes out exactly symmetric.
+// the FP64-accurate tensor-core product of the split Z with itself in one launch (the blocks meeting the
+// upper triangle, the rest mirrored). A column of Z has the same scale and digits on either side, so
+// Z^T Z comes out exactly symmetric.
 int tc_grams(eda_ctx* h, cudaStream_t s) {
     const int64_t d = h->d;
     const int n = (int)h->n, k = h->k, nk = n + k;
     ProfScope prof("gram", s, (double)d * nk * (nk + 1.0), 8.0 * (double)d * nk);
     double* GZ = nullptr;
     EDA_CUDA_TRY(cudaMalloc(&GZ, (size_t)nk * nk * 8));
-    int rc = EDA_OK;
-    for (int j0 = 0; j0 < nk && rc == EDA_OK; j0 += 32)
-        rc = oz_gemm(h->ozT, h->oznb, std::min(32, nk - j0), h->HW + (size_t)j0 * d, d, 1.0, 0.0, nullptr, 0,
-                     GZ + (size_t)j0 * nk, nk, h->status, s);
+    int rc = oz_gemm_tiled(h->ozT, h->ozT, 1.0, 0.0, nullptr, 0, GZ, nk, true, h->status, s);
     if (rc == EDA_OK && !h->GWB) {
         const size_t xb = ((size_t)n * k * 8 + 255) & ~size_t(255);
         void* xp = nullptr;
@@ -838,9 +851,21 @@ int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_
     if (m == 0) return EDA_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t pcap = std::max<size_t>(1u << 19, (size_t)t * m);
+    const double* X = static_cast<const double*>(Xq);
+    if (h->cfg.prec == EDA_F64_TC && m <= (int64_t)INT32_MAX) {
+        // both factors split (columns of V and of Xq over the d pixels), one tensor-core launch
+        const size_t bv = align256(oz_operand_bytes(t, h->d)), bx = align256(oz_operand_bytes(m, h->d));
+        EDA_TRY(eda::ensure_workspace(h, align256(pcap * 8) * 4 + bv + bx + 4096));
+        char* w = static_cast<char*>(h->ws);
+        double* part = reinterpret_cast<double*>(w);
+        OzOperand ov, ox;
+        EDA_TRY(oz_operand_make(V, h->d, t, h->d, true, w + align256(pcap * 8) * 4, &ov, h->status, s));
+        EDA_TRY(oz_operand_make(X, ldq, m, h->d, true, w + align256(pcap * 8) * 4 + bv, &ox, h->status, s));
+        return oz_gemm_tiled(ov, ox, 1.0, 0.0, nullptr, 0, P, t, false, h->status, s, part, pcap * 4);
+    }
     EDA_TRY(eda::ensure_workspace(h, align256(pcap * 8) + 4096));
     double* part = static_cast<double*>(h->ws);
-    return gemm_tn_f64(h->d, t, (int)m, 1.0, V, h->d, static_cast<const double*>(Xq), ldq, 0.0, P, t, part, pcap, s);
+    return gemm_tn_f64(h->d, t, (int)m, 1.0, V, h->d, X, ldq, 0.0, P, t, part, pcap, s);
 }
 
 int eda_get_factors(eda_handle h, double* HW, double* HB, int32_t* counts, int32_t* perm, double* GW, double* GB,

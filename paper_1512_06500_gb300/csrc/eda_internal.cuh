@@ -309,12 +309,21 @@ int oz_narrow_make(int64_t Kmax, int max_splits, int64_t Mmax, void* mem, OzNarr
 int oz_gemm(const OzOperand& A, OzNarrow& nb, int p, const double* B, int64_t ldb, double alpha, double beta,
             const double* C0, int64_t ldc0, double* D, int64_t ldd, int* status, cudaStream_t s);
 
+// D (A.M x B.M, ldd) = alpha A B^T + beta C0 for two split operands over the same K (both in the
+// column-scaled layout: D_ij = sum_k A_ik B_jk), one launch over (128-row band of A, 32-row block of B).
+// upper (A and B the same operand, beta = 0): only the blocks meeting the upper triangle are computed and
+// the others mirrored; the product of an operand with itself is exactly symmetric. part (pcap doubles,
+// optional): K-split partials, used when the output grid alone leaves SMs idle (not with upper).
+int oz_gemm_tiled(const OzOperand& A, const OzOperand& B, double alpha, double beta, const double* C0, int64_t ldc0,
+                  double* D, int64_t ldd, bool upper, int* status, cudaStream_t s, double* part = nullptr,
+                  size_t pcap = 0);
+
 // K(alpha) = alpha phi(alpha G) from G itself by scaling and squaring (dense products only), given
 // lmax >= the largest eigenvalue of G. work: 6 m^2 doubles. With oz the m x m products run on the
-// tensor cores: abuf holds oz_operand_bytes(m, m) bytes, nb a narrow staging area for K = m.
+// tensor cores: abuf and bbuf hold oz_operand_bytes(m, m) bytes each (the two factors' splits).
 struct OzSquare {
-    OzNarrow* nb = nullptr;
     void* abuf = nullptr;
+    void* bbuf = nullptr;
     int* status = nullptr;
 };
 int phi_by_squaring(int m, const double* G, double alpha, double lmax, double* K, double* work,
@@ -328,6 +337,7 @@ struct eda_ctx {
     int32_t k = 0;          // number of columns of H_B
     eda_config cfg{};
     double c2 = 0, lmax_w = 0, lmax_b = 0;
+    double lmax_w_bound = 0;   // an upper bound of lambda_max(G_W) (lmax_w itself unless only estimated)
     // owned device memory
     void* block = nullptr;  // one allocation for everything below
     size_t block_bytes = 0;

@@ -226,9 +226,8 @@ int phi_operator(int n, int ns, const double* lam, const double* W, int ldw, dou
 // evaluated in Paterson-Stockmeyer form in the powers B, B^2, B^3 and B^4; e^B = I + B phi(B); then s
 // doublings phi(2B) = phi(B) (I + e^B) / 2 and e^(2B) = (e^B)^2. Every factor is a polynomial in G, so
 // all products commute in exact arithmetic; the result is symmetrised. 7 + 2 s dense m x m x m
-// products, on the FP64 pipe or, given oz, as FP64-accurate tensor-core products (the left factor
-// split into oz->abuf, the right one 32 columns at a time; a factor is symmetric, so its columns serve
-// as the rows of the split operand). work: 6 m^2 doubles.
+// products, on the FP64 pipe or, given oz, as FP64-accurate tensor-core products (both factors split, by
+// columns: D_ij = sum_k A_ki B_kj, and A is symmetric, so this is (A B)_ij). work: 6 m^2 doubles.
 int phi_by_squaring(int m, const double* G, double alpha, double lmax, double* K, double* work, cudaStream_t s,
                     const OzSquare* oz) {
     if (m <= 0) return EDA_OK;
@@ -254,12 +253,10 @@ int phi_by_squaring(int m, const double* G, double alpha, double lmax, double* K
     // C = alpha A B + beta C
     auto mulab = [&](double alpha_, const double* A, const double* B, double beta, double* C) -> int {
         if (!oz) return gemm_small_f64(false, false, m, m, m, alpha_, A, m, B, m, beta, C, m, s);
-        OzOperand op;
-        EDA_TRY(oz_operand_make(A, m, m, m, true, oz->abuf, &op, oz->status, s));
-        for (int c0 = 0; c0 < m; c0 += 32)
-            EDA_TRY(oz_gemm(op, *oz->nb, std::min(32, m - c0), B + (size_t)c0 * m, m, alpha_, beta,
-                            beta != 0.0 ? C + (size_t)c0 * m : nullptr, m, C + (size_t)c0 * m, m, oz->status, s));
-        return EDA_OK;
+        OzOperand oa, ob;
+        EDA_TRY(oz_operand_make(A, m, m, m, true, oz->abuf, &oa, oz->status, s));
+        EDA_TRY(oz_operand_make(B, m, m, m, true, oz->bbuf, &ob, oz->status, s));
+        return oz_gemm_tiled(oa, ob, alpha_, beta, beta != 0.0 ? C : nullptr, m, C, m, false, oz->status, s);
     };
     auto mul = [&](const double* A, const double* B, double beta, double* C) { return mulab(1.0, A, B, beta, C); };
     k_scale_sq<<<eb, 256, 0, s>>>(m, std::ldexp(alpha, -sq), G, P1);

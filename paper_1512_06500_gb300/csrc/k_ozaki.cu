@@ -61,20 +61,38 @@ __device__ __forceinline__ OzRing& oz_ring(unsigned char* raw) {
     return *reinterpret_cast<OzRing*>(raw + ((1024u - mis) & 1023u));
 }
 
+// B from a pre-tiled split operand (BT mode): its planes at tiles + q * slice, the same K tiling as A; the
+// product's 32-column block z (blockIdx.z) is the quarter z % 4 of B's 128-row band z / 4, one contiguous
+// 4 KB image per plane and stage. upper: skip the blocks wholly below the diagonal (z 32 + 32 <= band 128).
+struct OzBTiles {
+    const __nv_bfloat16* tiles = nullptr;
+    int64_t slice = 0;
+    int upper = 0;
+};
+
 // D[i, j] (i < M, j < N) = alpha * sum_k A_ik B_jk + beta * C0[i, j]; D, C0 column-major (ld ldd, ldc0),
 // the split-th slice of D at D + split * split_stride. A: digit planes at At + q * aslice, pre-tiled
 // (128-row bands, kbs tiles of 64 along K per band), row scales expA. B: digit planes read through tmB
-// (inner = K, outer = 7 x 32 rows: plane q is rows 32 q .. 32 q + 31), row scales expB. K stages
-// [split * kps, min(kst, (split + 1) * kps)).
+// (inner = K, outer = 7 x 32 rows: plane q is rows 32 q .. 32 q + 31), or in BT mode from bt (N rows, the
+// CTA's 32 of them chosen by blockIdx.z), row scales expB. K stages [split * kps, min(kst, (split + 1) * kps)).
+template <bool BT>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const __nv_bfloat16* __restrict__ At, int64_t aslice, int kbs, const __grid_constant__ CUtensorMap tmB,
-              const int* __restrict__ expA, const int* __restrict__ expB, int M, int N, int kst, int kps,
-              double alpha, double beta, const double* C0, int64_t ldc0, double* D, int64_t ldd,
+              const OzBTiles bt, const int* __restrict__ expA, const int* __restrict__ expB, int M, int N, int kst,
+              int kps, double alpha, double beta, const double* C0, int64_t ldc0, double* D, int64_t ldd,
               int64_t split_stride, int* status) {
     extern __shared__ unsigned char smraw[];
     OzRing& sm = oz_ring(smraw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int band = blockIdx.x, split = blockIdx.y;
+    const int blk = BT ? (int)blockIdx.z : 0;
+    if (BT) {
+        if (bt.upper && blk * OZ_N + OZ_N <= band * TC_M) return;   // the whole CTA: a uniform exit
+        expB += blk * OZ_N;
+        N -= blk * OZ_N;
+        D += (int64_t)blk * OZ_N * ldd;
+        if (C0) C0 += (int64_t)blk * OZ_N * ldc0;
+    }
     const int ks0 = split * kps;
     const int nks = max(0, min(kst, ks0 + kps) - ks0);
     const int nchunks = (nks + 1) >> 1;
@@ -114,8 +132,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const int bslot = s % OZ_BST;
             if (s >= OZ_BST && !(ok = mbar_wait(&sm.emptyB[bslot], ((s / OZ_BST) - 1) & 1, status))) break;
             mbar_expect_tx(&sm.fullB[bslot], bbytes);
+            if (BT) {
+                const __nv_bfloat16* src =
+                    bt.tiles + ((((int64_t)(blk >> 2)) * kbs + kstage) << 13) + (int64_t)(blk & 3) * (OZ_N * TC_KS);
 #pragma unroll
-            for (int q = 0; q < OZ_S; ++q) tma_load_2d(sm.B[bslot][q], &tmB, kstage * TC_KS, q * OZ_N, &sm.fullB[bslot]);
+                for (int q = 0; q < OZ_S; ++q)
+                    bulk_load(sm.B[bslot][q], src + q * bt.slice, OZ_N * TC_KS * 2, &sm.fullB[bslot]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < OZ_S; ++q)
+                    tma_load_2d(sm.B[bslot][q], &tmB, kstage * TC_KS, q * OZ_N, &sm.fullB[bslot]);
+            }
             issuedB = s + 1;
             for (int a = 0; a < OZ_S; ++a) {
                 const int idx = s * OZ_S + a;
@@ -411,7 +438,10 @@ int oz_attr() {
     static std::once_flag once;
     static cudaError_t rc = cudaSuccess;
     std::call_once(once, [] {
-        rc = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+        rc = cudaFuncSetAttribute(k_oz_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+        if (rc == cudaSuccess)
+            rc = cudaFuncSetAttribute(k_oz_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)oz_smem_bytes());
     });
     EDA_CUDA_TRY(rc);
     return EDA_OK;
@@ -556,22 +586,85 @@ int oz_gemm(const OzOperand& A, OzNarrow& nb, int p, const double* B, int64_t ld
     const int64_t sstride = splits == 1 ? 0 : (int64_t)p * A.M;
     {
         // the tensor-core kernel alone: it must read the seven digit planes of A and of B once and write D
-        ProfScope kprof("oz_kernel", s, 2.0 * OZ_S * OZ_S * (double)A.M * A.K * p,
+        // tensor work: the 28 digit-plane products of 2 M K p flops each
+        ProfScope kprof("oz_kernel", s, 56.0 * (double)A.M * A.K * p,
                         2.0 * OZ_S * ((double)A.M * A.K + (double)A.K * p) + 8.0 * (double)A.M * p);
+        const OzBTiles none{};
         if (splits == 1)
-            k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps,
-                                                                (int)A.M, p, kst, kps, alpha, beta, C0, ldc0, D, ldd,
-                                                                0, status);
+            k_oz_gemm<false><<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, none, A.exps,
+                                                                       nb.exps, (int)A.M, p, kst, kps, alpha, beta, C0,
+                                                                       ldc0, D, ldd, 0, status);
         else
-            k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, A.exps, nb.exps,
-                                                                (int)A.M, p, kst, kps, 1.0, 0.0, nullptr, 0,
-                                                                nb.partial, A.M, sstride, status);
+            k_oz_gemm<false><<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, nb.map, none, A.exps,
+                                                                       nb.exps, (int)A.M, p, kst, kps, 1.0, 0.0,
+                                                                       nullptr, 0, nb.partial, A.M, sstride, status);
         EDA_LAUNCHED();
     }
     if (splits == 1) return EDA_OK;
     k_oz_reduce<<<ceil_div((int64_t)A.M * p, 256), 256, 0, s>>>((int)A.M, p, splits, nb.partial, sstride, alpha,
                                                                  beta, C0, ldc0, D, ldd);
     EDA_LAUNCHED();
+    return EDA_OK;
+}
+
+// D[i, j] = alpha sum_k A_ik B_jk + beta C0[i, j] for two split operands with the same K (i < A.M, j < B.M):
+// one launch over (A band, B 32-row block); upper: only the blocks meeting the upper triangle i <= j, the
+// rest filled by the mirror image (A and B the same operand: the product is then exactly symmetric).
+__global__ void k_oz_mirror_lower(int n, double* D, int64_t ldd) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    const int i = (int)(t % n), j = (int)(t / n);
+    if (i > j && (j + OZ_N) / OZ_N * OZ_N <= (i / TC_M) * TC_M) D[(int64_t)j * ldd + i] = D[(int64_t)i * ldd + j];
+}
+
+int oz_gemm_tiled(const OzOperand& A, const OzOperand& B, double alpha, double beta, const double* C0, int64_t ldc0,
+                  double* D, int64_t ldd, bool upper, int* status, cudaStream_t s, double* part, size_t pcap) {
+    if (A.K != B.K || A.kbs != B.kbs || A.M < 1 || B.M < 1) return EDA_ERR_INVALID_ARG;
+    if (upper && (A.tiles != B.tiles || beta != 0.0)) return EDA_ERR_INVALID_ARG;
+    EDA_TRY(oz_attr());
+    const int kst = A.kbs;
+    const int nblk = ceil_div(B.M, OZ_N);
+    // K splits only when the (band, block) grid leaves SMs idle and a partial buffer is given
+    int splits = 1;
+    if (part && !upper) {
+        splits = std::max(1, std::min(kst / 8, sm_count() / std::max(1, A.mtiles * nblk)));
+        while (splits > 1 && (size_t)splits * A.M * B.M > pcap) --splits;
+    }
+    const int kps = ceil_div(kst, splits);
+    splits = ceil_div(kst, kps);
+    const dim3 grid((unsigned)A.mtiles, (unsigned)splits, (unsigned)nblk);
+    OzBTiles bt;
+    bt.tiles = B.tiles;
+    bt.slice = B.slice;
+    bt.upper = upper ? 1 : 0;
+    // tensor work of the computed blocks: 28 digit-plane products of 2 x 128 x 32 x K flops per (band, block)
+    double blocks = 0.0;
+    for (int b = 0; b < A.mtiles; ++b)
+        for (int z = 0; z < nblk; ++z) blocks += (upper && z * OZ_N + OZ_N <= b * TC_M) ? 0.0 : 1.0;
+    {
+        ProfScope kprof("oz_tiled", s, 56.0 * TC_M * OZ_N * (double)kst * TC_KS * blocks,
+                        2.0 * OZ_S * ((double)A.M * A.K + (double)A.K * B.M) + 8.0 * (double)A.M * B.M);
+        // tmB is not read in this mode; the operand's planes are passed in bt
+        static const CUtensorMap unused{};
+        if (splits == 1)
+            k_oz_gemm<true><<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, unused, bt, A.exps,
+                                                                      B.exps, (int)A.M, (int)B.M, kst, kps, alpha, beta,
+                                                                      C0, ldc0, D, ldd, 0, status);
+        else
+            k_oz_gemm<true><<<grid, OZ_THREADS, oz_smem_bytes(), s>>>(A.tiles, A.slice, A.kbs, unused, bt, A.exps,
+                                                                      B.exps, (int)A.M, (int)B.M, kst, kps, 1.0, 0.0,
+                                                                      nullptr, 0, part, A.M, (int64_t)A.M * B.M, status);
+        EDA_LAUNCHED();
+    }
+    if (splits > 1) {
+        k_oz_reduce<<<ceil_div((int64_t)A.M * B.M, 256), 256, 0, s>>>((int)A.M, (int)B.M, splits, part,
+                                                                     (int64_t)A.M * B.M, alpha, beta, C0, ldc0, D, ldd);
+        EDA_LAUNCHED();
+    }
+    if (upper) {
+        k_oz_mirror_lower<<<ceil_div((int64_t)A.M * A.M, 256), 256, 0, s>>>((int)A.M, D, ldd);
+        EDA_LAUNCHED();
+    }
     return EDA_OK;
 }
 

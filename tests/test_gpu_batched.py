@@ -3,7 +3,8 @@
 The batch runs the single-problem path for every problem on several host workers and streams; the
 results must be what the oracle gives for each problem alone: eigenvalues to 1e-10 relative and
 principal angles to 1e-8 for the FP64 path, 1e-6 for the bf16 tensor-core path, identical 1-NN labels.
-The 64-problem workload of uneven d, k, n_j is checked on a sample of its problems.
+The 64-problem workload of uneven d, k, n_j is checked problem by problem, in FP64 and in the tensor-core
+FP64 mode.
 """
 import numpy as np
 import pytest
@@ -29,9 +30,10 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
 
 
-def _check(eda, p, res, c2, eig_tol, angle_tol):
+def _check(eda, p, res, c2, eig_tol, angle_tol, ref=None):
     t = res["lam"].shape[0]
-    ref = O.eda(p.X, p.labels, p.k, t, c2=c2, tier="projected")
+    if ref is None:
+        ref = O.eda(p.X, p.labels, p.k, t, c2=c2, tier="projected")
     lam = res["lam"].cpu().numpy()
     rel = np.abs(lam - ref["lam_t"]) / ref["lam_t"]
     assert rel.max() <= eig_tol, (p.name, rel.max())
@@ -84,18 +86,28 @@ def test_batched_bf16_matches_oracle(eda):
         _check(eda, p, r, _c2(p, tau), 1e-6, 1e-5)
 
 
-def test_batched_64_problem_workload_sampled(eda):
+@pytest.fixture(scope="module")
+def batch64():
+    # the 64-problem workload and the oracle's answer for every problem (computed once for both precisions)
     ps = synth.batched_problems(64)
     tau = synth.BATCHED["tau"]
-    cfg = eda.config(prec=eda.EDA_F64, block_b=0, tau=tau)
+    refs = []
+    for p in ps:
+        c2 = _c2(p, tau)
+        refs.append((c2, O.eda(p.X, p.labels, p.k, p.k - 1, c2=c2, tier="projected")))
+    return ps, tau, refs
+
+
+@pytest.mark.parametrize("prec_name", ["f64", "tc"])
+def test_batched_64_problem_workload_all(eda, batch64, prec_name):
+    ps, tau, refs = batch64
+    prec = eda.EDA_F64 if prec_name == "f64" else eda.EDA_F64_TC
+    cfg = eda.config(prec=prec, block_b=0, tau=tau)
     probs = [dict(X=_dev(p.X), labels=_dev(p.labels), k=p.k, t=p.k - 1, tol=1e-10) for p in ps]
     res, code = eda.solve_batched(probs, cfg, workers=16)
     assert code == 0, [r["status"] for r in res]
     assert all(r["status"] == 0 for r in res)
-    # a sample spanning the three dimensions, checked against the oracle one by one
-    by_d = {}
-    for i, p in enumerate(ps):
-        by_d.setdefault(p.d, []).append(i)
-    sample = [v[0] for v in by_d.values()] + [max(range(len(ps)), key=lambda i: ps[i].n)]
-    for i in sample:
-        _check(eda, ps[i], res[i], _c2(ps[i], tau), 1e-9, 1e-7)
+    # every problem against the oracle, one by one
+    for p, r, (c2, ref) in zip(ps, res, refs):
+        assert abs(r["info"]["c2"] - c2) <= 1e-13 * c2, p.name
+        _check(eda, p, r, c2, 1e-9, 1e-7, ref=ref)

@@ -85,6 +85,31 @@ def test_m_apply_tc_zero_and_constant_columns(eda):
         assert _colwise(Y, Yr) <= 1e-12
 
 
+def test_m_apply_tc_extreme_magnitudes(eda):
+    # the digit split reads mantissa and exponent from the bits: columns spanning 300 decades, subnormal
+    # columns and one dominant entry over tiny ones are reproduced to 1e-12 of each column's largest entry
+    p = synth.gaussian_clusters(d=700, k=7, n_per_class=5, seed=612)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    c2 = _oracle_c2(f, 10.0)
+    rng = np.random.default_rng(613)
+    sgn = lambda: rng.choice([-1.0, 1.0], size=700)
+    X = np.empty((700, 3))
+    X[:, 0] = sgn() * 10.0 ** rng.uniform(-150, 150, 700)
+    X[:, 1] = sgn() * 10.0 ** rng.uniform(-318, -309, 700)       # subnormal entries only
+    X[::5, 1] = 0.0
+    X[:, 2] = sgn() * 1e-200
+    X[17, 2] = 1e200
+    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=2, tau=10.0)
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        Y = h.apply_exp(eda.OP_M, _dev(X.T)).cpu().numpy().T
+    # the oracle on each column scaled by a power of two to a largest entry near 1 (exact in FP64, and M
+    # is linear), so that its own products do not round in the subnormal range
+    e = np.frexp(np.abs(X).max(axis=0))[1]
+    Yr = np.ldexp(O.m_apply(f["HW"], f["HB"], c2, np.ldexp(X, -e[None, :])), e[None, :])
+    assert np.all(np.isfinite(Y))
+    assert _colwise(Y, Yr) <= 1e-12, _colwise(Y, Yr)
+
+
 def _solve_compare(eda, p, t, b, tau, tol, ref):
     cfg = eda.config(prec=eda.EDA_F64_TC, block_b=b, tau=tau, true_residuals=1)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
