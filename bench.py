@@ -146,16 +146,19 @@ def workload_config(args, name=None):
         return {"workload": "batched64: 64 independent problems, d in {1024, 4096, 16384}, k ~ U[10, 100], "
                             f"n_j ~ U[3, 10] per class, t = k - 1, tau = {synth.BATCHED['tau']}, tol={args.tol}",
                 "l2": "flushed (256 MB write) before every step",
-                "precision": "plain FP64 sweeps and small steps; block size tuned per problem shape",
+                "precision": ("FP64 solver with FP64-accurate tensor-core products (7 bf16 digit planes, exact "
+                              "integer accumulation)" if getattr(args, "prec", "f64") == "tc" else
+                              "plain FP64 sweeps and small steps") + "; block size tuned per problem shape",
                 "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form],
                 "workers": args.workers}
     c = synth.CONFIGS[name]
     return {"workload": f"{name}: d={c['d']}, k={c['k']}, n_j={c['n_j']} (n={c['k'] * c['n_j']}), "
                         f"t={c['t']}, b={c['b']}, tau={c['tau']}, tol={args.tol}",
             "l2": "flushed (256 MB write) before every step; the samples (d n 8 bytes) are read from HBM",
-            "precision": ("FP64 solver; the products with [H_W H_B] (Grams, M-apply sweeps, recovery) as FP64-accurate "
-                          "tensor-core products: operands split exactly into 7 bf16 digit planes, exact integer "
-                          "accumulation" if getattr(args, "prec", "f64") == "tc" else
+            "precision": ("FP64 solver; the products with [H_W H_B], the Krylov basis and the n x n Grams (Grams, "
+                          "M-apply sweeps, reorthogonalisation, Ritz vectors, K_W, recovery, projection) as "
+                          "FP64-accurate tensor-core products: operands split exactly into 7 bf16 digit planes, exact "
+                          "integer accumulation" if getattr(args, "prec", "f64") == "tc" else
                           "plain FP64 sweeps and small steps"),
             "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form]}
 
@@ -330,7 +333,7 @@ def run_gpu_batched(args, rank, world, local_rank):
     Xs = [torch.from_numpy(p.X).to(dev) for p in ps]
     labs = [torch.from_numpy(p.labels).to(dev) for p in ps]
     probs = [dict(X=X, labels=lab, k=p.k, t=p.k - 1, tol=args.tol) for X, lab, p in zip(Xs, labs, ps)]
-    cfg = eda.config(block_b=0, tau=synth.BATCHED["tau"], m_form=args.m_form)
+    cfg = eda.config(prec=PRECS[args.prec], block_b=0, tau=synth.BATCHED["tau"], m_form=args.m_form)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -379,7 +382,13 @@ def run_gpu_batched(args, rank, world, local_rank):
     exp_bytes = sum(v[1] for v in ewk)
     pk = peaks()
     tri_tf = tri_flops / (tri_ms / 1e3) / 1e12 if tri_ms > 0 else float("nan")
-    roofline = {
+    rr = dict(regions={r: eda.profile_read(r) for r in REGIONS},
+              work={r: eda.profile_work(r) for r in ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "oz_tiled")})
+    roofline = roofline_of("batched64", rr, args.steps, args.prec, pk)
+    roofline["note"] = ("achieved = algorithmic work / summed per-launch durations; the problems run concurrently "
+                        "on several streams, so a launch's duration includes time shared with other problems' "
+                        "kernels and the figure is a lower bound")
+    tridiag = {
         "kernel": "k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the FP64 "
                   "Grams and Rayleigh-Ritz matrices, summed over concurrent problems",
         "bound": "alu", "achieved": tri_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
@@ -425,7 +434,7 @@ def run_gpu_batched(args, rank, world, local_rank):
         "config": dict(workload_config(args), problems_per_s=1e3 * world * len(ps) / ms),
         "clocks": clk, "gpu_launches": launches,
         "e2e": {"value": e2e_v, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "roofline": roofline, "exp_apply_fp64": exp_apply_fp64,
+        "roofline": roofline, "tridiag": tridiag, "exp_apply_fp64": exp_apply_fp64,
         "breakdown_ms_per_step_summed_over_streams": breakdown,
         "solve_info": {"mapplies_total": sum(r["info"]["mapplies"] for r in res),
                        "max_relres_est": max(r["info"]["max_relres_est"] for r in res)},

@@ -51,7 +51,7 @@ int tune_block(eda_handle h, int t, cudaStream_t s, int* b_out) {
     }
     const int cand[4] = {4, 8, 16, 32};
     const int bmax = 32;
-    const bool f32io = prec != EDA_F64;
+    const bool f32io = prec == EDA_F32 || prec == EDA_BF16;   // the FP64 solvers (also EDA_F64_TC) take FP64 blocks
     const size_t esz = f32io ? 4 : 8;
     void* buf = nullptr;
     EDA_CUDA_TRY(cudaMalloc(&buf, 2 * (size_t)h->d * bmax * esz));
