@@ -663,8 +663,8 @@ def run_gpu(args, rank, world, local_rank):
     tri_ms, tri_calls = regions["tridiag"]
     tri_flops, _ = r["work"]["tridiag"]
     latency_bound = {
-        "kernel": "k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the Gram "
-                  "(n > 256) and of the Rayleigh-Ritz matrices",
+        "kernel": "k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the Rayleigh-Ritz "
+                  "matrices (and of a Gram taking the eigensolver route)",
         "achieved_tflops": rate(tri_flops, tri_ms) if tri_ms > 0 else None,
         "avg_call_us": tri_ms * 1e3 / max(tri_calls, 1), "calls": tri_calls,
         "note": "latency-bound: n dependent column steps, each a chain of FP64 instructions (64 cycles per warp "
