@@ -302,6 +302,11 @@ int oz_operand_init(int64_t Mcap, int64_t Kcap, void* mem, OzOperand* op, cudaSt
 int oz_append_cols(const double* A, int64_t lda, int i0, int i1, int64_t K, OzOperand* op, int* status,
                    cudaStream_t s);
 int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperand* op, int* status, cudaStream_t s);
+// Grow a row-scaled operand (made by oz_operand_init, grown only by this call) from k0 to k1 columns of A:
+// new digits for the rows whose scale the new columns leave unchanged, a full re-split of the others.
+// list: M + 1 ints of scratch.
+int oz_grow_rows(const double* A, int64_t lda, int64_t M, int64_t k0, int64_t k1, OzOperand* op, int* list,
+                 int* status, cudaStream_t s);
 size_t oz_narrow_bytes(int64_t Kmax, int max_splits, int64_t Mmax);
 int oz_narrow_make(int64_t Kmax, int max_splits, int64_t Mmax, void* mem, OzNarrow* nb);
 // D (M x p, ldd) = alpha * op(A) B + beta * C0 (ldc0), op(A) the M x K split operand, B: K x p (ldb),

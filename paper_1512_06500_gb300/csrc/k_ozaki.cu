@@ -17,8 +17,8 @@
 // (q + 1) 128 2^14 < 2^24, so the tensor cores' FP32 accumulation of a chunk is exact. Each chunk's
 // seven levels are read out of tensor memory, converted to integers and folded into two 64-bit
 // integer sums per output (G_0 = L_0 2^16 + L_1 2^8 + L_2 and G_1 = L_3 2^24 + L_4 2^16 + L_5 2^8 + L_6),
-// so the reduction over k is exact as well; the only roundings are the final conversion to FP64 and the
-// 2^-56 truncation of the digits.
+// so the reduction over k is exact as well; the only roundings are the final conversion to FP64 (one
+// rounding of the exact G_0 2^32 + G_1) and the 2^-56 truncation of the digits.
 //
 // Kernel. One CTA per (128-row band of M, split of K), 256 threads: thread 0 issues the bulk copies of
 // the pre-tiled digit planes of A (one contiguous 16 KB swizzled tile per K stage of 64 and plane) and
@@ -69,6 +69,40 @@ struct OzBTiles {
     int64_t slice = 0;
     int upper = 0;
 };
+
+// G_0 2^(e - 30) + G_1 2^(e - 62) rounded once to the nearest double (ties to even), from the exact 128-bit
+// integer G_0 2^32 + G_1 with integer operations: the two conversions, two scalings and the addition this
+// replaces took eight FP64 instructions per output, the FP64 pipe being GB300's narrowest. Results
+// outside the normal range take ldexp.
+__device__ __forceinline__ double oz_combine(long long g0, long long g1, int e) {
+    const __int128 x = (__int128)g0 * ((__int128)1 << 32) + (__int128)g1;
+    if (x == 0) return 0.0;
+    const bool neg = x < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-(x + 1)) + 1 : (unsigned __int128)x;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+    int sh = nb - 53;
+    unsigned long long m;
+    if (sh <= 0) {
+        m = (unsigned long long)(u << (-sh));
+    } else {
+        unsigned __int128 r = u >> sh;
+        const unsigned __int128 rem = u - (r << sh), half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (r & 1))) ++r;
+        if (r >> 53) {
+            r >>= 1;
+            ++sh;
+        }
+        m = (unsigned long long)r;
+    }
+    // the value is m 2^(sh + e - 62) with m in [2^52, 2^53)
+    const long long E = (long long)sh + e - 62 + 52 + 1023;
+    if (E >= 1 && E <= 2046)
+        return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)E << 52) |
+                                                (m & ((1ull << 52) - 1))));
+    const double v = ldexp((double)m, (int)(sh + e - 62));
+    return neg ? -v : v;
+}
 
 // D[i, j] (i < M, j < N) = alpha * sum_k A_ik B_jk + beta * C0[i, j]; D, C0 column-major (ld ldd, ldc0),
 // the split-th slice of D at D + split * split_stride. A: digit planes at At + q * aslice, pre-tiled
@@ -246,9 +280,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int c = 0; c < OZ_N; ++c) {
                 if (c >= N) break;
                 const int e = ea + expB[c];
-                double v = (s_ok && nks > 0) ? ldexp((double)g0[c], e - 30) + ldexp((double)g1[c], e - 62) : 0.0;
+                double v = (s_ok && nks > 0) ? oz_combine(g0[c], g1[c], e) : 0.0;
                 if (!s_ok) v = nan("");
-                double out = alpha * v;
+                double out = alpha == 1.0 ? v : alpha * v;
                 if (beta != 0.0) out = fma(beta, C0[(int64_t)c * ldc0 + i], out);
                 Ds[(int64_t)c * ldd + i] = out;
             }
@@ -421,6 +455,75 @@ __global__ void k_oz_split_rows8(const double* __restrict__ A, int64_t lda, int6
         *reinterpret_cast<uint4*>(out + q * slice + off) = *reinterpret_cast<const uint4*>(dg[q]);
 }
 
+// Growing a row-scaled operand (the Krylov basis, M = d rows, K = the columns so far) from k0 to k1 columns:
+// thread per row. A row whose scale is unchanged by the new columns gets the digits of its new 8-groups
+// [k0 rounded down to 8, k1) (the part of a group below k0 rewritten with identical digits); a row whose
+// scale grows records the new scale and joins list (count in list[0]) for a full re-split by
+// k_oz_resplit_listed. Zero rows keep the scale kOzExpZero.
+__global__ void k_oz_grow_rows(const double* __restrict__ A, int64_t lda, int64_t M, int64_t k0, int64_t k1,
+                               int* __restrict__ e, int kbs, __nv_bfloat16* __restrict__ out, int64_t slice,
+                               int* __restrict__ list, int* __restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int mnew = kOzExpZero;
+    for (int64_t k = k0; k < k1; ++k) mnew = max(mnew, oz_frexp_exp(A[k * lda + i]));
+    int eold = k0 == 0 ? mnew : e[i];
+    if (k0 == 0) {
+        e[i] = mnew;   // the first columns: their digits below, with their own scale
+    } else if (mnew > eold) {
+        e[i] = mnew;
+        list[1 + atomicAdd(&list[0], 1)] = (int)i;
+        return;
+    }
+    bool fin = true;
+    for (int64_t kg = k0 & ~(int64_t)7; kg < k1; kg += 8) {
+        __align__(16) __nv_bfloat16 dg[OZ_S][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t k = kg + u;
+            const double v = k < k1 ? A[k * lda + i] : 0.0;
+            __nv_bfloat16 sq[OZ_S];
+            fin &= oz_digits(v, eold, sq);
+#pragma unroll
+            for (int q = 0; q < OZ_S; ++q) dg[q][u] = sq[q];
+        }
+        const int64_t off = tile_off(i, kg, kbs);
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q)
+            *reinterpret_cast<uint4*>(out + q * slice + off) = *reinterpret_cast<const uint4*>(dg[q]);
+    }
+    if (!fin) atomicOr(status, ST_NONFINITE);
+}
+
+// Full re-split, columns 0 .. K, of the rows in list (count list[0]), one (row, 8-group) per thread step.
+__global__ void k_oz_resplit_listed(const double* __restrict__ A, int64_t lda, int64_t K, const int* __restrict__ e,
+                                    int kbs, __nv_bfloat16* __restrict__ out, int64_t slice,
+                                    const int* __restrict__ list, int* __restrict__ status) {
+    const int64_t groups = (K + 7) / 8;
+    const int64_t total = (int64_t)list[0] * groups;
+    bool fin = true;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = list[1 + t % list[0]];
+        const int64_t kg = (t / list[0]) * 8;
+        const int ex = e[i];
+        __align__(16) __nv_bfloat16 dg[OZ_S][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t k = kg + u;
+            const double v = k < K ? A[k * lda + i] : 0.0;
+            __nv_bfloat16 sq[OZ_S];
+            fin &= oz_digits(v, ex, sq);
+#pragma unroll
+            for (int q = 0; q < OZ_S; ++q) dg[q][u] = sq[q];
+        }
+        const int64_t off = tile_off(i, kg, kbs);
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q)
+            *reinterpret_cast<uint4*>(out + q * slice + off) = *reinterpret_cast<const uint4*>(dg[q]);
+    }
+    if (!fin) atomicOr(status, ST_NONFINITE);
+}
+
 // D[i, j] = alpha * sum_s P[s][j][i] + beta * D[i, j], splits added in order (deterministic).
 __global__ void k_oz_reduce(int M, int N, int splits, const double* __restrict__ P, int64_t sstride, double alpha,
                             double beta, const double* C0, int64_t ldc0, double* D, int64_t ldd) {
@@ -442,6 +545,7 @@ int oz_attr() {
         if (rc == cudaSuccess)
             rc = cudaFuncSetAttribute(k_oz_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)oz_smem_bytes());
+
     });
     EDA_CUDA_TRY(rc);
     return EDA_OK;
@@ -533,6 +637,22 @@ int oz_resplit_rows(const double* A, int64_t lda, int64_t M, int64_t K, OzOperan
     EDA_LAUNCHED();
     op->M = M;
     op->K = K;
+    op->mtiles = ceil_div(M, TC_M);
+    return EDA_OK;
+}
+
+int oz_grow_rows(const double* A, int64_t lda, int64_t M, int64_t k0, int64_t k1, OzOperand* op, int* list,
+                 int* status, cudaStream_t s) {
+    if (k1 <= k0) return EDA_OK;
+    EDA_CUDA_TRY(cudaMemsetAsync(list, 0, sizeof(int), s));
+    k_oz_grow_rows<<<ceil_div(M, 256), 256, 0, s>>>(A, lda, M, k0, k1, op->exps, op->kbs, op->tiles, op->slice, list,
+                                                    status);
+    EDA_LAUNCHED();
+    k_oz_resplit_listed<<<2 * sm_count(), 256, 0, s>>>(A, lda, k1, op->exps, op->kbs, op->tiles, op->slice, list,
+                                                        status);
+    EDA_LAUNCHED();
+    op->M = M;
+    op->K = k1;
     op->mtiles = ceil_div(M, TC_M);
     return EDA_OK;
 }

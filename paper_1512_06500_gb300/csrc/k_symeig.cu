@@ -1121,7 +1121,9 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     } else {
     int per_sm = 0;
     EDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, TRI_THREADS, smem));
-    int ctas = std::max(1, std::min(n / 16, sms));
+    // about 8 rows per CTA: more CTAs shorten each column step's FP64 chains (16 rows per CTA measured
+    // 10 % slower at the Rayleigh-Ritz sizes 576-704; fewer than 8 rows gained nothing)
+    int ctas = std::max(1, std::min(n / 8, sms));
     ctas = std::min(ctas, std::max(1, per_sm * sms));
     double* pglob = ws->vbuf;
     EDA_CUDA_TRY(cudaMemsetAsync(ws->bar.count, 0, sizeof(unsigned), s));

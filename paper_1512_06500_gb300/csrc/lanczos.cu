@@ -117,6 +117,7 @@ struct SolveWs {
     bool oz = false;
     OzOperand VT, VN;
     int oz_cap = 0;                  // columns the basis operands hold (m_max)
+    int* olist = nullptr;            // d + 1 ints: rows of VN to split afresh
 };
 
 // tc products with the split basis, 32 columns at a time: C (cols x p, ldc) = V^T X, and X -= V C
@@ -149,7 +150,8 @@ int oz_basis_grow(SolveWs<T>& w, int64_t d, int cols0, int cols1, int* status, c
     if (!w.oz) return EDA_OK;
     const double* V = reinterpret_cast<const double*>(w.V);
     EDA_TRY(oz_append_cols(V, d, cols0, cols1, d, &w.VT, status, s));
-    return oz_resplit_rows(V, d, d, cols1, &w.VN, status, s);
+    // row scales over all columns so far: only rows whose scale the new block raises are split afresh
+    return oz_grow_rows(V, d, d, cols0, cols1, &w.VN, w.olist, status, s);
 }
 
 template <class T>
@@ -675,7 +677,8 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
     need += symeig_work_bytes(eig_n, t) + 16384;
     const bool oz = !mixed && h->cfg.prec == EDA_F64_TC && h->ozblock;
     const size_t ozT_bytes = oz ? a256(oz_operand_bytes(m_max, d)) : 0, ozN_bytes = oz ? a256(oz_operand_bytes(d, m_max)) : 0;
-    need += ozT_bytes + ozN_bytes;
+    const size_t olist_bytes = oz ? a256((size_t)(d + 64) * sizeof(int)) : 0;
+    need += ozT_bytes + ozN_bytes + olist_bytes;
     EDA_TRY(ensure_workspace(h, need));
     Arena a{static_cast<char*>(h->ws), h->ws_bytes, 0};
     w.V = a.take<T>((size_t)d * m_max);
@@ -726,6 +729,8 @@ int solve_t(eda_ctx* h, int t, double tol, const double* V0, int b0, double* Vou
         if (!mT || !mN) return EDA_ERR_OOM;
         EDA_TRY(oz_operand_init(m_max, d, mT, &w.VT, s));
         EDA_TRY(oz_operand_init(d, m_max, mN, &w.VN, s));
+        w.olist = a.take<int>((size_t)d + 64);
+        if (!w.olist) return EDA_ERR_OOM;
         w.oz = true;
         w.oz_cap = m_max;
     }
