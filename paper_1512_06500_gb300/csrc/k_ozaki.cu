@@ -17,8 +17,8 @@
 // (q + 1) 128 2^14 < 2^24, so the tensor cores' FP32 accumulation of a chunk is exact. Each chunk's
 // seven levels are read out of tensor memory, converted to integers and folded into two 64-bit
 // integer sums per output (G_0 = L_0 2^16 + L_1 2^8 + L_2 and G_1 = L_3 2^24 + L_4 2^16 + L_5 2^8 + L_6),
-// so the reduction over k is exact as well; the only roundings are the final conversion to FP64 (one
-// rounding of the exact G_0 2^32 + G_1) and the 2^-56 truncation of the digits.
+// so the reduction over k is exact as well; the only roundings are the final conversion to FP64 and the
+// 2^-56 truncation of the digits.
 //
 // Kernel. One CTA per (128-row band of M, split of K), 256 threads: thread 0 issues the bulk copies of
 // the pre-tiled digit planes of A (one contiguous 16 KB swizzled tile per K stage of 64 and plane) and
@@ -69,40 +69,6 @@ struct OzBTiles {
     int64_t slice = 0;
     int upper = 0;
 };
-
-// G_0 2^(e - 30) + G_1 2^(e - 62) rounded once to the nearest double (ties to even), from the exact 128-bit
-// integer G_0 2^32 + G_1 with integer operations: the two conversions, two scalings and the addition this
-// replaces took eight FP64 instructions per output, the FP64 pipe being GB300's narrowest. Results
-// outside the normal range take ldexp.
-__device__ __forceinline__ double oz_combine(long long g0, long long g1, int e) {
-    const __int128 x = (__int128)g0 * ((__int128)1 << 32) + (__int128)g1;
-    if (x == 0) return 0.0;
-    const bool neg = x < 0;
-    const unsigned __int128 u = neg ? (unsigned __int128)(-(x + 1)) + 1 : (unsigned __int128)x;
-    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-    const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-    int sh = nb - 53;
-    unsigned long long m;
-    if (sh <= 0) {
-        m = (unsigned long long)(u << (-sh));
-    } else {
-        unsigned __int128 r = u >> sh;
-        const unsigned __int128 rem = u - (r << sh), half = (unsigned __int128)1 << (sh - 1);
-        if (rem > half || (rem == half && (r & 1))) ++r;
-        if (r >> 53) {
-            r >>= 1;
-            ++sh;
-        }
-        m = (unsigned long long)r;
-    }
-    // the value is m 2^(sh + e - 62) with m in [2^52, 2^53)
-    const long long E = (long long)sh + e - 62 + 52 + 1023;
-    if (E >= 1 && E <= 2046)
-        return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)E << 52) |
-                                                (m & ((1ull << 52) - 1))));
-    const double v = ldexp((double)m, (int)(sh + e - 62));
-    return neg ? -v : v;
-}
 
 // D[i, j] (i < M, j < N) = alpha * sum_k A_ik B_jk + beta * C0[i, j]; D, C0 column-major (ld ldd, ldc0),
 // the split-th slice of D at D + split * split_stride. A: digit planes at At + q * aslice, pre-tiled
@@ -280,9 +246,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int c = 0; c < OZ_N; ++c) {
                 if (c >= N) break;
                 const int e = ea + expB[c];
-                double v = (s_ok && nks > 0) ? oz_combine(g0[c], g1[c], e) : 0.0;
+                double v = (s_ok && nks > 0) ? ldexp((double)g0[c], e - 30) + ldexp((double)g1[c], e - 62) : 0.0;
                 if (!s_ok) v = nan("");
-                double out = alpha == 1.0 ? v : alpha * v;
+                double out = alpha * v;
                 if (beta != 0.0) out = fma(beta, C0[(int64_t)c * ldc0 + i], out);
                 Ds[(int64_t)c * ldd + i] = out;
             }

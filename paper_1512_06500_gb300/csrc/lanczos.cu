@@ -347,27 +347,42 @@ int run_lanczos(eda_ctx* h, int t, double tol, const double* V0, int b0, int m_m
             ++st.checks;
             st.rr_cols = cols;
             ProfScope prof("rr", s);
+            // residual estimates of the t Ritz pairs in S: from the last block row of S, or from W when
+            // directions of W below the rank threshold were dropped from B (||W s_last|| / |theta|, W the
+            // reorthogonalised remainder of M V_j)
+            auto estimate = [&]() -> int {
+                if (lostc > 0) {
+                    EDA_TRY(gemm_nn<T>(d, b, t, 1.0, w.W, d, w.S + (cols - b), cols, 0.0, nullptr, 0, w.Yt, d, s));
+                    EDA_TRY(col_norms<T>(d, t, w.Yt, d, w.relres, s));
+                    k_divide<<<ceil_div(t, 128), 128, 0, s>>>(t, w.relres, w.theta);
+                    EDA_LAUNCHED();
+                } else {
+                    k_ritz_residuals<<<ceil_div(t, 128), 128, 0, s>>>(t, b, w.Bm, b, w.S, cols, cols - b, w.theta,
+                                                                     w.relres);
+                    EDA_LAUNCHED();
+                }
+                EDA_CUDA_TRY(
+                    cudaMemcpyAsync(st.relres.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
+                EDA_CUDA_TRY(cudaStreamSynchronize(s));
+                st.max_rel = 0.0;
+                st.conv_count = 0;
+                for (int i = 0; i < t; ++i) {
+                    if (st.relres[i] <= tol) ++st.conv_count;
+                    st.max_rel = std::max(st.max_rel, st.relres[i]);
+                }
+                return EDA_OK;
+            };
+            // A check that will not stop the iteration only needs the estimates, for which each inverse
+            // iteration vector serves alone: the Gram-Schmidt inside clusters of close Ritz values (here
+            // the many just above 1, close in units of 1e-7 theta_1) is done only when the estimates say
+            // converged, or at the basis limit, and the estimates are then taken again from the
+            // orthogonalised vectors, which the Ritz vectors are formed from.
             EDA_TRY(symeig_f64(cols, w.Tm, m_max, cols - t, cols - 1, w.theta, w.S, cols, &w.eig, h->status,
-                               h->cfg.seed + 7, 1e-7, s));
-            if (lostc > 0) {
-                // directions of W below the rank threshold were dropped from B: estimate from W itself,
-                // ||W s_last|| / |theta| (W is the reorthogonalised remainder of M V_j)
-                EDA_TRY(gemm_nn<T>(d, b, t, 1.0, w.W, d, w.S + (cols - b), cols, 0.0, nullptr, 0, w.Yt, d, s));
-                EDA_TRY(col_norms<T>(d, t, w.Yt, d, w.relres, s));
-                k_divide<<<ceil_div(t, 128), 128, 0, s>>>(t, w.relres, w.theta);
-                EDA_LAUNCHED();
-            } else {
-                k_ritz_residuals<<<ceil_div(t, 128), 128, 0, s>>>(t, b, w.Bm, b, w.S, cols, cols - b, w.theta,
-                                                                 w.relres);
-                EDA_LAUNCHED();
-            }
-            EDA_CUDA_TRY(cudaMemcpyAsync(st.relres.data(), w.relres, t * sizeof(double), cudaMemcpyDeviceToHost, s));
-            EDA_CUDA_TRY(cudaStreamSynchronize(s));
-            st.max_rel = 0.0;
-            st.conv_count = 0;
-            for (int i = 0; i < t; ++i) {
-                if (st.relres[i] <= tol) ++st.conv_count;
-                st.max_rel = std::max(st.max_rel, st.relres[i]);
+                               h->cfg.seed + 7, last ? 1e-7 : 0.0, s));
+            EDA_TRY(estimate());
+            if (!last && st.conv_count == t) {
+                EDA_TRY(symeig_vectors(cols, t, w.theta, w.S, cols, &w.eig, h->cfg.seed + 7, 1e-7, s));
+                EDA_TRY(estimate());
             }
             if (st.conv_count == t) st.converged = true;
             // no usable rate (no progress since the last check): wait a quarter of the basis width (the
