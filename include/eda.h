@@ -85,7 +85,12 @@ typedef struct {
                                  /* symmetric eigensolver, n > 512) before it gives up and    */
                                  /* the call returns EDA_ERR_TIMEOUT; <= 0: the default,      */
                                  /* 20,000,000 (about 1-2 s)                                  */
-    int32_t reserved[5];
+    int32_t tc_min_mi;           /* EDA_F64_TC: the size of Z = [H_W H_B], d (n + k), in units  */
+                                 /* of 2^20 entries, from which the tensor-core products are  */
+                                 /* used; below it the FP64 ones (the two agree to FP64       */
+                                 /* rounding; the splitting launches cost more than they save */
+                                 /* on small factors); 0: the default, 4; < 0: always         */
+    int32_t reserved[4];
 } eda_config;
 
 typedef struct {

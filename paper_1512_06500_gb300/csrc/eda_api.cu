@@ -84,6 +84,7 @@ constexpr double kSigRel = 32.0;   // eigenvalues <= kSigRel * n * eps * lambda_
 constexpr int kLanczosSteps = 64;  // steps of the largest-eigenvalue Lanczos run on a Gram
 constexpr double kLmaxAccept = 8.0;  // accept its theta_1 when its residual is <= kLmaxAccept * eps * theta_1
 constexpr int kLanczosStepsLarge = 64;    // the same run on a large Gram (n >= kOzSmallMinN, tensor-core mode)
+constexpr int64_t kTcMinMiDefault = 4;    // EDA_F64_TC: tensor-core products from d (n + k) >= 4 x 2^20 on
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -456,7 +457,9 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
     AuxStream aux;
     double* partB = nullptr;
     size_t pcapB = 0;
-    const bool tc = h->cfg.prec == EDA_F64_TC;
+    // the tensor-core products from a size of Z on (tc_min_mi), the FP64 ones below it
+    const int64_t zmi = h->cfg.tc_min_mi == 0 ? kTcMinMiDefault : h->cfg.tc_min_mi;
+    const bool tc = h->cfg.prec == EDA_F64_TC && (zmi < 0 || d * (int64_t)(n + k) >= (zmi << 20));
     // Large G_W in tensor-core mode: lambda_max by Lanczos and K_W by scaling and squaring with
     // FP64-accurate tensor-core products, instead of the n-step tridiagonalisation and the
     // back-transformation of the eigensolver; G_B keeps its route.
@@ -852,7 +855,7 @@ int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t pcap = std::max<size_t>(1u << 19, (size_t)t * m);
     const double* X = static_cast<const double*>(Xq);
-    if (h->cfg.prec == EDA_F64_TC && m <= (int64_t)INT32_MAX) {
+    if (h->cfg.prec == EDA_F64_TC && h->ozblock && m <= (int64_t)INT32_MAX) {
         // both factors split (columns of V and of Xq over the d pixels), one tensor-core launch
         const size_t bv = align256(oz_operand_bytes(t, h->d)), bx = align256(oz_operand_bytes(m, h->d));
         EDA_TRY(eda::ensure_workspace(h, align256(pcap * 8) * 4 + bv + bx + 4096));

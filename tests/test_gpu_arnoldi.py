@@ -59,14 +59,14 @@ def test_n_apply_matches_oracle(eda, prec_name, d, k, nj, b, tau):
     Xb = rng.standard_normal((d, b))
     Yr = O.n_apply(f["HW"], f["HB"], c2, Xb)
     prec = eda.EDA_F64 if prec_name == "f64" else eda.EDA_F64_TC
-    with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(prec=prec, block_b=2, tau=tau)) as h:
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(prec=prec, block_b=2, tau=tau, tc_min_mi=-1)) as h:
         assert abs(h.c2 - c2) <= 1e-13 * c2
         Y = h.apply_exp(eda.OP_N, _dev(Xb.T)).cpu().numpy().T
     assert _colwise(Y, Yr) <= 1e-12, _colwise(Y, Yr)
 
 
 def _solve(eda, p, t, b, tau, tol, prec):
-    cfg = eda.config(prec=prec, block_b=b, tau=tau)
+    cfg = eda.config(prec=prec, block_b=b, tau=tau, tc_min_mi=-1)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         V, lam, info, code = h.solve_arnoldi(t, tol, relres=True)
         assert code == 0, info

@@ -1,7 +1,8 @@
 """The FP64 solver with its M-apply sweeps on the bf16 tensor cores (prec EDA_F64_TC) against the oracle.
 
 The sweeps over Z = [H_W H_B] of the composed M-apply run as error-free split products (seven bf16 digit
-planes per operand, exact integer accumulation); everything else is the FP64 solver. The products are as
+planes per operand, exact integer accumulation); everything else is the FP64 solver. The tests force the
+tensor-core products at every size (tc_min_mi = -1), below the size from which the library would pick them. The products are as
 accurate as FP64 ones, so the FP64 bars apply unchanged: M-apply element by element within 1e-12 of the
 column's largest entry (the oracle's three Theorem 3.1 products through its QR / SVD route), eigenvalues
 within max(1e-10, 64 eps lambda_1 / lambda_i), the subspace within the Davis-Kahan bound of the residuals,
@@ -59,7 +60,7 @@ def test_m_apply_tc_matches_oracle(eda, d, k, nj, b, tau):
     Yr = O.m_apply(f["HW"], f["HB"], c2, Xb)
     out = {}
     for prec in (eda.EDA_F64_TC, eda.EDA_F64):
-        cfg = eda.config(prec=prec, block_b=2, tau=tau, m_form=1)
+        cfg = eda.config(prec=prec, block_b=2, tau=tau, m_form=1, tc_min_mi=-1)
         with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
             assert abs(h.c2 - c2) <= 1e-13 * c2
             out[prec] = h.apply_exp(eda.OP_M, _dev(Xb.T)).cpu().numpy().T
@@ -74,7 +75,7 @@ def test_m_apply_tc_zero_and_constant_columns(eda):
     p = synth.gaussian_clusters(d=500, k=6, n_per_class=4, seed=611)
     f = O.scatter_factors(p.X, p.labels, p.k)
     c2 = _oracle_c2(f, 8.0)
-    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=2, tau=8.0)
+    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=2, tau=8.0, tc_min_mi=-1)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         Z = np.zeros((3, 500))
         Y = h.apply_exp(eda.OP_M, _dev(Z)).cpu().numpy()
@@ -99,7 +100,7 @@ def test_m_apply_tc_extreme_magnitudes(eda):
     X[::5, 1] = 0.0
     X[:, 2] = sgn() * 1e-200
     X[17, 2] = 1e200
-    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=2, tau=10.0)
+    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=2, tau=10.0, tc_min_mi=-1)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         Y = h.apply_exp(eda.OP_M, _dev(X.T)).cpu().numpy().T
     # the oracle on each column scaled by a power of two to a largest entry near 1 (exact in FP64, and M
@@ -111,7 +112,7 @@ def test_m_apply_tc_extreme_magnitudes(eda):
 
 
 def _solve_compare(eda, p, t, b, tau, tol, ref):
-    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=b, tau=tau, true_residuals=1)
+    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=b, tau=tau, true_residuals=1, tc_min_mi=-1)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         assert abs(h.c2 - ref["c2"]) <= 1e-13 * ref["c2"]
         V, lam, _, info, code = h.solve(t, tol, relres=True)
@@ -172,7 +173,8 @@ def test_grams_tc_match_oracle(eda, d, k, nj):
     # above through M); n + k = 310 at the last size takes the eigenpair route for K
     p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=640 + d)
     f = O.scatter_factors(p.X, p.labels, p.k)
-    with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(prec=eda.EDA_F64_TC, block_b=4, tau=10.0)) as h:
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, eda.config(prec=eda.EDA_F64_TC, block_b=4, tau=10.0,
+                                                                        tc_min_mi=-1)) as h:
         g = h.factors()
         for key, H in (("GW", f["HW"]), ("GB", f["HB"])):
             G = g[key].cpu().numpy()
