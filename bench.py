@@ -60,6 +60,9 @@ def parse():
                          "tensor-core products (error-free splitting); f64: plain FP64 throughout")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 comparison leg on the same workload (0: skip it)")
+    ap.add_argument("--direct-steps", type=int, default=2,
+                    help="timed calls of the exact solve in span([H_W H_B]) (eda_solve_direct) beside the Krylov "
+                         "solve on one handle of the workload (0: skip it)")
     ap.add_argument("--workers", type=int, default=32, help="host workers of the batched solve")
     ap.add_argument("--m-form", type=int, default=1, choices=[0, 1],
                     help="FP64 M-apply: 0 = the three products one after another, 1 = their composed form")
@@ -566,6 +569,38 @@ REGIONS = ("gram", "tn_f64", "nn_f64", "oz_gemm", "oz_kernel", "oz_tiled", "clus
            "refine")
 
 
+def direct_leg(name, prec, tol, steps, dev):
+    """The exact solve in span([H_W H_B]) (eda_solve_direct) and the Krylov solve (eda_solve) timed on one
+    handle of the workload (build excluded), with the largest relative difference of their eigenvalues."""
+    import torch
+    from paper_1512_06500_gb300 import eda
+
+    c = synth.CONFIGS[name]
+    p = synth.config_problem(name)
+    cfg = eda.config(prec=PRECS[prec], block_b=c["b"], tau=c["tau"], check_every=1, m_form=1)
+    out = {"workload": name, "unit": "ms"}
+    with eda.build(torch.from_numpy(p.X).to(dev), torch.from_numpy(p.labels).to(dev), p.k, cfg) as h:
+        for key, call in (("direct_ms", lambda: h.solve_direct(c["t"])[:2]),
+                          ("krylov_ms", lambda: h.solve(c["t"], tol)[:2])):
+            res = call()   # warm-up
+            ts = []
+            for _ in range(steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                res = call()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            out[key] = sum(ts) / len(ts)
+            out["lam_" + key] = res[1].cpu().numpy()
+    lam_d, lam_k = out.pop("lam_direct_ms"), out.pop("lam_krylov_ms")
+    out["max_rel_diff_lambda"] = float(max(abs(lam_d / lam_k - 1.0)))
+    out["note"] = ("eda_solve_direct: Cholesky of the Gram of n - 1 independent columns of [H_W H_B], the t largest "
+                   "eigenpairs of the (n - 1)-dimensional projected matrix, recovery and orth in coordinates, one "
+                   "pass over [H_W H_B]; eda_solve: block Lanczos to rel-res " + str(tol))
+    return out
+
+
 def rate(flops, ms):
     return flops / (ms / 1e3) / 1e12 if ms > 0 else float("nan")
 
@@ -712,6 +747,9 @@ def run_gpu(args, rank, world, local_rank):
                     "breakdown_ms_per_step": {k: v[0] / args.fp64_steps for k, v in rf["regions"].items()},
                     "solve_info": {kk: rf["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols",
                                                                      "refills", "refine_iters")}}
+    direct = None
+    if args.direct_steps > 0 and rank == 0 and args.workload != "batched64":
+        direct = direct_leg(args.workload, args.prec, args.tol, args.direct_steps, dev)
     exp_leg = None
     if not args.no_exp_apply and rank == 0:
         exp_leg = exp_apply_leg(dev, flush, args.exp_apply_reps)
@@ -730,6 +768,7 @@ def run_gpu(args, rank, world, local_rank):
         "exp_apply_bf16": exp_leg,
         "small_config": small,
         "fp64_plain": fp64_leg,
+        "direct_solve": direct,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in regions.items()},
         "solve_info": {kk: r["infos"][-1][kk] for kk in ("iters", "mapplies", "checks", "basis_cols", "refills",
                                                          "refine_iters", "max_relres_est")},

@@ -182,6 +182,25 @@ int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0,
 int eda_solve_arnoldi(eda_handle h, int32_t t, double tol, double* V, double* lambda, eda_solve_info* info,
                       void* stream);
 
+/* The t dominant eigenpairs of the symmetric form solved exactly in the span of Z = [H_W H_B], without
+ * Krylov iteration: a cross-check of eda_solve at the cost of two small dense eigenproblems.
+ * Theorem 3.1 for each factor of M (Eq. (3.15)) gives M = I + Z C Z^T with C built from K_W, K_B and the
+ * Grams, so every eigenvector of M whose eigenvalue is not 1 lies in range(Z) (Theorem 3.7). Z has k + 1
+ * known dependent columns (each class's columns of H_W sum to zero; so do the sqrt(n_j)-weighted columns
+ * of H_B); without them the Gram of the other n - 1 columns is Cholesky-factored, the (n - 1) x (n - 1)
+ * symmetric matrix I + P^T C P (P = Z^T Q, Q the orthonormal basis this gives) is solved for its t
+ * largest eigenpairs, and the recovery x = exp(-c^2 S_W / 2) y (Eq. (3.14)) and orth (Algorithm 3 step 6)
+ * are done in the coordinates of Z, followed by one pass over Z for V and one CholQR pass on V.
+ *   t      : 1 <= t <= n - 1 (the eigenvalues above 1 are k - 1 of the n - 1 nontrivial ones).
+ *   V      : d x t output, orthonormal basis of the t generalized eigenvectors (ld d).
+ *   lambda : t output eigenvalues, descending.
+ *   info   : optional; converged = t, basis_cols = n - 1, ms_solve = device time of the call.
+ * Needs a handle from eda_build (the class structure), prec EDA_F64 or EDA_F64_TC (tensor-core FP64
+ * products for the n x n operators and the pass over Z when the handle has them); INVALID_ARG otherwise.
+ * BREAKDOWN when the n - 1 kept columns are numerically dependent (samples not affinely independent).
+ * Other errors as for eda_solve. Synchronises the stream. */
+int eda_solve_direct(eda_handle h, int32_t t, double* V, double* lambda, eda_solve_info* info, void* stream);
+
 /* P = V^T Xq (t x m, column-major, ld t): the projected samples of the
  * nearest-neighbour classifier (Section 3.3, d_ij = ||V^T (x_i - y_j)||).
  * V: d x t (ld d); Xq: d x m (EDA_F64 or EDA_F32, ld ldq). */

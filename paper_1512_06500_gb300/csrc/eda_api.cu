@@ -48,6 +48,7 @@ int m_apply(eda_ctx* h, int b, const double* X, int64_t ldx, double* Y, int64_t 
 int m_apply_f32(eda_ctx* h, int b, const float* X, int64_t ldx, float* Y, int64_t ldy, float* tmp, double* P,
                 double* Q, double* partial, size_t partial_cap, cudaStream_t s);
 int arnoldi_impl(eda_ctx* h, int t, double tol, double* Vout, double* lambda, eda_solve_info* info, cudaStream_t s);
+int direct_impl(eda_ctx* h, int t, double* Vout, double* lambda, eda_solve_info* info, cudaStream_t s);
 
 namespace {
 // B (k x n) = A^T for A (n x k), both column-major.
@@ -845,6 +846,12 @@ int eda_solve_arnoldi(eda_handle h, int32_t t, double tol, double* V, double* la
     if (!h || !V || !lambda || t < 1 || !(tol > 0.0)) return EDA_ERR_INVALID_ARG;
     if (h->cfg.prec != EDA_F64 && h->cfg.prec != EDA_F64_TC) return EDA_ERR_INVALID_ARG;
     return arnoldi_impl(h, t, tol, V, lambda, info, static_cast<cudaStream_t>(stream));
+}
+
+int eda_solve_direct(eda_handle h, int32_t t, double* V, double* lambda, eda_solve_info* info, void* stream) {
+    if (!h || !V || !lambda || t < 1) return EDA_ERR_INVALID_ARG;
+    if (h->cfg.prec != EDA_F64 && h->cfg.prec != EDA_F64_TC) return EDA_ERR_INVALID_ARG;
+    return direct_impl(h, t, V, lambda, info, static_cast<cudaStream_t>(stream));
 }
 
 int eda_project(eda_handle h, const double* V, int32_t t, const void* Xq, int32_t xq_dtype, int64_t m, int64_t ldq,

@@ -34,7 +34,7 @@ EXPORTS = [
     "eda_project", "eda_get_factors", "eda_get_dims", "eda_destroy", "eda_strerror",
     "eda_last_cuda_error", "eda_last_cuda_error_string", "eda_kernel_launches",
     "eda_profile_enable", "eda_profile_reset", "eda_profile_read", "eda_profile_work",
-    "eda_lowrank_exp_apply_noalloc", "eda_solve_batched", "eda_solve_arnoldi",
+    "eda_lowrank_exp_apply_noalloc", "eda_solve_batched", "eda_solve_arnoldi", "eda_solve_direct",
 ]
 
 
@@ -114,6 +114,7 @@ def load(path: str | None = None):
         "eda_lowrank_exp_apply_noalloc": ([vp, i64, i32, vp, vp, vp, i64, i32, vp], ctypes.c_int),
         "eda_solve_batched": ([P(Problem), i32, P(Config), i32, vp], ctypes.c_int),
         "eda_solve_arnoldi": ([vp, i32, f64, vp, vp, P(SolveInfo), vp], ctypes.c_int),
+        "eda_solve_direct": ([vp, i32, vp, vp, P(SolveInfo), vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -305,6 +306,17 @@ class Handle:
         if rr is not None:
             out["relres"] = list(rr)
         return V, lam, out, code
+
+    def solve_direct(self, t, stream=None, check=True):
+        """t dominant pairs solved exactly in span([H_W H_B]): returns (V (t, d), lam (t,), info, status)."""
+        dev = self.device
+        V = torch.empty((t, self.d), dtype=torch.float64, device=dev)
+        lam = torch.empty(t, dtype=torch.float64, device=dev)
+        info = SolveInfo()
+        code = load().eda_solve_direct(self._h, t, _ptr(V), _ptr(lam), ctypes.byref(info), _stream(stream))
+        if check and code != 0:
+            raise EdaError(code, "eda_solve_direct")
+        return V, lam, info.as_dict(), code
 
     def project(self, V, Xq, stream=None):
         """P = V^T Xq; V: (t, d) float64, Xq: (m, d) float64 -> P (m, t)."""

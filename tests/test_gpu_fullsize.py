@@ -151,3 +151,35 @@ def test_d311040_k10_matches_oracle(eda, prec, oracle_solutions):
     assert O.sin_angle(ref["V"], V.cpu().numpy().T) <= 1e-8
     lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
     assert np.array_equal(lab_g, ref["lab"])
+
+
+@pytest.mark.parametrize("prec", ["tc", "f64"])
+def test_direct_d65536_k200_matches_oracle(eda, prec, oracle_solutions):
+    # the exact solve in span([H_W H_B]) (eda_solve_direct) at the benchmark's workload: every eigenvalue
+    # within the FP64 floor, the subspace within the rounding floor of both routes over the gap lambda_t - 1
+    # (the direct solve has no residual term), identical 1-NN labels
+    name = "d65536_k200"
+    c = synth.CONFIGS[name]
+    p, ref = oracle_solutions(name)
+    t = c["t"]
+    cfg = eda.config(prec=eda.EDA_F64 if prec == "f64" else eda.EDA_F64_TC, block_b=c["b"], tau=c["tau"])
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        assert abs(h.c2 - ref["c2"]) <= 1e-13 * ref["c2"]
+        V, lam, info, code = h.solve_direct(t)
+        assert code == 0
+        Ptr = h.project(V, _dev(p.X)).cpu().numpy()
+        Pte = h.project(V, _dev(p.Xtest)).cpu().numpy()
+    lam = lam.cpu().numpy()
+    Vg = V.cpu().numpy().T
+    assert np.abs(Vg.T @ Vg - np.eye(t)).max() <= 1e-12
+    lam_ref = ref["lam_t"]
+    rel = np.abs(lam - lam_ref) / lam_ref
+    floor = 64 * EPS * lam_ref[0] / lam_ref
+    assert np.all(rel <= np.maximum(1e-10, floor)), rel.max()
+    gap = lam_ref[t - 1] - 1.0
+    kappa = np.exp(0.5 * ref["c2"] * ref["lmax_w"])
+    s = O.sin_angle(ref["V"], Vg)
+    assert s <= kappa * 64 * EPS * np.sqrt(t) * lam_ref[0] / gap, s
+    lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
+    assert np.array_equal(lab_g, ref["lab"]), np.flatnonzero(lab_g != ref["lab"])
+    print(f"\nd65536_k200 direct ({prec}): max eig rel err {rel.max():.2e}, sin {s:.2e}, {info['ms_solve']:.1f} ms")
