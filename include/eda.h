@@ -90,7 +90,12 @@ typedef struct {
                                  /* used; below it the FP64 ones (the two agree to FP64       */
                                  /* rounding; the splitting launches cost more than they save */
                                  /* on small factors); 0: the default, 4; < 0: always         */
-    int32_t reserved[4];
+    int32_t tc_fused;            /* EDA_BF16: >= 0 (default 0) applies exp(alpha H H^T) in one  */
+                                 /* resident launch when the factor fits the SMs' shared      */
+                                 /* memory (d <= 128 x resident CTAs, n <= 768): bf16 of      */
+                                 /* B = H R^T with sign(alpha) K = R^T R, read once; < 0: the */
+                                 /* four-launch sweeps of bf16 H and bf16 H K                 */
+    int32_t reserved[3];
 } eda_config;
 
 typedef struct {

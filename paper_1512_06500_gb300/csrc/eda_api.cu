@@ -608,6 +608,23 @@ int finish_build(eda_ctx* h, cudaStream_t s) {
         EDA_TRY(tc_factor_make(h->HW, d, n, h->KW, HcW, HKW, &h->tcW, h->status, s));
         EDA_TRY(tc_factor_make(h->HB, d, k, h->KB, HcB, HKB, &h->tcB, h->status, s));
         EDA_TRY(tc_buffers_make(ldh, ldq, Xhi, Xlo, Qhi, Qlo, partial, tc_partial_floats(std::max(n, k)), &h->tcbuf));
+        // the one-pass form for both factors (decided together: the M-apply chains them) when the larger fits
+        if (h->cfg.tc_fused >= 0 && tc_fused_grid(d, std::max(n, k)) > 0) {
+            const size_t fz[4] = {align256((size_t)tc_fused_elems(d, n) * 2), align256((size_t)tc_fused_elems(d, k) * 2),
+                                  align256(tc_fused_partial_floats(d, std::max(n, k)) * 4), 256};
+            void* fp = nullptr;
+            EDA_CUDA_TRY(cudaMalloc(&fp, fz[0] + fz[1] + fz[2] + fz[3]));
+            h->fblock = fp;
+            char* fc = static_cast<char*>(fp);
+            EDA_CUDA_TRY(cudaMemsetAsync(fc + fz[0] + fz[1] + fz[2], 0, fz[3], s));   // grid-barrier words
+            EDA_TRY(tc_fused_make(h->HW, d, n, h->KW, -0.5 * h->c2, reinterpret_cast<__nv_bfloat16*>(fc), &h->tcW,
+                                  h->status, s));
+            EDA_TRY(tc_fused_make(h->HB, d, k, h->KB, h->c2, reinterpret_cast<__nv_bfloat16*>(fc + fz[0]), &h->tcB,
+                                  h->status, s));
+            h->tcbuf.fpartial = reinterpret_cast<float*>(fc + fz[0] + fz[1]);
+            h->tcbuf.fbar = reinterpret_cast<unsigned*>(fc + fz[0] + fz[1] + fz[2]);
+            h->tcbuf.fspin = h->bar.spin_limit;
+        }
     }
     int st = 0;
     EDA_TRY(read_status(h, s, &st));
@@ -923,6 +940,7 @@ void eda_destroy(eda_handle h) {
     if (h->ozsmall) cudaFree(h->ozsmall);
     if (h->nblock) cudaFree(h->nblock);
     if (h->block32) cudaFree(h->block32);
+    if (h->fblock) cudaFree(h->fblock);
     if (h->block) cudaFree(h->block);
     delete h;
 }

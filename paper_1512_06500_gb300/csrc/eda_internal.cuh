@@ -235,6 +235,11 @@ struct TcFactor {
     const __nv_bfloat16* A2 = nullptr;    // bf16(H K(alpha)): tile rows = rows of H, K along m (sweep 2)
     int64_t d = 0, ldh = 0;               // ldh = d rounded up to 64
     int m = 0, ldm = 0;                   // ldm = m rounded up to 64
+    // one-pass form (when bf16 B = H R^T, sign(alpha) K = R^T R, fits in the SMs' shared memory):
+    // exp(alpha H H^T) X = X + fsign B (B^T X), B tiled for the resident kernel, fgrid CTAs
+    const __nv_bfloat16* F = nullptr;
+    float fsign = 0.f;
+    int fgrid = 0;
 };
 // Per-handle staging buffers of the sweeps (bf16 hi/lo pairs of X and of P = H^T X, 32 columns
 // each) with their tensor maps for N = 16 ([0]) and N = 32 ([1]) column boxes.
@@ -245,6 +250,11 @@ struct TcBuffers {
     __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Qhi = nullptr, *Qlo = nullptr;
     int64_t ldh = 0;
     int ldq = 0;
+    // one-pass form: per-CTA partials of B^T X (fgrid x m x 32 floats), its grid barrier (arrival count
+    // at fbar[0], the launch base at fbar[32], zeroed once) and the barrier's poll limit
+    float* fpartial = nullptr;
+    unsigned* fbar = nullptr;
+    long long fspin = 0;
 };
 inline int64_t tc_pad_rows(int64_t d) { return (d + 63) / 64 * 64; }
 inline int tc_pad_cols(int m) { return (m + 63) / 64 * 64; }
@@ -262,7 +272,19 @@ int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo
 // exp_apply_tc flags: the staging pair already holds the split of X (skip the split step); write the
 // split of Y into the staging pair (for the next exp-apply). Both apply only when b <= 32.
 enum : int { TC_X_SPLIT_READY = 1, TC_EMIT_SPLIT = 2 };
-// Y = X + H K (H^T X) with bf16 H on the tensor cores; X, Y single precision, Y may alias X.
+// One-pass form: CTAs of the resident kernel for a d x m factor (0 when it does not fit: m > 768, or more
+// 128-row chunks than CTAs that can be resident at once); elements of its tiled image; floats of its
+// partials for factors up to m_max columns; the image of B = H R^T for sign(alpha) K = R^T R (synchronises
+// the stream); the product X + fsign B (B^T X) itself (b columns, in launches of at most 32).
+int tc_fused_grid(int64_t d, int m);
+int64_t tc_fused_elems(int64_t d, int m);
+size_t tc_fused_partial_floats(int64_t d, int m_max);
+int tc_fused_make(const double* H, int64_t d, int m, const double* K, double alpha, __nv_bfloat16* img, TcFactor* f,
+                  int* status, cudaStream_t s);
+int exp_apply_tc_fused(const TcFactor& f, const TcBuffers& bufs, int b, const float* X, int64_t ldx, float* Y,
+                       int64_t ldy, int* status, cudaStream_t s);
+// Y = X + H K (H^T X) with bf16 H on the tensor cores; X, Y single precision, Y may alias X. Uses the
+// one-pass form when the factor has it.
 int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
                  float* Y, int64_t ldy, int flags, int* status, cudaStream_t s);
 
@@ -359,6 +381,7 @@ struct eda_ctx {
     float *HW32 = nullptr, *HB32 = nullptr;
     eda::TcFactor tcW, tcB;
     eda::TcBuffers tcbuf;
+    void* fblock = nullptr;                // the one-pass images of both factors, their partials, barrier
     int* status = nullptr;                 // device status word
     eda::GridBarrier bar{};
     size_t build_arena_off = 0;            // start of the build scratch inside `block`

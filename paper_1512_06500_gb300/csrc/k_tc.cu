@@ -572,6 +572,11 @@ int tc_buffers_make(int64_t ldh, int ldq, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo
 
 int exp_apply_tc(const TcFactor& f, const TcBuffers& bufs, const char* tag, int b, const float* X, int64_t ldx,
                  float* Y, int64_t ldy, int flags, int* status, cudaStream_t s) {
+    if (f.F && bufs.fpartial) {
+        // one pass: B read once from HBM (its bf16 image), X read twice, Y written once
+        ProfScope prof(tag, s, 4.0 * f.d * f.m * b, 2.0 * f.d * f.m + 3.0 * 4.0 * f.d * b);
+        return exp_apply_tc_fused(f, bufs, b, X, ldx, Y, ldy, status, s);
+    }
     ProfScope prof(tag, s, 4.0 * f.d * f.m * b, 2.0 * 2.0 * f.d * f.m + 3.0 * 4.0 * f.d * b);
     // the split pair lives in one 32-column staging buffer: chaining needs a single slice
     const bool chain = b <= 32;

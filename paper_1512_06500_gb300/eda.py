@@ -52,7 +52,8 @@ class Config(ctypes.Structure):
         ("prec", ctypes.c_int32), ("block_b", ctypes.c_int32), ("m_max", ctypes.c_int32),
         ("check_every", ctypes.c_int32), ("tau", ctypes.c_double), ("c2", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("true_residuals", ctypes.c_int32), ("m_form", ctypes.c_int32),
-        ("wait_limit", ctypes.c_int32), ("tc_min_mi", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("wait_limit", ctypes.c_int32), ("tc_min_mi", ctypes.c_int32), ("tc_fused", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

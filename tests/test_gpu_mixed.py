@@ -104,7 +104,7 @@ def test_tc_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
     f = O.scatter_factors(p.X, p.labels, p.k)
     GW, GB = O.gram(f["HW"]), O.gram(f["HB"])
     c2 = O.scale_c2(np.linalg.eigvalsh(GW)[-1], np.linalg.eigvalsh(GB)[-1], 10.0)
-    cfg = eda.config(prec=eda.EDA_BF16, block_b=min(b, 16), tau=10.0)
+    cfg = eda.config(prec=eda.EDA_BF16, block_b=min(b, 16), tau=10.0, tc_fused=-1)   # the four-launch sweeps
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         assert abs(h.c2 - c2) <= 1e-13 * c2
         rng = np.random.default_rng(d + b)
@@ -126,6 +126,44 @@ def test_tc_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
             # against the exact FP64 operator: the bf16 rounding of H and H K (2^-9) sets the scale
             exact = O.lowrank_exp_apply(H, a_ref, X64)
             scale = np.abs(X64) + np.abs(HK) @ np.abs(P)
+            assert np.all(np.abs(Y - exact) <= 2e-2 * scale.max(axis=0)[None, :]), op
+
+
+@pytest.mark.parametrize("d,k,nj,b", [(4096, 40, 5, 8), (1000, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 16), (2048, 20, 7, 20),
+                                      (777, 5, 3, 40), (16384, 100, 7, 16), (300, 150, 2, 32)])
+def test_tc_fused_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
+    # The one-pass product is X + sigma bf16(B) (bf16(B)^T X) with B = H R^T, sigma K = R^T R (Cholesky of the
+    # definite K = alpha phi(alpha G), sigma = sign(alpha)): one d x m bf16 matrix serves both sweeps and stays
+    # in shared memory. The reference forms B from the oracle's H, Gram and scale in FP64, rounds it to bf16
+    # as the library does, and applies it in FP64; allowed: 1e-4 of the column's largest entry (hi + lo
+    # rounding of X and P, FP32 accumulation) plus one bf16 ulp of each entry of B within 1e-4 of a rounding
+    # midpoint times |P|. Covers one to six 128-column bands, ragged d, b of 8 to 40 (two launches); the
+    # in-place form (Y = X) runs inside the bf16 solver's M-apply chain (test_bf16_tensor_core_solver).
+    p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=900 + d)
+    f = O.scatter_factors(p.X, p.labels, p.k)
+    GW, GB = O.gram(f["HW"]), O.gram(f["HB"])
+    c2 = O.scale_c2(np.linalg.eigvalsh(GW)[-1], np.linalg.eigvalsh(GB)[-1], 10.0)
+    cfg = eda.config(prec=eda.EDA_BF16, block_b=min(b, 16), tau=10.0)
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        assert abs(h.c2 - c2) <= 1e-13 * c2
+        rng = np.random.default_rng(d + b)
+        Xb = rng.standard_normal((b, d)).astype(np.float32)
+        for op, H, G, a_lib, a_ref in ((eda.OP_SW, f["HW"], GW, -0.5 * h.c2, -0.5 * c2),
+                                       (eda.OP_SB, f["HB"], GB, h.c2, c2)):
+            Y = h.apply_exp(op, _dev(Xb), alpha=a_lib).cpu().numpy().astype(np.float64).T
+            K = O.phi_operator(G, a_ref)
+            sigma = 1.0 if a_ref > 0 else -1.0
+            L = np.linalg.cholesky(sigma * K)          # sigma K = L L^T, B = H L
+            B = H @ L
+            Bb = _bf16_round(B)
+            X64 = Xb.astype(np.float64).T
+            P = Bb.T @ X64
+            ref = X64 + sigma * (Bb @ P)
+            tol = 1e-4 * np.abs(ref).max(axis=0)[None, :] + _near_midpoint_ulp(B, 1e-4) @ np.abs(P)
+            err = np.abs(Y - ref)
+            assert np.all(err <= tol), (op, float((err / tol).max()))
+            exact = O.lowrank_exp_apply(H, a_ref, X64)
+            scale = np.abs(X64) + np.abs(B) @ np.abs(P)
             assert np.all(np.abs(Y - exact) <= 2e-2 * scale.max(axis=0)[None, :]), op
 
 
