@@ -253,8 +253,13 @@ int gram_eigen_pair(eda_ctx* h, Arena& scratch, double* partW, size_t pcapW, int
             rc = EDA_ERR_CUDA;
             break;
         }
-        if ((rc = symeig_values(n, h->GW, n, 0, n - 1, h->evals_w, &wsW, h->status, s)) != EDA_OK) break;
-        if ((rc = symeig_values(k, h->GB, k, 0, k - 1, h->evals_b, &wsB, h->status, s2)) != EDA_OK) break;
+        // two reductions in flight at once: both on the cluster path (a cooperative grid needs every SM it
+        // spans, and the two would share the handle's grid-barrier words)
+        const bool prev_shared = symeig_set_shared_gpu(true);
+        rc = symeig_values(n, h->GW, n, 0, n - 1, h->evals_w, &wsW, h->status, s);
+        if (rc == EDA_OK) rc = symeig_values(k, h->GB, k, 0, k - 1, h->evals_b, &wsB, h->status, s2);
+        symeig_set_shared_gpu(prev_shared);
+        if (rc != EDA_OK) break;
         if (cudaMemcpyAsync(ww.data(), h->evals_w, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaMemcpyAsync(wb.data(), h->evals_b, k * sizeof(double), cudaMemcpyDeviceToHost, s2) != cudaSuccess ||
             cudaStreamSynchronize(s2) != cudaSuccess) {

@@ -175,8 +175,9 @@ int symeig_f64(int n, const double* A, int lda, int il, int iu, double* w, doubl
                SymEigWork* ws, int* status, uint64_t seed, double cluster_rel, cudaStream_t s);
 // The two halves of symeig_f64: reduction + eigenvalues, then eigenvectors of nv eigenvalues w
 // (any subset, ascending) reusing the reduction left in ws.
-// Calling thread shares the GPU with other problems' kernels: avoid grid-wide software barriers.
-void symeig_set_shared_gpu(bool on);
+// Calling thread shares the GPU with other problems' kernels (or runs two eigensolves side by side):
+// avoid grid-wide software barriers. Returns the previous setting.
+bool symeig_set_shared_gpu(bool on);
 int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, SymEigWork* ws,
                   int* status, cudaStream_t s);
 int symeig_vectors(int n, int nv, const double* w, double* Z, int ldz, SymEigWork* ws, uint64_t seed,

@@ -9,6 +9,7 @@
 // Gram-Schmidt inside tight clusters (one warp per cluster) -> back-transformation with the
 // stored reflectors. Callers add a Newton-Schulz step for orthogonality across near clusters.
 #include "eda_internal.cuh"
+#include "grid_bar.cuh"
 
 #include <cooperative_groups.h>
 
@@ -341,6 +342,138 @@ __global__ void __launch_bounds__(CT_THREADS) k_tridiag_cluster(int n, const dou
         if (tid == 0) eoff[n - 1] = 0.0;
     }
     cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// Householder tridiagonalisation on a cooperative grid of G CTAs with the matrix resident in shared
+// memory: column c is owned by CTA c % G (slot c / G, n doubles). Per column j, after the grid barrier
+// that publishes reflector j (global memory, read through L2): every CTA copies it into shared memory,
+// forms p[r] = tau v^T A[:, r] for its own columns r and its share of p^T v (its columns in increasing
+// order), publishes both; after a second barrier every CTA reads p and the G shares (summed in CTA
+// order: the same value everywhere), forms w = p - (tau / 2)(p^T v) v and updates its columns
+// (A -= v w^T + w v^T). The owner of column j + 1 updates that column first and publishes reflector
+// j + 1 while the others update theirs (look-ahead). Two bounded grid barriers per column on the
+// monotonic arrival counter; the columns never leave shared memory.
+__global__ void __launch_bounds__(TRI_THREADS) k_tridiag_res(int n, const double* __restrict__ Ain, int lda,
+                                                             double* vglob, double* pglob, double* pshare, double* HV,
+                                                             double* dgl, double* eoff, double* tau, GridBarWords bw,
+                                                             int* status) {
+    extern __shared__ double sm[];
+    __shared__ double red[32];
+    __shared__ double s_pv;
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int ncl = (n + G - 1) / G;
+    double* vs = sm;             // n: reflector j
+    double* ws = sm + n;         // n: p, then w
+    double* Aloc = sm + 2 * n;   // ncl x n: the owned columns
+    double* shs = Aloc + (size_t)ncl * n;   // G: the CTAs' shares of p^T v
+    const int tid = threadIdx.x, bd = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = bd >> 5;
+    const unsigned base = gb_base(bw);
+    unsigned nb = 0;
+
+    for (int q = 0; q < ncl; ++q) {
+        const int c = q * G + cta;
+        if (c >= n) break;
+        for (int i = tid; i < n; i += bd)
+            Aloc[(size_t)q * n + i] = 0.5 * (Ain[(int64_t)c * lda + i] + Ain[(int64_t)i * lda + c]);
+    }
+    __syncthreads();
+    if (n >= 3 && cta == 0) make_reflector(0, n, Aloc, vglob, HV, eoff, tau, red);
+    gb_sync(bw, base, ++nb, status);
+
+    for (int j = 0; j + 2 < n; ++j) {
+        const int i0 = j + 1;
+        const int next = j + 1;
+        const bool own_next = (next + 2 < n) && (next % G == cta);
+        const int q0 = (i0 - cta + G - 1) / G;   // first owned slot with a column >= i0
+        const double tj = __ldcg(vglob + n);
+        if (tj == 0.0) {
+            // no reflection at this column: every CTA has read tau before the owner of j + 1 overwrites it
+            gb_sync(bw, base, ++nb, status);
+            if (own_next) make_reflector(next, n, Aloc + (size_t)(next / G) * n, vglob, HV, eoff, tau, red);
+            gb_sync(bw, base, ++nb, status);
+            continue;
+        }
+        for (int i = i0 + tid; i < n; i += bd) vs[i] = __ldcg(vglob + i);
+        __syncthreads();
+        // p over the owned columns, one warp per column (lane-strided dot, fixed shuffle tree)
+        for (int q = q0 + warp; q < ncl; q += nw) {
+            const int r = q * G + cta;
+            if (r >= n) break;
+            const double* col = Aloc + (size_t)q * n;
+            double a0 = 0.0, a1 = 0.0;
+            int c = i0 + lane;
+            for (; c + 32 < n; c += 64) {
+                a0 = fma(col[c], vs[c], a0);
+                a1 = fma(col[c + 32], vs[c + 32], a1);
+            }
+            if (c < n) a0 = fma(col[c], vs[c], a0);
+            double acc = a0 + a1;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                const double p = tj * acc;
+                pglob[r] = p;
+                ws[r] = p;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double sh = 0.0;
+            for (int q = q0; q < ncl; ++q) {
+                const int r = q * G + cta;
+                if (r >= n) break;
+                sh = fma(ws[r], vs[r], sh);
+            }
+            pshare[cta] = sh;
+        }
+        gb_sync(bw, base, ++nb, status);
+        // w = p - (tau / 2)(p^T v) v
+        for (int i = i0 + tid; i < n; i += bd) ws[i] = __ldcg(pglob + i);
+        for (int g = tid; g < G; g += bd) shs[g] = __ldcg(pshare + g);
+        __syncthreads();
+        if (warp == 0) {
+            // the G shares in a fixed order (lane-strided runs, then a shuffle tree): the same value in every CTA
+            double pv = 0.0;
+            for (int g = lane; g < G; g += 32) pv += shs[g];
+            for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+            if (lane == 0) s_pv = pv;
+        }
+        __syncthreads();
+        const double kk = 0.5 * tj * s_pv;
+        for (int i = i0 + tid; i < n; i += bd) ws[i] = fma(-kk, vs[i], ws[i]);
+        __syncthreads();
+        if (own_next) {
+            double* col = Aloc + (size_t)(next / G) * n;
+            const double vc = vs[next], wc = ws[next];
+            for (int i = i0 + tid; i < n; i += bd) col[i] -= fma(vs[i], wc, ws[i] * vc);
+            __syncthreads();
+            make_reflector(next, n, col, vglob, HV, eoff, tau, red);
+        }
+        for (int q = q0; q < ncl; ++q) {
+            const int c = q * G + cta;
+            if (c >= n) break;
+            if (own_next && c == next) continue;
+            double* col = Aloc + (size_t)q * n;
+            const double vc = vs[c], wc = ws[c];
+            for (int i = i0 + tid; i < n; i += bd) col[i] -= fma(vs[i], wc, ws[i] * vc);
+        }
+        gb_sync(bw, base, ++nb, status);
+    }
+    for (int q = 0; q < ncl; ++q) {
+        const int c = q * G + cta;
+        if (c >= n) break;
+        if (tid == 0) {
+            dgl[c] = Aloc[(size_t)q * n + c];
+            if (c == n - 2) eoff[c] = Aloc[(size_t)q * n + c + 1];
+        }
+    }
+    if (cta == 0) {
+        for (int jj = (n >= 2 ? n - 2 : 0); jj < n; ++jj) {
+            if (tid == 0) tau[jj] = 0.0;
+            for (int i = tid; i < n; i += bd) HV[(int64_t)jj * n + i] = 0.0;
+        }
+        if (tid == 0) eoff[n - 1] = 0.0;
+    }
+    gb_finish(bw, base, nb);
 }
 
 // Number of eigenvalues below x of the tridiagonal with diagonal d and squared off-diagonal e2, in
@@ -995,6 +1128,7 @@ int symeig_work_carve(Arena& a, int n, int nv, GridBarrier bar, SymEigWork* w) {
 
 constexpr int kClusterMaxN = 512;        // the cluster path up to here; a cooperative grid beyond
 constexpr int kClusterMaxNShared = 1024; // limit of the cluster path when the GPU is shared (see below)
+constexpr int kResMinN = 288;            // the resident-column cooperative grid from here (when it fits)
 
 // Host threads that run many problems side by side (the batched solver) set this: a cooperative
 // grid with a software grid barrier needs all its CTAs resident at once, which concurrent kernels
@@ -1092,6 +1226,46 @@ int tridiag_cluster(int n, const double* A, int lda, SymEigWork* ws, cudaStream_
     return launch_tridiag_c(C, n, A, lda, ws, s, false, nullptr);
 }
 
+// The resident-column grid (k_tridiag_res): about four columns per CTA, at most one CTA per SM, when the
+// owned columns and two work vectors fit in 200 KB of shared memory. INVALID_ARG: does not apply.
+int tridiag_res(int n, const double* A, int lda, double* HV, SymEigWork* ws, int* status, int sms, cudaStream_t s) {
+    const int G = std::max(1, std::min(sms, (n + 3) / 4));
+    const int ncl = (n + G - 1) / G;
+    const size_t smem = ((size_t)(ncl + 2) * n + G) * sizeof(double);
+    if (smem > 200 * 1024 || 2 * (size_t)n + 2 + G > 4 * (size_t)n) return EDA_ERR_INVALID_ARG;
+    {
+        static std::mutex mu;
+        static size_t set = 0;
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > set && smem > 40 * 1024) {
+            EDA_CUDA_TRY(cudaFuncSetAttribute(k_tridiag_res, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)std::max<size_t>(smem, 48 * 1024)));
+            set = std::max<size_t>(smem, 48 * 1024);
+        }
+    }
+    int per_sm = 0;
+    EDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_res, TRI_THREADS, smem));
+    if (per_sm < 1 || G > per_sm * sms) return EDA_ERR_INVALID_ARG;
+    // both barrier words to zero: the launch starts its arrival count from 0
+    EDA_CUDA_TRY(cudaMemsetAsync(ws->bar.count, 0, 256, s));
+    ProfScope prof("tridiag", s, 4.0 / 3.0 * (double)n * n * n);
+    int nn = n, ld = lda;
+    const double* a0 = A;
+    double* vg = ws->vbuf;
+    double* pg = ws->vbuf + n + 2;
+    double* ps = ws->vbuf + 2 * n + 2;
+    double* a1 = HV;
+    double* a2 = ws->dgl;
+    double* a3 = ws->eoff;
+    double* a4 = ws->tau;
+    GridBarWords bw{ws->bar.count, ws->bar.gen, ws->bar.spin_limit};
+    int* st = status;
+    void* args[] = {&nn, &a0, &ld, &vg, &pg, &ps, &a1, &a2, &a3, &a4, &bw, &st};
+    EDA_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_tridiag_res, dim3(G), dim3(TRI_THREADS), args, smem, s));
+    launch_counter()++;
+    return EDA_OK;
+}
+
 int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, SymEigWork* ws, int* status,
                   cudaStream_t s) {
     if (n <= 0 || il < 0 || iu >= n || il > iu) return EDA_ERR_INVALID_ARG;
@@ -1116,7 +1290,12 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
             set = smem;
         }
     }
-    if (n <= (tl_shared_gpu ? kClusterMaxNShared : kClusterMaxN)) {
+    int res = EDA_ERR_INVALID_ARG;   // the resident-column grid when it applies and fits
+    if (!tl_shared_gpu && n >= kResMinN) res = tridiag_res(n, A, lda, HV, ws, status, sms, s);
+    if (res == EDA_OK) {
+    } else if (res != EDA_ERR_INVALID_ARG) {
+        return res;
+    } else if (n <= (tl_shared_gpu ? kClusterMaxNShared : kClusterMaxN)) {
         EDA_TRY(tridiag_cluster(n, A, lda, ws, s));
     } else {
     int per_sm = 0;
@@ -1437,6 +1616,10 @@ int lanczos_top(int n, const double* A, int lda, int m, uint64_t seed, SymEigWor
     return EDA_OK;
 }
 
-void symeig_set_shared_gpu(bool on) { tl_shared_gpu = on; }
+bool symeig_set_shared_gpu(bool on) {
+    const bool prev = tl_shared_gpu;
+    tl_shared_gpu = on;
+    return prev;
+}
 
 }  // namespace eda

@@ -114,7 +114,9 @@ def test_fp64_d65536_k200_sampled_pairs_three_products(eda, oracle_solutions):
     name = "d65536_k200"
     c = synth.CONFIGS[name]
     p, ref = oracle_solutions(name)
-    tol = 1e-7
+    # three times the FP64 residual floor of the smallest wanted pairs, eps lambda_1 / lambda_t ~ 1.1e-7 at
+    # tau = 20 (reading A8): a tolerance below it is met or missed by the luck of the rounding
+    tol = 3.0 * EPS * ref["lam_t"][0] / ref["lam_t"][c["t"] - 1]
     cfg = eda.config(prec=eda.EDA_F64, block_b=c["b"], tau=c["tau"], m_form=1)
     with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
         V, lam, Y, info, code = h.solve(c["t"], tol, want_y=True)
