@@ -42,7 +42,7 @@ GRAM_TRAFFIC_BYTES = {}
 # DRAM bytes (read + write) per launch of k_oz_gemm with a narrow operand, averaged over those launches of
 # one timed step of the workload, from an ncu capture of the same command (profiles/); absent until captured
 # for the current kernel
-OZ_TRAFFIC_BYTES = {"d65536_k200": 599.06e6}
+OZ_TRAFFIC_BYTES = {"d65536_k200": 599.07e6}
 FALLBACK_HBM_GBS = 6800.0           # profiling recipe fallback when no measured peaks exist
 FALLBACK_BF16_TFLOPS = 1900.0
 
@@ -411,7 +411,7 @@ def run_gpu_batched(args, rank, world, local_rank):
                             "time (launches of 64 problems overlap on many streams): a lower bound")
         roofline.pop("avg_launch_us", None)
     tridiag = {
-        "kernel": "k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the FP64 "
+        "kernel": "k_tridiag_res / k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the FP64 "
                   "Grams and Rayleigh-Ritz matrices, summed over concurrent problems",
         "bound": "alu", "achieved": tri_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
         "frac": tri_tf / NOMINAL_FP64_TFLOPS, "traffic": None,
@@ -711,7 +711,7 @@ def run_gpu(args, rank, world, local_rank):
     tri_ms, tri_calls = regions["tridiag"]
     tri_flops, _ = r["work"]["tridiag"]
     latency_bound = {
-        "kernel": "k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the Rayleigh-Ritz "
+        "kernel": "k_tridiag_res / k_tridiag_cluster / k_tridiag: Householder tridiagonalisation (4/3 n^3 flops) of the Rayleigh-Ritz "
                   "matrices (and of a Gram taking the eigensolver route)",
         "achieved_tflops": rate(tri_flops, tri_ms) if tri_ms > 0 else None,
         "avg_call_us": tri_ms * 1e3 / max(tri_calls, 1), "calls": tri_calls,
