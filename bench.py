@@ -55,9 +55,11 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=HEADLINE, choices=list(synth.CONFIGS) + ["batched64"])
     ap.add_argument("--small-steps", type=int, default=20, help="steps of the d4096_k40 leg (0: skip it)")
-    ap.add_argument("--prec", default="tc", choices=["tc", "f64"],
+    ap.add_argument("--prec", default="tc", choices=["tc", "f64", "bf16"],
                     help="tc: FP64 solver whose sweeps over [H_W H_B], Grams and recovery run as FP64-accurate "
-                         "tensor-core products (error-free splitting); f64: plain FP64 throughout")
+                         "tensor-core products (error-free splitting); f64: plain FP64 throughout; bf16: bf16 "
+                         "sweeps on the tensor cores with FP64 small steps and refinement (the batched "
+                         "workload's own precision; at tau = 20 and d = 65536 it does not converge)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 comparison leg on the same workload (0: skip it)")
     ap.add_argument("--direct-steps", type=int, default=2,
@@ -149,9 +151,12 @@ def workload_config(args, name=None):
         return {"workload": "batched64: 64 independent problems, d in {1024, 4096, 16384}, k ~ U[10, 100], "
                             f"n_j ~ U[3, 10] per class, t = k - 1, tau = {synth.BATCHED['tau']}, tol={args.tol}",
                 "l2": "flushed (256 MB write) before every step",
-                "precision": ("FP64 solver with FP64-accurate tensor-core products (7 bf16 digit planes, exact "
-                              "integer accumulation)" if getattr(args, "prec", "f64") == "tc" else
-                              "plain FP64 sweeps and small steps") + "; block size tuned per problem shape",
+                "precision": {"tc": "FP64 solver with FP64-accurate tensor-core products (7 bf16 digit planes, exact "
+                                    "integer accumulation)",
+                              "bf16": "bf16 sweeps on the tensor cores (FP32 accumulation), FP64 Grams, small steps "
+                                      "and refinement to tol",
+                              }.get(getattr(args, "prec", "f64"), "plain FP64 sweeps and small steps")
+                             + "; block size tuned per problem shape",
                 "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form],
                 "workers": args.workers}
     c = synth.CONFIGS[name]
@@ -162,7 +167,9 @@ def workload_config(args, name=None):
                           "M-apply sweeps, reorthogonalisation, Ritz vectors, K_W, recovery, projection) as "
                           "FP64-accurate tensor-core products: operands split exactly into 7 bf16 digit planes, exact "
                           "integer accumulation" if getattr(args, "prec", "f64") == "tc" else
-                          "plain FP64 sweeps and small steps"),
+                          ("bf16 sweeps on the tensor cores (FP32 accumulation), FP64 Grams, small steps and "
+                           "refinement to tol" if getattr(args, "prec", "f64") == "bf16" else
+                           "plain FP64 sweeps and small steps")),
             "m_form": ["three products one after another", "composed form I + Z C Z^T"][args.m_form]}
 
 
@@ -464,7 +471,7 @@ def run_gpu_batched(args, rank, world, local_rank):
     return line, ps
 
 
-PRECS = {"tc": 4, "f64": 0}   # eda_prec codes: EDA_F64_TC, EDA_F64
+PRECS = {"tc": 4, "f64": 0, "bf16": 2}   # eda_prec codes: EDA_F64_TC, EDA_F64, EDA_BF16
 
 
 def time_workload(name, steps, warmup, m_form, tol, dev, flush, rank, world, e2e=True, prec="tc",

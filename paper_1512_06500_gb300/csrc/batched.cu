@@ -157,6 +157,9 @@ extern "C" int eda_solve_batched(eda_problem* probs, int32_t nprob, const eda_co
             eda_problem& p = probs[order[q]];
             eda_config pc = c;
             if (p.block_b > 0) pc.block_b = p.block_b;
+            // the one-pass bf16 exp-apply is a cooperative launch with grid-wide barriers: like the eigensolver's
+            // cooperative grid, it is kept off threads whose problems share the GPU with others
+            pc.tc_fused = -1;
             eda_handle h = nullptr;
             int rc = eda_build(p.X, p.x_dtype, p.d, p.n, p.ldx, p.labels, p.k, &pc, s, &h);
             handles[order[q]] = h;

@@ -3,8 +3,8 @@
 The batch runs the single-problem path for every problem on several host workers and streams; the
 results must be what the oracle gives for each problem alone: eigenvalues to 1e-10 relative and
 principal angles to 1e-8 for the FP64 path, 1e-6 for the bf16 tensor-core path, identical 1-NN labels.
-The 64-problem workload of uneven d, k, n_j is checked problem by problem, in FP64 and in the tensor-core
-FP64 mode.
+The 64-problem workload of uneven d, k, n_j is checked problem by problem, in FP64, in the tensor-core
+FP64 mode and with bf16 sweeps.
 """
 import numpy as np
 import pytest
@@ -98,16 +98,22 @@ def batch64():
     return ps, tau, refs
 
 
-@pytest.mark.parametrize("prec_name", ["f64", "tc"])
+@pytest.mark.parametrize("prec_name", ["f64", "tc", "bf16"])
 def test_batched_64_problem_workload_all(eda, batch64, prec_name):
+    # bf16: the batch's own precision (bf16 sweeps on the tensor cores, FP64 small steps and refinement) to
+    # tol 1e-8, held to the mixed-precision bars (eigenvalues 1e-6 relative, identical 1-NN labels)
     ps, tau, refs = batch64
-    prec = eda.EDA_F64 if prec_name == "f64" else eda.EDA_F64_TC
+    prec = {"f64": eda.EDA_F64, "tc": eda.EDA_F64_TC, "bf16": eda.EDA_BF16}[prec_name]
+    tol = 1e-8 if prec_name == "bf16" else 1e-10
     cfg = eda.config(prec=prec, block_b=0, tau=tau)
-    probs = [dict(X=_dev(p.X), labels=_dev(p.labels), k=p.k, t=p.k - 1, tol=1e-10) for p in ps]
+    probs = [dict(X=_dev(p.X), labels=_dev(p.labels), k=p.k, t=p.k - 1, tol=tol) for p in ps]
     res, code = eda.solve_batched(probs, cfg, workers=16)
     assert code == 0, [r["status"] for r in res]
     assert all(r["status"] == 0 for r in res)
     # every problem against the oracle, one by one
     for p, r, (c2, ref) in zip(ps, res, refs):
         assert abs(r["info"]["c2"] - c2) <= 1e-13 * c2, p.name
-        _check(eda, p, r, c2, 1e-9, 1e-7, ref=ref)
+        if prec_name == "bf16":
+            _check(eda, p, r, c2, 1e-6, 1e-5, ref=ref)
+        else:
+            _check(eda, p, r, c2, 1e-9, 1e-7, ref=ref)
