@@ -181,7 +181,10 @@ int eda_solve(eda_handle h, int32_t t, double tol, const double* V0, int32_t b0,
  * generalized eigenvectors x themselves.
  *   V      : d x t output, orthonormal basis of the t generalized eigenvectors.
  *   lambda : t output eigenvalues, descending.
- * tol bounds ||N x - theta x|| / (theta ||x||) for each pair (from the Arnoldi relation). The handle's
+ * tol bounds ||N x - theta x|| / (theta ||x||) for each pair (from the Arnoldi relation; when directions
+ * were refilled, from true residuals, one N-apply of the Ritz vectors, once the relation's estimates are
+ * within a factor 100 of tol or the basis is full: info->max_relres_true >= 0 and info->refine_iters counts
+ * those verifications). The handle's
  * prec selects FP64 or tensor-core FP64 sweeps (EDA_F64, EDA_F64_TC); block size, basis limit, check
  * schedule and seed come from its configuration. Errors as for eda_solve. */
 int eda_solve_arnoldi(eda_handle h, int32_t t, double tol, double* V, double* lambda, eda_solve_info* info,

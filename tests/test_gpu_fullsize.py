@@ -185,3 +185,39 @@ def test_direct_d65536_k200_matches_oracle(eda, prec, oracle_solutions):
     lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
     assert np.array_equal(lab_g, ref["lab"]), np.flatnonzero(lab_g != ref["lab"])
     print(f"\nd65536_k200 direct ({prec}): max eig rel err {rel.max():.2e}, sin {s:.2e}, {info['ms_solve']:.1f} ms")
+
+
+def test_arnoldi_d65536_k200_matches_oracle(eda, oracle_solutions):
+    # Arnoldi-EDA (the nonsymmetric form of Eq. (3.1)) at the benchmark's workload, tensor-core FP64 mode,
+    # tol 1e-6: the relation's residual estimates carry the refills' rounding (about 64 eps ||N||), so the
+    # pairs are accepted on true residuals; every eigenvalue within the FP64 floor, the subspace within the
+    # rounding floor plus the residual bound over the gap lambda_t - 1, identical 1-NN labels
+    name = "d65536_k200"
+    c = synth.CONFIGS[name]
+    p, ref = oracle_solutions(name)
+    t = c["t"]
+    tol = 1e-6
+    cfg = eda.config(prec=eda.EDA_F64_TC, block_b=c["b"], tau=c["tau"])
+    with eda.build(_dev(p.X), _dev(p.labels), p.k, cfg) as h:
+        V, lam, info, code = h.solve_arnoldi(t, tol, relres=True)
+        assert code == 0, info
+        Ptr = h.project(V, _dev(p.X)).cpu().numpy()
+        Pte = h.project(V, _dev(p.Xtest)).cpu().numpy()
+    assert info["max_relres_true"] >= 0.0 and info["max_relres_true"] <= tol, info
+    lam = lam.cpu().numpy()
+    Vg = V.cpu().numpy().T
+    assert np.abs(Vg.T @ Vg - np.eye(t)).max() <= 1e-12
+    lam_ref = ref["lam_t"]
+    rel = np.abs(lam - lam_ref) / lam_ref
+    floor = 64 * EPS * lam_ref[0] / lam_ref
+    assert np.all(rel <= np.maximum(1e-10, floor)), rel.max()
+    gap = lam_ref[t - 1] - 1.0
+    rr = np.asarray(info["relres"]) * lam
+    dk = np.sqrt(np.sum((rr / np.maximum(lam - 1.0, gap)) ** 2))
+    kappa = np.exp(0.5 * ref["c2"] * ref["lmax_w"])
+    s = O.sin_angle(ref["V"], Vg)
+    assert s <= kappa * (dk + 64 * EPS * np.sqrt(t) * lam_ref[0] / gap), (s, dk)
+    lab_g, _, _ = O.nn_classify(Ptr, p.labels, Pte)
+    assert np.array_equal(lab_g, ref["lab"]), np.flatnonzero(lab_g != ref["lab"])
+    print(f"\nd65536_k200 Arnoldi: {info['iters']} blocks, {info['refills']} refills, {info['refine_iters']} "
+          f"true-residual checks, max true rel-res {info['max_relres_true']:.2e}, {info['ms_solve']:.1f} ms")
