@@ -2,8 +2,10 @@
 // G = H^T H (the spectra D = Sigma^2 of Eqs. (3.4)-(3.6)) and the block-tridiagonal Lanczos
 // matrix T of the Rayleigh-Ritz step.
 //
-// Route: Householder reduction to tridiagonal form (one cooperative launch, rows owned
-// cyclically by CTAs, two bounded grid barriers per column) -> eigenvalues by 33-way
+// Route: Householder reduction to tridiagonal form (from n = 288 a cooperative grid with the columns
+// resident in its CTAs' shared memory; below that, or when the GPU is shared, one thread-block cluster;
+// beyond what shared memory holds, a cooperative grid streaming the matrix through L2; all with bounded
+// barriers) -> eigenvalues by 33-way
 // multisection on Sturm counts (one warp per eigenvalue) -> eigenvectors of the tridiagonal
 // by inverse iteration with partial pivoting (one thread per eigenvector) -> modified
 // Gram-Schmidt inside tight clusters (one warp per cluster) -> back-transformation with the
@@ -1272,7 +1274,7 @@ int symeig_values(int n, const double* A, int lda, int il, int iu, double* w, Sy
     EDA_CUDA_TRY(cudaPeekAtLastError());   // surface an error left by an earlier call at its own site
     const int nv = iu - il + 1;
     double* HV = ws->partial;
-    // ---- tridiagonal reduction: one cluster for small n, a cooperative grid otherwise ----
+    // ---- tridiagonal reduction: resident-column grid, cluster, or L2-streaming grid (see the file header) ----
     int dev = 0;
     EDA_CUDA_TRY(cudaGetDevice(&dev));
     int sms = 0;

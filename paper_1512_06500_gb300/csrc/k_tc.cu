@@ -17,6 +17,9 @@
 // hi and lo per step, each K-step a 32-byte advance of the descriptor start inside the swizzle
 // atom) and commits each stage to the stage's "empty" mbarrier; the four warps read the 128 x N
 // FP32 accumulator out of tensor memory at the end. Every wait is bounded (ST_TIMEOUT on give-up).
+//
+// A factor small enough to stay in the SMs' shared memory has a one-pass form (k_tc_fused.cu):
+// exp_apply_tc uses it whenever the handle built it.
 #include "tc_ptx.cuh"
 
 #include <cuda.h>

@@ -130,14 +130,15 @@ def test_tc_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
 
 
 @pytest.mark.parametrize("d,k,nj,b", [(4096, 40, 5, 8), (1000, 9, [2, 5, 3, 4, 6, 2, 3, 7, 1], 16), (2048, 20, 7, 20),
-                                      (777, 5, 3, 40), (16384, 100, 7, 16), (300, 150, 2, 32)])
+                                      (777, 5, 3, 40), (16384, 100, 7, 16), (300, 150, 2, 32), (100, 6, 4, 5)])
 def test_tc_fused_exp_apply_matches_bf16_reference(eda, d, k, nj, b):
     # The one-pass product is X + sigma bf16(B) (bf16(B)^T X) with B = H R^T, sigma K = R^T R (Cholesky of the
     # definite K = alpha phi(alpha G), sigma = sign(alpha)): one d x m bf16 matrix serves both sweeps and stays
     # in shared memory. The reference forms B from the oracle's H, Gram and scale in FP64, rounds it to bf16
     # as the library does, and applies it in FP64; allowed: 1e-4 of the column's largest entry (hi + lo
     # rounding of X and P, FP32 accumulation) plus one bf16 ulp of each entry of B within 1e-4 of a rounding
-    # midpoint times |P|. Covers one to six 128-column bands, ragged d, b of 8 to 40 (two launches); the
+    # midpoint times |P|. Covers one to six 128-column bands, ragged d, a single CTA (d = 100), b of 5 to 40
+    # (two launches); the
     # in-place form (Y = X) runs inside the bf16 solver's M-apply chain (test_bf16_tensor_core_solver).
     p = synth.gaussian_clusters(d=d, k=k, n_per_class=nj, seed=900 + d)
     f = O.scatter_factors(p.X, p.labels, p.k)
