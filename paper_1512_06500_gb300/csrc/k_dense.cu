@@ -244,34 +244,39 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t d, int m, int p, double
 }
 
 // Small C (m x p) = alpha A B + beta C (both operands untransposed) with a long inner dimension:
-// CTA = 4 warps for one (32-row block, column); warp w sums its quarter of the inner dimension
-// with four independent chains, the quarters are added in a fixed order through shared memory.
-__global__ void __launch_bounds__(128) k_gemm_small_nn_splitk(int m, int p, int kk, double alpha,
-                                                              const double* __restrict__ A, int lda,
-                                                              const double* __restrict__ B, int ldb, double beta,
-                                                              double* __restrict__ C, int ldc) {
-    __shared__ double part[4][32];
+// CTA = 8 warps for one (32-row block, column); warp w sums its eighth of the inner dimension with
+// eight independent chains (eight loads of A in flight per lane: at these sizes the product is bound
+// by load latency, then by the FP64 pipe), and the eighths are added in a fixed order through shared
+// memory.
+constexpr int kSplitkWarps = 8;
+__global__ void __launch_bounds__(32 * kSplitkWarps) k_gemm_small_nn_splitk(int m, int p, int kk, double alpha,
+                                                                           const double* __restrict__ A, int lda,
+                                                                           const double* __restrict__ B, int ldb,
+                                                                           double beta, double* __restrict__ C,
+                                                                           int ldc) {
+    __shared__ double part[kSplitkWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
     const int j = blockIdx.y;
-    const int q = (kk + 3) / 4;
+    const int q = (kk + kSplitkWarps - 1) / kSplitkWarps;
     const int lb = w * q, le = min(kk, lb + q);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = 0.0;
     if (i < m) {
         const double* Bj = B + (int64_t)j * ldb;
         int l = lb;
-        for (; l + 3 < le; l += 4) {
-            a0 = fma(A[(int64_t)l * lda + i], Bj[l], a0);
-            a1 = fma(A[(int64_t)(l + 1) * lda + i], Bj[l + 1], a1);
-            a2 = fma(A[(int64_t)(l + 2) * lda + i], Bj[l + 2], a2);
-            a3 = fma(A[(int64_t)(l + 3) * lda + i], Bj[l + 3], a3);
+        for (; l + 7 < le; l += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = fma(A[(int64_t)(l + u) * lda + i], Bj[l + u], a[u]);
         }
-        for (; l < le; ++l) a0 = fma(A[(int64_t)l * lda + i], Bj[l], a0);
+        for (; l < le; ++l) a[0] = fma(A[(int64_t)l * lda + i], Bj[l], a[0]);
     }
-    part[w][lane] = (a0 + a1) + (a2 + a3);
+    part[w][lane] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     __syncthreads();
     if (w == 0 && i < m) {
-        const double acc = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
+        const double acc = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+                           ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
         double v = alpha * acc;
         if (beta != 0.0) v = fma(beta, C[(int64_t)j * ldc + i], v);
         C[(int64_t)j * ldc + i] = v;
@@ -770,7 +775,8 @@ int gemm_small_f64(bool ta, bool tb, int m, int p, int kk, double alpha, const d
                    int ldb, double beta, double* C, int ldc, cudaStream_t s) {
     if (m <= 0 || p <= 0) return EDA_OK;
     if (!ta && !tb && kk >= 64) {
-        k_gemm_small_nn_splitk<<<dim3(ceil_div(m, 32), p), 128, 0, s>>>(m, p, kk, alpha, A, lda, B, ldb, beta, C, ldc);
+        k_gemm_small_nn_splitk<<<dim3(ceil_div(m, 32), p), 32 * kSplitkWarps, 0, s>>>(m, p, kk, alpha, A, lda, B, ldb,
+                                                                                  beta, C, ldc);
         EDA_LAUNCHED();
         return EDA_OK;
     }

@@ -307,17 +307,34 @@ __device__ __forceinline__ bool oz_digits(double v, int e, __nv_bfloat16 (&s)[OZ
 }
 
 // Column scales: e[c] = max over rows r of the frexp exponent of A[r, c] (d x ncols, lda), kOzExpZero for
-// a zero column. One CTA per (column, chunk of kOzExpChunk rows), merged by atomicMax into e, which the
-// host fills with kOzExpZero first.
-constexpr int kOzExpChunk = 8192;
-__global__ void k_oz_exp_cols(int64_t rows, const double* __restrict__ A, int64_t lda, int* __restrict__ e) {
+// a zero column. One CTA per (column, chunk of kOzExpChunk rows); each thread issues its eight loads
+// before it reduces them (the scan is bound by the number of loads in flight), and the CTA's maximum is
+// merged by one atomicMax into e, which the host fills with kOzExpZero first.
+constexpr int kOzExpThreads = 256;
+constexpr int kOzExpPer = 8;
+constexpr int kOzExpChunk = kOzExpThreads * kOzExpPer;
+__global__ void __launch_bounds__(kOzExpThreads) k_oz_exp_cols(int64_t rows, const double* __restrict__ A,
+                                                              int64_t lda, int* __restrict__ e) {
+    __shared__ int wmax[kOzExpThreads / 32];
     const int c = blockIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.y * kOzExpChunk;
-    const int64_t r1 = min(rows, r0 + kOzExpChunk);
+    const double* col = A + (int64_t)c * lda;
+    const int64_t r0 = (int64_t)blockIdx.y * kOzExpChunk + threadIdx.x;
+    double v[kOzExpPer];
+#pragma unroll
+    for (int u = 0; u < kOzExpPer; ++u) {
+        const int64_t r = r0 + (int64_t)u * kOzExpThreads;
+        v[u] = r < rows ? col[r] : 0.0;
+    }
     int mx = kOzExpZero;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) mx = max(mx, oz_frexp_exp(A[(int64_t)c * lda + r]));
+#pragma unroll
+    for (int u = 0; u < kOzExpPer; ++u) mx = max(mx, oz_frexp_exp(v[u]));
     mx = __reduce_max_sync(0xffffffffu, mx);
-    if ((threadIdx.x & 31) == 0 && mx != kOzExpZero) atomicMax(&e[c], mx);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kOzExpThreads / 32; ++w) mx = max(mx, wmax[w]);
+        if (mx != kOzExpZero) atomicMax(&e[c], mx);
+    }
 }
 
 // Row scales of a split operand whose M rows are the ROWS of A (d x m, lda): thread per row, 0 for a
@@ -530,7 +547,7 @@ static int oz_col_exps(int64_t K, const double* A, int64_t lda, int ncols, int* 
     if (ncols <= 0) return EDA_OK;
     EDA_CUDA_TRY(cudaMemsetAsync(e, 0xC0, (size_t)ncols * sizeof(int), s));   // kOzExpZero in every entry
     const dim3 grid((unsigned)ncols, (unsigned)ceil_div(std::max<int64_t>(K, 1), kOzExpChunk));
-    k_oz_exp_cols<<<grid, 256, 0, s>>>(K, A, lda, e);
+    k_oz_exp_cols<<<grid, kOzExpThreads, 0, s>>>(K, A, lda, e);
     EDA_LAUNCHED();
     return EDA_OK;
 }
