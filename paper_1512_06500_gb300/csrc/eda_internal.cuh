@@ -144,9 +144,12 @@ int gemm_tn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, cons
 template <class T>
 int syrk_tn(int64_t d, int m, double alpha, const T* A, int64_t lda, double beta, double* C, int ldc,
             void* partial_buf, size_t partial_cap, cudaStream_t s);
+// b_upper: B is upper triangular with its zeros stored (B[l, c] = 0 for l > c, as R^{-1} from
+// chol_inv_small); the product then skips rows of B that are zero for a whole column slice (exact zero
+// terms, so the result is bit-for-bit that of the full product for finite A).
 template <class T>
 int gemm_nn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const double* B, int ldb, double beta,
-            const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s);
+            const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s, bool b_upper = false);
 template <class Ti, class To>
 int copy_mat(int64_t rows, int cols, const Ti* A, int64_t lda, To* B, int64_t ldb, cudaStream_t s);
 template <class T>

@@ -170,11 +170,13 @@ __global__ void k_gemm_tn_reduce_warp(int m, int p, int splits, const T* __restr
 // (m x p). A CTA owns 32 rows and NC columns; its eight warps (two per SM sub-partition, so that
 // one issues FP64 work while the other waits on a load) split the inner dimension into eighths,
 // each thread keeps NC independent accumulators, the slice of B sits in shared memory, and the
-// partial sums of the eighths are added in a fixed pairwise order at the end.
+// partial sums of the eighths are added in a fixed pairwise order at the end. For an upper
+// triangular B (ub) each warp stops at row c0 + NC of B, below which the CTA's columns are zero: the
+// partition of the inner dimension is unchanged and only exact zero terms are left out.
 template <int NC, class T>
 __global__ void __launch_bounds__(256) k_gemm_nn(int64_t d, int m, int p, double alpha, const T* __restrict__ A,
                                                  int64_t lda, const double* __restrict__ B, int ldb, double beta,
-                                                 const T* C0, int64_t ldc0, T* C, int64_t ldc) {
+                                                 const T* C0, int64_t ldc0, T* C, int64_t ldc, int ub) {
     constexpr int LCH = 256;                 // rows of B staged per pass
     __shared__ T Bs[LCH][NC];
     __shared__ T red[7][32][NC];
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t d, int m, int p, double
     const int64_t r = (int64_t)blockIdx.x * 32 + lane;
     const int c0 = blockIdx.y * NC;
     const int nc = min(NC, p - c0);
+    const int lim = ub ? min(m, c0 + NC) : m;   // rows of B that can be nonzero in these columns
     T acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = T(0);
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t d, int m, int p, double
         }
         __syncthreads();
         const int q = (lc + 7) / 8;
-        const int lb = w * q, le = min(lc, lb + q);
+        const int lb = w * q, le = min(min(lc, lb + q), lim - l0);
         int l = lb;
         // groups of four rows of A, the next group read while the current one is multiplied
         T a[4];
@@ -315,70 +318,76 @@ __global__ void k_gemm_small(bool ta, bool tb, int m, int p, int kk, double alph
 }
 
 // Single-CTA right-looking upper Cholesky G = R^T R with rank detection, then R^{-1}.
-// The same factorisation for b <= 32 by one warp with the matrix in shared memory: lane c owns
-// column c; one reciprocal per pivot; warp-level synchronisation only. Rank decisions (threshold,
-// lost list in pivot order, status bits) are those of k_chol_inv.
+// The same factorisation for b <= 32 by one warp with the matrix in registers: lane c holds column c
+// (col[r] = G[r, c] for r <= c, then R[r, c]); the entries of row j of R that lane c needs come by shuffle
+// from the lanes that own them, and every loop is unrolled over the 32 possible rows, so the trailing
+// updates and the triangular inverse run from registers (one reciprocal per pivot; each entry is
+// updated in the same order and by the same fused multiply-adds as a column-by-column elimination).
+// Rank decisions (threshold, lost list in pivot order, status bits) are those of k_chol_inv.
 __global__ void __launch_bounds__(32) k_chol_inv_warp(int b, double* G, int ldg, double* Rinv, double rank_tol,
                                                       double piv_min2, int* status, int* lost) {
-    __shared__ double sg[32][33];   // sg[c][r] = G[r, c]
-    __shared__ double sx[32][33];   // sx[c][i] = Rinv[i, c]
     __shared__ double inv[32];
     const int lane = threadIdx.x;
     const bool live = lane < b;
-    if (live)
-        for (int r = 0; r <= lane; ++r) sg[lane][r] = G[(int64_t)lane * ldg + r];
-    double dg = live ? G[(int64_t)lane * ldg + lane] : 0.0;
+    double col[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) col[r] = (live && r <= lane) ? G[(int64_t)lane * ldg + r] : 0.0;
+    const double dg = live ? G[(int64_t)lane * ldg + lane] : 0.0;
     const bool bad = live && !isfinite(dg);
     double mx = fabs(dg);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
     const double thr = fmax(rank_tol * mx, piv_min2);
     int nlost = 0;
-    __syncwarp();
-    for (int j = 0; j < b; ++j) {
-        const double g = sg[j][j];
-        const bool lost_j = !(g > thr) || mx == 0.0;
-        const double piv = lost_j ? 0.0 : sqrt(g);
-        const double ip = lost_j ? 0.0 : 1.0 / piv;
-        __syncwarp();   // every lane has read the pivot before lane 0 overwrites it
-        if (lane == 0) {
-            if (lost_j) {
-                if (lost) lost[nlost] = j;
-                atomicOr(status, ST_RANKLOSS);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < b) {
+            const double g = __shfl_sync(0xffffffffu, col[j], j);
+            const bool lost_j = !(g > thr) || mx == 0.0;
+            const double piv = lost_j ? 0.0 : sqrt(g);
+            const double ip = lost_j ? 0.0 : 1.0 / piv;
+            if (lane == 0) {
+                if (lost_j) {
+                    if (lost) lost[nlost] = j;
+                    atomicOr(status, ST_RANKLOSS);
+                }
+                inv[j] = ip;
             }
-            sg[j][j] = piv;
-            inv[j] = ip;
-        }
-        nlost += lost_j ? 1 : 0;
-        // row j of R (entries (j, c) for c > j), then the trailing update of column c
-        if (live && lane > j) sg[lane][j] *= ip;
-        __syncwarp();
-        if (live && lane > j) {
-            const double rjc = sg[lane][j];
-            for (int c1 = j + 1; c1 <= lane; ++c1) sg[lane][c1] -= sg[c1][j] * rjc;
-        }
-        __syncwarp();
-    }
-    // Rinv = R^{-1} (upper triangular): lane c solves R x = e_c from the bottom up
-    if (live) {
-        const int c = lane;
-        for (int i = b - 1; i > c; --i) sx[c][i] = 0.0;
-        for (int i = c; i >= 0; --i) {
-            double a0 = (i == c) ? 1.0 : 0.0, a1 = 0.0;
-            int l = i + 1;
-            for (; l + 1 <= c; l += 2) {
-                a0 -= sg[l][i] * sx[c][l];
-                a1 -= sg[l + 1][i] * sx[c][l + 1];
+            nlost += lost_j ? 1 : 0;
+            if (lane == j) col[j] = piv;
+            if (lane > j) col[j] *= ip;   // R[j, lane]
+            // trailing update of column lane: G[c1, lane] -= R[j, c1] R[j, lane] for j < c1 <= lane
+#pragma unroll
+            for (int c1 = j + 1; c1 < 32; ++c1) {
+                const double rjc1 = __shfl_sync(0xffffffffu, col[j], c1);
+                if (c1 <= lane) col[c1] = fma(-rjc1, col[j], col[c1]);
             }
-            if (l <= c) a0 -= sg[l][i] * sx[c][l];
-            sx[c][i] = (a0 + a1) * inv[i];
         }
     }
     __syncwarp();
+    // Rinv = R^{-1} (upper triangular): lane c solves R x = e_c from the bottom up, the terms of row i
+    // in two alternating chains in increasing column order
+    double x[32];
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+        double a0 = (i == lane) ? 1.0 : 0.0, a1 = 0.0;
+#pragma unroll
+        for (int l = i + 1; l < 32; ++l) {
+            const double ril = __shfl_sync(0xffffffffu, col[i], l);   // R[i, l], held by lane l
+            if (l <= lane) {
+                if (((l - i - 1) & 1) == 0) a0 = fma(-ril, x[l], a0);
+                else a1 = fma(-ril, x[l], a1);
+            }
+        }
+        x[i] = (i <= lane && i < b) ? (a0 + a1) * inv[i] : 0.0;
+    }
     if (live) {
-        for (int r = 0; r < b; ++r) {
-            G[(int64_t)lane * ldg + r] = (r <= lane) ? sg[lane][r] : 0.0;
-            Rinv[(int64_t)lane * b + r] = sx[lane][r];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            if (r < b) {
+                G[(int64_t)lane * ldg + r] = (r <= lane) ? col[r] : 0.0;
+                Rinv[(int64_t)lane * b + r] = x[r];
+            }
         }
     }
     if (lane == 0 && lost) lost[b] = nlost;
@@ -691,21 +700,28 @@ int syrk_tn(int64_t d, int m, double alpha, const T* A, int64_t lda, double beta
 
 template <class T>
 int gemm_nn(int64_t d, int m, int p, double alpha, const T* A, int64_t lda, const double* B, int ldb, double beta,
-            const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s) {
+            const T* C0, int64_t ldc0, T* C, int64_t ldc, cudaStream_t s, bool b_upper) {
     if (d <= 0 || p <= 0) return EDA_OK;
-    // algorithmic work: 2 d m p flops; A read once, C0 read (beta != 0) and C written once
-    ProfScope prof(std::is_same<T, double>::value ? "nn_f64" : "nn_f32", s, 2.0 * (double)d * m * p,
+    // algorithmic work: 2 d m p flops (2 d sum_c min(m, c + 1) for an upper triangular B); A read once,
+    // C0 read (beta != 0) and C written once
+    double terms = (double)m * p;
+    if (b_upper) {
+        terms = 0.0;
+        for (int c = 0; c < p; ++c) terms += std::min(m, c + 1);
+    }
+    ProfScope prof(std::is_same<T, double>::value ? "nn_f64" : "nn_f32", s, 2.0 * (double)d * terms,
                    (double)sizeof(T) * (double)d * (m + (beta != 0.0 ? 2.0 : 1.0) * p) + 8.0 * m * p);
+    const int ub = b_upper ? 1 : 0;
     const int rowblocks = ceil_div(d, 32);
     // columns per thread: as many as possible while at least ~one CTA per SM stays busy
     if (p >= 6 && (int64_t)rowblocks * ceil_div(p, 8) >= 120) {
-        k_gemm_nn<8, T><<<dim3(rowblocks, ceil_div(p, 8)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<8, T><<<dim3(rowblocks, ceil_div(p, 8)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc, ub);
     } else if (p >= 3 && (int64_t)rowblocks * ceil_div(p, 4) >= 120) {
-        k_gemm_nn<4, T><<<dim3(rowblocks, ceil_div(p, 4)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<4, T><<<dim3(rowblocks, ceil_div(p, 4)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc, ub);
     } else if (p >= 2) {
-        k_gemm_nn<2, T><<<dim3(rowblocks, ceil_div(p, 2)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<2, T><<<dim3(rowblocks, ceil_div(p, 2)), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc, ub);
     } else {
-        k_gemm_nn<1, T><<<dim3(rowblocks, p), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc);
+        k_gemm_nn<1, T><<<dim3(rowblocks, p), 256, 0, s>>>(d, m, p, alpha, A, lda, B, ldb, beta, C0, ldc0, C, ldc, ub);
     }
     EDA_LAUNCHED();
     return EDA_OK;
@@ -744,9 +760,9 @@ template int syrk_tn<double>(int64_t, int, double, const double*, int64_t, doubl
 template int syrk_tn<float>(int64_t, int, double, const float*, int64_t, double, double*, int, void*, size_t,
                             cudaStream_t);
 template int gemm_nn<double>(int64_t, int, int, double, const double*, int64_t, const double*, int, double,
-                             const double*, int64_t, double*, int64_t, cudaStream_t);
+                             const double*, int64_t, double*, int64_t, cudaStream_t, bool);
 template int gemm_nn<float>(int64_t, int, int, double, const float*, int64_t, const double*, int, double,
-                            const float*, int64_t, float*, int64_t, cudaStream_t);
+                            const float*, int64_t, float*, int64_t, cudaStream_t, bool);
 template int copy_mat<double, double>(int64_t, int, const double*, int64_t, double*, int64_t, cudaStream_t);
 template int copy_mat<float, float>(int64_t, int, const float*, int64_t, float*, int64_t, cudaStream_t);
 template int copy_mat<double, float>(int64_t, int, const double*, int64_t, float*, int64_t, cudaStream_t);

@@ -159,7 +159,8 @@ int cholqr_pass(int64_t d, int b, T* X, int64_t ldx, double* Rm, double* Rinv, T
                 int* lost, SolveWs<T>& w, cudaStream_t s) {
     EDA_TRY(syrk_tn<T>(d, b, 1.0, X, ldx, 0.0, Rm, b, w.part, w.pcap, s));
     EDA_TRY(chol_inv_small(b, Rm, b, Rinv, 1e-28, piv_min2, status, lost, s));
-    EDA_TRY(gemm_nn<T>(d, b, b, 1.0, X, ldx, Rinv, b, 0.0, nullptr, 0, out, ldx, s));
+    // R^{-1} is upper triangular with its zeros stored: the product skips the zero rows of each column slice
+    EDA_TRY(gemm_nn<T>(d, b, b, 1.0, X, ldx, Rinv, b, 0.0, nullptr, 0, out, ldx, s, true));
     return EDA_OK;
 }
 
