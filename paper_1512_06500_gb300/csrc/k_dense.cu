@@ -318,76 +318,70 @@ __global__ void k_gemm_small(bool ta, bool tb, int m, int p, int kk, double alph
 }
 
 // Single-CTA right-looking upper Cholesky G = R^T R with rank detection, then R^{-1}.
-// The same factorisation for b <= 32 by one warp with the matrix in registers: lane c holds column c
-// (col[r] = G[r, c] for r <= c, then R[r, c]); the entries of row j of R that lane c needs come by shuffle
-// from the lanes that own them, and every loop is unrolled over the 32 possible rows, so the trailing
-// updates and the triangular inverse run from registers (one reciprocal per pivot; each entry is
-// updated in the same order and by the same fused multiply-adds as a column-by-column elimination).
-// Rank decisions (threshold, lost list in pivot order, status bits) are those of k_chol_inv.
+// The same factorisation for b <= 32 by one warp with the matrix in shared memory: lane c owns
+// column c; one reciprocal per pivot; warp-level synchronisation only. Rank decisions (threshold,
+// lost list in pivot order, status bits) are those of k_chol_inv.
 __global__ void __launch_bounds__(32) k_chol_inv_warp(int b, double* G, int ldg, double* Rinv, double rank_tol,
                                                       double piv_min2, int* status, int* lost) {
+    __shared__ double sg[32][33];   // sg[c][r] = G[r, c]
+    __shared__ double sx[32][33];   // sx[c][i] = Rinv[i, c]
     __shared__ double inv[32];
     const int lane = threadIdx.x;
     const bool live = lane < b;
-    double col[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) col[r] = (live && r <= lane) ? G[(int64_t)lane * ldg + r] : 0.0;
-    const double dg = live ? G[(int64_t)lane * ldg + lane] : 0.0;
+    if (live)
+        for (int r = 0; r <= lane; ++r) sg[lane][r] = G[(int64_t)lane * ldg + r];
+    double dg = live ? G[(int64_t)lane * ldg + lane] : 0.0;
     const bool bad = live && !isfinite(dg);
     double mx = fabs(dg);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
     const double thr = fmax(rank_tol * mx, piv_min2);
     int nlost = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        if (j < b) {
-            const double g = __shfl_sync(0xffffffffu, col[j], j);
-            const bool lost_j = !(g > thr) || mx == 0.0;
-            const double piv = lost_j ? 0.0 : sqrt(g);
-            const double ip = lost_j ? 0.0 : 1.0 / piv;
-            if (lane == 0) {
-                if (lost_j) {
-                    if (lost) lost[nlost] = j;
-                    atomicOr(status, ST_RANKLOSS);
-                }
-                inv[j] = ip;
+    __syncwarp();
+    for (int j = 0; j < b; ++j) {
+        const double g = sg[j][j];
+        const bool lost_j = !(g > thr) || mx == 0.0;
+        const double piv = lost_j ? 0.0 : sqrt(g);
+        const double ip = lost_j ? 0.0 : 1.0 / piv;
+        __syncwarp();   // every lane has read the pivot before lane 0 overwrites it
+        if (lane == 0) {
+            if (lost_j) {
+                if (lost) lost[nlost] = j;
+                atomicOr(status, ST_RANKLOSS);
             }
-            nlost += lost_j ? 1 : 0;
-            if (lane == j) col[j] = piv;
-            if (lane > j) col[j] *= ip;   // R[j, lane]
-            // trailing update of column lane: G[c1, lane] -= R[j, c1] R[j, lane] for j < c1 <= lane
-#pragma unroll
-            for (int c1 = j + 1; c1 < 32; ++c1) {
-                const double rjc1 = __shfl_sync(0xffffffffu, col[j], c1);
-                if (c1 <= lane) col[c1] = fma(-rjc1, col[j], col[c1]);
+            sg[j][j] = piv;
+            inv[j] = ip;
+        }
+        nlost += lost_j ? 1 : 0;
+        // row j of R (entries (j, c) for c > j), then the trailing update of column c
+        if (live && lane > j) sg[lane][j] *= ip;
+        __syncwarp();
+        if (live && lane > j) {
+            const double rjc = sg[lane][j];
+            for (int c1 = j + 1; c1 <= lane; ++c1) sg[lane][c1] -= sg[c1][j] * rjc;
+        }
+        __syncwarp();
+    }
+    // Rinv = R^{-1} (upper triangular): lane c solves R x = e_c from the bottom up
+    if (live) {
+        const int c = lane;
+        for (int i = b - 1; i > c; --i) sx[c][i] = 0.0;
+        for (int i = c; i >= 0; --i) {
+            double a0 = (i == c) ? 1.0 : 0.0, a1 = 0.0;
+            int l = i + 1;
+            for (; l + 1 <= c; l += 2) {
+                a0 -= sg[l][i] * sx[c][l];
+                a1 -= sg[l + 1][i] * sx[c][l + 1];
             }
+            if (l <= c) a0 -= sg[l][i] * sx[c][l];
+            sx[c][i] = (a0 + a1) * inv[i];
         }
     }
     __syncwarp();
-    // Rinv = R^{-1} (upper triangular): lane c solves R x = e_c from the bottom up, the terms of row i
-    // in two alternating chains in increasing column order
-    double x[32];
-#pragma unroll
-    for (int i = 31; i >= 0; --i) {
-        double a0 = (i == lane) ? 1.0 : 0.0, a1 = 0.0;
-#pragma unroll
-        for (int l = i + 1; l < 32; ++l) {
-            const double ril = __shfl_sync(0xffffffffu, col[i], l);   // R[i, l], held by lane l
-            if (l <= lane) {
-                if (((l - i - 1) & 1) == 0) a0 = fma(-ril, x[l], a0);
-                else a1 = fma(-ril, x[l], a1);
-            }
-        }
-        x[i] = (i <= lane && i < b) ? (a0 + a1) * inv[i] : 0.0;
-    }
     if (live) {
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            if (r < b) {
-                G[(int64_t)lane * ldg + r] = (r <= lane) ? col[r] : 0.0;
-                Rinv[(int64_t)lane * b + r] = x[r];
-            }
+        for (int r = 0; r < b; ++r) {
+            G[(int64_t)lane * ldg + r] = (r <= lane) ? sg[lane][r] : 0.0;
+            Rinv[(int64_t)lane * b + r] = sx[lane][r];
         }
     }
     if (lane == 0 && lost) lost[b] = nlost;

@@ -808,33 +808,41 @@ __global__ void k_backtransform(int n, int nv, const double* __restrict__ HV, co
     }
 }
 
-// The same with the column held in registers (NPL entries per lane, n <= 32 * NPL), so that the
-// chain of reflectors never waits on memory: reflector j - 1 and its scalar are read while
+// The same with the column held in the registers of four warps (n <= 128 NPL), one warp per SM
+// sub-partition: carried by a single warp, the chain of reflectors is bound by the FP64 issue rate of one
+// sub-partition. Rows are dealt in 32-row stripes, row 32 (4 k + w) + lane in register k of warp w; a
+// warp skips the stripes that lie wholly at or above reflector j's first nonzero row j + 1 (exact zero
+// terms), the four partial dot products are added in a fixed order through shared memory (one barrier
+// per reflector, the partials double-buffered), and reflector j - 1 and its scalar are read while
 // reflector j is applied.
 template <int NPL>
-__global__ void __launch_bounds__(32) k_backtransform_reg(int n, int nv, const double* __restrict__ HV,
+__global__ void __launch_bounds__(128) k_backtransform_w4(int n, int nv, const double* __restrict__ HV,
                                                           const double* __restrict__ tau, double* Z, int ldz) {
-    const int lane = threadIdx.x & 31;
+    __shared__ double red[2][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int col = blockIdx.x;
-    if (col >= nv) return;
+    if (col >= nv) return;   // uniform over the CTA
     double* zc = Z + (int64_t)col * ldz;
     double z[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
-        const int i = lane + 32 * k;
+        const int i = 32 * (4 * k + w) + lane;
         z[k] = (i < n) ? zc[i] : 0.0;
     }
-    double un[NPL];   // the next reflector (zero for i <= j)
+    // stripe k of this warp holds a row below j exactly when its last row 32 (4 k + w) + 31 exceeds j
+    double un[NPL];
     double tn = 0.0;
     if (n >= 3) {
-        const double* u = HV + (int64_t)(n - 3) * n;
-        tn = __ldg(tau + n - 3);
+        const int j = n - 3;
+        const double* u = HV + (int64_t)j * n;
+        tn = __ldg(tau + j);
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            const int i = lane + 32 * k;
-            un[k] = (i < n) ? __ldg(u + i) : 0.0;
+            const int i = 32 * (4 * k + w) + lane;
+            un[k] = (i < n && 32 * (4 * k + w) + 31 > j) ? __ldg(u + i) : 0.0;
         }
     }
+    int par = 0;
     for (int j = n - 3; j >= 0; --j) {
         double uu[NPL];
 #pragma unroll
@@ -845,26 +853,33 @@ __global__ void __launch_bounds__(32) k_backtransform_reg(int n, int nv, const d
             tn = __ldg(tau + j - 1);
 #pragma unroll
             for (int k = 0; k < NPL; ++k) {
-                const int i = lane + 32 * k;
-                un[k] = (i < n) ? __ldg(u + i) : 0.0;
+                const int i = 32 * (4 * k + w) + lane;
+                un[k] = (i < n && 32 * (4 * k + w) + 31 > j - 1) ? __ldg(u + i) : 0.0;
             }
         }
-        if (tj == 0.0) continue;
+        if (tj == 0.0) continue;   // uniform over the CTA
         double d0 = 0.0, d1 = 0.0;
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            if (k & 1) d1 = fma(uu[k], z[k], d1);
-            else d0 = fma(uu[k], z[k], d0);
+            if (32 * (4 * k + w) + 31 > j) {
+                if (k & 1) d1 = fma(uu[k], z[k], d1);
+                else d0 = fma(uu[k], z[k], d0);
+            }
         }
         double dot = d0 + d1;
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        const double f = tj * dot;
+        if (lane == 0) red[par][w] = dot;
+        __syncthreads();
+        const double tot = (red[par][0] + red[par][1]) + (red[par][2] + red[par][3]);
+        par ^= 1;
+        const double f = tj * tot;
 #pragma unroll
-        for (int k = 0; k < NPL; ++k) z[k] = fma(-f, uu[k], z[k]);
+        for (int k = 0; k < NPL; ++k)
+            if (32 * (4 * k + w) + 31 > j) z[k] = fma(-f, uu[k], z[k]);
     }
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
-        const int i = lane + 32 * k;
+        const int i = 32 * (4 * k + w) + lane;
         if (i < n) zc[i] = z[k];
     }
 }
@@ -1526,9 +1541,9 @@ int symeig_orth_clusters(int n, int nv, const double* w, double* Z, int ldz, Sym
 int symeig_backtransform(int n, int nv, double* Z, int ldz, SymEigWork* ws, cudaStream_t s) {
     if (n >= 3) {
         ProfScope prof("backtransform", s);
-        if (n <= 256) k_backtransform_reg<8><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
-        else if (n <= 512) k_backtransform_reg<16><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
-        else if (n <= 1024) k_backtransform_reg<32><<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
+        if (n <= 256) k_backtransform_w4<2><<<nv, 128, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
+        else if (n <= 512) k_backtransform_w4<4><<<nv, 128, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
+        else if (n <= 1024) k_backtransform_w4<8><<<nv, 128, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
         else k_backtransform<<<nv, 32, 0, s>>>(n, nv, ws->partial, ws->tau, Z, ldz);
         EDA_LAUNCHED();
     }
